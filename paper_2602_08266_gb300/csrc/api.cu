@@ -1,0 +1,561 @@
+// C ABI of the scorer (declared in include/nbvgs.h): context, memory, and the
+// per-view launch sequence
+//   project -> scan -> duplicate -> radix sort -> ranges -> composite(+IG)
+//   -> per-Gaussian log-det gains -> reduction -> scores.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nbv_internal.cuh"
+
+namespace nbv {
+size_t scan_scratch_elems(int64_t n);
+size_t radix_hist_elems(int64_t count);
+}  // namespace nbv
+
+using namespace nbv;
+
+struct nbv_ctx {
+  nbv_config cfg;
+  Consts c;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  std::string err;
+  bool cuda_dead = false;
+  int64_t launches = 0;
+  int nB = 0, nBp = 0;
+
+  // scene
+  int64_t n = 0;
+  float *mu = nullptr, *logs = nullptr, *q = nullptr, *rho = nullptr, *sh = nullptr, *obj = nullptr;
+  float4 *mu_sig = nullptr, *scale_skip = nullptr, *qn = nullptr, *aux = nullptr;
+  float* p = nullptr;
+  int prepared_target = -2;
+
+  // cameras
+  std::vector<nbv_camera> train, cand;
+  DevCam* d_train_cams = nullptr;
+
+  // per-view projection
+  DevProj pr{};
+  // sort
+  SortBuffers sb{};
+  uint32_t* h_total = nullptr;   // pinned
+  size_t ranges_cap = 0;
+
+  // blocks and factors
+  float* blocks = nullptr;        // [n][nBp]
+  float* train_blocks = nullptr;  // [n_train][n][nBp]
+  size_t train_blocks_cap = 0;
+  Factors F{};
+  bool prepared = false;
+
+  // gains and scores
+  double* partial = nullptr;
+  int partial_cap = 0;
+  double* ig_train = nullptr;   // [n_train][3]
+  double* ig_cand = nullptr;    // [n_cand][3]
+  size_t ig_train_cap = 0, ig_cand_cap = 0;
+  float* out4 = nullptr;
+  size_t out4_cap = 0;
+  int* d_flags = nullptr;       // [0] best, [1] empty flag, [2] factor error
+  float* d_best_score = nullptr;
+  bool scored = false;
+  int* d_err = nullptr;
+};
+
+namespace {
+
+int fail(nbv_ctx* x, int code, const std::string& msg) {
+  x->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      ctx->cuda_dead = true;                                                           \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? NBV_ERR_OOM : NBV_ERR_CUDA,   \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    }                                                                                  \
+  } while (0)
+
+#define CKR(expr)                  \
+  do {                             \
+    int r_ = (expr);               \
+    if (r_ != NBV_OK) return r_;   \
+  } while (0)
+
+template <class T>
+int grow(nbv_ctx* ctx, T** ptr, size_t* cap, size_t count) {
+  if (*ptr && *cap >= count) return NBV_OK;
+  if (*ptr) cudaFree(*ptr);
+  *ptr = nullptr;
+  *cap = 0;
+  size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(ctx, NBV_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  *cap = count;
+  return NBV_OK;
+}
+
+template <class T>
+int alloc(nbv_ctx* ctx, T** ptr, size_t count) {
+  size_t cap = 0;
+  if (*ptr) { cudaFree(*ptr); *ptr = nullptr; }
+  return grow(ctx, ptr, &cap, count);
+}
+
+bool finite_cam(const nbv_camera& c) {
+  for (float v : c.R) if (!std::isfinite(v)) return false;
+  for (float v : c.t) if (!std::isfinite(v)) return false;
+  return std::isfinite(c.fx) && std::isfinite(c.fy) && std::isfinite(c.cx) && std::isfinite(c.cy) &&
+         c.fx > 0.0f && c.fy > 0.0f && c.width >= 1 && c.height >= 1 && c.width <= 16384 &&
+         c.height <= 16384;
+}
+
+DevCam to_dev(const nbv_camera& c) {
+  DevCam d;
+  for (int i = 0; i < 9; ++i) d.R[i] = c.R[i];
+  for (int i = 0; i < 3; ++i) d.t[i] = c.t[i];
+  d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+  for (int i = 0; i < 3; ++i)   // camera centre -R^T t, in double then rounded
+    d.campos[i] = (float)(-((double)c.R[i] * c.t[0] + (double)c.R[3 + i] * c.t[1] +
+                            (double)c.R[6 + i] * c.t[2]));
+  d.W = c.width; d.H = c.height;
+  d.GX = (c.width + kTile - 1) / kTile;
+  d.GY = (c.height + kTile - 1) / kTile;
+  return d;
+}
+
+DevScene dev_scene(nbv_ctx* ctx) {
+  DevScene s;
+  s.n = ctx->n;
+  s.mu_raw = ctx->mu; s.logs_raw = ctx->logs; s.q_raw = ctx->q; s.rho_raw = ctx->rho;
+  s.sh = ctx->sh; s.obj_raw = ctx->obj;
+  s.mu_sig = ctx->mu_sig; s.scale_skip = ctx->scale_skip; s.qn = ctx->qn; s.aux = ctx->aux;
+  s.p = ctx->p;
+  return s;
+}
+
+int check_launch(nbv_ctx* ctx, int nl) {
+  ctx->launches += nl;
+  CK(cudaGetLastError());
+  return NBV_OK;
+}
+
+// Project, bin and sort one view; composite it (images and/or IG blocks).
+int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, float* depth,
+                float* alpha, float* obj, bool keep_lists = false) {
+  cudaStream_t st = ctx->st;
+  const DevCam dc = to_dev(cam);
+  const int ntiles = dc.GX * dc.GY;
+  DevScene s = dev_scene(ctx);
+  CKR(check_launch(ctx, launch_project(s, ctx->c, dc, ctx->pr, st)));
+  CKR(check_launch(ctx, launch_scan_u32(ctx->pr.touched, ctx->sb.offsets, ctx->n, ctx->sb.scan_tmp, st)));
+  CK(cudaMemcpyAsync(ctx->h_total, ctx->sb.offsets + ctx->n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const int64_t total = (int64_t)*ctx->h_total;
+  if ((size_t)total > ctx->sb.cap) {
+    size_t cap = ctx->sb.cap;
+    size_t want = (size_t)(total * 1.25) + 1024;
+    size_t c0 = cap, c1 = cap, c2 = cap, c3 = cap;
+    CKR(grow(ctx, &ctx->sb.keys[0], &c0, want));
+    CKR(grow(ctx, &ctx->sb.keys[1], &c1, want));
+    CKR(grow(ctx, &ctx->sb.vals[0], &c2, want));
+    CKR(grow(ctx, &ctx->sb.vals[1], &c3, want));
+    ctx->sb.cap = want;
+    CKR(grow(ctx, &ctx->sb.hist, &ctx->sb.hist_cap, radix_hist_elems((int64_t)want)));
+  }
+  CKR(grow(ctx, &ctx->sb.ranges, &ctx->ranges_cap, (size_t)ntiles));
+  CKR(check_launch(ctx, launch_duplicate(ctx->pr, ctx->n, dc.GX, ctx->sb.offsets, ctx->sb.keys[0],
+                                         ctx->sb.vals[0], st)));
+  int tile_bits = 1;
+  while ((1 << tile_bits) < ntiles) ++tile_bits;
+  int which = 0;
+  CKR(check_launch(ctx, launch_radix_sort(ctx->sb, total, 32 + tile_bits, &which, st)));
+  if (which != 0) {
+    // keep the sorted result in buffer 0
+    std::swap(ctx->sb.keys[0], ctx->sb.keys[1]);
+    std::swap(ctx->sb.vals[0], ctx->sb.vals[1]);
+  }
+  CKR(check_launch(ctx, launch_ranges(ctx->sb.keys[0], total, ctx->sb.ranges, ntiles, st)));
+  CompositeArgs a;
+  a.cam = dc;
+  a.r0 = ctx->pr.r0; a.r1 = ctx->pr.r1; a.r2 = ctx->pr.r2;
+  a.p = ctx->p;
+  a.vals = ctx->sb.vals[0];
+  a.ranges = ctx->sb.ranges;
+  a.blocks = blocks;
+  a.rgb = rgb; a.depth = depth; a.alpha = alpha; a.obj = obj;
+  a.nB = ctx->nB;
+  if (blocks || rgb || depth || alpha || obj)
+    CKR(check_launch(ctx, launch_composite(a, ctx->c, st)));
+  (void)keep_lists;
+  return NBV_OK;
+}
+
+// Gains of one view from its blocks: per-Gaussian deltas (optional) and the
+// double-precision sum into out3 (device).
+int view_gains(nbv_ctx* ctx, const nbv_camera& cam, const float* blocks, float* delta, double* out3) {
+  int used = 0;
+  CKR(check_launch(ctx, launch_view_gains(dev_scene(ctx), ctx->c, to_dev(cam), blocks, ctx->F, delta,
+                                          ctx->partial, ctx->partial_cap, &used, ctx->st)));
+  CKR(check_launch(ctx, launch_reduce_gains(ctx->partial, used, out3, ctx->st)));
+  return NBV_OK;
+}
+
+int ensure_scene_buffers(nbv_ctx* ctx, int64_t n) {
+  const int KC = ctx->c.KC, nb = ctx->c.nb;
+  CKR(alloc(ctx, &ctx->mu, 3 * n)); CKR(alloc(ctx, &ctx->logs, 3 * n)); CKR(alloc(ctx, &ctx->q, 4 * n));
+  CKR(alloc(ctx, &ctx->rho, n)); CKR(alloc(ctx, &ctx->sh, (size_t)n * nb * 3));
+  CKR(alloc(ctx, &ctx->obj, (size_t)n * KC));
+  CKR(alloc(ctx, &ctx->mu_sig, n)); CKR(alloc(ctx, &ctx->scale_skip, n)); CKR(alloc(ctx, &ctx->qn, n));
+  CKR(alloc(ctx, &ctx->aux, n)); CKR(alloc(ctx, &ctx->p, (size_t)n * KC));
+  CKR(alloc(ctx, &ctx->pr.r0, n)); CKR(alloc(ctx, &ctx->pr.r1, n)); CKR(alloc(ctx, &ctx->pr.r2, n));
+  CKR(alloc(ctx, &ctx->pr.rect, n)); CKR(alloc(ctx, &ctx->pr.zbits, n));
+  CKR(alloc(ctx, &ctx->pr.touched, n)); CKR(alloc(ctx, &ctx->pr.radius, n));
+  CKR(alloc(ctx, &ctx->sb.offsets, n + 1));
+  CKR(alloc(ctx, &ctx->sb.scan_tmp, scan_scratch_elems(n + 1)));
+  CKR(alloc(ctx, &ctx->blocks, (size_t)n * ctx->nBp));
+  for (int f = 0; f < 3; ++f) {
+    const int l = f == 0 ? kNG + 3 * nb : (f == 1 ? kNG : kNG + KC);
+    ctx->F.l[f] = l;
+    CKR(alloc(ctx, &ctx->F.L[f], (size_t)n * l * (l + 1) / 2));
+    CKR(alloc(ctx, &ctx->F.dinv[f], (size_t)n * l));
+  }
+  ctx->partial_cap = 152 * 16;
+  CKR(alloc(ctx, &ctx->partial, (size_t)ctx->partial_cap * 3));
+  return NBV_OK;
+}
+
+bool check_host_floats(const float* a, size_t m) {
+  for (size_t i = 0; i < m; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+void nbv_config_default(nbv_config* cfg, int K, int sh_degree) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->K = K;
+  cfg->sh_degree = sh_degree;
+  cfg->alpha_obj = 0.3f;
+  cfg->alpha_opa = 0.3f;
+  cfg->beta_d = 10.0f;
+  cfg->beta_o = 1.0f;
+  cfg->lambda_damp = 0.1f;
+  cfg->near_z = 0.2f;
+  cfg->alpha_min = 1.0f / 255.0f;
+  cfg->alpha_max = 0.99f;
+  cfg->t_min = 1e-4f;
+  cfg->dilation = 0.3f;
+  cfg->guard = 1.3f;
+  cfg->tile_w = 16;
+  cfg->tile_h = 16;
+  cfg->batched = 0;
+}
+
+int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
+  if (!cfg || !out) return NBV_ERR_ARG;
+  *out = nullptr;
+  if (cfg->K < 1 || cfg->K > kMaxK || cfg->sh_degree < 0 || cfg->sh_degree > 3 || cfg->tile_w != 16 ||
+      cfg->tile_h != 16)
+    return NBV_ERR_ARG;
+  const float fl[] = {cfg->alpha_obj, cfg->alpha_opa, cfg->beta_d, cfg->beta_o, cfg->lambda_damp,
+                      cfg->near_z, cfg->alpha_min, cfg->alpha_max, cfg->t_min, cfg->dilation, cfg->guard};
+  for (float v : fl)
+    if (!std::isfinite(v)) return NBV_ERR_ARG;
+  if (!(cfg->lambda_damp > 0.0f) || !(cfg->alpha_min > 0.0f) || !(cfg->alpha_max < 1.0f) ||
+      !(cfg->alpha_max > cfg->alpha_min) || !(cfg->t_min > 0.0f) || !(cfg->near_z > 0.0f) ||
+      !(cfg->guard > 0.0f) || cfg->dilation < 0.0f)
+    return NBV_ERR_ARG;
+  nbv_ctx* ctx = new nbv_ctx();
+  ctx->cfg = *cfg;
+  Consts& c = ctx->c;
+  c.K = cfg->K; c.KC = cfg->K + 1; c.deg = cfg->sh_degree; c.nb = (cfg->sh_degree + 1) * (cfg->sh_degree + 1);
+  c.alpha_obj = cfg->alpha_obj; c.alpha_opa = cfg->alpha_opa; c.beta_d = cfg->beta_d; c.beta_o = cfg->beta_o;
+  c.lam = cfg->lambda_damp; c.near_z = cfg->near_z; c.alpha_min = cfg->alpha_min;
+  c.alpha_max = cfg->alpha_max; c.t_min = cfg->t_min; c.dilation = cfg->dilation; c.guard = cfg->guard;
+  ctx->nB = block_floats(c.K);
+  ctx->nBp = (ctx->nB + 3) & ~3;
+  ctx->st = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&ctx->h_total), sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&ctx->d_flags), 4 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&ctx->d_best_score), sizeof(float)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&ctx->d_err), sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    nbv_destroy(ctx);
+    return NBV_ERR_CUDA;
+  }
+  *out = ctx;
+  return NBV_OK;
+}
+
+void nbv_destroy(nbv_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st || true) cudaStreamSynchronize(ctx->st);
+  void* ptrs[] = {ctx->mu, ctx->logs, ctx->q, ctx->rho, ctx->sh, ctx->obj, ctx->mu_sig, ctx->scale_skip,
+                  ctx->qn, ctx->aux, ctx->p, ctx->d_train_cams, ctx->pr.r0, ctx->pr.r1, ctx->pr.r2,
+                  ctx->pr.rect, ctx->pr.zbits, ctx->pr.touched, ctx->pr.radius, ctx->sb.keys[0],
+                  ctx->sb.keys[1], ctx->sb.vals[0], ctx->sb.vals[1], ctx->sb.offsets, ctx->sb.scan_tmp,
+                  ctx->sb.hist, ctx->sb.ranges, ctx->blocks, ctx->train_blocks, ctx->partial,
+                  ctx->ig_train, ctx->ig_cand, ctx->out4, ctx->d_flags, ctx->d_best_score, ctx->d_err,
+                  ctx->F.L[0], ctx->F.L[1], ctx->F.L[2], ctx->F.dinv[0], ctx->F.dinv[1], ctx->F.dinv[2]};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (ctx->h_total) cudaFreeHost(ctx->h_total);
+  delete ctx;
+}
+
+int nbv_load_gaussians(nbv_ctx* ctx, int64_t n, const float* means, const float* log_scales,
+                       const float* quats, const float* opacity, const float* sh,
+                       const float* obj_logits, int ptrs_on_device) {
+  if (!ctx) return NBV_ERR_ARG;
+  if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
+  if (n < 1 || n > (int64_t)1 << 31 || !means || !log_scales || !quats || !opacity || !sh || !obj_logits)
+    return fail(ctx, NBV_ERR_ARG, "nbv_load_gaussians: bad size or NULL pointer");
+  const int KC = ctx->c.KC, nb = ctx->c.nb;
+  const size_t sizes[6] = {(size_t)3 * n, (size_t)3 * n, (size_t)4 * n, (size_t)n, (size_t)n * nb * 3,
+                           (size_t)n * KC};
+  const float* src[6] = {means, log_scales, quats, opacity, sh, obj_logits};
+  // validate on the host (device inputs are read back once for this)
+  std::vector<std::vector<float>> hostcopy;
+  const float* hv[6];
+  if (ptrs_on_device) {
+    hostcopy.resize(6);
+    for (int i = 0; i < 6; ++i) {
+      hostcopy[i].resize(sizes[i]);
+      CK(cudaMemcpyAsync(hostcopy[i].data(), src[i], sizes[i] * 4, cudaMemcpyDeviceToHost, ctx->st));
+      hv[i] = hostcopy[i].data();
+    }
+    CK(cudaStreamSynchronize(ctx->st));
+  } else {
+    for (int i = 0; i < 6; ++i) hv[i] = src[i];
+  }
+  for (int i = 0; i < 6; ++i)
+    if (!check_host_floats(hv[i], sizes[i])) return fail(ctx, NBV_ERR_ARG, "non-finite Gaussian parameter");
+  for (int64_t g = 0; g < n; ++g) {
+    const float* qq = hv[2] + 4 * g;
+    if (qq[0] == 0.0f && qq[1] == 0.0f && qq[2] == 0.0f && qq[3] == 0.0f)
+      return fail(ctx, NBV_ERR_ARG, "zero quaternion");
+  }
+  if (n != ctx->n) {
+    CKR(ensure_scene_buffers(ctx, n));
+    ctx->n = n;
+  }
+  float* dst[6] = {ctx->mu, ctx->logs, ctx->q, ctx->rho, ctx->sh, ctx->obj};
+  for (int i = 0; i < 6; ++i)
+    CK(cudaMemcpyAsync(dst[i], src[i], sizes[i] * 4,
+                       ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st));
+  if (!ptrs_on_device) CK(cudaStreamSynchronize(ctx->st));   // the caller may reuse its host memory
+  ctx->prepared = false;
+  ctx->scored = false;
+  ctx->prepared_target = -2;
+  CKR(check_launch(ctx, launch_scene_prep(dev_scene(ctx), ctx->c, -1, ctx->st)));
+  return NBV_OK;
+}
+
+static int set_views(nbv_ctx* ctx, int n, const nbv_camera* cams, std::vector<nbv_camera>& dst) {
+  if (!ctx) return NBV_ERR_ARG;
+  if (n < 0 || n > 65535 || (n > 0 && !cams)) return fail(ctx, NBV_ERR_ARG, "bad view count");
+  for (int i = 0; i < n; ++i)
+    if (!finite_cam(cams[i])) return fail(ctx, NBV_ERR_ARG, "bad camera " + std::to_string(i));
+  dst.assign(cams, cams + n);
+  return NBV_OK;
+}
+
+int nbv_set_train_views(nbv_ctx* ctx, int n, const nbv_camera* cams) {
+  CKR(set_views(ctx, n, cams, ctx->train));
+  ctx->prepared = false;
+  ctx->scored = false;
+  return NBV_OK;
+}
+
+int nbv_set_candidates(nbv_ctx* ctx, int n, const nbv_camera* cams) {
+  CKR(set_views(ctx, n, cams, ctx->cand));
+  ctx->scored = false;
+  return NBV_OK;
+}
+
+int nbv_prepare(nbv_ctx* ctx, int target_obj) {
+  if (!ctx) return NBV_ERR_ARG;
+  if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
+  if (ctx->n < 1 || ctx->train.empty()) return fail(ctx, NBV_ERR_STATE, "nbv_prepare: no Gaussians or no training views");
+  if (target_obj < -1 || target_obj > ctx->c.K) return fail(ctx, NBV_ERR_ARG, "target_obj out of range");
+  cudaStream_t st = ctx->st;
+  const int nt = (int)ctx->train.size();
+  ctx->prepared = false;
+  ctx->scored = false;
+  CKR(check_launch(ctx, launch_scene_prep(dev_scene(ctx), ctx->c, target_obj, st)));
+  size_t cams_cap = 0;
+  CKR(alloc(ctx, &ctx->d_train_cams, (size_t)nt));
+  (void)cams_cap;
+  std::vector<DevCam> hc(nt);
+  for (int t = 0; t < nt; ++t) hc[t] = to_dev(ctx->train[t]);
+  CK(cudaMemcpyAsync(ctx->d_train_cams, hc.data(), sizeof(DevCam) * nt, cudaMemcpyHostToDevice, st));
+  CKR(grow(ctx, &ctx->train_blocks, &ctx->train_blocks_cap, (size_t)nt * ctx->n * ctx->nBp));
+  CK(cudaMemsetAsync(ctx->train_blocks, 0, sizeof(float) * (size_t)nt * ctx->n * ctx->nBp, st));
+  for (int t = 0; t < nt; ++t)
+    CKR(render_view(ctx, ctx->train[t], ctx->train_blocks + (size_t)t * ctx->n * ctx->nBp, nullptr,
+                    nullptr, nullptr, nullptr));
+  CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+  CKR(check_launch(ctx, launch_build_factors(dev_scene(ctx), ctx->c, ctx->d_train_cams, ctx->train_blocks,
+                                             nt, ctx->F, ctx->d_err, st)));
+  CKR(grow(ctx, &ctx->ig_train, &ctx->ig_train_cap, (size_t)nt * 3));
+  for (int t = 0; t < nt; ++t)
+    CKR(view_gains(ctx, ctx->train[t], ctx->train_blocks + (size_t)t * ctx->n * ctx->nBp, nullptr,
+                   ctx->ig_train + 3 * t));
+  int herr = 0;
+  CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr) return fail(ctx, NBV_ERR_CUDA, "training block not positive definite");
+  ctx->prepared = true;
+  ctx->prepared_target = target_obj;
+  return NBV_OK;
+}
+
+int nbv_render(nbv_ctx* ctx, int cand, float* rgb, float* depth, float* alpha, float* obj) {
+  if (!ctx) return NBV_ERR_ARG;
+  if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
+  if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "nbv_render: no Gaussians");
+  if (cand < 0 || cand >= (int)ctx->cand.size()) return fail(ctx, NBV_ERR_ARG, "candidate out of range");
+  return render_view(ctx, ctx->cand[cand], nullptr, rgb, depth, alpha, obj);
+}
+
+int nbv_score(nbv_ctx* ctx, float* ig_out, int out_on_device) {
+  if (!ctx) return NBV_ERR_ARG;
+  if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
+  if (!ctx->prepared) return fail(ctx, NBV_ERR_STATE, "nbv_score before nbv_prepare");
+  cudaStream_t st = ctx->st;
+  const int nc = (int)ctx->cand.size();
+  CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)(nc > 0 ? nc : 1) * 3));
+  CKR(grow(ctx, &ctx->out4, &ctx->out4_cap, (size_t)(nc > 0 ? nc : 1) * 4));
+  for (int v = 0; v < nc; ++v) {
+    CK(cudaMemsetAsync(ctx->blocks, 0, sizeof(float) * (size_t)ctx->n * ctx->nBp, st));
+    CKR(render_view(ctx, ctx->cand[v], ctx->blocks, nullptr, nullptr, nullptr, nullptr));
+    CKR(view_gains(ctx, ctx->cand[v], ctx->blocks, nullptr, ctx->ig_cand + 3 * v));
+  }
+  CKR(check_launch(ctx, launch_final_scores(ctx->ig_cand, ctx->ig_train, nc, (int)ctx->train.size(), ctx->c,
+                                            ctx->out4, ctx->d_flags, ctx->d_best_score, ctx->d_flags + 1, st)));
+  ctx->scored = true;
+  int empty = 0;
+  if (ig_out) {
+    if (out_on_device) {
+      CK(cudaMemcpyAsync(ig_out, ctx->out4, sizeof(float) * 4 * nc, cudaMemcpyDeviceToDevice, st));
+    } else {
+      CK(cudaMemcpyAsync(ig_out, ctx->out4, sizeof(float) * 4 * nc, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&empty, ctx->d_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (empty) return fail(ctx, NBV_ERR_EMPTY, "a training normaliser is zero");
+    }
+  }
+  return NBV_OK;
+}
+
+int nbv_argmax(nbv_ctx* ctx, int* best_view, float* best_score) {
+  if (!ctx) return NBV_ERR_ARG;
+  if (!ctx->scored) return fail(ctx, NBV_ERR_STATE, "nbv_argmax before nbv_score");
+  int flags[2] = {0, 0};
+  float bs = 0.0f;
+  CK(cudaMemcpyAsync(flags, ctx->d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(&bs, ctx->d_best_score, sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (best_view) *best_view = flags[0];
+  if (best_score) *best_score = bs;
+  if (flags[1]) return fail(ctx, NBV_ERR_EMPTY, "a training normaliser is zero");
+  return NBV_OK;
+}
+
+int nbv_train_gains(nbv_ctx* ctx, float* out) {
+  if (!ctx || !out) return NBV_ERR_ARG;
+  if (!ctx->prepared) return fail(ctx, NBV_ERR_STATE, "nbv_train_gains before nbv_prepare");
+  const int nt = (int)ctx->train.size();
+  std::vector<double> h((size_t)nt * 3);
+  CK(cudaMemcpyAsync(h.data(), ctx->ig_train, sizeof(double) * 3 * nt, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int i = 0; i < 3 * nt; ++i) out[i] = (float)h[i];
+  return NBV_OK;
+}
+
+int nbv_gaussian_gains(nbv_ctx* ctx, int cand, float* delta) {
+  if (!ctx || !delta) return NBV_ERR_ARG;
+  if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
+  if (!ctx->prepared) return fail(ctx, NBV_ERR_STATE, "nbv_gaussian_gains before nbv_prepare");
+  if (cand < 0 || cand >= (int)ctx->cand.size()) return fail(ctx, NBV_ERR_ARG, "candidate out of range");
+  cudaStream_t st = ctx->st;
+  CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)ctx->cand.size() * 3));
+  CK(cudaMemsetAsync(ctx->blocks, 0, sizeof(float) * (size_t)ctx->n * ctx->nBp, st));
+  CKR(render_view(ctx, ctx->cand[cand], ctx->blocks, nullptr, nullptr, nullptr, nullptr));
+  CKR(view_gains(ctx, ctx->cand[cand], ctx->blocks, delta, ctx->ig_cand + 3 * cand));
+  return NBV_OK;
+}
+
+int nbv_debug_project(nbv_ctx* ctx, int view_set, int view, int32_t* rect, float* radius,
+                      uint32_t* zbits, float* mean2d, float* conic) {
+  if (!ctx) return NBV_ERR_ARG;
+  if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "no Gaussians");
+  const std::vector<nbv_camera>& vs = view_set ? ctx->train : ctx->cand;
+  if (view < 0 || view >= (int)vs.size()) return fail(ctx, NBV_ERR_ARG, "view out of range");
+  cudaStream_t st = ctx->st;
+  CKR(check_launch(ctx, launch_project(dev_scene(ctx), ctx->c, to_dev(vs[view]), ctx->pr, st)));
+  const size_t n = (size_t)ctx->n;
+  if (rect) CK(cudaMemcpyAsync(rect, ctx->pr.rect, n * sizeof(int4), cudaMemcpyDeviceToDevice, st));
+  if (radius) CK(cudaMemcpyAsync(radius, ctx->pr.radius, n * 4, cudaMemcpyDeviceToDevice, st));
+  if (zbits) CK(cudaMemcpyAsync(zbits, ctx->pr.zbits, n * 4, cudaMemcpyDeviceToDevice, st));
+  if (mean2d) CK(cudaMemcpy2DAsync(mean2d, 8, ctx->pr.r0, sizeof(float4), 8, n, cudaMemcpyDeviceToDevice, st));
+  if (conic) CK(cudaMemcpy2DAsync(conic, 12, ctx->pr.r1, sizeof(float4), 12, n, cudaMemcpyDeviceToDevice, st));
+  return NBV_OK;
+}
+
+int nbv_debug_tile_lists(nbv_ctx* ctx, int view_set, int view, int64_t* offsets, int32_t* ids,
+                         int64_t cap, int64_t* count) {
+  if (!ctx || !count) return NBV_ERR_ARG;
+  if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "no Gaussians");
+  const std::vector<nbv_camera>& vs = view_set ? ctx->train : ctx->cand;
+  if (view < 0 || view >= (int)vs.size()) return fail(ctx, NBV_ERR_ARG, "view out of range");
+  CKR(render_view(ctx, vs[view], nullptr, nullptr, nullptr, nullptr, nullptr));
+  cudaStream_t st = ctx->st;
+  const int64_t total = (int64_t)*ctx->h_total;
+  *count = total;
+  if (total > cap || !offsets || !ids) return NBV_OK;
+  const DevCam dc = to_dev(vs[view]);
+  const int ntiles = dc.GX * dc.GY;
+  std::vector<uint2> hr(ntiles);
+  CK(cudaMemcpyAsync(hr.data(), ctx->sb.ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<int64_t> ho(ntiles + 1);
+  int64_t run = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    ho[t] = run;
+    run += (int64_t)(hr[t].y - hr[t].x);
+  }
+  ho[ntiles] = run;
+  if (run != total) return fail(ctx, NBV_ERR_CUDA, "tile ranges do not cover the sorted list");
+  CK(cudaMemcpyAsync(offsets, ho.data(), sizeof(int64_t) * (ntiles + 1), cudaMemcpyHostToDevice, st));
+  if (total > 0)
+    CK(cudaMemcpyAsync(ids, ctx->sb.vals[0], sizeof(int32_t) * total, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return NBV_OK;
+}
+
+const char* nbv_last_error(const nbv_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+int64_t nbv_launch_count(const nbv_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,605 @@
+// Information gain from the structured 2D blocks (Eqs. 5-12).
+//
+// For Gaussian g, output f in {rgb, d, o} and view v, the Gauss-Newton block
+// in the raw parameters theta_f is A^f_vg = M^T B^f_vg M, where B is the 2D
+// block the compositing kernel reduced (in u = (mx, my, A, B, C, sigma,
+// colour | z | p_1..p_K)) and M = d u / d theta_f is the projection
+// Jacobian of that view (recomputed here, never stored).
+//
+// Training state (once per NBV step):
+//   H^f_g = lambda I + c_g sum_t M_t^T B_t M_t          (Eqs. 6, 9 with C_g = c_g I)
+// Jacobi-scaled, H~ = D^-1/2 H D^-1/2, and Cholesky-factorised in double
+// precision, H~ = L L^T; L is kept in single precision.
+//
+// Per view, by Sylvester's determinant identity,
+//   log det(H + c A) - log det H = log det(I_u + c W B),
+//   W = M H^-1 M^T = Z^T Z,  Z = L^-1 D^-1/2 M^T,
+// which needs an l x u triangular solve and a u x u determinant instead of
+// an l x l factorisation (u = 9 against l = 59 for colour at SH degree 3).
+// The gains of all Gaussians summed give IG_f(T, v) (block-diagonal
+// determinant, Sec. III-B.1); the training mean normalises each output
+// (Eq. 10) and the weighted sum (Eq. 11) is maximised (Eq. 5).
+#include <math.h>
+
+#include "nbv_internal.cuh"
+
+namespace nbv {
+namespace {
+
+constexpr int kMaxWarps = 8;
+
+struct GJac {
+  float Jm[2][3];    // d(mx,my)/d mu
+  float Jc[3][10];   // d(A,B,C)/d(mu, log s, q)
+  float Jz[3];       // d z / d mu
+  float dsig;        // d sigma / d rho
+  float Jrgb[3][3];  // d rgb / d mu
+  float live[3];     // 1 where the colour is not clamped at 0
+  float Y[16];       // SH basis at the view direction
+};
+
+struct SHC {
+  float c0, c1, c2a, c2b, c2c, c3a, c3b, c3c, c3d, c3e;
+};
+__device__ __forceinline__ SHC shc() {
+  SHC k;
+  k.c0 = (float)(0.5 / 1.7724538509055160273);
+  k.c1 = (float)0.48860251190291992159;
+  k.c2a = (float)(0.5 * 3.8729833462074168852 / 1.7724538509055160273);
+  k.c2b = (float)(0.25 * 2.2360679774997896964 / 1.7724538509055160273);
+  k.c2c = (float)(0.25 * 3.8729833462074168852 / 1.7724538509055160273);
+  k.c3a = (float)(0.25 * 2.3601743597065740);
+  k.c3b = (float)(0.5 * 5.7812228852811080);
+  k.c3c = (float)(0.25 * 1.8281831978578629);
+  k.c3d = (float)(0.25 * 1.4927053303604616);
+  k.c3e = (float)(0.25 * 5.7812228852811080);
+  return k;
+}
+
+// Real SH values and gradients (of the polynomial forms) at direction (x,y,z).
+__device__ void sh_val_grad(int deg, float x, float y, float z, float* Y, float (*G)[3]) {
+  const SHC k = shc();
+  for (int i = 0; i < 16; ++i) { Y[i] = 0.0f; G[i][0] = G[i][1] = G[i][2] = 0.0f; }
+  Y[0] = k.c0;
+  if (deg < 1) return;
+  Y[1] = -k.c1 * y; G[1][1] = -k.c1;
+  Y[2] = k.c1 * z;  G[2][2] = k.c1;
+  Y[3] = -k.c1 * x; G[3][0] = -k.c1;
+  if (deg < 2) return;
+  Y[4] = k.c2a * x * y;  G[4][0] = k.c2a * y; G[4][1] = k.c2a * x;
+  Y[5] = -k.c2a * y * z; G[5][1] = -k.c2a * z; G[5][2] = -k.c2a * y;
+  Y[6] = k.c2b * (2.0f * z * z - x * x - y * y);
+  G[6][0] = -2.0f * k.c2b * x; G[6][1] = -2.0f * k.c2b * y; G[6][2] = 4.0f * k.c2b * z;
+  Y[7] = -k.c2a * x * z; G[7][0] = -k.c2a * z; G[7][2] = -k.c2a * x;
+  Y[8] = k.c2c * (x * x - y * y); G[8][0] = 2.0f * k.c2c * x; G[8][1] = -2.0f * k.c2c * y;
+  if (deg < 3) return;
+  Y[9] = -k.c3a * y * (3.0f * x * x - y * y);
+  G[9][0] = -6.0f * k.c3a * x * y; G[9][1] = -k.c3a * (3.0f * x * x - 3.0f * y * y);
+  Y[10] = k.c3b * x * y * z;
+  G[10][0] = k.c3b * y * z; G[10][1] = k.c3b * x * z; G[10][2] = k.c3b * x * y;
+  Y[11] = -k.c3c * y * (4.0f * z * z - x * x - y * y);
+  G[11][0] = 2.0f * k.c3c * x * y; G[11][1] = -k.c3c * (4.0f * z * z - x * x - 3.0f * y * y);
+  G[11][2] = -8.0f * k.c3c * y * z;
+  Y[12] = k.c3d * z * (2.0f * z * z - 3.0f * x * x - 3.0f * y * y);
+  G[12][0] = -6.0f * k.c3d * x * z; G[12][1] = -6.0f * k.c3d * y * z;
+  G[12][2] = k.c3d * (6.0f * z * z - 3.0f * x * x - 3.0f * y * y);
+  Y[13] = -k.c3c * x * (4.0f * z * z - x * x - y * y);
+  G[13][0] = -k.c3c * (4.0f * z * z - 3.0f * x * x - y * y); G[13][1] = 2.0f * k.c3c * x * y;
+  G[13][2] = -8.0f * k.c3c * x * z;
+  Y[14] = k.c3e * z * (x * x - y * y);
+  G[14][0] = 2.0f * k.c3e * x * z; G[14][1] = -2.0f * k.c3e * y * z; G[14][2] = k.c3e * (x * x - y * y);
+  Y[15] = -k.c3a * x * (x * x - 3.0f * y * y);
+  G[15][0] = -k.c3a * (3.0f * x * x - 3.0f * y * y); G[15][1] = 6.0f * k.c3a * x * y;
+}
+
+// Projection Jacobians of Gaussian g in view cam (values in single precision).
+__device__ void compute_gjac(const DevScene& s, const Consts& c, const DevCam& cam, int64_t g,
+                             GJac& J) {
+  const float4 ms = s.mu_sig[g], ss = s.scale_skip[g], qq = s.qn[g], ax = s.aux[g];
+  const float* R = cam.R;
+  const float mu[3] = {ms.x, ms.y, ms.z};
+  float tc[3];
+  for (int i = 0; i < 3; ++i) tc[i] = R[3 * i] * mu[0] + R[3 * i + 1] * mu[1] + R[3 * i + 2] * mu[2] + cam.t[i];
+  const float x = tc[0], y = tc[1], z = tc[2];
+  const float iz = 1.0f / z, iz2 = iz * iz;
+  // mean: d(mx,my)/d t, then * R
+  const float dmx[3] = {cam.fx * iz, 0.0f, -cam.fx * x * iz2};
+  const float dmy[3] = {0.0f, cam.fy * iz, -cam.fy * y * iz2};
+  for (int m = 0; m < 3; ++m) {
+    J.Jm[0][m] = dmx[0] * R[m] + dmx[1] * R[3 + m] + dmx[2] * R[6 + m];
+    J.Jm[1][m] = dmy[0] * R[m] + dmy[1] * R[3 + m] + dmy[2] * R[6 + m];
+    J.Jz[m] = R[6 + m];
+  }
+  // perspective Jacobian with the guard band
+  const float limx = c.guard * (0.5f * (float)cam.W / cam.fx);
+  const float limy = c.guard * (0.5f * (float)cam.H / cam.fy);
+  const float xr = x * iz, yr = y * iz;
+  const bool clx = fabsf(xr) > limx, cly = fabsf(yr) > limy;
+  const float xz = fminf(limx, fmaxf(-limx, xr)), yz = fminf(limy, fmaxf(-limy, yr));
+  const float j00 = cam.fx * iz, j02 = -cam.fx * xz * iz;
+  const float j11 = cam.fy * iz, j12 = -cam.fy * yz * iz;
+  float T0[3], T1[3];
+  for (int i = 0; i < 3; ++i) {
+    T0[i] = j00 * R[i] + j02 * R[6 + i];
+    T1[i] = j11 * R[3 + i] + j12 * R[6 + i];
+  }
+  // derivatives of j00, j02, j11, j12 w.r.t. t = (x, y, z)
+  float dj00[3] = {0.0f, 0.0f, -cam.fx * iz2};
+  float dj02[3], dj12[3];
+  if (clx) { dj02[0] = 0.0f; dj02[1] = 0.0f; dj02[2] = -j02 * iz; }
+  else { dj02[0] = -cam.fx * iz2; dj02[1] = 0.0f; dj02[2] = 2.0f * cam.fx * x * iz2 * iz; }
+  float dj11[3] = {0.0f, 0.0f, -cam.fy * iz2};
+  if (cly) { dj12[0] = 0.0f; dj12[1] = 0.0f; dj12[2] = -j12 * iz; }
+  else { dj12[0] = 0.0f; dj12[1] = -cam.fy * iz2; dj12[2] = 2.0f * cam.fy * y * iz2 * iz; }
+  // rotation of the Gaussian and Sigma3
+  const float qw = qq.x, qx = qq.y, qy = qq.z, qz = qq.w;
+  const float Rq[9] = {1.0f - 2.0f * (qy * qy + qz * qz), 2.0f * (qx * qy - qw * qz), 2.0f * (qx * qz + qw * qy),
+                       2.0f * (qx * qy + qw * qz), 1.0f - 2.0f * (qx * qx + qz * qz), 2.0f * (qy * qz - qw * qx),
+                       2.0f * (qx * qz - qw * qy), 2.0f * (qy * qz + qw * qx), 1.0f - 2.0f * (qx * qx + qy * qy)};
+  const float s2[3] = {ss.x * ss.x, ss.y * ss.y, ss.z * ss.z};
+  float S3[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      S3[3 * i + j] = Rq[3 * i] * s2[0] * Rq[3 * j] + Rq[3 * i + 1] * s2[1] * Rq[3 * j + 1] +
+                      Rq[3 * i + 2] * s2[2] * Rq[3 * j + 2];
+  float ST0[3], ST1[3];  // Sigma3 T0^T, Sigma3 T1^T
+  for (int i = 0; i < 3; ++i) {
+    ST0[i] = S3[3 * i] * T0[0] + S3[3 * i + 1] * T0[1] + S3[3 * i + 2] * T0[2];
+    ST1[i] = S3[3 * i] * T1[0] + S3[3 * i + 1] * T1[1] + S3[3 * i + 2] * T1[2];
+  }
+  const float a = T0[0] * ST0[0] + T0[1] * ST0[1] + T0[2] * ST0[2] + c.dilation;
+  const float b = T0[0] * ST1[0] + T0[1] * ST1[1] + T0[2] * ST1[2];
+  const float cc = T1[0] * ST1[0] + T1[1] * ST1[1] + T1[2] * ST1[2] + c.dilation;
+  const float det = a * cc - b * b;
+  const float A = cc / det, B = -b / det, C = a / det;
+  // d conic = -Q dSigma2 Q
+  auto dconic = [&](float da, float db, float dc, float* out) {
+    out[0] = -(A * A * da + 2.0f * A * B * db + B * B * dc);
+    out[1] = -(A * B * da + (A * C + B * B) * db + B * C * dc);
+    out[2] = -(B * B * da + 2.0f * B * C * db + C * C * dc);
+  };
+  // w.r.t. camera-space t, then mu
+  float dabc_t[3][3];
+  for (int n = 0; n < 3; ++n) {
+    float dT0[3], dT1[3];
+    for (int i = 0; i < 3; ++i) {
+      dT0[i] = dj00[n] * R[i] + dj02[n] * R[6 + i];
+      dT1[i] = dj11[n] * R[3 + i] + dj12[n] * R[6 + i];
+    }
+    const float da = 2.0f * (dT0[0] * ST0[0] + dT0[1] * ST0[1] + dT0[2] * ST0[2]);
+    const float db = dT0[0] * ST1[0] + dT0[1] * ST1[1] + dT0[2] * ST1[2] +
+                     dT1[0] * ST0[0] + dT1[1] * ST0[1] + dT1[2] * ST0[2];
+    const float dc = 2.0f * (dT1[0] * ST1[0] + dT1[1] * ST1[1] + dT1[2] * ST1[2]);
+    dconic(da, db, dc, dabc_t[n]);
+  }
+  for (int m = 0; m < 3; ++m)
+    for (int e = 0; e < 3; ++e)
+      J.Jc[e][m] = dabc_t[0][e] * R[m] + dabc_t[1][e] * R[3 + m] + dabc_t[2][e] * R[6 + m];
+  // w.r.t. log-scales: dSigma3 = 2 s_k^2 r_k r_k^T
+  float u0[3], u1[3];   // T0 . r_k, T1 . r_k
+  for (int k = 0; k < 3; ++k) {
+    u0[k] = T0[0] * Rq[k] + T0[1] * Rq[3 + k] + T0[2] * Rq[6 + k];
+    u1[k] = T1[0] * Rq[k] + T1[1] * Rq[3 + k] + T1[2] * Rq[6 + k];
+  }
+  for (int k = 0; k < 3; ++k) {
+    float o[3];
+    dconic(2.0f * s2[k] * u0[k] * u0[k], 2.0f * s2[k] * u0[k] * u1[k], 2.0f * s2[k] * u1[k] * u1[k], o);
+    for (int e = 0; e < 3; ++e) J.Jc[e][3 + k] = o[e];
+  }
+  // w.r.t. the normalised quaternion, then the raw one
+  const float dR[4][9] = {
+      {0.0f, -2.0f * qz, 2.0f * qy, 2.0f * qz, 0.0f, -2.0f * qx, -2.0f * qy, 2.0f * qx, 0.0f},
+      {0.0f, 2.0f * qy, 2.0f * qz, 2.0f * qy, -4.0f * qx, -2.0f * qw, 2.0f * qz, 2.0f * qw, -4.0f * qx},
+      {-4.0f * qy, 2.0f * qx, 2.0f * qw, 2.0f * qx, 0.0f, 2.0f * qz, -2.0f * qw, 2.0f * qz, -4.0f * qy},
+      {-4.0f * qz, -2.0f * qw, 2.0f * qx, 2.0f * qw, -4.0f * qz, 2.0f * qy, 2.0f * qx, 2.0f * qy, 0.0f}};
+  float dq_hat[4][3];
+  for (int e = 0; e < 4; ++e) {
+    float v0[3], v1[3];
+    for (int k = 0; k < 3; ++k) {
+      v0[k] = T0[0] * dR[e][k] + T0[1] * dR[e][3 + k] + T0[2] * dR[e][6 + k];
+      v1[k] = T1[0] * dR[e][k] + T1[1] * dR[e][3 + k] + T1[2] * dR[e][6 + k];
+    }
+    float da = 0.0f, db = 0.0f, dc = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+      da += 2.0f * v0[k] * s2[k] * u0[k];
+      db += s2[k] * (v0[k] * u1[k] + u0[k] * v1[k]);
+      dc += 2.0f * v1[k] * s2[k] * u1[k];
+    }
+    dconic(da, db, dc, dq_hat[e]);
+  }
+  const float qh[4] = {qw, qx, qy, qz};
+  const float inv_n = 1.0f / ax.z;
+  for (int i = 0; i < 4; ++i)
+    for (int e3 = 0; e3 < 3; ++e3) {
+      float acc = 0.0f;
+      for (int e = 0; e < 4; ++e) acc += ((e == i ? 1.0f : 0.0f) - qh[e] * qh[i]) * inv_n * dq_hat[e][e3];
+      J.Jc[e3][6 + i] = acc;
+    }
+  J.dsig = ms.w * (1.0f - ms.w);
+  // colour: SH at the view direction, d rgb / d mu through the direction
+  float dv[3] = {mu[0] - cam.campos[0], mu[1] - cam.campos[1], mu[2] - cam.campos[2]};
+  const float il = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+  const float d[3] = {dv[0] * il, dv[1] * il, dv[2] * il};
+  float G[16][3];
+  sh_val_grad(c.deg, d[0], d[1], d[2], J.Y, G);
+  const float* shg = s.sh + (size_t)g * c.nb * 3;
+  for (int ch = 0; ch < 3; ++ch) {
+    float val = 0.5f, gr[3] = {0.0f, 0.0f, 0.0f};
+    for (int k = 0; k < c.nb; ++k) {
+      const float co = shg[3 * k + ch];
+      val += J.Y[k] * co;
+      gr[0] += G[k][0] * co; gr[1] += G[k][1] * co; gr[2] += G[k][2] * co;
+    }
+    J.live[ch] = val < 0.0f ? 0.0f : 1.0f;
+    const float gd = gr[0] * d[0] + gr[1] * d[1] + gr[2] * d[2];
+    for (int m = 0; m < 3; ++m) J.Jrgb[ch][m] = J.live[ch] * (gr[m] - gd * d[m]) * il;
+  }
+}
+
+__host__ __device__ __forceinline__ int out_l(int f, const Consts& c) {
+  return f == 0 ? kNG + 3 * c.nb : (f == 1 ? kNG : kNG + c.KC);
+}
+__host__ __device__ __forceinline__ int out_u(int f, const Consts& c) {
+  return f == 0 ? 9 : (f == 1 ? 7 : 6 + c.K);
+}
+
+// Dense M (u x l, row-major) of output f. Lanes zero it; lane 0 fills it.
+__device__ void build_M(int f, const GJac& J, const Consts& c, const float* p, float* M, int lane) {
+  const int l = out_l(f, c), u = out_u(f, c);
+  for (int i = lane; i < u * l; i += 32) M[i] = 0.0f;
+  __syncwarp();
+  if (lane == 0) {
+    for (int m = 0; m < 3; ++m) { M[0 * l + m] = J.Jm[0][m]; M[1 * l + m] = J.Jm[1][m]; }
+    for (int e = 0; e < 3; ++e)
+      for (int k = 0; k < 10; ++k) M[(2 + e) * l + k] = J.Jc[e][k];
+    M[5 * l + 10] = J.dsig;
+    if (f == 0) {
+      for (int ch = 0; ch < 3; ++ch) {
+        for (int m = 0; m < 3; ++m) M[(6 + ch) * l + m] = J.Jrgb[ch][m];
+        for (int k = 0; k < c.nb; ++k) M[(6 + ch) * l + kNG + 3 * k + ch] = J.live[ch] * J.Y[k];
+      }
+    } else if (f == 1) {
+      for (int m = 0; m < 3; ++m) M[6 * l + m] = J.Jz[m];
+    } else {
+      for (int j = 1; j <= c.K; ++j)      // d p_j / d o_b = p_j (delta_jb - p_b)
+        for (int bb = 0; bb < c.KC; ++bb) M[(5 + j) * l + kNG + bb] = p[j] * ((j == bb ? 1.0f : 0.0f) - p[bb]);
+    }
+  }
+  __syncwarp();
+}
+
+// Dense B (u x u) of output f from the structured block.
+__device__ void build_B(int f, const float* blk, const Consts& c, float* Bm, int lane) {
+  const int u = out_u(f, c);
+  const int qoff = f == 0 ? kOffQrgb : (f == 1 ? kOffQd : kOffQo);
+  const float W2 = blk[kOffW2];
+  for (int i = lane; i < u * u; i += 32) {
+    const int r = i / u, cc = i - r * u;
+    float v;
+    if (r < 6 && cc < 6) v = r >= cc ? blk[qoff + tri(r, cc)] : blk[qoff + tri(cc, r)];
+    else if (r >= 6 && cc >= 6) {
+      if (f == 2) v = W2 * ((r == cc ? 1.0f : 0.0f) + 1.0f);
+      else v = r == cc ? W2 : 0.0f;
+    } else {
+      const int big = r >= 6 ? r : cc, small = r >= 6 ? cc : r;
+      const int xo = f == 0 ? kOffXrgb : (f == 1 ? kOffXd : kOffXo);
+      v = blk[xo + 6 * (big - 6) + small];
+    }
+    Bm[i] = v;
+  }
+  __syncwarp();
+}
+
+// --------------------------------------------------------- training factors
+__global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__ cams,
+                                const float* __restrict__ blocks, int n_train, Factors F,
+                                int* err, int lmax, int umax) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nB = block_floats(c.K), nBp = (nB + 3) & ~3;
+  const size_t per_warp_d = (size_t)lmax * (lmax + 1) / 2 + lmax;
+  const size_t per_warp_f = (size_t)umax * lmax * 2 + (size_t)umax * umax + sizeof(GJac) / 4 + 4;
+  double* Hs = reinterpret_cast<double*>(smem) + warp * per_warp_d;
+  double* dsc = Hs + (size_t)lmax * (lmax + 1) / 2;    // 1 / sqrt(H_ii)
+  float* fbase = reinterpret_cast<float*>(reinterpret_cast<double*>(smem) + nw * per_warp_d) +
+                 warp * per_warp_f;
+  float* M = fbase;
+  float* BM = M + umax * lmax;
+  float* Bm = BM + umax * lmax;
+  GJac* J = reinterpret_cast<GJac*>(Bm + umax * umax);
+  for (int64_t g = (int64_t)blockIdx.x * nw + warp; g < s.n; g += (int64_t)gridDim.x * nw) {
+    const float cg = s.aux[g].y;
+    const float* p = s.p + (size_t)g * c.KC;
+    for (int f = 0; f < 3; ++f) {
+      const int l = out_l(f, c), u = out_u(f, c), nt = l * (l + 1) / 2;
+      for (int i = lane; i < nt; i += 32) Hs[i] = 0.0;
+      __syncwarp();
+      if (cg > 0.0f) {
+        for (int t = 0; t < n_train; ++t) {
+          const float* blk = blocks + ((size_t)t * s.n + g) * nBp;
+          if (blk[kOffW2] == 0.0f) continue;   // not seen in this view
+          if (lane == 0) compute_gjac(s, c, cams[t], g, *J);
+          __syncwarp();
+          build_M(f, *J, c, p, M, lane);
+          build_B(f, blk, c, Bm, lane);
+          for (int i = lane; i < u * l; i += 32) {      // BM = B M
+            const int r = i / l, cc = i - r * l;
+            float acc = 0.0f;
+            for (int k = 0; k < u; ++k) acc += Bm[r * u + k] * M[k * l + cc];
+            BM[i] = acc;
+          }
+          __syncwarp();
+          for (int i = lane; i < nt; i += 32) {         // H += c M^T (B M)
+            int r = (int)((sqrtf(8.0f * i + 1.0f) - 1.0f) * 0.5f);
+            while (tri(r + 1, 0) <= i) ++r;
+            while (tri(r, 0) > i) --r;
+            const int cc = i - tri(r, 0);
+            float acc = 0.0f;
+            for (int k = 0; k < u; ++k) acc += M[k * l + r] * BM[k * l + cc];
+            Hs[i] += (double)cg * (double)acc;
+          }
+          __syncwarp();
+        }
+      }
+      // damping, Jacobi scaling, Cholesky (double), store
+      float* Lg = F.L[f] + (size_t)g * nt;
+      float* dg = F.dinv[f] + (size_t)g * l;
+      for (int i = lane; i < l; i += 32) Hs[tri(i, i)] += (double)c.lam;
+      __syncwarp();
+      for (int i = lane; i < l; i += 32) {
+        const double di = 1.0 / sqrt(Hs[tri(i, i)]);
+        dsc[i] = di;
+        dg[i] = (float)di;
+      }
+      __syncwarp();
+      for (int i = lane; i < nt; i += 32) {
+        int r = (int)((sqrtf(8.0f * i + 1.0f) - 1.0f) * 0.5f);
+        while (tri(r + 1, 0) <= i) ++r;
+        while (tri(r, 0) > i) --r;
+        const int cc = i - tri(r, 0);
+        Hs[i] = Hs[i] * dsc[r] * dsc[cc];
+      }
+      __syncwarp();
+      // the diagonal is now 1; right-looking Cholesky
+      for (int k = 0; k < l; ++k) {
+        const double dkk = Hs[tri(k, k)];
+        if (!(dkk > 0.0)) { if (lane == 0) atomicExch(err, 1); }
+        const double Lkk = sqrt(fmax(dkk, 1e-300));
+        __syncwarp();
+        if (lane == 0) Hs[tri(k, k)] = Lkk;
+        for (int i = k + 1 + lane; i < l; i += 32) Hs[tri(i, k)] /= Lkk;
+        __syncwarp();
+        for (int i = k + 1 + lane; i < l; i += 32) {
+          const double lik = Hs[tri(i, k)];
+          for (int j = k + 1; j <= i; ++j) Hs[tri(i, j)] -= lik * Hs[tri(j, k)];
+        }
+        __syncwarp();
+      }
+      for (int i = lane; i < nt; i += 32) Lg[i] = (float)Hs[i];
+      __syncwarp();
+    }
+  }
+}
+
+// -------------------------------------------------------------- view gains
+__global__ void k_view_gains(DevScene s, Consts c, DevCam cam, const float* __restrict__ blocks,
+                             Factors F, float* __restrict__ delta, double* __restrict__ partial,
+                             int lmax, int umax) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double wsum[kMaxWarps][3];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nB = block_floats(c.K), nBp = (nB + 3) & ~3;
+  const size_t per_warp = 2 * (size_t)lmax * umax + 3 * (size_t)umax * umax + sizeof(GJac) / 4 + 4;
+  float* Z = reinterpret_cast<float*>(smem) + warp * per_warp;
+  float* Mt = Z + lmax * umax;
+  float* Bm = Mt + lmax * umax;
+  float* W = Bm + umax * umax;
+  float* G = W + umax * umax;
+  GJac* J = reinterpret_cast<GJac*>(G + umax * umax);
+  double acc3[3] = {0.0, 0.0, 0.0};
+  for (int64_t g = (int64_t)blockIdx.x * nw + warp; g < s.n; g += (int64_t)gridDim.x * nw) {
+    const float cg = s.aux[g].y;
+    const float* blk = blocks + (size_t)g * nBp;
+    float dl[3] = {0.0f, 0.0f, 0.0f};
+    if (cg > 0.0f && blk[kOffW2] != 0.0f) {
+      if (lane == 0) compute_gjac(s, c, cam, g, *J);
+      __syncwarp();
+      const float* p = s.p + (size_t)g * c.KC;
+      for (int f = 0; f < 3; ++f) {
+        const int l = out_l(f, c), u = out_u(f, c), nt = l * (l + 1) / 2;
+        const float* Lg = F.L[f] + (size_t)g * nt;
+        const float* dg = F.dinv[f] + (size_t)g * l;
+        // Z = D^-1/2 M^T (l x u, row-major)
+        build_M(f, *J, c, p, Mt, lane);
+        for (int i = lane; i < l * u; i += 32) {
+          const int r = i / u, cc = i - r * u;
+          Z[i] = dg[r] * Mt[cc * l + r];
+        }
+        __syncwarp();
+        // forward substitution Z <- L^-1 Z
+        for (int k = 0; k < l; ++k) {
+          const float ik = 1.0f / Lg[tri(k, k)];
+          for (int j = lane; j < u; j += 32) Z[k * u + j] *= ik;
+          __syncwarp();
+          for (int i = lane; i < (l - k - 1) * u; i += 32) {
+            const int r = k + 1 + i / u, cc = i % u;
+            Z[r * u + cc] -= Lg[tri(r, k)] * Z[k * u + cc];
+          }
+          __syncwarp();
+        }
+        // W = Z^T Z
+        for (int i = lane; i < u * u; i += 32) {
+          const int r = i / u, cc = i - r * u;
+          if (cc > r) continue;
+          float a = 0.0f;
+          for (int k = 0; k < l; ++k) a += Z[k * u + r] * Z[k * u + cc];
+          W[r * u + cc] = a;
+          W[cc * u + r] = a;
+        }
+        __syncwarp();
+        build_B(f, blk, c, Bm, lane);
+        // G = I + c W B
+        for (int i = lane; i < u * u; i += 32) {
+          const int r = i / u, cc = i - r * u;
+          float a = 0.0f;
+          for (int k = 0; k < u; ++k) a += W[r * u + k] * Bm[k * u + cc];
+          G[i] = (r == cc ? 1.0f : 0.0f) + cg * a;
+        }
+        __syncwarp();
+        // log det G by LU with partial pivoting
+        float ld = 0.0f;
+        for (int k = 0; k < u; ++k) {
+          float best = -1.0f;
+          int bi = k;
+          for (int i = k + lane; i < u; i += 32) {
+            const float v = fabsf(G[i * u + k]);
+            if (v > best) { best = v; bi = i; }
+          }
+          for (int o = 16; o >= 1; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+          }
+          if (bi != k) {
+            for (int j = lane; j < u; j += 32) {
+              const float tmp = G[k * u + j];
+              G[k * u + j] = G[bi * u + j];
+              G[bi * u + j] = tmp;
+            }
+          }
+          __syncwarp();
+          const float piv = G[k * u + k];
+          ld += logf(fabsf(piv));
+          for (int i = k + 1 + lane; i < u; i += 32) {
+            const float fct = G[i * u + k] / piv;
+            for (int j = k + 1; j < u; ++j) G[i * u + j] -= fct * G[k * u + j];
+          }
+          __syncwarp();
+        }
+        dl[f] = ld;
+      }
+    }
+    if (lane == 0) {
+      if (delta) { delta[3 * g] = dl[0]; delta[3 * g + 1] = dl[1]; delta[3 * g + 2] = dl[2]; }
+      acc3[0] += dl[0]; acc3[1] += dl[1]; acc3[2] += dl[2];
+    }
+    __syncwarp();
+  }
+  if (lane == 0) { wsum[warp][0] = acc3[0]; wsum[warp][1] = acc3[1]; wsum[warp][2] = acc3[2]; }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += wsum[w][threadIdx.x];
+    partial[3 * blockIdx.x + threadIdx.x] = t;
+  }
+}
+
+__global__ void k_reduce_partial(const double* __restrict__ partial, int nblocks, double* out3) {
+  __shared__ double sm[3][256];
+  const int tid = threadIdx.x;
+  double a[3] = {0.0, 0.0, 0.0};
+  for (int i = tid; i < nblocks; i += 256)
+    for (int f = 0; f < 3; ++f) a[f] += partial[3 * i + f];
+  for (int f = 0; f < 3; ++f) sm[f][tid] = a[f];
+  __syncthreads();
+  for (int h = 128; h >= 1; h >>= 1) {
+    if (tid < h)
+      for (int f = 0; f < 3; ++f) sm[f][tid] += sm[f][tid + h];
+    __syncthreads();
+  }
+  if (tid < 3) out3[tid] = sm[tid][0];
+}
+
+__global__ void k_final_scores(const double* __restrict__ igc, const double* __restrict__ igt,
+                               int n_cand, int n_train, Consts c, float* __restrict__ out4,
+                               int* best, float* best_score, int* err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double nrm[3] = {0.0, 0.0, 0.0};
+  for (int t = 0; t < n_train; ++t)
+    for (int f = 0; f < 3; ++f) nrm[f] += igt[3 * t + f];
+  for (int f = 0; f < 3; ++f) nrm[f] /= (double)n_train;
+  const bool empty = !(nrm[0] != 0.0 && nrm[1] != 0.0 && nrm[2] != 0.0);
+  *err = empty ? 1 : 0;
+  int bi = -1;
+  float bs = 0.0f;
+  for (int v = 0; v < n_cand; ++v) {
+    double tot = empty ? (double)NAN
+                       : igc[3 * v] / nrm[0] + (double)c.beta_d * igc[3 * v + 1] / nrm[1] +
+                             (double)c.beta_o * igc[3 * v + 2] / nrm[2];
+    out4[4 * v] = (float)igc[3 * v];
+    out4[4 * v + 1] = (float)igc[3 * v + 1];
+    out4[4 * v + 2] = (float)igc[3 * v + 2];
+    out4[4 * v + 3] = (float)tot;
+    if (!empty && (bi < 0 || tot > (double)bs)) { bi = v; bs = (float)tot; }
+  }
+  *best = bi;
+  *best_score = bs;
+}
+
+size_t factors_smem_per_warp(int lmax, int umax) {
+  const size_t per_warp_d = (size_t)lmax * (lmax + 1) / 2 + lmax;
+  const size_t per_warp_f = (size_t)umax * lmax * 2 + (size_t)umax * umax + sizeof(GJac) / 4 + 4;
+  return per_warp_d * sizeof(double) + per_warp_f * sizeof(float);
+}
+
+size_t gains_smem_per_warp(int lmax, int umax) {
+  return (2 * (size_t)lmax * umax + 3 * (size_t)umax * umax + sizeof(GJac) / 4 + 4) * sizeof(float);
+}
+
+int warps_for(size_t per_warp) {
+  const size_t budget = 200 * 1024;
+  int w = (int)(budget / per_warp);
+  return w < 1 ? 1 : (w > 4 ? 4 : w);
+}
+
+}  // namespace
+
+static void sizes(const Consts& c, int* lmax, int* umax) {
+  *lmax = kNG + 3 * c.nb > kNG + c.KC ? kNG + 3 * c.nb : kNG + c.KC;
+  *umax = 9 > 6 + c.K ? 9 : 6 + c.K;
+}
+
+int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams, const float* blocks,
+                         int n_train, const Factors& f, int* d_err, cudaStream_t st) {
+  int lmax, umax;
+  sizes(c, &lmax, &umax);
+  const size_t pw = factors_smem_per_warp(lmax, umax);
+  const int nw = warps_for(pw);
+  const size_t sm = pw * nw;
+  cudaFuncSetAttribute(k_build_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int64_t nblk = (s.n + nw - 1) / nw;
+  const int grid = (int)(nblk < 152 * 32 ? nblk : 152 * 32);
+  k_build_factors<<<grid, 32 * nw, sm, st>>>(s, c, cams, blocks, n_train, f, d_err, lmax, umax);
+  return 1;
+}
+
+int launch_view_gains(const DevScene& s, const Consts& c, const DevCam& cam, const float* blocks,
+                      const Factors& f, float* delta, double* partial, int nblocks_cap,
+                      int* nblocks_used, cudaStream_t st) {
+  int lmax, umax;
+  sizes(c, &lmax, &umax);
+  const size_t pw = gains_smem_per_warp(lmax, umax);
+  const int nw = warps_for(pw);
+  const size_t sm = pw * nw;
+  cudaFuncSetAttribute(k_view_gains, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int64_t nblk = (s.n + nw - 1) / nw;
+  int grid = (int)(nblk < nblocks_cap ? nblk : nblocks_cap);
+  if (grid < 1) grid = 1;
+  *nblocks_used = grid;
+  k_view_gains<<<grid, 32 * nw, sm, st>>>(s, c, cam, blocks, f, delta, partial, lmax, umax);
+  return 1;
+}
+
+int launch_reduce_gains(const double* partial, int nblocks, double* out3, cudaStream_t st) {
+  k_reduce_partial<<<1, 256, 0, st>>>(partial, nblocks, out3);
+  return 1;
+}
+
+int launch_final_scores(const double* ig_cand, const double* ig_train, int n_cand, int n_train,
+                        const Consts& c, float* out4, int* best, float* best_score, int* err,
+                        cudaStream_t st) {
+  k_final_scores<<<1, 32, 0, st>>>(ig_cand, ig_train, n_cand, n_train, c, out4, best, best_score, err);
+  return 1;
+}
+
+}  // namespace nbv

@@ -1,0 +1,141 @@
+// Internal declarations shared by the translation units of libnbvgs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "nbvgs.h"
+
+namespace nbv {
+
+constexpr int kTile = 16;           // 16x16 screen tiles, one thread per pixel
+constexpr int kTilePix = kTile * kTile;
+constexpr int kMaxK = 127;          // at most 128 object channels
+constexpr int kNG = 11;             // geometric parameters: mu(3) log-scale(3) quat(4) opacity logit(1)
+
+// Structured per-(view, Gaussian) 2D block layout (floats). With
+// a = d alpha / d(mx, my, A, B, C, sigma), s_X = d X / d alpha and the
+// blend weight w = alpha T, every pixel adds:
+//   Q_rgb += (sum_c s_c^2) a a^T      Q_d += s_D^2 a a^T
+//   Q_o   += (sum_k s_k^2) a a^T      (k over the K+1 object channels)
+//   X_rgb[c] += w s_c a               X_d += w s_D a
+//   X_o[j]   += w (s_j - s_0) a  (j = 1..K)
+//   W2 += w^2
+// which is everything the rgb / depth / object Gauss-Newton blocks in the
+// 2D splat parameters need (their colour, depth and probability blocks are
+// W2 I_3, W2 and W2 (I_K + 1 1^T)).
+constexpr int kOffQrgb = 0;
+constexpr int kOffQd = 21;
+constexpr int kOffQo = 42;
+constexpr int kOffXrgb = 63;
+constexpr int kOffXd = 81;
+constexpr int kOffW2 = 87;
+constexpr int kOffXo = 88;
+__host__ __device__ constexpr int block_floats(int K) { return kOffXo + 6 * K; }
+// packed lower-triangle index of (i, j), i >= j
+__host__ __device__ __forceinline__ int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+struct DevCam {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  float campos[3];
+  int W, H, GX, GY;
+};
+
+struct Consts {
+  int K, KC, deg, nb;
+  float alpha_obj, alpha_opa, beta_d, beta_o, lam;
+  float near_z, alpha_min, alpha_max, t_min, dilation, guard;
+};
+
+// Scene on the device (structure of arrays).
+struct DevScene {
+  int64_t n;
+  const float* mu_raw;       // [n][3]
+  const float* logs_raw;     // [n][3]
+  const float* q_raw;        // [n][4]
+  const float* rho_raw;      // [n]
+  const float* sh;           // [n][nb][3]
+  const float* obj_raw;      // [n][KC]
+  float4* mu_sig;            // {mu, sigma}
+  float4* scale_skip;        // {s, power threshold of alpha_min}
+  float4* qn;                // normalised quaternion (w,x,y,z)
+  float4* aux;               // {power threshold of alpha_max, c_g, |q|, argmax id}
+  float* p;                  // softmax(o) [n][KC]
+};
+
+// Per-view projection (structure of arrays).
+struct DevProj {
+  float4* r0;                // {mx, my, power threshold skip, power threshold clamp}
+  float4* r1;                // {A, B, C, sigma}
+  float4* r2;                // {r, g, b, z}
+  int4* rect;                // {x0, x1, y0, y1}
+  uint32_t* zbits;
+  uint32_t* touched;         // tiles covered (0 = culled)
+  float* radius;
+};
+
+// ------------------------------------------------------------ kernels (host wrappers)
+// Each wrapper launches on `st` and returns the number of launches issued.
+int launch_scene_prep(const DevScene& s, const Consts& c, int target, cudaStream_t st);
+int launch_project(const DevScene& s, const Consts& c, const DevCam& cam, const DevProj& pr,
+                   cudaStream_t st);
+
+struct SortBuffers {
+  uint64_t* keys[2];
+  uint32_t* vals[2];
+  uint32_t* offsets;     // [n+1] exclusive scan of touched
+  uint32_t* scan_tmp;    // scan scratch
+  uint32_t* hist;        // radix histograms
+  uint2* ranges;         // [ntiles]
+  size_t cap;            // capacity of keys / vals
+  size_t scan_tmp_cap, hist_cap;
+};
+// Exclusive scan of touched into offsets; total written to *d_total (device).
+int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st);
+int launch_duplicate(const DevProj& pr, int64_t n, int GX, const uint32_t* offsets, uint64_t* keys,
+                     uint32_t* vals, cudaStream_t st);
+// Stable LSD radix sort of (keys, vals) on the low `bits` key bits; the
+// result is in buffer index *which (0 or 1).
+int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaStream_t st);
+int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st);
+
+struct CompositeArgs {
+  DevCam cam;
+  const float4* r0;
+  const float4* r1;
+  const float4* r2;
+  const float* p;          // [n][KC]
+  const uint32_t* vals;    // sorted Gaussian ids
+  const uint2* ranges;     // per tile
+  float* blocks;           // [n][nB] structured blocks (IG pass), or NULL
+  float* rgb;              // optional images
+  float* depth;
+  float* alpha;
+  float* obj;
+  int nB;
+};
+int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st);
+
+struct Factors {
+  float* L[3];        // packed lower-triangle Cholesky factor of the scaled H, per output
+  float* dinv[3];     // D^-1/2 Jacobi scaling per parameter
+  int l[3];
+};
+// Training Hessians: H^f_g = lambda I + c_g sum_t M_t^T B_t M_t, scaled and factorised.
+int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams, const float* blocks,
+                         int n_train, const Factors& f, int* d_err, cudaStream_t st);
+// Per-Gaussian log-det gains of one view: delta [n][3]; per-block partial sums
+// into partial [nblocks][3] (double).
+int launch_view_gains(const DevScene& s, const Consts& c, const DevCam& cam, const float* blocks,
+                      const Factors& f, float* delta, double* partial, int nblocks_cap,
+                      int* nblocks_used, cudaStream_t st);
+int launch_reduce_gains(const double* partial, int nblocks, double* out3, cudaStream_t st);
+int launch_final_scores(const double* ig_cand, const double* ig_train, int n_cand, int n_train,
+                        const Consts& c, float* out4, int* best, float* best_score, int* err,
+                        cudaStream_t st);
+
+}  // namespace nbv

@@ -1,0 +1,233 @@
+// Scene preparation and projection (the rasterizer's first stage).
+//
+// Scene preparation, once per scene and target: opacity sigma = sigmoid(rho),
+// object probabilities p = softmax(o) (Sec. III-A.1), the confidence c_g of
+// Eq. 7 or its object-centric form of Eq. 12, per-axis scales, the
+// normalised quaternion, and the two exponent thresholds that turn the
+// alpha cut-off (1/255) and clamp (0.99) into comparisons on the splat
+// exponent:  sigma e^p < alpha_min  <=>  p < log(alpha_min / sigma).
+//
+// Projection, per (view, Gaussian): camera-space centre, EWA 2D covariance
+// with dilation, conic, 3-sigma radius, tile rectangle and depth key, and
+// the view-dependent colour from the real spherical harmonics.
+//
+// The key path (everything that decides culling, the tile rectangle, the
+// depth key and the per-pixel alpha decisions) uses only correctly rounded
+// single-precision operations in one fixed order (explicit __f*_rn
+// intrinsics, so no contraction into FMA), which makes it reproducible bit
+// for bit by any IEEE implementation following the same order.
+#include <math.h>
+
+#include "nbv_internal.cuh"
+
+namespace nbv {
+namespace {
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fd(float a, float b) { return __fdiv_rn(a, b); }
+
+__global__ void k_scene_prep(DevScene s, Consts c, int target) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= s.n) return;
+  const int KC = c.KC;
+  // per-axis scale, rounded once from a double exp
+  float sc[3];
+  for (int k = 0; k < 3; ++k) sc[k] = (float)exp((double)s.logs_raw[3 * g + k]);
+  // normalised quaternion in correctly rounded single precision
+  const float q0 = s.q_raw[4 * g], q1 = s.q_raw[4 * g + 1], q2 = s.q_raw[4 * g + 2],
+              q3 = s.q_raw[4 * g + 3];
+  const float n2 = fa(fa(fa(fm(q0, q0), fm(q1, q1)), fm(q2, q2)), fm(q3, q3));
+  const float nr = __fsqrt_rn(n2);
+  s.qn[g] = make_float4(fd(q0, nr), fd(q1, nr), fd(q2, nr), fd(q3, nr));
+  // opacity and the two exponent thresholds
+  const double sig = 1.0 / (1.0 + exp(-(double)s.rho_raw[g]));
+  const float sig32 = (float)sig;
+  const float pw_skip = (float)log((double)c.alpha_min / (double)sig32);
+  const float pw_clamp = (float)log((double)c.alpha_max / (double)sig32);
+  const float* m = s.mu_raw + 3 * g;
+  s.mu_sig[g] = make_float4(m[0], m[1], m[2], sig32);
+  s.scale_skip[g] = make_float4(sc[0], sc[1], sc[2], pw_skip);
+  // p = softmax(o); argmax on the logits, lowest id on ties
+  const float* o = s.obj_raw + (size_t)g * KC;
+  int am = 0;
+  double mx = (double)o[0];
+  for (int k = 1; k < KC; ++k) {
+    if (o[k] > o[am]) am = k;
+    mx = fmax(mx, (double)o[k]);
+  }
+  double z = 0.0;
+  for (int k = 0; k < KC; ++k) z += exp((double)o[k] - mx);
+  double pmax = 0.0, ptgt = 0.0;
+  float* p = s.p + (size_t)g * KC;
+  for (int k = 0; k < KC; ++k) {
+    const double pk = exp((double)o[k] - mx) / z;
+    p[k] = (float)pk;
+    pmax = fmax(pmax, pk);
+    if (k == target) ptgt = pk;
+  }
+  // Eq. 7, or Eq. 12 when a target object is given
+  double cg;
+  if (target < 0)
+    cg = pow(pmax, -(double)c.alpha_obj) * pow(sig, -(double)c.alpha_opa);
+  else
+    cg = (am == target) ? pow(ptgt, -(double)c.alpha_obj) * pow(sig, -(double)c.alpha_opa) : 0.0;
+  s.aux[g] = make_float4(pw_clamp, (float)cg, nr, __int_as_float(am));
+}
+
+// Real spherical harmonics (Condon-Shortley phase) of a unit direction,
+// index l*l + l + m, written as polynomials in (x, y, z).
+__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float* Y) {
+  constexpr double kPi = 3.14159265358979323846;
+  const float c0 = (float)(0.5 / 1.7724538509055160273);            // 1/(2 sqrt(pi))
+  Y[0] = c0;
+  if (deg < 1) return;
+  const float c1 = (float)0.48860251190291992159;                     // sqrt(3/(4 pi))
+  Y[1] = -c1 * y; Y[2] = c1 * z; Y[3] = -c1 * x;
+  if (deg < 2) return;
+  const float c2a = (float)(0.5 * 3.8729833462074168852 / 1.7724538509055160273);   // sqrt(15/pi)/2
+  const float c2b = (float)(0.25 * 2.2360679774997896964 / 1.7724538509055160273);  // sqrt(5/pi)/4
+  const float c2c = (float)(0.25 * 3.8729833462074168852 / 1.7724538509055160273);  // sqrt(15/pi)/4
+  Y[4] = c2a * x * y;
+  Y[5] = -c2a * y * z;
+  Y[6] = c2b * (2.0f * z * z - x * x - y * y);
+  Y[7] = -c2a * x * z;
+  Y[8] = c2c * (x * x - y * y);
+  if (deg < 3) return;
+  const float c3a = (float)(0.25 * 2.3601743597065740);   // sqrt(35/(2 pi))/4
+  const float c3b = (float)(0.5 * 5.7812228852811080);    // sqrt(105/pi)/2
+  const float c3c = (float)(0.25 * 1.8281831978578629);   // sqrt(21/(2 pi))/4
+  const float c3d = (float)(0.25 * 1.4927053303604616);   // sqrt(7/pi)/4
+  const float c3e = (float)(0.25 * 5.7812228852811080);   // sqrt(105/pi)/4
+  Y[9] = -c3a * y * (3.0f * x * x - y * y);
+  Y[10] = c3b * x * y * z;
+  Y[11] = -c3c * y * (4.0f * z * z - x * x - y * y);
+  Y[12] = c3d * z * (2.0f * z * z - 3.0f * x * x - 3.0f * y * y);
+  Y[13] = -c3c * x * (4.0f * z * z - x * x - y * y);
+  Y[14] = c3e * z * (x * x - y * y);
+  Y[15] = -c3a * x * (x * x - 3.0f * y * y);
+  (void)kPi;
+}
+
+__global__ void k_project(DevScene s, Consts c, DevCam cam, DevProj pr) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= s.n) return;
+  const float4 ms = s.mu_sig[g];
+  const float4 ss = s.scale_skip[g];
+  const float4 qq = s.qn[g];
+  const float4 ax = s.aux[g];
+  const float* R = cam.R;
+  pr.touched[g] = 0u;
+  pr.rect[g] = make_int4(-1, -1, -1, -1);
+  pr.radius[g] = 0.0f;
+  pr.zbits[g] = 0u;
+  // ---- key path: correctly rounded single precision, fixed order
+  const float tx = fa(fa(fa(fm(R[0], ms.x), fm(R[1], ms.y)), fm(R[2], ms.z)), cam.t[0]);
+  const float ty = fa(fa(fa(fm(R[3], ms.x), fm(R[4], ms.y)), fm(R[5], ms.z)), cam.t[1]);
+  const float tz = fa(fa(fa(fm(R[6], ms.x), fm(R[7], ms.y)), fm(R[8], ms.z)), cam.t[2]);
+  if (!(tz > c.near_z)) return;
+  const float xr = fd(tx, tz), yr = fd(ty, tz);
+  const float mx = fa(fm(cam.fx, xr), cam.cx);
+  const float my = fa(fm(cam.fy, yr), cam.cy);
+  const float limx = fm(c.guard, fd(fm(0.5f, (float)cam.W), cam.fx));
+  const float limy = fm(c.guard, fd(fm(0.5f, (float)cam.H), cam.fy));
+  const float xz = fminf(limx, fmaxf(-limx, xr));
+  const float yz = fminf(limy, fmaxf(-limy, yr));
+  const float txp = fm(xz, tz), typ = fm(yz, tz);
+  const float tz2 = fm(tz, tz);
+  const float j00 = fd(cam.fx, tz), j02 = -fd(fm(cam.fx, txp), tz2);
+  const float j11 = fd(cam.fy, tz), j12 = -fd(fm(cam.fy, typ), tz2);
+  float T0[3], T1[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T0[i] = fa(fm(j00, R[i]), fm(j02, R[6 + i]));
+    T1[i] = fa(fm(j11, R[3 + i]), fm(j12, R[6 + i]));
+  }
+  const float w = qq.x, x = qq.y, y = qq.z, z = qq.w;
+  float Rq[9];
+  Rq[0] = fs(1.0f, fm(2.0f, fa(fm(y, y), fm(z, z))));
+  Rq[1] = fm(2.0f, fs(fm(x, y), fm(w, z)));
+  Rq[2] = fm(2.0f, fa(fm(x, z), fm(w, y)));
+  Rq[3] = fm(2.0f, fa(fm(x, y), fm(w, z)));
+  Rq[4] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(z, z))));
+  Rq[5] = fm(2.0f, fs(fm(y, z), fm(w, x)));
+  Rq[6] = fm(2.0f, fs(fm(x, z), fm(w, y)));
+  Rq[7] = fm(2.0f, fa(fm(y, z), fm(w, x)));
+  Rq[8] = fs(1.0f, fm(2.0f, fa(fm(x, x), fm(y, y))));
+  const float sc[3] = {ss.x, ss.y, ss.z};
+  float V[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) V[3 * i + j] = fm(Rq[3 * i + j], sc[j]);
+  float Sg[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      Sg[3 * i + j] = fa(fa(fm(V[3 * i], V[3 * j]), fm(V[3 * i + 1], V[3 * j + 1])),
+                         fm(V[3 * i + 2], V[3 * j + 2]));
+  float U0[3], U1[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    U0[j] = fa(fa(fm(T0[0], Sg[j]), fm(T0[1], Sg[3 + j])), fm(T0[2], Sg[6 + j]));
+    U1[j] = fa(fa(fm(T1[0], Sg[j]), fm(T1[1], Sg[3 + j])), fm(T1[2], Sg[6 + j]));
+  }
+  const float a = fa(fa(fa(fm(U0[0], T0[0]), fm(U0[1], T0[1])), fm(U0[2], T0[2])), c.dilation);
+  const float b = fa(fa(fm(U0[0], T1[0]), fm(U0[1], T1[1])), fm(U0[2], T1[2]));
+  const float cc = fa(fa(fa(fm(U1[0], T1[0]), fm(U1[1], T1[1])), fm(U1[2], T1[2])), c.dilation);
+  const float det = fs(fm(a, cc), fm(b, b));
+  if (!(det > 0.0f)) return;
+  const float A = fd(cc, det), B = fd(-b, det), C = fd(a, det);
+  const float mid = fm(0.5f, fa(a, cc));
+  const float lam = fa(mid, __fsqrt_rn(fmaxf(0.1f, fs(fm(mid, mid), det))));
+  const float r = ceilf(fm(3.0f, __fsqrt_rn(lam)));
+  const float twf = (float)kTile;
+  const float fx0 = floorf(fd(fs(mx, r), twf)), fx1 = fa(floorf(fd(fa(mx, r), twf)), 1.0f);
+  const float fy0 = floorf(fd(fs(my, r), twf)), fy1 = fa(floorf(fd(fa(my, r), twf)), 1.0f);
+  const int x0 = (int)fminf(fmaxf(fx0, 0.0f), (float)cam.GX);
+  const int x1 = (int)fminf(fmaxf(fx1, 0.0f), (float)cam.GX);
+  const int y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)cam.GY);
+  const int y1 = (int)fminf(fmaxf(fy1, 0.0f), (float)cam.GY);
+  if (x0 >= x1 || y0 >= y1) return;
+  // ---- view-dependent colour (values; ordinary single precision)
+  float dv[3] = {ms.x - cam.campos[0], ms.y - cam.campos[1], ms.z - cam.campos[2]};
+  const float il = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+  float Y[16];
+  sh_eval(c.deg, dv[0] * il, dv[1] * il, dv[2] * il, Y);
+  const float* shg = s.sh + (size_t)g * c.nb * 3;
+  float rgb[3];
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float acc = 0.5f;
+    for (int k = 0; k < c.nb; ++k) acc += Y[k] * shg[3 * k + ch];
+    rgb[ch] = fmaxf(acc, 0.0f);
+  }
+  pr.r0[g] = make_float4(mx, my, ss.w, ax.x);
+  pr.r1[g] = make_float4(A, B, C, ms.w);
+  pr.r2[g] = make_float4(rgb[0], rgb[1], rgb[2], tz);
+  pr.rect[g] = make_int4(x0, x1, y0, y1);
+  pr.zbits[g] = __float_as_uint(tz);
+  pr.radius[g] = r;
+  pr.touched[g] = (uint32_t)((x1 - x0) * (y1 - y0));
+}
+
+}  // namespace
+
+int launch_scene_prep(const DevScene& s, const Consts& c, int target, cudaStream_t st) {
+  if (s.n <= 0) return 0;
+  const int bs = 128;
+  k_scene_prep<<<(unsigned)((s.n + bs - 1) / bs), bs, 0, st>>>(s, c, target);
+  return 1;
+}
+
+int launch_project(const DevScene& s, const Consts& c, const DevCam& cam, const DevProj& pr,
+                   cudaStream_t st) {
+  if (s.n <= 0) return 0;
+  const int bs = 256;
+  k_project<<<(unsigned)((s.n + bs - 1) / bs), bs, 0, st>>>(s, c, cam, pr);
+  return 1;
+}
+
+}  // namespace nbv

@@ -1,0 +1,234 @@
+// Tile binning and depth sort (the rasterizer's second stage).
+//
+// Every projected Gaussian is duplicated once per screen tile its 3-sigma
+// rectangle covers, keyed (tile << 32 | float bits of camera z). A stable
+// LSD radix sort over the used key bits then orders each tile's entries
+// front to back, ties going to the lower Gaussian index (duplication emits
+// in index order and every pass is stable). Per-tile [start, end) ranges
+// are read off the sorted keys.
+#include "nbv_internal.cuh"
+
+namespace nbv {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Block-wide exclusive scan of kScanTile elements; writes the block total.
+__global__ void k_scan_tile(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
+                            uint32_t* __restrict__ sums) {
+  __shared__ uint32_t warp_tot[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)tid * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t t = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    t += v[k];
+  }
+  // inclusive warp scan of per-thread totals
+  uint32_t x = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_tot[lane] = w;  // inclusive
+  }
+  __syncthreads();
+  uint32_t run = x - t + (wid > 0 ? warp_tot[wid - 1] : 0u);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (tid == kScanThreads - 1 && sums) sums[blockIdx.x] = run;
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, int64_t n, const uint32_t* __restrict__ sums) {
+  const int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+  const uint32_t add = sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int64_t j = i + (int64_t)k * kScanThreads;
+    if (j < n) out[j] += add;
+  }
+}
+
+__global__ void k_set_total(const uint32_t* in, uint32_t* out, int64_t n) {
+  // out[n] = out[n-1] + in[n-1]
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[n] = n > 0 ? out[n - 1] + in[n - 1] : 0u;
+}
+
+int scan_rec(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st) {
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  int launches = 0;
+  if (nb <= 1) {
+    k_scan_tile<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+    return 1;
+  }
+  k_scan_tile<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, tmp);
+  ++launches;
+  launches += scan_rec(tmp, tmp, nb, tmp + nb, st);
+  k_scan_add<<<(unsigned)nb, kScanThreads, 0, st>>>(out, n, tmp);
+  return launches + 1;
+}
+
+__global__ void k_duplicate(const int4* __restrict__ rect, const uint32_t* __restrict__ zbits,
+                            int64_t n, int GX, const uint32_t* __restrict__ offsets,
+                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const int4 r = rect[g];
+  if (r.x < 0) return;
+  uint32_t o = offsets[g];
+  const uint64_t zb = zbits[g];
+  for (int ty = r.z; ty < r.w; ++ty)
+    for (int tx = r.x; tx < r.y; ++tx) {
+      keys[o] = ((uint64_t)(ty * GX + tx) << 32) | zb;
+      vals[o] = (uint32_t)g;
+      ++o;
+    }
+}
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixRounds = 8;
+constexpr int kRadixTile = kRadixThreads * kRadixRounds;
+
+__global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                             uint32_t* __restrict__ ghist, int nblocks) {
+  __shared__ uint32_t h[256];
+  const int tid = threadIdx.x;
+  h[tid] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+#pragma unroll
+  for (int r = 0; r < kRadixRounds; ++r) {
+    const int64_t i = base + r * kRadixThreads + tid;
+    if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  ghist[(int64_t)tid * nblocks + blockIdx.x] = h[tid];
+}
+
+__global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
+                                int shift, const uint32_t* __restrict__ gscan, int nblocks) {
+  __shared__ uint32_t cnt[kRadixThreads / 32][256];
+  __shared__ uint32_t run[256];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  run[tid] = gscan[(int64_t)tid * nblocks + blockIdx.x];
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  for (int r = 0; r < kRadixRounds; ++r) {
+#pragma unroll
+    for (int w = 0; w < kRadixThreads / 32; ++w) cnt[w][tid] = 0;
+    __syncthreads();
+    const int64_t i = base + r * kRadixThreads + tid;
+    const bool valid = i < n;
+    uint64_t key = 0;
+    uint32_t val = 0;
+    int digit = 256;
+    if (valid) {
+      key = kin[i];
+      val = vin[i];
+      digit = (int)((key >> shift) & 255u);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    const int lrank = __popc(peers & lt);
+    if (valid && lrank == 0) cnt[wid][digit] = (uint32_t)__popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t off = run[digit] + (uint32_t)lrank;
+      for (int w = 0; w < wid; ++w) off += cnt[w][digit];
+      kout[off] = key;
+      vout[off] = val;
+    }
+    __syncthreads();
+    uint32_t add = 0;
+#pragma unroll
+    for (int w = 0; w < kRadixThreads / 32; ++w) add += cnt[w][tid];
+    run[tid] += add;
+    __syncthreads();
+  }
+}
+
+__global__ void k_ranges(const uint64_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t t = (uint32_t)(keys[i] >> 32);
+  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
+  if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+}  // namespace
+
+int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st) {
+  int l = 0;
+  if (n > 0) l += scan_rec(in, out, n, tmp, st);
+  k_set_total<<<1, 1, 0, st>>>(in, out, n);
+  return l + 1;
+}
+
+int launch_duplicate(const DevProj& pr, int64_t n, int GX, const uint32_t* offsets, uint64_t* keys,
+                     uint32_t* vals, cudaStream_t st) {
+  if (n <= 0) return 0;
+  k_duplicate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pr.rect, pr.zbits, n, GX, offsets, keys, vals);
+  return 1;
+}
+
+int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaStream_t st) {
+  *which = 0;
+  if (count <= 1) return 0;
+  const int nblocks = (int)((count + kRadixTile - 1) / kRadixTile);
+  int l = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    const int src = *which, dst = 1 - src;
+    k_radix_hist<<<nblocks, kRadixThreads, 0, st>>>(b.keys[src], count, shift, b.hist, nblocks);
+    const int64_t hn = 256LL * nblocks;
+    l += 1 + scan_rec(b.hist, b.hist + hn, hn, b.hist + 2 * hn, st);
+    k_radix_scatter<<<nblocks, kRadixThreads, 0, st>>>(b.keys[src], b.vals[src], b.keys[dst],
+                                                       b.vals[dst], count, shift, b.hist + hn,
+                                                       nblocks);
+    ++l;
+    *which = dst;
+  }
+  return l;
+}
+
+int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st) {
+  cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
+  if (count <= 0) return 0;
+  k_ranges<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(keys, count, ranges);
+  return 1;
+}
+
+// Scratch needed by launch_scan_u32 / launch_radix_sort for n elements.
+size_t scan_scratch_elems(int64_t n) {
+  size_t tot = 0;
+  int64_t m = n;
+  while (m > kScanTile) {
+    m = (m + kScanTile - 1) / kScanTile;
+    tot += (size_t)m;
+  }
+  return tot + 64;
+}
+
+size_t radix_hist_elems(int64_t count) {
+  const int64_t nblocks = (count + kRadixTile - 1) / kRadixTile;
+  const int64_t hn = 256 * nblocks;
+  return (size_t)(2 * hn) + scan_scratch_elems(hn);
+}
+
+}  // namespace nbv

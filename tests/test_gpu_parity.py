@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (element by element on the same seeded inputs):
+  - projection key path, tile rectangles, depth bits and tile lists: bit-exact;
+  - colour, depth, opacity and object channels: <= 1e-4 max abs, on pixels
+    whose transmittance-stop decision is not within 1e-4 (relative) of the
+    threshold (those are counted and must stay rare);
+  - IG per output and view: <= 1e-4 relative; the NBV argmax identical
+    unless the top two totals are within 1e-4 (relative).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import nbv_synth as S
+from oracle import oracle as O
+from tests.helpers import axis_camera, make_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+IG_RTOL = 1e-4
+IMG_ATOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2602_08266_gb300 as P
+    P.build()
+    P.load_library()
+    assert torch.cuda.is_available()
+    return P
+
+
+def _scorer(P, wl, target=-1):
+    sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree)
+    sc.load_scene(wl.scene)
+    sc.set_train_views(wl.train)
+    sc.set_candidates(wl.cand)
+    return sc
+
+
+def _ragged(wl, W=70, H=50, f=60.0):
+    """A ragged-tile copy of the candidates (W, H not multiples of 16)."""
+    c = wl.cand
+    return S.Cameras(c.R.copy(), c.t.copy(), np.full(c.n, f, np.float32), np.full(c.n, f, np.float32),
+                     np.full(c.n, W / 2, np.float32), np.full(c.n, H / 2, np.float32),
+                     np.full(c.n, W, np.int32), np.full(c.n, H, np.int32))
+
+
+# --------------------------------------------------------------- key path
+@pytest.mark.parametrize("ragged", [False, True])
+def test_projection_keys_and_tile_lists_bit_exact(P, ragged):
+    wl = S.make_workload("tiny")
+    if ragged:
+        wl.cand = _ragged(wl)
+    sc = _scorer(P, wl)
+    o = O.OracleScene(wl.scene)
+    for v in range(wl.cand.n):
+        g = sc.debug_project(0, v)
+        r = o.project32(wl.cand, v)
+        rect = g["rect"].cpu().numpy()
+        np.testing.assert_array_equal(rect, r["rect"])
+        ok = r["rect"][:, 0] >= 0
+        np.testing.assert_array_equal(g["zbits"].cpu().numpy().view(np.uint32)[ok], r["zbits"][ok])
+        np.testing.assert_array_equal(g["radius"].cpu().numpy()[ok], r["radius"][ok])
+        np.testing.assert_array_equal(g["mean2d"].cpu().numpy()[ok], r["mean2d"][ok])
+        np.testing.assert_array_equal(g["conic"].cpu().numpy()[ok], r["conic"][ok])
+        off, ids = sc.debug_tile_lists(0, v)
+        ooff, oids = o.tile_lists(wl.cand, v)
+        np.testing.assert_array_equal(off.cpu().numpy(), ooff)
+        np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+
+
+# ---------------------------------------------------------------- renders
+def _compare_render(sc, o, cams, v, K):
+    g = {k: t.cpu().numpy().astype(np.float64) for k, t in sc.render(v).items()}
+    r = o.render(cams, v)
+    ok = r["margin"] >= 1e-4
+    frac_flag = 1.0 - ok.mean()
+    assert frac_flag < 0.01, frac_flag
+    for k in ("rgb", "depth", "alpha", "obj"):
+        d = np.abs(g[k] - r[k])
+        if d.ndim == 3:
+            d = d.max(-1)
+        assert d[ok].max() <= IMG_ATOL, (k, v, d[ok].max())
+    return frac_flag
+
+
+@pytest.mark.parametrize("ragged", [False, True])
+def test_render_parity_tiny(P, ragged):
+    wl = S.make_workload("tiny")
+    if ragged:
+        wl.cand = _ragged(wl)
+    sc = _scorer(P, wl)
+    o = O.OracleScene(wl.scene)
+    for v in range(wl.cand.n):
+        _compare_render(sc, o, wl.cand, v, wl.scene.K)
+
+
+def test_render_parity_scene_scale_one_view(P):
+    """Full scene-scale workload (120k Gaussians, SH degree 3, K=16,
+    640x480): keys and tile lists bit-exact, render within tolerance."""
+    wl = S.make_workload("scene", n_views=2)
+    sc = _scorer(P, wl)
+    o = O.OracleScene(wl.scene)
+    v = 1
+    g = sc.debug_project(0, v)
+    r = o.project32(wl.cand, v)
+    np.testing.assert_array_equal(g["rect"].cpu().numpy(), r["rect"])
+    off, ids = sc.debug_tile_lists(0, v)
+    ooff, oids = o.tile_lists(wl.cand, v)
+    np.testing.assert_array_equal(off.cpu().numpy(), ooff)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    _compare_render(sc, o, wl.cand, v, wl.scene.K)
+
+
+# ------------------------------------------------------------------- IG
+def _check_scores(gpu4, ref, train_gpu=None):
+    igc = ref["ig_cand"]
+    np.testing.assert_allclose(gpu4[:, :3], igc, rtol=IG_RTOL, atol=0)
+    if train_gpu is not None:
+        np.testing.assert_allclose(train_gpu, ref["ig_train"], rtol=IG_RTOL, atol=0)
+    tot = ref["score"]
+    np.testing.assert_allclose(gpu4[:, 3], tot, rtol=IG_RTOL)
+    order = np.argsort(-tot)
+    best_g = int(np.argmax(gpu4[:, 3]))
+    if len(tot) > 1 and (tot[order[0]] - tot[order[1]]) > IG_RTOL * abs(tot[order[0]]):
+        assert best_g == ref["best"]
+
+
+@pytest.mark.parametrize("target", [-1, 2])
+def test_ig_parity_tiny(P, target):
+    wl = S.make_workload("tiny")
+    sc = _scorer(P, wl)
+    sc.prepare(target)
+    g4 = sc.score_host().astype(np.float64)
+    best, bs = sc.argmax()
+    ref = O.OracleScene(wl.scene, target=target).score(wl.train, wl.cand)
+    _check_scores(g4, ref, sc.train_gains().astype(np.float64))
+    assert best == int(np.argmax(g4[:, 3]))
+
+
+def test_per_gaussian_gains_tiny(P):
+    wl = S.make_workload("tiny")
+    sc = _scorer(P, wl)
+    sc.prepare(-1)
+    v = 3
+    d = sc.gaussian_gains(v).cpu().numpy().astype(np.float64)
+    ref = O.OracleScene(wl.scene).score(wl.train, wl.cand, delta_view=v)["delta"]
+    assert (d >= -1e-6).all()
+    scale = np.abs(ref).max(0)
+    err = np.abs(d - ref) / scale
+    assert err.max() < 1e-3, err.max(0)
+    np.testing.assert_allclose(d.sum(0), ref.sum(0), rtol=IG_RTOL)
+
+
+def test_ig_parity_ragged_and_sh_degree_3(P):
+    """SH degree 3, K = 6, ragged 70x50 views: exercises the colour
+    direction Jacobian and partial tiles."""
+    wl = S.make_workload("tiny")
+    rng = np.random.default_rng(5)
+    sc0 = wl.scene
+    sh = np.zeros((sc0.n, 16, 3), np.float32)
+    sh[:, 0, :] = sc0.sh[:, 0, :]
+    sh[:, 1:, :] = rng.normal(0, 0.1, (sc0.n, 15, 3))
+    K = 6
+    obj = np.zeros((sc0.n, K + 1), np.float32)
+    obj[:, : sc0.K + 1] = sc0.obj_logits
+    wl.scene = S.Scene(sc0.means, sc0.log_scales, sc0.quats, sc0.opacity, sh, obj, 3, K)
+    wl.cand = _ragged(wl)
+    wl.train = S.training_cameras(70, 50, 60.0)
+    sc = _scorer(P, wl)
+    sc.prepare(-1)
+    ref = O.OracleScene(wl.scene).score(wl.train, wl.cand)
+    _check_scores(sc.score_host().astype(np.float64), ref, sc.train_gains().astype(np.float64))
+
+
+def test_ig_parity_scene_scale_reduced(P):
+    """The scene-scale structure (blobs + table, SH 3, K=16) with a
+    twentieth of the Gaussians at 320x240 (f = 262.5), 2 training views and
+    2 candidates: sized so that the oracle finishes in well under a minute."""
+    wl = S.make_workload("scene", n_views=2, scale=0.05)
+    wl.cand = _ragged(wl, 320, 240, 262.5)
+    wl.train = S.training_cameras(320, 240, 262.5).subset([0, 2])
+    sc = _scorer(P, wl)
+    sc.prepare(-1)
+    ref = O.OracleScene(wl.scene).score(wl.train, wl.cand)
+    _check_scores(sc.score_host().astype(np.float64), ref, sc.train_gains().astype(np.float64))
+
+
+# ------------------------------------------------------------- edge cases
+def test_empty_view_and_single_pixel(P):
+    wl = S.make_workload("tiny")
+    away = S.Cameras(np.eye(3, dtype=np.float32)[None], np.array([[0, 0, -5.0]], np.float32),
+                     np.array([60.0], np.float32), np.array([60.0], np.float32),
+                     np.array([32.0], np.float32), np.array([24.0], np.float32),
+                     np.array([64], np.int32), np.array([48], np.int32))
+    one = axis_camera(1, 1, 60.0, 0.6)
+    sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree)
+    sc.load_scene(wl.scene)
+    sc.set_train_views(wl.train)
+    sc.set_candidates(S.Cameras.concat([away, one]))
+    sc.prepare(-1)
+    g4 = sc.score_host()
+    assert np.all(g4[0, :3] == 0.0)                       # nothing visible: no gain
+    r = sc.render(0)
+    assert float(r["alpha"].abs().max()) == 0.0
+    assert float((r["obj"][..., 0] - 1).abs().max()) == 0.0   # all background
+    o = O.OracleScene(wl.scene)
+    ref = o.score(wl.train, S.Cameras.concat([away, one]))
+    np.testing.assert_allclose(g4[:, :3], ref["ig_cand"], rtol=IG_RTOL, atol=1e-9)
+
+
+def test_target_without_gaussians_is_empty(P):
+    wl = S.make_workload("tiny")
+    wl.scene.obj_logits[:, 3] = -5.0
+    sc = _scorer(P, wl)
+    sc.prepare(3)
+    with pytest.raises(P.NBVError) as e:
+        sc.score_host()
+    assert e.value.code == -6
+    with pytest.raises(P.NBVError):
+        sc.argmax()
+
+
+def test_invalid_inputs_are_rejected(P):
+    wl = S.make_workload("tiny")
+    sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree)
+    q = wl.scene.quats.copy(); q[5] = 0
+    with pytest.raises(P.NBVError) as e:
+        sc.load_gaussians(wl.scene.means, wl.scene.log_scales, q, wl.scene.opacity, wl.scene.sh,
+                          wl.scene.obj_logits)
+    assert e.value.code == -1
+    m = wl.scene.means.copy(); m[3, 1] = np.nan
+    with pytest.raises(P.NBVError):
+        sc.load_gaussians(m, wl.scene.log_scales, wl.scene.quats, wl.scene.opacity, wl.scene.sh,
+                          wl.scene.obj_logits)
+    sc.load_scene(wl.scene)
+    with pytest.raises(P.NBVError) as e:
+        sc.prepare(-1)                                     # no training views yet
+    assert e.value.code == -4
+    sc.set_train_views(wl.train)
+    with pytest.raises(P.NBVError) as e:
+        sc.prepare(wl.scene.K + 1)
+    assert e.value.code == -1
+
+
+def test_device_inputs_match_host_inputs(P):
+    wl = S.make_workload("tiny")
+    a = _scorer(P, wl)
+    a.prepare(-1)
+    ga = a.score_host()
+    b = P.NBVScorer(wl.scene.K, wl.scene.sh_degree)
+    sc = wl.scene
+    b.load_gaussians(*[torch.from_numpy(x).cuda() for x in
+                       (sc.means, sc.log_scales, sc.quats, sc.opacity, sc.sh, sc.obj_logits)])
+    b.set_train_views(wl.train)
+    b.set_candidates(wl.cand)
+    b.prepare(-1)
+    gb = b.score_host()
+    np.testing.assert_allclose(ga, gb, rtol=1e-6)
