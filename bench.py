@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 NBV scorer: candidate views scored per second.
+
+One step = one NBV scoring pass of the scene-scale workload (120,000
+Gaussians: 100k in 16 object blobs + a 20k table layer, K = 16 objects,
+SH degree 3, 4 training views + 64 candidate views at 640x480, f = 525):
+scene preparation, the training state (render + information blocks of the 4
+training views, factorised training Hessians, training gains), render +
+information blocks + log-det gains of all 64 candidates, normalisation,
+weighting and the argmax. Inputs are resident in HBM; L2 is flushed
+(256 MB write) between timed steps, outside the timed events.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank scores its own candidate set on its own
+GPU (no data-path collective; scaling "weak"); the max over ranks is taken.
+`--impl reference` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidate views scored/sec at stated IG tolerance; compositing FP32-pipe % of peak"
+UNIT = "views/s"
+SMS = 152
+FP32_LANES = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scene")
+    ap.add_argument("--target", type=int, default=-1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_desc(wl):
+    m = wl.meta
+    return (f"{wl.name}: {wl.scene.n} Gaussians ({m.get('n_obj', wl.scene.n)} in {m.get('blobs', 0)} "
+            f"object blobs + {m.get('n_table', 0)} table), K={wl.scene.K}, SH degree "
+            f"{wl.scene.sh_degree}, {wl.train.n} training + {wl.cand.n} candidate views at "
+            f"{int(wl.cand.width[0])}x{int(wl.cand.height[0])}, f={float(wl.cand.fx[0])}, "
+            f"target {wl.target}, plain per-view path")
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.uuid = device_uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="nbv_clocks_", suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ------------------------------------------------------- roofline numbers
+def composite_flops(stats, K):
+    """Algorithmic FP32 operations of the fused compositing kernel:
+    forward: 11 per evaluated (pixel, splat) pair (the splat exponent) and
+    13 + 2(K+1) per blended pair (alpha, transmittance, colour, depth and
+    K+1 object accumulations); information pass: 266 + 21 K per blended pair
+    (exponent, transmittance recovery, d out / d alpha for 4 + K+1 outputs,
+    the structured block contributions and their sums over pixels)."""
+    KC = K + 1
+    ev, bl = stats["pairs_evaluated"], stats["pairs_blended"]
+    return 11 * ev + (13 + 2 * KC) * bl + (266 + 21 * K) * bl
+
+
+def fp32_peak_tflops(clock_mhz):
+    return SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------- our GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import nbv_synth as S
+    import paper_2602_08266_gb300 as P
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    if rank == 0:
+        P.build()
+    if world > 1:
+        torch.distributed.barrier()
+    P.load_library()
+
+    wl = S.make_workload(args.workload, seed=0)
+    # every rank scores its own candidate set (weak scaling)
+    if world > 1:
+        wl.cand = S.sphere_cameras(np.random.default_rng(1000 + rank), wl.cand.n, 0.6,
+                                   int(wl.cand.width[0]), int(wl.cand.height[0]), float(wl.cand.fx[0]))
+    dev = torch.device("cuda", local)
+    sc_arrays = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
+                 (wl.scene.means, wl.scene.log_scales, wl.scene.quats, wl.scene.opacity,
+                  wl.scene.sh, wl.scene.obj_logits)]
+    scorer = P.NBVScorer(wl.scene.K, wl.scene.sh_degree)
+    scorer.load_gaussians(*sc_arrays)
+    scorer.set_train_views(wl.train)
+    scorer.set_candidates(wl.cand)
+    out = torch.empty((wl.cand.n, 4), device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        scorer.prepare(args.target)
+        scorer.score(out)
+        return scorer.argmax()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    scorer.set_profiling(True)
+    l0 = scorer.launch_count()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if uuid and not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = Clocks(uuid)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    best = None
+    stream = torch.cuda.current_stream()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        best = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = scorer.launch_count() - l0
+    phases = scorer.phase_times()
+    stats = scorer.work_stats()
+    scorer.set_profiling(False)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    views = wl.cand.n * world * args.steps
+    value = views / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the fused compositing + information kernel)
+    comp_ms, comp_launch = phases["composite"]
+    n_comp = max(stats["composite_launches"], 1)
+    flops_per_launch = composite_flops(stats, wl.scene.K) / n_comp
+    avg_launch_s = comp_ms / 1e3 / n_comp
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    peak = fp32_peak_tflops(2070.0)
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_composite (fused compositing + information blocks)",
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz max SM clock (derived)",
+                "flops_per_launch": flops_per_launch, "avg_launch_ms": avg_launch_s * 1e3}
+    phase_ms = {k: round(v[0] / args.steps, 3) for k, v in phases.items()}
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded tabletop-clutter scene; no dataset)",
+        "config": {"workload": workload_desc(wl), "candidates_per_rank": wl.cand.n,
+                   "training_views": wl.train.n, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replica per GPU x{world}"},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "phase_ms_per_step": phase_ms,
+        "work_per_step": {k: v // args.steps for k, v in stats.items()},
+        "clocks": ck,
+        "best_view": best[0] if best else None,
+    }
+
+    if not args.no_e2e:
+        result["e2e"] = e2e_host(args, P, wl, torch, np)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def e2e_host(args, P, wl, torch, np):
+    """Same metric through the C ABI with HOST buffers: every step copies the
+    scene from pinned host memory, sets the cameras, prepares, scores into a
+    host array and reads the argmax."""
+    sc = wl.scene
+    pinned = []
+    for a in (sc.means, sc.log_scales, sc.quats, sc.opacity, sc.sh, sc.obj_logits):
+        t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = a
+        pinned.append(t.numpy())
+    h2d = sum(a.nbytes for a in pinned) + 64 * (wl.train.n + wl.cand.n)
+    d2h = wl.cand.n * 4 * 4 + 8
+    scorer = P.NBVScorer(sc.K, sc.sh_degree)
+
+    def step():
+        scorer.load_gaussians(*pinned)
+        scorer.set_train_views(wl.train)
+        scorer.set_candidates(wl.cand)
+        scorer.prepare(args.target)
+        scorer.score_host()
+        return scorer.argmax()
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    scorer.close()
+    return {"value": round(wl.cand.n * args.steps / dt, 3), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# --------------------------------------------------------- CPU oracle legs
+def oracle_view_time(wl, strides=(32, 16)):
+    """Oracle time of one full candidate view, from two row-subsampled runs:
+    t(s) = a + b/s fitted on strides s1 > s2 and evaluated at s = 1."""
+    from oracle import oracle as O
+    o = O.OracleScene(wl.scene, target=wl.target)
+    t0 = time.perf_counter()
+    o.prepare(wl.train.subset([0]), row_stride=strides[0])
+    t_prep = time.perf_counter() - t0
+    ts = []
+    for s in strides:
+        t0 = time.perf_counter()
+        o.score_views(wl.cand.subset([0]), row_stride=s)
+        ts.append(time.perf_counter() - t0)
+    s1, s2 = strides
+    b = (ts[1] - ts[0]) / (1.0 / s2 - 1.0 / s1)
+    a = ts[0] - b / s1
+    return max(a + b, ts[1]), ts, t_prep, O.num_threads()
+
+
+def cpu_baseline(wl):
+    t_view, ts, t_prep, cores = oracle_view_time(wl)
+    return {"value": round(1.0 / t_view, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one candidate view of the same workload at pixel-row strides 32 and 16 "
+                       f"({ts[0]:.1f} s, {ts[1]:.1f} s; training state from 1 training view at "
+                       f"stride 32, {t_prep:.1f} s, not counted); full-view time extrapolated "
+                       f"linearly in the row fraction: {t_view:.1f} s")}
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import nbv_synth as S
+    from oracle import oracle as O
+    O.build()
+    wl = S.make_workload(args.workload, seed=0)
+    per_view = []
+    t_all0 = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        t_view, ts, t_prep, cores = oracle_view_time(wl)
+        if i >= args.warmup:
+            per_view.append(t_view)
+    mean_view = statistics.mean(per_view)
+    value = 1.0 / mean_view
+    cb = {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": "per step: one candidate view at pixel-row strides 32 and 16, full-view time "
+                    "extrapolated linearly in the row fraction (training state from 1 training "
+                    "view at stride 32, not counted)"}
+    result = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean_view * 1e3, 1),
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+              "data": "synthetic (seeded tabletop-clutter scene; no dataset)",
+              "config": {"workload": workload_desc(wl)}, "impl": "reference",
+              "cpu_baseline": cb,
+              "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                      "d2h_bytes_per_step": 0},
+              "wall_s": round(time.perf_counter() - t_all0, 1)}
+    print(json.dumps(result), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

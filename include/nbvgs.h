@@ -173,6 +173,32 @@ int nbv_debug_project(nbv_ctx* ctx, int view_set, int view, int32_t* rect, float
 int nbv_debug_tile_lists(nbv_ctx* ctx, int view_set, int view, int64_t* offsets, int32_t* ids,
                          int64_t cap, int64_t* count);
 
+/* Phases timed by the profiler. */
+enum {
+  NBV_PHASE_PREP = 0,      /* scene preparation: sigmoid, softmax, confidences (Eqs. 7, 12) */
+  NBV_PHASE_PROJECT = 1,   /* projection, EWA covariance, SH colour */
+  NBV_PHASE_SORT = 2,      /* scan, tile duplication, radix sort, tile ranges */
+  NBV_PHASE_COMPOSITE = 3, /* fused compositing + information blocks (Eqs. 1-2, 6-9) */
+  NBV_PHASE_FACTORS = 4,   /* training Hessians and their factorisation */
+  NBV_PHASE_GAINS = 5,     /* per-Gaussian log-det gains and their sums (Eqs. 5-6) */
+  NBV_PHASE_SCORE = 6,     /* normalisation, weighting, argmax (Eqs. 10-11) */
+  NBV_NUM_PHASES = 7
+};
+
+/* Switch per-phase timing on (1) or off (0). Switching on clears the
+ * accumulated times and work counters. While on, every phase of every call
+ * is bracketed by CUDA events recorded on the context stream. */
+int nbv_set_profiling(nbv_ctx* ctx, int on);
+
+/* Accumulated device time (ms) and kernel launches per phase since
+ * profiling was switched on; arrays of NBV_NUM_PHASES. Synchronises. */
+int nbv_phase_times(nbv_ctx* ctx, double* ms, int64_t* launches);
+
+/* Work counters of the compositing kernel since profiling was switched on:
+ * [0] (pixel, splat) pairs evaluated in the forward pass, [1] pairs blended,
+ * [2] (tile, Gaussian) block flushes, [3] compositing launches. Synchronises. */
+int nbv_work_stats(nbv_ctx* ctx, int64_t* out4);
+
 /* Message of the last error on this context (never NULL). */
 const char* nbv_last_error(const nbv_ctx* ctx);
 

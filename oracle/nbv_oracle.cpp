@@ -124,6 +124,9 @@ struct Scene {
   std::vector<float> scale32, qn32, sigma32, pw_skip32, pw_clamp32;
   // value-path (double) per-Gaussian values
   std::vector<double> sigma64, p64, conf;
+  // training state of orc_prepare: H_T blocks (l x l per Gaussian) and log det H_T
+  std::vector<double> H[3], ldH;
+  bool prepared = false;
 };
 
 // --------------------------------------------------- real spherical harmonics
@@ -500,7 +503,7 @@ struct Blocks {
 };
 
 static void accumulate_view_blocks(const Scene& s, const ViewData& v, Blocks& B,
-                                   std::vector<float>* margins) {
+                                   std::vector<float>* margins, int row_stride = 1) {
   const int KC = s.K + 1, nb = s.nb;
   const int lr = B.lr, ld = B.ld, lo = B.lo;
   const int ur = 9, ud = 7, uo = 6 + KC;
@@ -515,8 +518,8 @@ static void accumulate_view_blocks(const Scene& s, const ViewData& v, Blocks& B,
     PixelOut o;
     std::vector<double> Mr(ur * lr), Md(ud * ld), Mo(uo * lo), gu(uo), J(std::max(lr, lo));
     std::vector<double> Rrgb(3), Ro(KC);
-#pragma omp for schedule(dynamic, 4)
-    for (int py = 0; py < H; ++py) {
+#pragma omp for schedule(dynamic, 1)
+    for (int py = 0; py < H; py += row_stride) {
       for (int px = 0; px < W; ++px) {
         composite_pixel(s, v, px, py, o);
         if (margins) (*margins)[(size_t)py * W + px] = o.margin;
@@ -846,24 +849,18 @@ void orc_view_blocks(void* h, const float* cam, const int* wh, const uint8_t* ma
   std::memcpy(Ao, B.Ao.data(), B.Ao.size() * sizeof(double));
 }
 
-// The whole score (Eqs. 5-12): training views build H_T; every training view
-// and every candidate is scored; scores are normalised per output by the
-// training mean and weighted. ig_train [n_train][3], ig_cand [n_cand][3],
-// score [n_cand]. If delta != NULL it receives the per-Gaussian log-det
-// gains [n][3] of candidate `dv`. Returns the argmax candidate (lowest index
-// on ties), -1 if a normaliser is zero, -2 if a block is not positive definite.
-int orc_score(void* h, int n_train, const float* tcams, const int* twh, int n_cand,
-              const float* ccams, const int* cwh, double* ig_train, double* ig_cand, double* score,
-              double* delta, int dv) {
-  Scene* s = static_cast<Scene*>(h);
+// Training state (Eqs. 6, 9): H_T,g = lambda I + c_g sum_t A_t,g and its log
+// det, for every Gaussian and output. Returns 0, or -2 if a block is not
+// positive definite. row_stride > 1 keeps every row_stride-th pixel row only
+// (a bounded sample for timing; 1 = the definition).
+static int prepare_state(Scene* s, int n_train, const float* tcams, const int* twh, int row_stride) {
   Blocks HB;
   alloc_blocks(*s, HB, nullptr);
   const int ls[3] = {HB.lr, HB.ld, HB.lo};
-  // H_T,g = lambda I + c_g sum_t A_t,g
   for (int t = 0; t < n_train; ++t) {
     ViewData v;
     build_view(*s, read_cam(tcams + 16 * t, twh + 2 * t), v, true);
-    accumulate_view_blocks(*s, v, HB, nullptr);
+    accumulate_view_blocks(*s, v, HB, nullptr, row_stride);
   }
   std::vector<double>* Hs[3] = {&HB.Ar, &HB.Ad, &HB.Ao};
   for (int f = 0; f < 3; ++f) symmetrize(*Hs[f], s->n, ls[f]);
@@ -875,58 +872,91 @@ int orc_score(void* h, int n_train, const float* tcams, const int* twh, int n_ca
       for (int i = 0; i < l; ++i) M[i * l + i] += (double)s->hp.lambda;
     }
   }
-  std::vector<double> ldH((size_t)s->n * 3);
+  s->ldH.assign((size_t)s->n * 3, 0.0);
   int bad = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
   for (int64_t g = 0; g < s->n; ++g)
     for (int f = 0; f < 3; ++f) {
       const int l = ls[f];
       std::vector<double> M((*Hs[f]).begin() + (size_t)g * l * l, (*Hs[f]).begin() + (size_t)(g + 1) * l * l);
-      ldH[3 * g + f] = logdet_spd(M, l);
-      if (std::isnan(ldH[3 * g + f])) bad++;
+      s->ldH[3 * g + f] = logdet_spd(M, l);
+      if (std::isnan(s->ldH[3 * g + f])) bad++;
     }
-  if (bad) return -2;
-  auto score_view = [&](const Cam32& c, double* out3, double* dg) -> int {
-    ViewData v;
-    build_view(*s, c, v, true);
-    Blocks AB;
-    alloc_blocks(*s, AB, nullptr);
-    accumulate_view_blocks(*s, v, AB, nullptr);
-    std::vector<double>* As[3] = {&AB.Ar, &AB.Ad, &AB.Ao};
-    for (int f = 0; f < 3; ++f) symmetrize(*As[f], s->n, ls[f]);
-    std::vector<double> dl((size_t)s->n * 3, 0.0);
-    int nbad = 0;
+  for (int f = 0; f < 3; ++f) s->H[f].swap(*Hs[f]);
+  s->prepared = (bad == 0);
+  return bad ? -2 : 0;
+}
+
+// IG_f(T, v) = sum_g [log det(H_T,g + c_g A_v,g) - log det H_T,g] (Eqs. 5, 6, 9).
+static int score_view(Scene* s, const Cam32& c, double* out3, double* dg, int row_stride) {
+  const int ls[3] = {NG + 3 * s->nb, NG, NG + s->K + 1};
+  ViewData v;
+  build_view(*s, c, v, true);
+  Blocks AB;
+  alloc_blocks(*s, AB, nullptr);
+  accumulate_view_blocks(*s, v, AB, nullptr, row_stride);
+  std::vector<double>* As[3] = {&AB.Ar, &AB.Ad, &AB.Ao};
+  for (int f = 0; f < 3; ++f) symmetrize(*As[f], s->n, ls[f]);
+  std::vector<double> dl((size_t)s->n * 3, 0.0);
+  int nbad = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : nbad)
-    for (int64_t g = 0; g < s->n; ++g)
-      for (int f = 0; f < 3; ++f) {
-        const int l = ls[f];
-        const double* A = &(*As[f])[(size_t)g * l * l];
-        bool zero = true;
-        for (int i = 0; i < l * l && zero; ++i) zero = (A[i] == 0.0);
-        if (zero || s->conf[g] == 0.0) { dl[3 * g + f] = 0.0; continue; }
-        std::vector<double> M((*Hs[f]).begin() + (size_t)g * l * l, (*Hs[f]).begin() + (size_t)(g + 1) * l * l);
-        for (int i = 0; i < l * l; ++i) M[i] += s->conf[g] * A[i];
-        double ld = logdet_spd(M, l);
-        if (std::isnan(ld)) nbad++;
-        dl[3 * g + f] = ld - ldH[3 * g + f];
-      }
+  for (int64_t g = 0; g < s->n; ++g)
     for (int f = 0; f < 3; ++f) {
-      double acc = 0.0;
-      for (int64_t g = 0; g < s->n; ++g) acc += dl[3 * g + f];
-      out3[f] = acc;
+      const int l = ls[f];
+      const double* A = &(*As[f])[(size_t)g * l * l];
+      bool zero = true;
+      for (int i = 0; i < l * l && zero; ++i) zero = (A[i] == 0.0);
+      if (zero || s->conf[g] == 0.0) { dl[3 * g + f] = 0.0; continue; }
+      std::vector<double> M(s->H[f].begin() + (size_t)g * l * l, s->H[f].begin() + (size_t)(g + 1) * l * l);
+      for (int i = 0; i < l * l; ++i) M[i] += s->conf[g] * A[i];
+      double ld = logdet_spd(M, l);
+      if (std::isnan(ld)) nbad++;
+      dl[3 * g + f] = ld - s->ldH[3 * g + f];
     }
-    if (dg) std::memcpy(dg, dl.data(), dl.size() * sizeof(double));
-    return nbad;
-  };
+  for (int f = 0; f < 3; ++f) {
+    double acc = 0.0;
+    for (int64_t g = 0; g < s->n; ++g) acc += dl[3 * g + f];
+    out3[f] = acc;
+  }
+  if (dg) std::memcpy(dg, dl.data(), dl.size() * sizeof(double));
+  return nbad ? -2 : 0;
+}
+
+// Build and keep the training state (see prepare_state).
+int orc_prepare(void* h, int n_train, const float* tcams, const int* twh, int row_stride) {
+  return prepare_state(static_cast<Scene*>(h), n_train, tcams, twh, row_stride < 1 ? 1 : row_stride);
+}
+
+// Raw gains of n views against the kept training state: ig [n][3].
+int orc_score_views(void* h, int n, const float* cams, const int* wh, double* ig, int row_stride) {
+  Scene* s = static_cast<Scene*>(h);
+  if (!s->prepared) return -3;
+  for (int i = 0; i < n; ++i)
+    if (score_view(s, read_cam(cams + 16 * i, wh + 2 * i), &ig[3 * i], nullptr, row_stride < 1 ? 1 : row_stride))
+      return -2;
+  return 0;
+}
+
+// The whole score (Eqs. 5-12): training views build H_T; every training view
+// and every candidate is scored; scores are normalised per output by the
+// training mean and weighted. ig_train [n_train][3], ig_cand [n_cand][3],
+// score [n_cand]. If delta != NULL it receives the per-Gaussian log-det
+// gains [n][3] of candidate `dv`. Returns the argmax candidate (lowest index
+// on ties), -1 if a normaliser is zero, -2 if a block is not positive definite.
+int orc_score(void* h, int n_train, const float* tcams, const int* twh, int n_cand,
+              const float* ccams, const int* cwh, double* ig_train, double* ig_cand, double* score,
+              double* delta, int dv) {
+  Scene* s = static_cast<Scene*>(h);
+  if (prepare_state(s, n_train, tcams, twh, 1)) return -2;
   for (int t = 0; t < n_train; ++t)
-    if (score_view(read_cam(tcams + 16 * t, twh + 2 * t), &ig_train[3 * t], nullptr)) return -2;
+    if (score_view(s, read_cam(tcams + 16 * t, twh + 2 * t), &ig_train[3 * t], nullptr, 1)) return -2;
   double norm[3] = {0, 0, 0};
   for (int f = 0; f < 3; ++f) {
     for (int t = 0; t < n_train; ++t) norm[f] += ig_train[3 * t + f];
     norm[f] /= n_train;
   }
   for (int c = 0; c < n_cand; ++c)
-    if (score_view(read_cam(ccams + 16 * c, cwh + 2 * c), &ig_cand[3 * c], (delta && c == dv) ? delta : nullptr))
+    if (score_view(s, read_cam(ccams + 16 * c, cwh + 2 * c), &ig_cand[3 * c], (delta && c == dv) ? delta : nullptr, 1))
       return -2;
   if (norm[0] == 0.0 || norm[1] == 0.0 || norm[2] == 0.0) {
     for (int c = 0; c < n_cand; ++c) score[c] = std::nan("");

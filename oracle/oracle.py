@@ -58,6 +58,10 @@ def _load():
     lib.orc_score.restype = i32
     lib.orc_score.argtypes = [P, i32, P, P, i32, P, P, P, P, P, P, i32]
     lib.orc_sh_basis.argtypes = [i32, i64, P, P]
+    lib.orc_prepare.restype = i32
+    lib.orc_prepare.argtypes = [P, i32, P, P, i32]
+    lib.orc_score_views.restype = i32
+    lib.orc_score_views.argtypes = [P, i32, P, P, P, i32]
     lib.orc_freeze.restype = P
     lib.orc_freeze.argtypes = [P, P, P]
     lib.orc_frozen_destroy.argtypes = [P]
@@ -229,6 +233,22 @@ class OracleScene:
         mk = None if mask is None else np.ascontiguousarray(mask, np.uint8)
         self.lib.orc_view_blocks(self._h, _ptr(c), _ptr(wh), _ptr(mk), _ptr(Ar), _ptr(Ad), _ptr(Ao))
         return Ar, Ad, Ao
+
+    def prepare(self, train, row_stride: int = 1):
+        """Keep the training state H_T (Eqs. 6, 9) for score_views()."""
+        tc, twh = all_cam_arrays(train)
+        rc = self.lib.orc_prepare(self._h, train.n, _ptr(tc), _ptr(twh), int(row_stride))
+        if rc != 0:
+            raise RuntimeError(f"orc_prepare failed: {rc}")
+
+    def score_views(self, cams, row_stride: int = 1):
+        """Raw gains IG_f of each view against the kept training state."""
+        cc, cwh = all_cam_arrays(cams)
+        ig = np.zeros((cams.n, 3))
+        rc = self.lib.orc_score_views(self._h, cams.n, _ptr(cc), _ptr(cwh), _ptr(ig), int(row_stride))
+        if rc != 0:
+            raise RuntimeError(f"orc_score_views failed: {rc}")
+        return ig
 
     def score(self, train, cand, delta_view: int = -1):
         """IG of every training view and candidate (Eqs. 5-11 or 12), the

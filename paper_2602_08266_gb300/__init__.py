@@ -73,6 +73,9 @@ _SIGS = [
     ("nbv_debug_project", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P]),
     ("nbv_debug_tile_lists", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int64,
                                             ctypes.POINTER(ctypes.c_int64)]),
+    ("nbv_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
+    ("nbv_phase_times", ctypes.c_int, [_P, _P, _P]),
+    ("nbv_work_stats", ctypes.c_int, [_P, _P]),
     ("nbv_last_error", ctypes.c_char_p, [_P]),
     ("nbv_launch_count", ctypes.c_int64, [_P]),
 ]
@@ -284,6 +287,26 @@ class NBVScorer:
         self._check(self.lib.nbv_debug_tile_lists(self._h, int(view_set), int(view), _dptr(off),
                                                   _dptr(ids), total, ctypes.byref(cnt)))
         return off, ids[:total]
+
+    PHASES = ("prep", "project", "sort", "composite", "factors", "gains", "score")
+
+    def set_profiling(self, on: bool):
+        self._check(self.lib.nbv_set_profiling(self._h, 1 if on else 0))
+
+    def phase_times(self):
+        """{phase: (device ms, kernel launches)} since profiling was switched on."""
+        ms = np.zeros(len(self.PHASES), np.float64)
+        ln = np.zeros(len(self.PHASES), np.int64)
+        self._check(self.lib.nbv_phase_times(self._h, ctypes.c_void_p(ms.ctypes.data),
+                                             ctypes.c_void_p(ln.ctypes.data)))
+        return {p: (float(ms[i]), int(ln[i])) for i, p in enumerate(self.PHASES)}
+
+    def work_stats(self):
+        """Compositing work since profiling was switched on."""
+        out = np.zeros(4, np.int64)
+        self._check(self.lib.nbv_work_stats(self._h, ctypes.c_void_p(out.ctypes.data)))
+        return dict(pairs_evaluated=int(out[0]), pairs_blended=int(out[1]),
+                    block_flushes=int(out[2]), composite_launches=int(out[3]))
 
     def launch_count(self) -> int:
         return int(self.lib.nbv_launch_count(self._h))

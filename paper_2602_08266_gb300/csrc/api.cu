@@ -66,6 +66,16 @@ struct nbv_ctx {
   float* d_best_score = nullptr;
   bool scored = false;
   int* d_err = nullptr;
+
+  // profiling: CUDA events bracketing each phase on the context stream
+  struct PhaseRec { int phase; cudaEvent_t a, b; int launches; };
+  bool prof = false;
+  std::vector<PhaseRec> recs;
+  std::vector<cudaEvent_t> pool;
+  double acc_ms[NBV_NUM_PHASES] = {0};
+  int64_t acc_launch[NBV_NUM_PHASES] = {0};
+  unsigned long long* d_stats = nullptr;   // composite work counters
+  int64_t composite_launches = 0;
 };
 
 namespace {
@@ -153,6 +163,38 @@ int check_launch(nbv_ctx* ctx, int nl) {
   return NBV_OK;
 }
 
+cudaEvent_t take_event(nbv_ctx* ctx) {
+  if (!ctx->pool.empty()) {
+    cudaEvent_t e = ctx->pool.back();
+    ctx->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one phase with CUDA events on the context stream while profiling.
+struct Phase {
+  nbv_ctx* ctx;
+  int ph;
+  cudaEvent_t a = nullptr;
+  int64_t l0;
+  Phase(nbv_ctx* c, int p) : ctx(c), ph(p), l0(c->launches) {
+    if (ctx->prof) {
+      a = take_event(ctx);
+      cudaEventRecord(a, ctx->st);
+    }
+  }
+  ~Phase() {
+    if (ctx->prof && a) {
+      cudaEvent_t b = take_event(ctx);
+      cudaEventRecord(b, ctx->st);
+      ctx->recs.push_back({ph, a, b, (int)(ctx->launches - l0)});
+    }
+  }
+};
+
 // Project, bin and sort one view; composite it (images and/or IG blocks).
 int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, float* depth,
                 float* alpha, float* obj, bool keep_lists = false) {
@@ -160,9 +202,15 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
   const DevCam dc = to_dev(cam);
   const int ntiles = dc.GX * dc.GY;
   DevScene s = dev_scene(ctx);
-  CKR(check_launch(ctx, launch_project(s, ctx->c, dc, ctx->pr, st)));
-  CKR(check_launch(ctx, launch_scan_u32(ctx->pr.touched, ctx->sb.offsets, ctx->n, ctx->sb.scan_tmp, st)));
-  CK(cudaMemcpyAsync(ctx->h_total, ctx->sb.offsets + ctx->n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  {
+    Phase ph(ctx, NBV_PHASE_PROJECT);
+    CKR(check_launch(ctx, launch_project(s, ctx->c, dc, ctx->pr, st)));
+  }
+  {
+    Phase ph(ctx, NBV_PHASE_SORT);
+    CKR(check_launch(ctx, launch_scan_u32(ctx->pr.touched, ctx->sb.offsets, ctx->n, ctx->sb.scan_tmp, st)));
+    CK(cudaMemcpyAsync(ctx->h_total, ctx->sb.offsets + ctx->n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  }
   CK(cudaStreamSynchronize(st));
   const int64_t total = (int64_t)*ctx->h_total;
   if ((size_t)total > ctx->sb.cap) {
@@ -177,18 +225,21 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
     CKR(grow(ctx, &ctx->sb.hist, &ctx->sb.hist_cap, radix_hist_elems((int64_t)want)));
   }
   CKR(grow(ctx, &ctx->sb.ranges, &ctx->ranges_cap, (size_t)ntiles));
-  CKR(check_launch(ctx, launch_duplicate(ctx->pr, ctx->n, dc.GX, ctx->sb.offsets, ctx->sb.keys[0],
-                                         ctx->sb.vals[0], st)));
-  int tile_bits = 1;
-  while ((1 << tile_bits) < ntiles) ++tile_bits;
-  int which = 0;
-  CKR(check_launch(ctx, launch_radix_sort(ctx->sb, total, 32 + tile_bits, &which, st)));
-  if (which != 0) {
-    // keep the sorted result in buffer 0
-    std::swap(ctx->sb.keys[0], ctx->sb.keys[1]);
-    std::swap(ctx->sb.vals[0], ctx->sb.vals[1]);
+  {
+    Phase ph(ctx, NBV_PHASE_SORT);
+    CKR(check_launch(ctx, launch_duplicate(ctx->pr, ctx->n, dc.GX, ctx->sb.offsets, ctx->sb.keys[0],
+                                           ctx->sb.vals[0], st)));
+    int tile_bits = 1;
+    while ((1 << tile_bits) < ntiles) ++tile_bits;
+    int which = 0;
+    CKR(check_launch(ctx, launch_radix_sort(ctx->sb, total, 32 + tile_bits, &which, st)));
+    if (which != 0) {
+      // keep the sorted result in buffer 0
+      std::swap(ctx->sb.keys[0], ctx->sb.keys[1]);
+      std::swap(ctx->sb.vals[0], ctx->sb.vals[1]);
+    }
+    CKR(check_launch(ctx, launch_ranges(ctx->sb.keys[0], total, ctx->sb.ranges, ntiles, st)));
   }
-  CKR(check_launch(ctx, launch_ranges(ctx->sb.keys[0], total, ctx->sb.ranges, ntiles, st)));
   CompositeArgs a;
   a.cam = dc;
   a.r0 = ctx->pr.r0; a.r1 = ctx->pr.r1; a.r2 = ctx->pr.r2;
@@ -198,8 +249,12 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
   a.blocks = blocks;
   a.rgb = rgb; a.depth = depth; a.alpha = alpha; a.obj = obj;
   a.nB = ctx->nB;
-  if (blocks || rgb || depth || alpha || obj)
+  a.stats = ctx->prof ? ctx->d_stats : nullptr;
+  if (blocks || rgb || depth || alpha || obj) {
+    Phase ph(ctx, NBV_PHASE_COMPOSITE);
     CKR(check_launch(ctx, launch_composite(a, ctx->c, st)));
+    ctx->composite_launches++;
+  }
   (void)keep_lists;
   return NBV_OK;
 }
@@ -207,6 +262,7 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
 // Gains of one view from its blocks: per-Gaussian deltas (optional) and the
 // double-precision sum into out3 (device).
 int view_gains(nbv_ctx* ctx, const nbv_camera& cam, const float* blocks, float* delta, double* out3) {
+  Phase ph(ctx, NBV_PHASE_GAINS);
   int used = 0;
   CKR(check_launch(ctx, launch_view_gains(dev_scene(ctx), ctx->c, to_dev(cam), blocks, ctx->F, delta,
                                           ctx->partial, ctx->partial_cap, &used, ctx->st)));
@@ -319,6 +375,9 @@ void nbv_destroy(nbv_ctx* ctx) {
                   ctx->F.L[0], ctx->F.L[1], ctx->F.L[2], ctx->F.dinv[0], ctx->F.dinv[1], ctx->F.dinv[2]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (ctx->d_stats) cudaFree(ctx->d_stats);
+  for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : ctx->pool) cudaEventDestroy(e);
   if (ctx->h_total) cudaFreeHost(ctx->h_total);
   delete ctx;
 }
@@ -402,7 +461,10 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
   const int nt = (int)ctx->train.size();
   ctx->prepared = false;
   ctx->scored = false;
-  CKR(check_launch(ctx, launch_scene_prep(dev_scene(ctx), ctx->c, target_obj, st)));
+  {
+    Phase ph(ctx, NBV_PHASE_PREP);
+    CKR(check_launch(ctx, launch_scene_prep(dev_scene(ctx), ctx->c, target_obj, st)));
+  }
   size_t cams_cap = 0;
   CKR(alloc(ctx, &ctx->d_train_cams, (size_t)nt));
   (void)cams_cap;
@@ -415,8 +477,11 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
     CKR(render_view(ctx, ctx->train[t], ctx->train_blocks + (size_t)t * ctx->n * ctx->nBp, nullptr,
                     nullptr, nullptr, nullptr));
   CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
-  CKR(check_launch(ctx, launch_build_factors(dev_scene(ctx), ctx->c, ctx->d_train_cams, ctx->train_blocks,
-                                             nt, ctx->F, ctx->d_err, st)));
+  {
+    Phase ph(ctx, NBV_PHASE_FACTORS);
+    CKR(check_launch(ctx, launch_build_factors(dev_scene(ctx), ctx->c, ctx->d_train_cams, ctx->train_blocks,
+                                               nt, ctx->F, ctx->d_err, st)));
+  }
   CKR(grow(ctx, &ctx->ig_train, &ctx->ig_train_cap, (size_t)nt * 3));
   for (int t = 0; t < nt; ++t)
     CKR(view_gains(ctx, ctx->train[t], ctx->train_blocks + (size_t)t * ctx->n * ctx->nBp, nullptr,
@@ -451,8 +516,12 @@ int nbv_score(nbv_ctx* ctx, float* ig_out, int out_on_device) {
     CKR(render_view(ctx, ctx->cand[v], ctx->blocks, nullptr, nullptr, nullptr, nullptr));
     CKR(view_gains(ctx, ctx->cand[v], ctx->blocks, nullptr, ctx->ig_cand + 3 * v));
   }
-  CKR(check_launch(ctx, launch_final_scores(ctx->ig_cand, ctx->ig_train, nc, (int)ctx->train.size(), ctx->c,
-                                            ctx->out4, ctx->d_flags, ctx->d_best_score, ctx->d_flags + 1, st)));
+  {
+    Phase ph(ctx, NBV_PHASE_SCORE);
+    CKR(check_launch(ctx, launch_final_scores(ctx->ig_cand, ctx->ig_train, nc, (int)ctx->train.size(),
+                                              ctx->c, ctx->out4, ctx->d_flags, ctx->d_best_score,
+                                              ctx->d_flags + 1, st)));
+  }
   ctx->scored = true;
   int empty = 0;
   if (ig_out) {
@@ -551,6 +620,56 @@ int nbv_debug_tile_lists(nbv_ctx* ctx, int view_set, int view, int64_t* offsets,
   if (total > 0)
     CK(cudaMemcpyAsync(ids, ctx->sb.vals[0], sizeof(int32_t) * total, cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
+  return NBV_OK;
+}
+
+int nbv_set_profiling(nbv_ctx* ctx, int on) {
+  if (!ctx) return NBV_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->st));
+  for (auto& r : ctx->recs) { ctx->pool.push_back(r.a); ctx->pool.push_back(r.b); }
+  ctx->recs.clear();
+  for (int i = 0; i < NBV_NUM_PHASES; ++i) { ctx->acc_ms[i] = 0.0; ctx->acc_launch[i] = 0; }
+  ctx->composite_launches = 0;
+  if (!ctx->d_stats) CK(cudaMalloc(reinterpret_cast<void**>(&ctx->d_stats), 4 * sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(ctx->d_stats, 0, 4 * sizeof(unsigned long long), ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->prof = on != 0;
+  return NBV_OK;
+}
+
+static int resolve_phases(nbv_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->st));
+  for (auto& r : ctx->recs) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    ctx->acc_ms[r.phase] += ms;
+    ctx->acc_launch[r.phase] += r.launches;
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->recs.clear();
+  return NBV_OK;
+}
+
+int nbv_phase_times(nbv_ctx* ctx, double* ms, int64_t* launches) {
+  if (!ctx) return NBV_ERR_ARG;
+  CKR(resolve_phases(ctx));
+  for (int i = 0; i < NBV_NUM_PHASES; ++i) {
+    if (ms) ms[i] = ctx->acc_ms[i];
+    if (launches) launches[i] = ctx->acc_launch[i];
+  }
+  return NBV_OK;
+}
+
+int nbv_work_stats(nbv_ctx* ctx, int64_t* out4) {
+  if (!ctx || !out4) return NBV_ERR_ARG;
+  unsigned long long h[4] = {0, 0, 0, 0};
+  if (ctx->d_stats) {
+    CK(cudaMemcpyAsync(h, ctx->d_stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  out4[0] = (int64_t)h[0]; out4[1] = (int64_t)h[1]; out4[2] = (int64_t)h[2];
+  out4[3] = ctx->composite_launches;
   return NBV_OK;
 }
 

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kTilePix, 1)
   for (int k = 0; k < KCM; ++k) O[k] = 0.0f;
   uint32_t last = rg.x;     // one past the list index of the last blended splat
   bool done = !inside;
+  uint32_t n_eval = 0, n_blend = 0;
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
     if (__syncthreads_count(done) == kTilePix) break;
     const uint32_t nj = min((uint32_t)kBatch, rg.y - start);
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(kTilePix, 1)
       for (uint32_t j = 0; j < nj; ++j) {
         const float4 a0 = s0[j], a1 = s1[j];
         const float pw = splat_power(a0.x, a0.y, a1.x, a1.y, a1.z, pxc, pyc);
+        ++n_eval;
         if (pw > 0.0f || pw < a0.z) continue;
         const float alpha = (pw >= a0.w) ? c.alpha_max : a1.w * expf(pw);
         const float tt = T * (1.0f - alpha);
@@ -149,8 +151,18 @@ __global__ void __launch_bounds__(kTilePix, 1)
           if (k < KC) O[k] += w * sp[j * KC + k];
         T = tt;
         last = start + j + 1;
+        ++n_blend;
       }
     }
+  }
+  if (args.stats) {
+    __shared__ unsigned long long s_cnt[2];
+    if (tid == 0) { s_cnt[0] = 0; s_cnt[1] = 0; }
+    __syncthreads();
+    atomicAdd(&s_cnt[0], (unsigned long long)n_eval);
+    atomicAdd(&s_cnt[1], (unsigned long long)n_blend);
+    __syncthreads();
+    if (tid == 0) { atomicAdd(&args.stats[0], s_cnt[0]); atomicAdd(&args.stats[1], s_cnt[1]); }
   }
   if (inside) {
     const size_t pix = (size_t)py * cam.W + px;
@@ -285,6 +297,7 @@ __global__ void __launch_bounds__(kTilePix, 1)
     __syncthreads();
     // flush the tile's share of each touched Gaussian's block
     const int n4 = nBp / 4;
+    if (args.stats && tid < nj && touched[tid]) atomicAdd(&args.stats[2], 1ull);
     for (int i = tid; i < nj * n4; i += kTilePix) {
       const int j = i / n4, q = i - j * n4;
       if (!touched[j]) continue;

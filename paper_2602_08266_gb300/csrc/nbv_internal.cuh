@@ -116,6 +116,7 @@ struct CompositeArgs {
   float* depth;
   float* alpha;
   float* obj;
+  unsigned long long* stats;   // optional work counters (evaluated, blended, flushes)
   int nB;
 };
 int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st);
