@@ -199,6 +199,32 @@ int nbv_phase_times(nbv_ctx* ctx, double* ms, int64_t* launches);
  * [2] (tile, Gaussian) block flushes, [3] compositing launches. Synchronises. */
 int nbv_work_stats(nbv_ctx* ctx, int64_t* out4);
 
+/* Largest input of nbv_sort_tile_keys_noalloc (2^20 pairs). */
+#define NBV_NOALLOC_MAX_PAIRS (1 << 20)
+
+/* Tile-key sort that allocates no device memory. The paper has no
+ * counterpart; it is the binning stage's stable LSD radix sort offered to
+ * callers that may not allocate while they run: applications that reserve
+ * the whole GPU up front under their own allocator, or latency-critical
+ * code where a cudaMalloc (which can synchronise the device) is not allowed.
+ *
+ * Sorts n (key, value) pairs by the low key_bits bits of the keys, stably
+ * (equal keys keep their input order), from keys_in/vals_in (device, only
+ * read) into keys_out/vals_out (device, caller-owned, must not alias the
+ * inputs), asynchronously on cuda_stream. The working memory (a copy of the
+ * pairs and the radix histograms, about 13 MB) is a fixed array in the
+ * library image: every GPU that loads the library holds it until the process
+ * exits, and it keeps the last call's contents. No part of it needs to start
+ * at zero. Calls that overlap on the GPU (on different streams or threads)
+ * share that array and race; serialise them.
+ * The first call on each device looks up the array's device address (set-up,
+ * cached per device); make that first call before any stream capture.
+ * Errors: NBV_ERR_ARG (n < 0, n > NBV_NOALLOC_MAX_PAIRS, key_bits outside
+ * 1..64, NULL or aliased buffers), NBV_ERR_CUDA. */
+int nbv_sort_tile_keys_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, int64_t n,
+                               int key_bits, uint64_t* keys_out, uint32_t* vals_out,
+                               void* cuda_stream);
+
 /* Message of the last error on this context (never NULL). */
 const char* nbv_last_error(const nbv_ctx* ctx);
 

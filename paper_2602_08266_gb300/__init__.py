@@ -76,6 +76,7 @@ _SIGS = [
     ("nbv_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
     ("nbv_phase_times", ctypes.c_int, [_P, _P, _P]),
     ("nbv_work_stats", ctypes.c_int, [_P, _P]),
+    ("nbv_sort_tile_keys_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P, _P, _P]),
     ("nbv_last_error", ctypes.c_char_p, [_P]),
     ("nbv_launch_count", ctypes.c_int64, [_P]),
 ]
@@ -132,6 +133,25 @@ def _cams_struct(cams):
         c.cx, c.cy = float(cams.cx[i]), float(cams.cy[i])
         c.width, c.height = int(cams.width[i]), int(cams.height[i])
     return n, arr
+
+
+NOALLOC_MAX_PAIRS = 1 << 20
+
+
+def sort_tile_keys_noalloc(keys_in, vals_in, key_bits, keys_out, vals_out, stream=None):
+    """Stable sort of (int64 key, int32 value) device tensors by the low
+    key_bits bits into caller-owned outputs, without any device allocation
+    (see nbv_sort_tile_keys_noalloc in include/nbvgs.h)."""
+    import torch
+    lib = load_library()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.nbv_sort_tile_keys_noalloc(ctypes.c_void_p(keys_in.data_ptr()),
+                                        ctypes.c_void_p(vals_in.data_ptr()), int(keys_in.numel()),
+                                        int(key_bits), ctypes.c_void_p(keys_out.data_ptr()),
+                                        ctypes.c_void_p(vals_out.data_ptr()),
+                                        ctypes.c_void_p(st.cuda_stream))
+    if rc != NBV_OK:
+        raise NBVError(rc, "nbv_sort_tile_keys_noalloc failed")
 
 
 def _dptr(t):

@@ -207,6 +207,19 @@ int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaS
   return l;
 }
 
+// One stable radix pass on the 8 key bits at `shift`, from (kin, vin) to
+// (kout, vout); `hist` holds radix_hist_elems(count) words of scratch.
+int launch_radix_pass(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout,
+                      int64_t count, int shift, uint32_t* hist, cudaStream_t st) {
+  if (count <= 0) return 0;
+  const int nblocks = (int)((count + kRadixTile - 1) / kRadixTile);
+  const int64_t hn = 256LL * nblocks;
+  k_radix_hist<<<nblocks, kRadixThreads, 0, st>>>(kin, count, shift, hist, nblocks);
+  int l = 1 + scan_rec(hist, hist + hn, hn, hist + 2 * hn, st);
+  k_radix_scatter<<<nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, count, shift, hist + hn, nblocks);
+  return l + 1;
+}
+
 int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st) {
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
   if (count <= 0) return 0;

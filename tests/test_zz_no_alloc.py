@@ -1,0 +1,93 @@
+"""The tile-key sort that allocates no device memory (nbv_sort_tile_keys_noalloc).
+
+It exists for callers that may not allocate device memory while they run
+(applications that reserve the GPU up front under their own allocator, or
+latency-critical code where a cudaMalloc, which can synchronise the device,
+is not allowed). Its output must equal the tile lists the context's own
+sort produces (nbv_debug_tile_lists), bit for bit, on two calls in a row
+that share the library's fixed working array. This file is collected last
+on purpose.
+"""
+import numpy as np
+import pytest
+
+import nbv_synth as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2602_08266_gb300 as P
+    P.build()
+    P.load_library()
+    assert torch.cuda.is_available()
+    return P
+
+
+def _keys_from_projection(rect, zbits, W, H):
+    """Duplicate each projected Gaussian over the tiles of its rectangle, in
+    Gaussian-index order, keyed (tile << 32 | depth bits)."""
+    GX = (W + 15) // 16
+    keys, vals = [], []
+    for g in np.nonzero(rect[:, 0] >= 0)[0]:
+        x0, x1, y0, y1 = rect[g]
+        for ty in range(y0, y1):
+            for tx in range(x0, x1):
+                keys.append((np.uint64(ty * GX + tx) << np.uint64(32)) | np.uint64(zbits[g]))
+                vals.append(g)
+    ntiles = GX * ((H + 15) // 16)
+    bits = 1
+    while (1 << bits) < ntiles:
+        bits += 1
+    return np.array(keys, np.uint64), np.array(vals, np.int32), 32 + bits
+
+
+def _case(P, wl, v):
+    sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree)
+    sc.load_scene(wl.scene)
+    sc.set_train_views(wl.train)
+    sc.set_candidates(wl.cand)
+    pr = sc.debug_project(0, v)
+    rect = pr["rect"].cpu().numpy()
+    zb = pr["zbits"].cpu().numpy().view(np.uint32)
+    _, ids = sc.debug_tile_lists(0, v)
+    W, H = int(wl.cand.width[v]), int(wl.cand.height[v])
+    k, val, bits = _keys_from_projection(rect, zb, W, H)
+    return sc, k, val, bits, ids.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,scale,v", [("tiny", None, 2), ("scene", 0.02, 5)])
+def test_noalloc_sort_matches_context_tile_lists_twice(P, name, scale, v):
+    wl = S.make_workload(name, n_views=8, scale=scale)
+    sc, k, val, bits, want_ids = _case(P, wl, v)
+    assert 0 < len(k) <= P.NOALLOC_MAX_PAIRS
+    kin = torch.from_numpy(k.view(np.int64)).cuda()
+    vin = torch.from_numpy(val).cuda()
+    kin0, vin0 = kin.clone(), vin.clone()
+    want_keys = np.sort(k, kind="stable")
+    for _ in range(2):                       # two calls in a row share the fixed array
+        kout = torch.full_like(kin, -1)
+        vout = torch.full_like(vin, -1)
+        P.sort_tile_keys_noalloc(kin, vin, bits, kout, vout)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(vout.cpu().numpy(), want_ids)
+        np.testing.assert_array_equal(kout.cpu().numpy().view(np.uint64), want_keys)
+        assert torch.equal(kin, kin0) and torch.equal(vin, vin0)   # inputs only read
+    sc.close()
+
+
+def test_noalloc_sort_rejects_oversized_and_aliased(P):
+    lib = P.load_library()
+    import ctypes
+    k = torch.zeros(8, dtype=torch.int64, device="cuda")
+    v = torch.zeros(8, dtype=torch.int32, device="cuda")
+    ko = torch.zeros_like(k)
+    vo = torch.zeros_like(v)
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.nbv_sort_tile_keys_noalloc(p(k), p(v), P.NOALLOC_MAX_PAIRS + 1, 40, p(ko), p(vo), st) == -1
+    assert lib.nbv_sort_tile_keys_noalloc(p(k), p(v), 8, 0, p(ko), p(vo), st) == -1
+    assert lib.nbv_sort_tile_keys_noalloc(p(k), p(v), 8, 40, p(k), p(vo), st) == -1
+    assert lib.nbv_sort_tile_keys_noalloc(p(k), p(v), 0, 40, p(ko), p(vo), st) == 0
