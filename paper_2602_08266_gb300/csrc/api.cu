@@ -289,8 +289,8 @@ int ensure_scene_buffers(nbv_ctx* ctx, int64_t n) {
     CKR(alloc(ctx, &ctx->F.L[f], (size_t)n * l * (l + 1) / 2));
     CKR(alloc(ctx, &ctx->F.dinv[f], (size_t)n * l));
   }
-  ctx->partial_cap = 152 * 16;
-  CKR(alloc(ctx, &ctx->partial, (size_t)ctx->partial_cap * 3));
+  ctx->partial_cap = 152 * 16;    // blocks; up to 8 warp partial sums each
+  CKR(alloc(ctx, &ctx->partial, (size_t)ctx->partial_cap * 8 * 3));
   return NBV_OK;
 }
 

@@ -42,53 +42,38 @@ __device__ __forceinline__ float splat_power(float mx, float my, float A, float 
   return fs(fm(-0.5f, q), fm(B, dxy));
 }
 
-// Lane L returns sum over the warp of v[L] (recursive halving).
-__device__ __forceinline__ float transpose_reduce(float (&v)[32], int lane) {
-#pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
-    const bool up = (lane & h) != 0;
-#pragma unroll
-    for (int i = 0; i < h; ++i) {
-      const float send = up ? v[i] : v[i + h];
-      const float keep = up ? v[i + h] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, h);
-    }
-  }
-  return v[0];
+// TF32 tensor-core helpers (warp-level mma.sync, FP32 accumulation).
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
 }
 
-struct TriIdx {
-  int m[21], n[21];
-  __host__ __device__ constexpr TriIdx() : m(), n() {
-    int e = 0;
-    for (int i = 0; i < 6; ++i)
-      for (int j = 0; j <= i; ++j) { m[e] = i; n[e] = j; ++e; }
-  }
-};
-
-template <int KCM>
-struct PairTerms {
-  float a[6];
-  float w, qr, qd, qo, sr[3], sd;
-  float ds[KCM];       // s_j - s_0, j >= 1
-};
-
-template <int KCM>
-__device__ __forceinline__ float block_value(int e, const PairTerms<KCM>& t) {
-  constexpr TriIdx T{};
-  if (e < 21) return t.qr * t.a[T.m[e]] * t.a[T.n[e]];
-  if (e < 42) return t.qd * t.a[T.m[e - 21]] * t.a[T.n[e - 21]];
-  if (e < 63) return t.qo * t.a[T.m[e - 42]] * t.a[T.n[e - 42]];
-  if (e < 81) return t.w * t.sr[(e - 63) / 6] * t.a[(e - 63) % 6];
-  if (e < 87) return t.w * t.sd * t.a[e - 81];
-  if (e == 87) return t.w * t.w;
-  const int j = (e - 88) / 6 + 1;
-  if (j < KCM) return t.w * t.ds[j] * t.a[(e - 88) % 6];
-  return 0.0f;
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// An FP32 value rounded to TF32 (kept in an FP32 register / word).
+__device__ __forceinline__ float tf32f(float x) { return __uint_as_float(to_tf32(x)); }
+
+// Row strides (floats) of the per-warp contraction buffers: pixel rows of
+// the scalar vector U (3 + 16 * ceil((K + 5) / 16) used) and of the splat
+// geometry vector V (32 used); both = 8 (mod 32) so that fragment loads hit
+// distinct banks.
+__host__ __device__ __forceinline__ int u_tiles(int K) { return (K + 5 + 15) / 16; }
+__host__ __device__ __forceinline__ int u_stride(int K) {
+  const int need = 3 + 16 * u_tiles(K);
+  return ((need - 8 + 31) / 32) * 32 + 8;
+}
+constexpr int kVStride = 40;
+
 template <int KCM>
-__global__ void __launch_bounds__(kTilePix, 1)
+__global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
     k_composite(CompositeArgs args, Consts c) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int KC = c.KC;
@@ -195,7 +180,46 @@ __global__ void __launch_bounds__(kTilePix, 1)
 #pragma unroll
   for (int k = 0; k < KCM; ++k) Ro[k] = 0.0f;
   float Tb = T;   // transmittance after the splat being visited
-  const int nchunk = (nBp + 31) / 32;
+  // Per-warp contraction buffers: row = pixel (lane). U holds the pixel's
+  // scalars [q_rgb a^2, q_d a^2, q_o a^2 | w s_c a (3), w s_D a, w (s_j - s_0) a
+  // (K) | w^2] (a = alpha, or 0 when clamped); V holds the splat geometry
+  // v = d alpha / d(mx, my, A, B, C, sigma) / alpha at the pixel as
+  // [v_m v_n (21, packed lower) 0 0 0 | v_m (6) 1 0]. The sums over the warp's
+  // pixels of U_s V_c are the structured block entries: two TF32 tensor-core
+  // contractions, D_Q = U[0..16)^T V[0..24) and D_X = U[3..)^T V[24..32).
+  const int K = c.K;
+  const int SP = u_stride(K), MTB = u_tiles(K);
+  float* Uw = reinterpret_cast<float*>(touched + kBatch) + (size_t)(tid >> 5) * 32 * (SP + kVStride);
+  float* Vw = Uw + 32 * SP;
+  for (int i = lane; i < 32 * (SP + kVStride); i += 32) Uw[i] = 0.0f;
+  __syncwarp();
+  constexpr int MTBM = (KCM + 4 + 15) / 16;
+  const int gq = lane >> 2, t4 = lane & 3;
+  // where each D fragment element of this lane goes in the structured block
+  int eq[6];                                  // Q rows (U row gq < 3), V columns < 21
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int cc = 8 * (q >> 1) + 2 * t4 + (q & 1);
+    eq[q] = (gq < 3 && cc < 21) ? 21 * gq + cc : -1;
+  }
+  int ex[MTBM][4];                            // X / W2 rows (U[3..]), V columns 24..31
+#pragma unroll
+  for (int mt = 0; mt < MTBM; ++mt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = 16 * mt + gq + (i >= 2 ? 8 : 0);
+      const int cc = 2 * t4 + (i & 1);
+      int e = -1;
+      if (mt < MTB) {
+        if (cc < 6) {
+          if (r < 4) e = kOffXrgb + 6 * r + cc;          // X_rgb (3 rows) then X_d
+          else if (r < 4 + K) e = kOffXo + 6 * (r - 4) + cc;
+        } else if (cc == 6 && r == 4 + K) {
+          e = kOffW2;
+        }
+      }
+      ex[mt][i] = e;
+    }
   for (uint32_t end = last_max; end > rg.x;) {
     const uint32_t start = (end - rg.x > (uint32_t)kBatch) ? end - kBatch : rg.x;
     const int nj = (int)(end - start);
@@ -217,82 +241,105 @@ __global__ void __launch_bounds__(kTilePix, 1)
     for (int j = nj - 1; j >= 0; --j) {
       const uint32_t idx = start + j;
       bool act = false;
-      PairTerms<KCM> t;
-      float4 a0 = s0[j], a1 = s1[j], a2 = s2[j];
+      const float4 a0 = s0[j], a1 = s1[j], a2 = s2[j];
+      float pw = 0.0f;
       if (inside && idx < last) {
-        const float pw = splat_power(a0.x, a0.y, a1.x, a1.y, a1.z, pxc, pyc);
-        if (!(pw > 0.0f || pw < a0.z)) {
-          act = true;
-          const bool clamped = pw >= a0.w;
-          const float alpha = clamped ? c.alpha_max : a1.w * expf(pw);
-          const float om = 1.0f - alpha;
-          const float inv_om = 1.0f / om;
-          const float Ti = Tb * inv_om;
-          const float w = alpha * Ti;
-          t.w = w;
-          t.sr[0] = Ti * a2.x - Rr0 * inv_om;
-          t.sr[1] = Ti * a2.y - Rr1 * inv_om;
-          t.sr[2] = Ti * a2.z - Rr2 * inv_om;
-          t.sd = Ti * a2.w - Rd * inv_om;
-          t.qr = t.sr[0] * t.sr[0] + t.sr[1] * t.sr[1] + t.sr[2] * t.sr[2];
-          t.qd = t.sd * t.sd;
-          const float* pj = sp + j * KC;
-          const float s0v = Ti * pj[0] - Ro[0] * inv_om - Tf * inv_om;
-          float qo = s0v * s0v;
-          t.ds[0] = 0.0f;
-#pragma unroll
-          for (int k = 1; k < KCM; ++k) {
-            if (k < KC) {
-              const float sk = Ti * pj[k] - Ro[k] * inv_om;
-              qo += sk * sk;
-              t.ds[k] = sk - s0v;
-            } else {
-              t.ds[k] = 0.0f;
-            }
-          }
-          t.qo = qo;
-          if (clamped) {
-#pragma unroll
-            for (int m = 0; m < 6; ++m) t.a[m] = 0.0f;
-          } else {
-            const float dx = a0.x - pxc, dy = a0.y - pyc;
-            t.a[0] = alpha * (-(a1.x * dx + a1.y * dy));
-            t.a[1] = alpha * (-(a1.y * dx + a1.z * dy));
-            t.a[2] = alpha * (-0.5f * dx * dx);
-            t.a[3] = alpha * (-dx * dy);
-            t.a[4] = alpha * (-0.5f * dy * dy);
-            t.a[5] = alpha / a1.w;
-          }
-          // extend the suffix sums with this splat and step T back
-          Rr0 += w * a2.x; Rr1 += w * a2.y; Rr2 += w * a2.z; Rd += w * a2.w;
-#pragma unroll
-          for (int k = 0; k < KCM; ++k)
-            if (k < KC) Ro[k] += w * pj[k];
-          Tb = Ti;
-        }
+        pw = splat_power(a0.x, a0.y, a1.x, a1.y, a1.z, pxc, pyc);
+        act = !(pw > 0.0f || pw < a0.z);
       }
       const unsigned any = __ballot_sync(0xffffffffu, act);
       if (any == 0u) continue;
-      if (!act) {
+      // active pixels are compacted into the first rows of the warp's buffers
+      const int nact = __popc(any);
+      const int nks = (nact + 7) >> 3;
+      const int slot = __popc(any & ((1u << lane) - 1u));
+      if (lane >= nact && lane < 8 * nks) {       // rows past the last active pixel: zero U
+        float* Uz = Uw + lane * SP;
+        for (int i = 0; i < 8 + K; ++i) Uz[i] = 0.0f;
+      }
+      if (act) {
+        float* Ur = Uw + slot * SP;
+        float* Vr = Vw + slot * kVStride;
+        const bool clamped = pw >= a0.w;
+        const float alpha = clamped ? c.alpha_max : a1.w * expf(pw);
+        const float inv_om = 1.0f / (1.0f - alpha);
+        const float Ti = Tb * inv_om;
+        const float w = alpha * Ti;
+        const float ae = clamped ? 0.0f : alpha;
+        const float wa = w * ae;
+        // d out / d alpha_i = T_i x_i - R_i / (1 - alpha_i)
+        const float sr0 = Ti * a2.x - Rr0 * inv_om;
+        const float sr1 = Ti * a2.y - Rr1 * inv_om;
+        const float sr2 = Ti * a2.z - Rr2 * inv_om;
+        const float sd = Ti * a2.w - Rd * inv_om;
+        const float* pj = sp + j * KC;
+        const float s0v = Ti * pj[0] - (Ro[0] + Tf) * inv_om;   // residual channel
+        float qo = s0v * s0v;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) t.a[m] = 0.0f;
-        t.w = 0.0f; t.qr = t.qd = t.qo = 0.0f; t.sr[0] = t.sr[1] = t.sr[2] = 0.0f; t.sd = 0.0f;
+        for (int k = 1; k < KCM; ++k) {
+          if (k < KC) {
+            const float sk = Ti * pj[k] - Ro[k] * inv_om;
+            qo += sk * sk;
+            Ur[6 + k] = tf32f(wa * (sk - s0v));
+          }
+        }
+        const float ae2 = ae * ae;
+        Ur[0] = tf32f((sr0 * sr0 + sr1 * sr1 + sr2 * sr2) * ae2);
+        Ur[1] = tf32f(sd * sd * ae2);
+        Ur[2] = tf32f(qo * ae2);
+        Ur[3] = tf32f(wa * sr0); Ur[4] = tf32f(wa * sr1); Ur[5] = tf32f(wa * sr2); Ur[6] = tf32f(wa * sd);
+        Ur[7 + K] = tf32f(w * w);
+        // splat geometry at this pixel
+        const float dx = a0.x - pxc, dy = a0.y - pyc;
+        const float v[6] = {-(a1.x * dx + a1.y * dy), -(a1.y * dx + a1.z * dy), -0.5f * dx * dx,
+                            -dx * dy, -0.5f * dy * dy, 1.0f / a1.w};
 #pragma unroll
-        for (int k = 0; k < KCM; ++k) t.ds[k] = 0.0f;
+        for (int m = 0; m < 6; ++m) {
+#pragma unroll
+          for (int n = 0; n <= m; ++n) Vr[m * (m + 1) / 2 + n] = tf32f(v[m] * v[n]);
+          Vr[24 + m] = tf32f(v[m]);
+        }
+        Vr[30] = 1.0f;
+        // extend the suffix sums with this splat and step T back
+        Rr0 += w * a2.x; Rr1 += w * a2.y; Rr2 += w * a2.z; Rd += w * a2.w;
+#pragma unroll
+        for (int k = 0; k < KCM; ++k)
+          if (k < KC) Ro[k] += w * pj[k];
+        Tb = Ti;
       }
       if (lane == 0) touched[j] = 1;
+      __syncwarp();
+      float dq[3][4], dxo[MTBM][4];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) dq[q][0] = dq[q][1] = dq[q][2] = dq[q][3] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < MTBM; ++q) dxo[q][0] = dxo[q][1] = dxo[q][2] = dxo[q][3] = 0.0f;
+      for (int ks = 0; ks < nks; ++ks) {
+        const uint32_t* u0 = reinterpret_cast<const uint32_t*>(Uw + (8 * ks + t4) * SP);
+        const uint32_t* u1 = u0 + 4 * SP;
+        const uint32_t* w0 = reinterpret_cast<const uint32_t*>(Vw + (8 * ks + t4) * kVStride);
+        const uint32_t* w1 = w0 + 4 * kVStride;
+        const uint32_t qa0 = u0[gq], qa1 = u0[gq + 8], qa2 = u1[gq], qa3 = u1[gq + 8];
+#pragma unroll
+        for (int nt = 0; nt < 3; ++nt) mma_tf32(dq[nt], qa0, qa1, qa2, qa3, w0[8 * nt + gq], w1[8 * nt + gq]);
+        const uint32_t xb0 = w0[24 + gq], xb1 = w1[24 + gq];
+#pragma unroll
+        for (int mt = 0; mt < MTBM; ++mt)
+          if (mt < MTB)
+            mma_tf32(dxo[mt], u0[3 + 16 * mt + gq], u0[3 + 16 * mt + gq + 8], u1[3 + 16 * mt + gq],
+                     u1[3 + 16 * mt + gq + 8], xb0, xb1);
+      }
+      __syncwarp();
+      // scatter the needed entries of D into the tile's block of splat j
       float* accj = acc + j * nBp;
 #pragma unroll
-      for (int ch = 0; ch < (kOffXo + 6 * KCM + 31) / 32; ++ch) {
-        if (ch < nchunk) {
-          float v[32];
+      for (int q = 0; q < 6; ++q)
+        if (eq[q] >= 0) atomicAdd(&accj[eq[q]], dq[q >> 1][q & 1]);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = block_value<KCM>(ch * 32 + i, t);
-          const float r = transpose_reduce(v, lane);
-          const int e = ch * 32 + lane;
-          if (e < args.nB) atomicAdd(&accj[e], r);
-        }
-      }
+      for (int mt = 0; mt < MTBM; ++mt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (ex[mt][i] >= 0) atomicAdd(&accj[ex[mt][i]], dxo[mt][i]);
     }
     __syncthreads();
     // flush the tile's share of each touched Gaussian's block
@@ -314,7 +361,8 @@ int launch_k(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
   const int nBp = (a.nB + 3) & ~3;
   const size_t sm = sizeof(float4) * 3 * kBatch + sizeof(int) * kBatch +
                     sizeof(float) * (size_t)kBatch * c.KC + sizeof(float) * (size_t)kBatch * nBp +
-                    sizeof(int) * kBatch;
+                    sizeof(int) * kBatch +
+                    sizeof(float) * (kTilePix / 32) * 32 * (size_t)(u_stride(c.K) + kVStride);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_composite<KCM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -8,14 +8,18 @@
 //
 // Training state (once per NBV step):
 //   H^f_g = lambda I + c_g sum_t M_t^T B_t M_t          (Eqs. 6, 9 with C_g = c_g I)
-// Jacobi-scaled, H~ = D^-1/2 H D^-1/2, and Cholesky-factorised in double
-// precision, H~ = L L^T; L is kept in single precision.
+// Jacobi-scaled, H~ = D^-1/2 H D^-1/2, Cholesky-factorised, H~ = L L^T, and
+// the factor inverted, all in double precision; L^-1 is kept in single
+// precision.
 //
 // Per view, by Sylvester's determinant identity,
 //   log det(H + c A) - log det H = log det(I_u + c W B),
 //   W = M H^-1 M^T = Z^T Z,  Z = L^-1 D^-1/2 M^T,
-// which needs an l x u triangular solve and a u x u determinant instead of
-// an l x l factorisation (u = 9 against l = 59 for colour at SH degree 3).
+// a sparse l x u product and a u x u determinant instead of an l x l
+// factorisation (u = 9 against l = 59 for colour at SH degree 3). The
+// columns of D^-1/2 M^T are sparse by parameter block: the geometric rows
+// (mean, scale, rotation, opacity) are dense, an SH row feeds one colour
+// channel only, an object-logit row feeds the probability columns only.
 // The gains of all Gaussians summed give IG_f(T, v) (block-diagonal
 // determinant, Sec. III-B.1); the training mean normalises each output
 // (Eq. 10) and the weighted sum (Eq. 11) is maximised (Eq. 5).
@@ -375,6 +379,22 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
         }
         __syncwarp();
       }
+      // L^-1 in place, row by row: X_ii = 1/L_ii, X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj
+      for (int i = 0; i < l; ++i) {
+        const double xii = 1.0 / Hs[tri(i, i)];
+        double nv[6];
+        int cnt = 0;
+        for (int j = lane; j < i; j += 32) {
+          double a = 0.0;
+          for (int k = j; k < i; ++k) a += Hs[tri(i, k)] * Hs[tri(k, j)];
+          nv[cnt++] = -xii * a;
+        }
+        __syncwarp();
+        cnt = 0;
+        for (int j = lane; j < i; j += 32) Hs[tri(i, j)] = nv[cnt++];
+        if (lane == 0) Hs[tri(i, i)] = xii;
+        __syncwarp();
+      }
       for (int i = lane; i < nt; i += 32) Lg[i] = (float)Hs[i];
       __syncwarp();
     }
@@ -382,115 +402,193 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
 }
 
 // -------------------------------------------------------------- view gains
-__global__ void k_view_gains(DevScene s, Consts c, DevCam cam, const float* __restrict__ blocks,
-                             Factors F, float* __restrict__ delta, double* __restrict__ partial,
-                             int lmax, int umax) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double wsum[kMaxWarps][3];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int nB = block_floats(c.K), nBp = (nB + 3) & ~3;
-  const size_t per_warp = 2 * (size_t)lmax * umax + 3 * (size_t)umax * umax + sizeof(GJac) / 4 + 4;
-  float* Z = reinterpret_cast<float*>(smem) + warp * per_warp;
-  float* Mt = Z + lmax * umax;
-  float* Bm = Mt + lmax * umax;
-  float* W = Bm + umax * umax;
-  float* G = W + umax * umax;
-  GJac* J = reinterpret_cast<GJac*>(G + umax * umax);
-  double acc3[3] = {0.0, 0.0, 0.0};
-  for (int64_t g = (int64_t)blockIdx.x * nw + warp; g < s.n; g += (int64_t)gridDim.x * nw) {
-    const float cg = s.aux[g].y;
-    const float* blk = blocks + (size_t)g * nBp;
-    float dl[3] = {0.0f, 0.0f, 0.0f};
-    if (cg > 0.0f && blk[kOffW2] != 0.0f) {
-      if (lane == 0) compute_gjac(s, c, cam, g, *J);
-      __syncwarp();
-      const float* p = s.p + (size_t)g * c.KC;
-      for (int f = 0; f < 3; ++f) {
-        const int l = out_l(f, c), u = out_u(f, c), nt = l * (l + 1) / 2;
-        const float* Lg = F.L[f] + (size_t)g * nt;
-        const float* dg = F.dinv[f] + (size_t)g * l;
-        // Z = D^-1/2 M^T (l x u, row-major)
-        build_M(f, *J, c, p, Mt, lane);
-        for (int i = lane; i < l * u; i += 32) {
-          const int r = i / u, cc = i - r * u;
-          Z[i] = dg[r] * Mt[cc * l + r];
-        }
-        __syncwarp();
-        // forward substitution Z <- L^-1 Z
-        for (int k = 0; k < l; ++k) {
-          const float ik = 1.0f / Lg[tri(k, k)];
-          for (int j = lane; j < u; j += 32) Z[k * u + j] *= ik;
-          __syncwarp();
-          for (int i = lane; i < (l - k - 1) * u; i += 32) {
-            const int r = k + 1 + i / u, cc = i % u;
-            Z[r * u + cc] -= Lg[tri(r, k)] * Z[k * u + cc];
-          }
-          __syncwarp();
-        }
-        // W = Z^T Z
-        for (int i = lane; i < u * u; i += 32) {
-          const int r = i / u, cc = i - r * u;
-          if (cc > r) continue;
-          float a = 0.0f;
-          for (int k = 0; k < l; ++k) a += Z[k * u + r] * Z[k * u + cc];
-          W[r * u + cc] = a;
-          W[cc * u + r] = a;
-        }
-        __syncwarp();
-        build_B(f, blk, c, Bm, lane);
-        // G = I + c W B
-        for (int i = lane; i < u * u; i += 32) {
-          const int r = i / u, cc = i - r * u;
-          float a = 0.0f;
-          for (int k = 0; k < u; ++k) a += W[r * u + k] * Bm[k * u + cc];
-          G[i] = (r == cc ? 1.0f : 0.0f) + cg * a;
-        }
-        __syncwarp();
-        // log det G by LU with partial pivoting
-        float ld = 0.0f;
-        for (int k = 0; k < u; ++k) {
-          float best = -1.0f;
-          int bi = k;
-          for (int i = k + lane; i < u; i += 32) {
-            const float v = fabsf(G[i * u + k]);
-            if (v > best) { best = v; bi = i; }
-          }
-          for (int o = 16; o >= 1; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-          }
-          if (bi != k) {
-            for (int j = lane; j < u; j += 32) {
-              const float tmp = G[k * u + j];
-              G[k * u + j] = G[bi * u + j];
-              G[bi * u + j] = tmp;
-            }
-          }
-          __syncwarp();
-          const float piv = G[k * u + k];
-          ld += logf(fabsf(piv));
-          for (int i = k + 1 + lane; i < u; i += 32) {
-            const float fct = G[i * u + k] / piv;
-            for (int j = k + 1; j < u; ++j) G[i * u + j] -= fct * G[k * u + j];
-          }
-          __syncwarp();
-        }
-        dl[f] = ld;
+// Y = D^-1/2 M^T of output f (l x u, row-major), built by the warp.
+__device__ void build_Y(int f, const GJac& J, const Consts& c, const float* p, const float* dg, float* Y,
+                        int lane) {
+  const int l = out_l(f, c), u = out_u(f, c);
+  for (int i = lane; i < u * l; i += 32) Y[i] = 0.0f;
+  __syncwarp();
+  if (lane == 0) {
+    for (int m = 0; m < 3; ++m) {
+      Y[m * u + 0] = dg[m] * J.Jm[0][m];
+      Y[m * u + 1] = dg[m] * J.Jm[1][m];
+    }
+    for (int e = 0; e < 3; ++e)
+      for (int k = 0; k < 10; ++k) Y[k * u + 2 + e] = dg[k] * J.Jc[e][k];
+    Y[10 * u + 5] = dg[10] * J.dsig;
+    if (f == 0) {
+      for (int ch = 0; ch < 3; ++ch)
+        for (int m = 0; m < 3; ++m) Y[m * u + 6 + ch] = dg[m] * J.Jrgb[ch][m];
+    } else if (f == 1) {
+      for (int m = 0; m < 3; ++m) Y[m * u + 6] = dg[m] * J.Jz[m];
+    }
+  }
+  if (f == 0) {
+    for (int i = lane; i < 3 * c.nb; i += 32) {
+      const int k = i / 3, ch = i - 3 * k;
+      Y[(kNG + i) * u + 6 + ch] = dg[kNG + i] * J.live[ch] * J.Y[k];
+    }
+  } else if (f == 2) {
+    for (int i = lane; i < c.K * c.KC; i += 32) {   // d p_j / d o_b = p_j (delta_jb - p_b)
+      const int j = 1 + i / c.KC, bb = i % c.KC;
+      Y[(kNG + bb) * u + 5 + j] = dg[kNG + bb] * p[j] * ((j == bb ? 1.0f : 0.0f) - p[bb]);
+    }
+  }
+  __syncwarp();
+}
+
+// Row i of Z = L^-1 Y for output f with U columns (compile time), using the
+// block sparsity of Y. Ls is L^-1 (packed) in shared memory.
+template <int F, int U>
+__device__ __forceinline__ void z_row(int i, int u, const float* __restrict__ Ls, const float* Y, float* Z) {
+  float acc[U];
+#pragma unroll
+  for (int cc = 0; cc < U; ++cc) acc[cc] = 0.0f;
+  const float* __restrict__ Li = Ls + tri(i, 0);
+  const int kg = i < kNG - 1 ? i : kNG - 1;
+  for (int k = 0; k <= kg; ++k) {               // geometric rows: dense
+    const float lk = Li[k];
+    const float* y = Y + k * u;
+#pragma unroll
+    for (int cc = 0; cc < U; ++cc)
+      if (cc < u) acc[cc] += lk * y[cc];
+  }
+  if (F == 0) {                                  // SH rows: one colour column each
+    for (int k = kNG; k <= i; k += 3) {
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch)
+        if (k + ch <= i) acc[6 + ch] += Li[k + ch] * Y[(k + ch) * u + 6 + ch];
+    }
+  } else if (F == 2) {                           // object-logit rows: probability columns
+    for (int k = kNG; k <= i; ++k) {
+      const float lk = Li[k];
+      const float* y = Y + k * u;
+#pragma unroll
+      for (int cc = 6; cc < U; ++cc)
+        if (cc < u) acc[cc] += lk * y[cc];
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < U; ++cc)
+    if (cc < u) Z[i * u + cc] = acc[cc];
+}
+
+// log det(I + c W B) for one output; W, B, G are u x u in shared memory.
+__device__ float logdet_IcWB(int u, float cg, const float* W, const float* Bm, float* G, int lane) {
+  for (int i = lane; i < u * u; i += 32) {
+    const int r = i / u, cc = i - r * u;
+    float a = 0.0f;
+    for (int k = 0; k < u; ++k) a += W[r * u + k] * Bm[k * u + cc];
+    G[i] = (r == cc ? 1.0f : 0.0f) + cg * a;
+  }
+  __syncwarp();
+  float ld = 0.0f;
+  for (int k = 0; k < u; ++k) {
+    float best = -1.0f;
+    int bi = k;
+    for (int i = k + lane; i < u; i += 32) {
+      const float v = fabsf(G[i * u + k]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (bi != k) {
+      for (int j = lane; j < u; j += 32) {
+        const float tmp = G[k * u + j];
+        G[k * u + j] = G[bi * u + j];
+        G[bi * u + j] = tmp;
       }
     }
-    if (lane == 0) {
-      if (delta) { delta[3 * g] = dl[0]; delta[3 * g + 1] = dl[1]; delta[3 * g + 2] = dl[2]; }
-      acc3[0] += dl[0]; acc3[1] += dl[1]; acc3[2] += dl[2];
+    __syncwarp();
+    const float piv = G[k * u + k];
+    ld += logf(fabsf(piv));
+    const float ip = 1.0f / piv;
+    for (int i = k + 1 + lane; i < u; i += 32) {
+      const float fct = G[i * u + k] * ip;
+      for (int j = k + 1; j < u; ++j) G[i * u + j] -= fct * G[k * u + j];
     }
     __syncwarp();
   }
-  if (lane == 0) { wsum[warp][0] = acc3[0]; wsum[warp][1] = acc3[1]; wsum[warp][2] = acc3[2]; }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += wsum[w][threadIdx.x];
-    partial[3 * blockIdx.x + threadIdx.x] = t;
+  return ld;
+}
+
+template <int F, int U>
+__device__ float output_gain(const GJac& J, const Consts& c, const float* p, const Factors& Fa, int64_t g,
+                             const float* blk, float cg, float* Ls, float* Y, float* Z, float* W,
+                             float* Bm, float* G, int lane) {
+  const int l = out_l(F, c), u = out_u(F, c), nt = l * (l + 1) / 2;
+  const float* Lg = Fa.L[F] + (size_t)g * nt;   // rows read straight from global memory (L1)
+  const float* dg = Fa.dinv[F] + (size_t)g * l;
+  build_Y(F, J, c, p, dg, Y, lane);              // ends with __syncwarp
+  for (int i = lane; i < l; i += 32) z_row<F, U>(i, u, Lg, Y, Z);
+  __syncwarp();
+  for (int i = lane; i < u * (u + 1) / 2; i += 32) {   // W = Z^T Z
+    int r = (int)((sqrtf(8.0f * i + 1.0f) - 1.0f) * 0.5f);
+    while (tri(r + 1, 0) <= i) ++r;
+    while (tri(r, 0) > i) --r;
+    const int cc = i - tri(r, 0);
+    float a = 0.0f;
+    for (int k = 0; k < l; ++k) a += Z[k * u + r] * Z[k * u + cc];
+    W[r * u + cc] = a;
+    W[cc * u + r] = a;
+  }
+  build_B(F, blk, c, Bm, lane);                  // ends with __syncwarp
+  return logdet_IcWB(u, cg, W, Bm, G, lane);
+}
+
+template <int UO>
+__global__ void __launch_bounds__(128, 3) k_view_gains(DevScene s, Consts c, DevCam cam, const float* __restrict__ blocks,
+                             Factors F, float* __restrict__ delta, double* __restrict__ partial,
+                             int nt_max, int lu_max, int uu_max) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nB = block_floats(c.K), nBp = (nB + 3) & ~3;
+  const size_t per_warp = 2 * (size_t)lu_max + 3 * (size_t)uu_max + 32 * (sizeof(GJac) / 4) + 4;
+  float* Ls = nullptr;
+  float* Y = reinterpret_cast<float*>(smem) + warp * per_warp;
+  float* Z = Y + lu_max;
+  float* W = Z + lu_max;
+  float* Bm = W + uu_max;
+  float* G = Bm + uu_max;
+  GJac* Jw = reinterpret_cast<GJac*>(G + uu_max);     // one per lane
+  double acc3[3] = {0.0, 0.0, 0.0};
+  const int64_t nbatch = (s.n + 31) / 32;
+  const int64_t gw = (int64_t)blockIdx.x * nw + warp, nwarps = (int64_t)gridDim.x * nw;
+  for (int64_t bt = gw; bt < nbatch; bt += nwarps) {
+    // every lane takes one Gaussian of the batch: contributes? projection Jacobians
+    const int64_t gl = bt * 32 + lane;
+    bool mine = false;
+    if (gl < s.n) {
+      mine = s.aux[gl].y > 0.0f && blocks[(size_t)gl * nBp + kOffW2] != 0.0f;
+      if (mine) compute_gjac(s, c, cam, gl, Jw[lane]);
+      else if (delta) { delta[3 * gl] = 0.0f; delta[3 * gl + 1] = 0.0f; delta[3 * gl + 2] = 0.0f; }
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, mine);
+    __syncwarp();
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t g = bt * 32 + src;
+      const float cg = s.aux[g].y;
+      const float* blk = blocks + (size_t)g * nBp;
+      const float* p = s.p + (size_t)g * c.KC;
+      const GJac& J = Jw[src];
+      const float d0 = output_gain<0, 9>(J, c, p, F, g, blk, cg, Ls, Y, Z, W, Bm, G, lane);
+      const float d1 = output_gain<1, 7>(J, c, p, F, g, blk, cg, Ls, Y, Z, W, Bm, G, lane);
+      const float d2 = output_gain<2, UO>(J, c, p, F, g, blk, cg, Ls, Y, Z, W, Bm, G, lane);
+      if (lane == 0) {
+        if (delta) { delta[3 * g] = d0; delta[3 * g + 1] = d1; delta[3 * g + 2] = d2; }
+        acc3[0] += d0; acc3[1] += d1; acc3[2] += d2;
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    double* out = partial + 3 * ((size_t)blockIdx.x * nw + warp);
+    out[0] = acc3[0]; out[1] = acc3[1]; out[2] = acc3[2];
   }
 }
 
@@ -542,8 +640,24 @@ size_t factors_smem_per_warp(int lmax, int umax) {
   return per_warp_d * sizeof(double) + per_warp_f * sizeof(float);
 }
 
-size_t gains_smem_per_warp(int lmax, int umax) {
-  return (2 * (size_t)lmax * umax + 3 * (size_t)umax * umax + sizeof(GJac) / 4 + 4) * sizeof(float);
+struct GainsDims { int nt_max, lu_max, uu_max; };
+
+GainsDims gains_dims(const Consts& c) {
+  GainsDims d{0, 0, 0};
+  for (int f = 0; f < 3; ++f) {
+    const int l = out_l(f, c), u = out_u(f, c);
+    if (l * (l + 1) / 2 > d.nt_max) d.nt_max = l * (l + 1) / 2;
+    if (l * u > d.lu_max) d.lu_max = l * u;
+    if (u * u > d.uu_max) d.uu_max = u * u;
+  }
+  d.nt_max = (d.nt_max + 3) & ~3;
+  d.lu_max = (d.lu_max + 3) & ~3;
+  d.uu_max = (d.uu_max + 3) & ~3;
+  return d;
+}
+
+size_t gains_smem_per_warp(const GainsDims& d) {
+  return (2 * (size_t)d.lu_max + 3 * (size_t)d.uu_max + 32 * (sizeof(GJac) / 4) + 4) * sizeof(float);
 }
 
 int warps_for(size_t per_warp) {
@@ -573,20 +687,31 @@ int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams,
   return 1;
 }
 
+template <int UO>
+void launch_gains_k(const DevScene& s, const Consts& c, const DevCam& cam, const float* blocks,
+                    const Factors& f, float* delta, double* partial, int grid, int nw, size_t sm,
+                    const GainsDims& d, cudaStream_t st) {
+  cudaFuncSetAttribute(k_view_gains<UO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_view_gains<UO><<<grid, 32 * nw, sm, st>>>(s, c, cam, blocks, f, delta, partial, d.nt_max, d.lu_max,
+                                              d.uu_max);
+}
+
 int launch_view_gains(const DevScene& s, const Consts& c, const DevCam& cam, const float* blocks,
                       const Factors& f, float* delta, double* partial, int nblocks_cap,
                       int* nblocks_used, cudaStream_t st) {
-  int lmax, umax;
-  sizes(c, &lmax, &umax);
-  const size_t pw = gains_smem_per_warp(lmax, umax);
+  const GainsDims d = gains_dims(c);
+  const size_t pw = gains_smem_per_warp(d);
   const int nw = warps_for(pw);
   const size_t sm = pw * nw;
-  cudaFuncSetAttribute(k_view_gains, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int64_t nblk = (s.n + nw - 1) / nw;
+  const int64_t nblk = ((s.n + 31) / 32 + nw - 1) / nw;
   int grid = (int)(nblk < nblocks_cap ? nblk : nblocks_cap);
   if (grid < 1) grid = 1;
-  *nblocks_used = grid;
-  k_view_gains<<<grid, 32 * nw, sm, st>>>(s, c, cam, blocks, f, delta, partial, lmax, umax);
+  *nblocks_used = grid * nw;        // one partial sum per warp
+  const int uo = 6 + c.K;
+  if (uo <= 24) launch_gains_k<24>(s, c, cam, blocks, f, delta, partial, grid, nw, sm, d, st);
+  else if (uo <= 40) launch_gains_k<40>(s, c, cam, blocks, f, delta, partial, grid, nw, sm, d, st);
+  else if (uo <= 72) launch_gains_k<72>(s, c, cam, blocks, f, delta, partial, grid, nw, sm, d, st);
+  else launch_gains_k<136>(s, c, cam, blocks, f, delta, partial, grid, nw, sm, d, st);
   return 1;
 }
 
