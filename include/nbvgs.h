@@ -185,9 +185,11 @@ enum {
   NBV_NUM_PHASES = 7
 };
 
-/* Switch per-phase timing on (1) or off (0). Switching on clears the
+/* Switch per-phase timing on (1) or off (0); either call clears the
  * accumulated times and work counters. While on, every phase of every call
- * is bracketed by CUDA events recorded on the context stream. */
+ * is bracketed by CUDA events recorded on the context stream, and the
+ * batched path enqueues its kernels directly instead of replaying its CUDA
+ * graph (same kernels, same order). Synchronises. */
 int nbv_set_profiling(nbv_ctx* ctx, int on);
 
 /* Accumulated device time (ms) and kernel launches per phase since

@@ -23,6 +23,7 @@ struct nbv_ctx {
   nbv_config cfg;
   Consts c;
   cudaStream_t st = nullptr;
+  cudaStream_t cap_st = nullptr;   // private stream on which graphs are captured
   int device = 0;
   std::string err;
   bool cuda_dead = false;
@@ -76,6 +77,30 @@ struct nbv_ctx {
   int64_t acc_launch[NBV_NUM_PHASES] = {0};
   unsigned long long* d_stats = nullptr;   // composite work counters
   int64_t composite_launches = 0;
+
+  // batched multi-view scoring (cfg.batched): buffers sized once per
+  // (scene, candidate set), the whole score captured in a CUDA graph
+  struct Batched {
+    bool ready = false;             // buffers sized for the current scene / candidates
+    int nv = 0, ntiles = 0;
+    int64_t total = 0;              // (view, tile, Gaussian) entries
+    DevCam* cams = nullptr;
+    uint32_t* tile_base = nullptr;  // [nv]
+    int* tile_view = nullptr;       // [ntiles]
+    DevProj pr{};                   // [nv][n] records
+    uint32_t* offsets = nullptr;    // [nv n + 1]
+    uint32_t* scan_tmp = nullptr;
+    SortBuffers sb{};               // entries
+    SortBuffers qb{};               // work queue
+    uint2* ranges = nullptr;        // [ntiles]
+    int* counter = nullptr;
+    float* blocks = nullptr;        // [nv][n][nBp]
+    double* partial = nullptr;
+    int parts_cap = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches_per_replay = 0;
+  } bt;
 };
 
 namespace {
@@ -142,8 +167,9 @@ DevCam to_dev(const nbv_camera& c) {
     d.campos[i] = (float)(-((double)c.R[i] * c.t[0] + (double)c.R[3 + i] * c.t[1] +
                             (double)c.R[6 + i] * c.t[2]));
   d.W = c.width; d.H = c.height;
-  d.GX = (c.width + kTile - 1) / kTile;
-  d.GY = (c.height + kTile - 1) / kTile;
+  d.TW = kTile; d.TH = kTile;
+  d.GX = (c.width + d.TW - 1) / d.TW;
+  d.GY = (c.height + d.TH - 1) / d.TH;
   return d;
 }
 
@@ -240,7 +266,7 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
     }
     CKR(check_launch(ctx, launch_ranges(ctx->sb.keys[0], total, ctx->sb.ranges, ntiles, st)));
   }
-  CompositeArgs a;
+  CompositeArgs a{};
   a.cam = dc;
   a.r0 = ctx->pr.r0; a.r1 = ctx->pr.r1; a.r2 = ctx->pr.r2;
   a.p = ctx->p;
@@ -267,6 +293,203 @@ int view_gains(nbv_ctx* ctx, const nbv_camera& cam, const float* blocks, float* 
   CKR(check_launch(ctx, launch_view_gains(dev_scene(ctx), ctx->c, to_dev(cam), blocks, ctx->F, delta,
                                           ctx->partial, ctx->partial_cap, &used, ctx->st)));
   CKR(check_launch(ctx, launch_reduce_gains(ctx->partial, used, out3, ctx->st)));
+  return NBV_OK;
+}
+
+int resolve_phases(nbv_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->st));
+
+  for (auto& r : ctx->recs) {
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    ctx->acc_ms[r.phase] += ms;
+    ctx->acc_launch[r.phase] += r.launches;
+    ctx->pool.push_back(r.a);
+    ctx->pool.push_back(r.b);
+  }
+  ctx->recs.clear();
+  return NBV_OK;
+}
+
+int bits_for(int64_t n) {
+  int b = 1;
+  while ((int64_t(1) << b) < n) ++b;
+  return b;
+}
+
+void batched_drop_graph(nbv_ctx* ctx) {
+  auto& B = ctx->bt;
+  if (B.exec) cudaGraphExecDestroy(B.exec);
+  if (B.graph) cudaGraphDestroy(B.graph);
+  B.exec = nullptr;
+  B.graph = nullptr;
+}
+
+void batched_invalidate(nbv_ctx* ctx) {
+  batched_drop_graph(ctx);
+  ctx->bt.ready = false;
+}
+
+// Size every buffer of the multi-view path: camera tables, records, and the
+// entry count (one eager projection + scan, one host read-back).
+int batched_setup(nbv_ctx* ctx) {
+  auto& B = ctx->bt;
+  cudaStream_t st = ctx->st;
+  const int nv = (int)ctx->cand.size();
+  const int64_t n = ctx->n;
+  B.nv = nv;
+  std::vector<DevCam> hc(nv);
+  std::vector<uint32_t> base(nv);
+  int64_t nt = 0;
+  for (int v = 0; v < nv; ++v) {
+    hc[v] = to_dev(ctx->cand[v]);
+    base[v] = (uint32_t)nt;
+    nt += (int64_t)hc[v].GX * hc[v].GY;
+  }
+  if (nt >= (int64_t(1) << 31)) return fail(ctx, NBV_ERR_ARG, "too many tiles in the candidate set");
+  B.ntiles = (int)nt;
+  std::vector<int> tv((size_t)nt);
+  for (int v = 0; v < nv; ++v)
+    for (int64_t t = 0; t < (int64_t)hc[v].GX * hc[v].GY; ++t) tv[base[v] + t] = v;
+  CKR(alloc(ctx, &B.cams, (size_t)nv));
+  CKR(alloc(ctx, &B.tile_base, (size_t)nv));
+  CKR(alloc(ctx, &B.tile_view, (size_t)nt));
+  CK(cudaMemcpyAsync(B.cams, hc.data(), sizeof(DevCam) * nv, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(B.tile_base, base.data(), sizeof(uint32_t) * nv, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(B.tile_view, tv.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
+  const size_t slots = (size_t)nv * n;
+  CKR(alloc(ctx, &B.pr.r0, slots)); CKR(alloc(ctx, &B.pr.r1, slots)); CKR(alloc(ctx, &B.pr.r2, slots));
+  CKR(alloc(ctx, &B.pr.rect, slots)); CKR(alloc(ctx, &B.pr.zbits, slots));
+  CKR(alloc(ctx, &B.pr.touched, slots)); CKR(alloc(ctx, &B.pr.radius, slots));
+  CKR(alloc(ctx, &B.offsets, slots + 1));
+  CKR(alloc(ctx, &B.scan_tmp, scan_scratch_elems((int64_t)slots + 1)));
+  CKR(alloc(ctx, &B.ranges, (size_t)nt));
+  CKR(alloc(ctx, &B.counter, 1));
+  CKR(alloc(ctx, &B.blocks, slots * ctx->nBp));
+  B.parts_cap = 152 * 16 * 4;
+  CKR(alloc(ctx, &B.partial, (size_t)nv * B.parts_cap * 3));
+  CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)(nv > 0 ? nv : 1) * 3));
+  CKR(grow(ctx, &ctx->out4, &ctx->out4_cap, (size_t)(nv > 0 ? nv : 1) * 4));
+  // queue sort buffers
+  CKR(alloc(ctx, &B.qb.keys[0], (size_t)nt)); CKR(alloc(ctx, &B.qb.keys[1], (size_t)nt));
+  CKR(alloc(ctx, &B.qb.vals[0], (size_t)nt)); CKR(alloc(ctx, &B.qb.vals[1], (size_t)nt));
+  CKR(alloc(ctx, &B.qb.hist, radix_hist_elems(nt)));
+  B.qb.cap = (size_t)nt;
+  // entry count
+  CKR(check_launch(ctx, launch_project_views(dev_scene(ctx), ctx->c, B.cams, nv, B.pr, st)));
+  CKR(check_launch(ctx, launch_scan_u32(B.pr.touched, B.offsets, (int64_t)slots, B.scan_tmp, st)));
+  CK(cudaMemcpyAsync(ctx->h_total, B.offsets + slots, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  B.total = (int64_t)*ctx->h_total;
+  const size_t cap = (size_t)B.total + 1024;
+  CKR(alloc(ctx, &B.sb.keys[0], cap)); CKR(alloc(ctx, &B.sb.keys[1], cap));
+  CKR(alloc(ctx, &B.sb.vals[0], cap)); CKR(alloc(ctx, &B.sb.vals[1], cap));
+  CKR(alloc(ctx, &B.sb.hist, radix_hist_elems((int64_t)cap)));
+  B.sb.cap = cap;
+  B.ready = true;
+  return NBV_OK;
+}
+
+// The whole multi-view score, enqueued on the context stream (captured into
+// a graph by batched_score).
+int batched_sequence(nbv_ctx* ctx) {
+  auto& B = ctx->bt;
+  cudaStream_t st = ctx->st;
+  const int nv = B.nv;
+  const int64_t n = ctx->n;
+  const size_t slots = (size_t)nv * n;
+  DevScene s = dev_scene(ctx);
+  CK(cudaMemsetAsync(B.blocks, 0, sizeof(float) * slots * ctx->nBp, st));
+  {
+    Phase ph(ctx, NBV_PHASE_PROJECT);
+    CKR(check_launch(ctx, launch_project_views(s, ctx->c, B.cams, nv, B.pr, st)));
+  }
+  uint32_t* qv = nullptr;
+  const uint64_t* skeys = nullptr;
+  const uint32_t* svals = nullptr;
+  {
+    Phase ph(ctx, NBV_PHASE_SORT);
+    CKR(check_launch(ctx, launch_scan_u32(B.pr.touched, B.offsets, (int64_t)slots, B.scan_tmp, st)));
+    CKR(check_launch(ctx, launch_duplicate_views(B.pr, n, nv, B.cams, B.tile_base, B.offsets, B.sb.keys[0],
+                                                 B.sb.vals[0], st)));
+    int which = 0;
+    CKR(check_launch(ctx, launch_radix_sort(B.sb, B.total, 32 + bits_for(B.ntiles), &which, st)));
+    skeys = B.sb.keys[which];
+    svals = B.sb.vals[which];
+    CKR(check_launch(ctx, launch_ranges(skeys, B.total, B.ranges, B.ntiles, st)));
+    CKR(check_launch(ctx, launch_queue_keys(B.ranges, B.ntiles, B.qb.keys[0], B.qb.vals[0], st)));
+    int qw = 0;
+    CKR(check_launch(ctx, launch_radix_sort(B.qb, B.ntiles, 32 + bits_for(B.ntiles), &qw, st)));
+    qv = B.qb.vals[qw];
+  }
+  {
+    Phase ph(ctx, NBV_PHASE_COMPOSITE);
+    CK(cudaMemsetAsync(B.counter, 0, sizeof(int), st));
+    if (ctx->prof) ctx->composite_launches++;
+    CompositeArgs a{};
+    a.cam = B.nv > 0 ? to_dev(ctx->cand[0]) : DevCam{};
+    a.r0 = B.pr.r0; a.r1 = B.pr.r1; a.r2 = B.pr.r2;
+    a.p = ctx->p;
+    a.vals = svals;
+    a.ranges = B.ranges;
+    a.blocks = B.blocks;
+    a.stats = ctx->prof ? ctx->d_stats : nullptr;
+    a.nB = ctx->nB;
+    a.queue = qv;
+    a.counter = B.counter;
+    a.n_items = B.ntiles;
+    a.tile_view = B.tile_view;
+    a.tile_base = B.tile_base;
+    a.cams = B.cams;
+    a.n = n;
+    CKR(check_launch(ctx, launch_composite(a, ctx->c, st)));   // records of view v start at slot v n
+  }
+  {
+    Phase ph(ctx, NBV_PHASE_GAINS);
+    int nparts = 0;
+    CKR(check_launch(ctx, launch_views_gains(s, ctx->c, B.cams, nv, B.blocks, ctx->F, B.partial, B.parts_cap,
+                                             &nparts, st)));
+    CKR(check_launch(ctx, launch_reduce_gains_views(B.partial, nparts, nv, ctx->ig_cand, st)));
+  }
+  {
+    Phase ph(ctx, NBV_PHASE_SCORE);
+    CKR(check_launch(ctx, launch_final_scores(ctx->ig_cand, ctx->ig_train, nv, (int)ctx->train.size(), ctx->c,
+                                              ctx->out4, ctx->d_flags, ctx->d_best_score, ctx->d_flags + 1, st)));
+  }
+  return NBV_OK;
+}
+
+int batched_score(nbv_ctx* ctx) {
+  auto& B = ctx->bt;
+  cudaStream_t st = ctx->st;
+  if (!B.ready) {
+    batched_drop_graph(ctx);
+    CKR(batched_setup(ctx));
+  }
+  if (ctx->prof) return batched_sequence(ctx);   // timed phase by phase, not replayed
+  if (!B.exec) {
+    // capture on the private stream (the caller's stream may be the legacy
+    // default stream, which cannot be captured)
+    struct StreamSwap {
+      nbv_ctx* c;
+      cudaStream_t keep;
+      ~StreamSwap() { c->st = keep; }
+    } swap{ctx, ctx->st};
+    ctx->st = ctx->cap_st;
+    const int64_t l0 = ctx->launches;
+    CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+    const int rc = batched_sequence(ctx);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->st, &g);
+    if (rc != NBV_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    CK(ec);
+    B.graph = g;
+    CK(cudaGraphInstantiate(&B.exec, B.graph, 0));
+    B.launches_per_replay = ctx->launches - l0;
+    ctx->launches = l0;
+  }
+  CK(cudaGraphLaunch(B.exec, st));
+  ctx->launches += B.launches_per_replay;
   return NBV_OK;
 }
 
@@ -351,6 +574,7 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   ctx->nBp = (ctx->nB + 3) & ~3;
   ctx->st = static_cast<cudaStream_t>(cuda_stream);
   if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&ctx->h_total), sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_flags), 4 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_best_score), sizeof(float)) != cudaSuccess ||
@@ -376,9 +600,20 @@ void nbv_destroy(nbv_ctx* ctx) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->d_stats) cudaFree(ctx->d_stats);
+  batched_drop_graph(ctx);
+  {
+    auto& B = ctx->bt;
+    void* bp[] = {B.cams, B.tile_base, B.tile_view, B.pr.r0, B.pr.r1, B.pr.r2, B.pr.rect, B.pr.zbits,
+                  B.pr.touched, B.pr.radius, B.offsets, B.scan_tmp, B.sb.keys[0], B.sb.keys[1], B.sb.vals[0],
+                  B.sb.vals[1], B.sb.hist, B.qb.keys[0], B.qb.keys[1], B.qb.vals[0], B.qb.vals[1], B.qb.hist,
+                  B.ranges, B.counter, B.blocks, B.partial};
+    for (void* q : bp)
+      if (q) cudaFree(q);
+  }
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   if (ctx->h_total) cudaFreeHost(ctx->h_total);
+  if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   delete ctx;
 }
 
@@ -426,6 +661,7 @@ int nbv_load_gaussians(nbv_ctx* ctx, int64_t n, const float* means, const float*
   ctx->prepared = false;
   ctx->scored = false;
   ctx->prepared_target = -2;
+  batched_invalidate(ctx);
   CKR(check_launch(ctx, launch_scene_prep(dev_scene(ctx), ctx->c, -1, ctx->st)));
   return NBV_OK;
 }
@@ -441,6 +677,7 @@ static int set_views(nbv_ctx* ctx, int n, const nbv_camera* cams, std::vector<nb
 
 int nbv_set_train_views(nbv_ctx* ctx, int n, const nbv_camera* cams) {
   CKR(set_views(ctx, n, cams, ctx->train));
+  batched_drop_graph(ctx);     // the graph reads the training gains buffer
   ctx->prepared = false;
   ctx->scored = false;
   return NBV_OK;
@@ -448,6 +685,7 @@ int nbv_set_train_views(nbv_ctx* ctx, int n, const nbv_camera* cams) {
 
 int nbv_set_candidates(nbv_ctx* ctx, int n, const nbv_camera* cams) {
   CKR(set_views(ctx, n, cams, ctx->cand));
+  batched_invalidate(ctx);
   ctx->scored = false;
   return NBV_OK;
 }
@@ -465,9 +703,7 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
     Phase ph(ctx, NBV_PHASE_PREP);
     CKR(check_launch(ctx, launch_scene_prep(dev_scene(ctx), ctx->c, target_obj, st)));
   }
-  size_t cams_cap = 0;
   CKR(alloc(ctx, &ctx->d_train_cams, (size_t)nt));
-  (void)cams_cap;
   std::vector<DevCam> hc(nt);
   for (int t = 0; t < nt; ++t) hc[t] = to_dev(ctx->train[t]);
   CK(cudaMemcpyAsync(ctx->d_train_cams, hc.data(), sizeof(DevCam) * nt, cudaMemcpyHostToDevice, st));
@@ -509,14 +745,16 @@ int nbv_score(nbv_ctx* ctx, float* ig_out, int out_on_device) {
   if (!ctx->prepared) return fail(ctx, NBV_ERR_STATE, "nbv_score before nbv_prepare");
   cudaStream_t st = ctx->st;
   const int nc = (int)ctx->cand.size();
-  CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)(nc > 0 ? nc : 1) * 3));
-  CKR(grow(ctx, &ctx->out4, &ctx->out4_cap, (size_t)(nc > 0 ? nc : 1) * 4));
-  for (int v = 0; v < nc; ++v) {
-    CK(cudaMemsetAsync(ctx->blocks, 0, sizeof(float) * (size_t)ctx->n * ctx->nBp, st));
-    CKR(render_view(ctx, ctx->cand[v], ctx->blocks, nullptr, nullptr, nullptr, nullptr));
-    CKR(view_gains(ctx, ctx->cand[v], ctx->blocks, nullptr, ctx->ig_cand + 3 * v));
-  }
-  {
+  if (ctx->cfg.batched && nc > 0) {
+    CKR(batched_score(ctx));
+  } else {
+    CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)(nc > 0 ? nc : 1) * 3));
+    CKR(grow(ctx, &ctx->out4, &ctx->out4_cap, (size_t)(nc > 0 ? nc : 1) * 4));
+    for (int v = 0; v < nc; ++v) {
+      CK(cudaMemsetAsync(ctx->blocks, 0, sizeof(float) * (size_t)ctx->n * ctx->nBp, st));
+      CKR(render_view(ctx, ctx->cand[v], ctx->blocks, nullptr, nullptr, nullptr, nullptr));
+      CKR(view_gains(ctx, ctx->cand[v], ctx->blocks, nullptr, ctx->ig_cand + 3 * v));
+    }
     Phase ph(ctx, NBV_PHASE_SCORE);
     CKR(check_launch(ctx, launch_final_scores(ctx->ig_cand, ctx->ig_train, nc, (int)ctx->train.size(),
                                               ctx->c, ctx->out4, ctx->d_flags, ctx->d_best_score,
@@ -631,23 +869,10 @@ int nbv_set_profiling(nbv_ctx* ctx, int on) {
   for (int i = 0; i < NBV_NUM_PHASES; ++i) { ctx->acc_ms[i] = 0.0; ctx->acc_launch[i] = 0; }
   ctx->composite_launches = 0;
   if (!ctx->d_stats) CK(cudaMalloc(reinterpret_cast<void**>(&ctx->d_stats), 4 * sizeof(unsigned long long)));
+  (void)0;                     // the batched path runs eagerly while profiling, from its graph otherwise
   CK(cudaMemsetAsync(ctx->d_stats, 0, 4 * sizeof(unsigned long long), ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   ctx->prof = on != 0;
-  return NBV_OK;
-}
-
-static int resolve_phases(nbv_ctx* ctx) {
-  CK(cudaStreamSynchronize(ctx->st));
-  for (auto& r : ctx->recs) {
-    float ms = 0.0f;
-    CK(cudaEventElapsedTime(&ms, r.a, r.b));
-    ctx->acc_ms[r.phase] += ms;
-    ctx->acc_launch[r.phase] += r.launches;
-    ctx->pool.push_back(r.a);
-    ctx->pool.push_back(r.b);
-  }
-  ctx->recs.clear();
   return NBV_OK;
 }
 

@@ -72,10 +72,12 @@ __host__ __device__ __forceinline__ int u_stride(int K) {
 }
 constexpr int kVStride = 40;
 
+// One 16x16 tile of one view: both passes. blocks_v is the view's block
+// array (NULL: render only).
 template <int KCM>
-__global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
-    k_composite(CompositeArgs args, Consts c) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void composite_tile(const CompositeArgs& args, const Consts& c, const DevCam& cam,
+                                               int tile, uint2 rg, float* blocks_v, size_t rec_off,
+                                               unsigned char* smem) {
   const int KC = c.KC;
   const int nBp = (args.nB + 3) & ~3;
   float4* s0 = reinterpret_cast<float4*>(smem);
@@ -87,14 +89,11 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
   int* touched = reinterpret_cast<int*>(acc + kBatch * nBp);      // [kBatch]
   __shared__ int s_last_max;
 
-  const DevCam& cam = args.cam;
-  const int tile = blockIdx.x;
   const int tx = tile % cam.GX, ty = tile / cam.GX;
   const int tid = threadIdx.x, lane = tid & 31;
   const int px = tx * kTile + (tid % kTile), py = ty * kTile + (tid / kTile);
   const bool inside = px < cam.W && py < cam.H;
   const float pxc = fa((float)px, 0.5f), pyc = fa((float)py, 0.5f);
-  const uint2 rg = args.ranges[tile];
 
   // ------------------------------------------------------------- pass 1
   float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
@@ -109,9 +108,9 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
     const uint32_t nj = min((uint32_t)kBatch, rg.y - start);
     if (tid < (int)nj) {
       const uint32_t g = args.vals[start + tid];
-      s0[tid] = args.r0[g];
-      s1[tid] = args.r1[g];
-      s2[tid] = args.r2[g];
+      s0[tid] = args.r0[rec_off + g];
+      s1[tid] = args.r1[rec_off + g];
+      s2[tid] = args.r2[rec_off + g];
       sid[tid] = (int)g;
     }
     for (int i = tid; i < (int)nj * KC; i += kTilePix) {
@@ -166,7 +165,7 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
         if (k < KC) args.obj[pix * KC + k] = O[k] + (k == 0 ? 1.0f - sum : 0.0f);
     }
   }
-  if (args.blocks == nullptr) return;
+  if (blocks_v == nullptr) return;
 
   // ------------------------------------------------------------- pass 2
   if (tid == 0) s_last_max = (int)rg.x;
@@ -226,9 +225,9 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
     __syncthreads();
     if (tid < nj) {
       const uint32_t g = args.vals[start + tid];
-      s0[tid] = args.r0[g];
-      s1[tid] = args.r1[g];
-      s2[tid] = args.r2[g];
+      s0[tid] = args.r0[rec_off + g];
+      s1[tid] = args.r1[rec_off + g];
+      s2[tid] = args.r2[rec_off + g];
       sid[tid] = (int)g;
       touched[tid] = 0;
     }
@@ -349,10 +348,34 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
       const int j = i / n4, q = i - j * n4;
       if (!touched[j]) continue;
       const float4 v = reinterpret_cast<const float4*>(acc + j * nBp)[q];
-      float4* dst = reinterpret_cast<float4*>(args.blocks + (size_t)sid[j] * nBp) + q;
+      float4* dst = reinterpret_cast<float4*>(blocks_v + (size_t)sid[j] * nBp) + q;
       atomicAdd(dst, v);
     }
     end = start;
+  }
+}
+
+template <int KCM>
+__global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
+    k_composite(CompositeArgs args, Consts c) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (args.queue == nullptr) {                 // one tile of one view per block
+    composite_tile<KCM>(args, c, args.cam, blockIdx.x, args.ranges[blockIdx.x], args.blocks, 0, smem);
+    return;
+  }
+  // persistent: (view, tile) items in queue order (longest lists first)
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(args.counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= args.n_items) break;
+    const uint32_t gt = args.queue[it];
+    const int v = args.tile_view[gt];
+    const DevCam cam = args.cams[v];
+    composite_tile<KCM>(args, c, cam, (int)(gt - args.tile_base[v]), args.ranges[gt],
+                        args.blocks + (size_t)v * args.n * ((args.nB + 3) & ~3), (size_t)v * args.n, smem);
   }
 }
 
@@ -367,6 +390,18 @@ int launch_k(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
   if (!attr_set) {
     cudaFuncSetAttribute(k_composite<KCM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
+  }
+  if (a.queue) {
+    int per_sm = 1, dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<KCM>, kTilePix, sm);
+    if (per_sm < 1) per_sm = 1;
+    int grid = nsm * per_sm;
+    if (grid > a.n_items) grid = a.n_items;
+    if (grid <= 0) return 0;
+    k_composite<KCM><<<grid, kTilePix, sm, st>>>(a, c);
+    return 1;
   }
   const int ntiles = a.cam.GX * a.cam.GY;
   if (ntiles <= 0) return 0;

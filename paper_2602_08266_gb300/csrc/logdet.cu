@@ -25,6 +25,8 @@
 // (Eq. 10) and the weighted sum (Eq. 11) is maximised (Eq. 5).
 #include <math.h>
 
+#include <type_traits>
+
 #include "nbv_internal.cuh"
 
 namespace nbv {
@@ -295,28 +297,42 @@ __device__ void build_B(int f, const float* blk, const Consts& c, float* Bm, int
 }
 
 // --------------------------------------------------------- training factors
+// Decode the linear index t of a packed lower triangle into (row, col).
+__device__ __forceinline__ void tri_decode(int t, int& r, int& cc) {
+  r = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while (tri(r + 1, 0) <= t) ++r;
+  while (tri(r, 0) > t) --r;
+  cc = t - tri(r, 0);
+}
+
+// One warp per Gaussian: H = lambda I + c_g sum_t M_t^T B_t M_t (single
+// precision sum), Jacobi scaling, Cholesky in double precision (trailing
+// updates spread evenly over the lanes), then L^-1 in single precision
+// (right-looking, also spread evenly), stored packed.
 __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__ cams,
                                 const float* __restrict__ blocks, int n_train, Factors F,
                                 int* err, int lmax, int umax) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int nB = block_floats(c.K), nBp = (nB + 3) & ~3;
-  const size_t per_warp_d = (size_t)lmax * (lmax + 1) / 2 + lmax;
-  const size_t per_warp_f = (size_t)umax * lmax * 2 + (size_t)umax * umax + sizeof(GJac) / 4 + 4;
+  const int ntm = lmax * (lmax + 1) / 2;
+  const size_t per_warp_d = (size_t)ntm + lmax;
+  const size_t per_warp_f = (size_t)umax * lmax * 2 + (size_t)umax * umax + sizeof(GJac) / 4 + ntm + 4;
   double* Hs = reinterpret_cast<double*>(smem) + warp * per_warp_d;
-  double* dsc = Hs + (size_t)lmax * (lmax + 1) / 2;    // 1 / sqrt(H_ii)
+  double* dsc = Hs + ntm;                              // 1 / sqrt(H_ii)
   float* fbase = reinterpret_cast<float*>(reinterpret_cast<double*>(smem) + nw * per_warp_d) +
                  warp * per_warp_f;
   float* M = fbase;
   float* BM = M + umax * lmax;
   float* Bm = BM + umax * lmax;
   GJac* J = reinterpret_cast<GJac*>(Bm + umax * umax);
+  float* Hf = reinterpret_cast<float*>(J + 1);         // ntm floats
   for (int64_t g = (int64_t)blockIdx.x * nw + warp; g < s.n; g += (int64_t)gridDim.x * nw) {
     const float cg = s.aux[g].y;
     const float* p = s.p + (size_t)g * c.KC;
     for (int f = 0; f < 3; ++f) {
       const int l = out_l(f, c), u = out_u(f, c), nt = l * (l + 1) / 2;
-      for (int i = lane; i < nt; i += 32) Hs[i] = 0.0;
+      for (int i = lane; i < nt; i += 32) Hf[i] = 0.0f;
       __syncwarp();
       if (cg > 0.0f) {
         for (int t = 0; t < n_train; ++t) {
@@ -333,69 +349,74 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
             BM[i] = acc;
           }
           __syncwarp();
-          for (int i = lane; i < nt; i += 32) {         // H += c M^T (B M)
-            int r = (int)((sqrtf(8.0f * i + 1.0f) - 1.0f) * 0.5f);
-            while (tri(r + 1, 0) <= i) ++r;
-            while (tri(r, 0) > i) --r;
-            const int cc = i - tri(r, 0);
+          for (int i = lane; i < nt; i += 32) {         // H += M^T (B M)
+            int r, cc;
+            tri_decode(i, r, cc);
             float acc = 0.0f;
             for (int k = 0; k < u; ++k) acc += M[k * l + r] * BM[k * l + cc];
-            Hs[i] += (double)cg * (double)acc;
+            Hf[i] += acc;
           }
           __syncwarp();
         }
       }
-      // damping, Jacobi scaling, Cholesky (double), store
       float* Lg = F.L[f] + (size_t)g * nt;
       float* dg = F.dinv[f] + (size_t)g * l;
-      for (int i = lane; i < l; i += 32) Hs[tri(i, i)] += (double)c.lam;
-      __syncwarp();
+      // damping and Jacobi scaling, in double
       for (int i = lane; i < l; i += 32) {
-        const double di = 1.0 / sqrt(Hs[tri(i, i)]);
+        const double hii = (double)c.lam + (double)cg * (double)Hf[tri(i, i)];
+        const double di = 1.0 / sqrt(hii);
         dsc[i] = di;
         dg[i] = (float)di;
       }
       __syncwarp();
       for (int i = lane; i < nt; i += 32) {
-        int r = (int)((sqrtf(8.0f * i + 1.0f) - 1.0f) * 0.5f);
-        while (tri(r + 1, 0) <= i) ++r;
-        while (tri(r, 0) > i) --r;
-        const int cc = i - tri(r, 0);
-        Hs[i] = Hs[i] * dsc[r] * dsc[cc];
+        int r, cc;
+        tri_decode(i, r, cc);
+        const double h = (double)cg * (double)Hf[i] + (r == cc ? (double)c.lam : 0.0);
+        Hs[i] = h * dsc[r] * dsc[cc];
       }
       __syncwarp();
-      // the diagonal is now 1; right-looking Cholesky
+      // Cholesky of the scaled matrix (diagonal 1), double precision
       for (int k = 0; k < l; ++k) {
         const double dkk = Hs[tri(k, k)];
-        if (!(dkk > 0.0)) { if (lane == 0) atomicExch(err, 1); }
+        if (!(dkk > 0.0) && lane == 0) atomicExch(err, 1);
         const double Lkk = sqrt(fmax(dkk, 1e-300));
+        const double iL = 1.0 / Lkk;
         __syncwarp();
         if (lane == 0) Hs[tri(k, k)] = Lkk;
-        for (int i = k + 1 + lane; i < l; i += 32) Hs[tri(i, k)] /= Lkk;
+        for (int i = k + 1 + lane; i < l; i += 32) Hs[tri(i, k)] *= iL;
         __syncwarp();
-        for (int i = k + 1 + lane; i < l; i += 32) {
-          const double lik = Hs[tri(i, k)];
-          for (int j = k + 1; j <= i; ++j) Hs[tri(i, j)] -= lik * Hs[tri(j, k)];
+        const int m = l - k - 1;                       // trailing triangle of size m
+        const int tot = m * (m + 1) / 2;
+        if (lane < tot) {
+          int ii, jj;
+          tri_decode(lane, ii, jj);
+          for (int t = lane; t < tot; t += 32) {
+            const int i = k + 1 + ii, j = k + 1 + jj;
+            Hs[tri(i, j)] -= Hs[tri(i, k)] * Hs[tri(j, k)];
+            jj += 32;
+            while (jj > ii) { jj -= ii + 1; ++ii; }
+          }
         }
         __syncwarp();
       }
-      // L^-1 in place, row by row: X_ii = 1/L_ii, X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj
-      for (int i = 0; i < l; ++i) {
-        const double xii = 1.0 / Hs[tri(i, i)];
-        double nv[6];
-        int cnt = 0;
-        for (int j = lane; j < i; j += 32) {
-          double a = 0.0;
-          for (int k = j; k < i; ++k) a += Hs[tri(i, k)] * Hs[tri(k, j)];
-          nv[cnt++] = -xii * a;
+      // X = L^-1 in single precision, right-looking:
+      //   X_kk = 1 / L_kk,  X_kj = -X_kk acc_kj (j < k),  acc_ij += L_ik X_kj (i > k, j <= k)
+      for (int i = lane; i < nt; i += 32) Hf[i] = 0.0f;
+      __syncwarp();
+      for (int k = 0; k < l; ++k) {
+        const float xkk = (float)(1.0 / Hs[tri(k, k)]);
+        for (int j = lane; j < k; j += 32) Hf[tri(k, j)] = -xkk * Hf[tri(k, j)];
+        if (lane == 0) Hf[tri(k, k)] = xkk;
+        __syncwarp();
+        const int rows = l - 1 - k, cols = k + 1, tot = rows * cols;
+        for (int t = lane; t < tot; t += 32) {
+          const int i = k + 1 + t / cols, j = t - (t / cols) * cols;
+          Hf[tri(i, j)] += (float)Hs[tri(i, k)] * Hf[tri(k, j)];
         }
         __syncwarp();
-        cnt = 0;
-        for (int j = lane; j < i; j += 32) Hs[tri(i, j)] = nv[cnt++];
-        if (lane == 0) Hs[tri(i, i)] = xii;
-        __syncwarp();
       }
-      for (int i = lane; i < nt; i += 32) Lg[i] = (float)Hs[i];
+      for (int i = lane; i < nt; i += 32) Lg[i] = Hf[i];
       __syncwarp();
     }
   }
@@ -540,12 +561,17 @@ __device__ float output_gain(const GJac& J, const Consts& c, const float* p, con
 }
 
 template <int UO>
-__global__ void __launch_bounds__(128, 3) k_view_gains(DevScene s, Consts c, DevCam cam, const float* __restrict__ blocks,
-                             Factors F, float* __restrict__ delta, double* __restrict__ partial,
-                             int nt_max, int lu_max, int uu_max) {
+__global__ void __launch_bounds__(128, 3) k_view_gains(DevScene s, Consts c, DevCam cam1, const DevCam* cams,
+                                                      const float* __restrict__ blocks, Factors F,
+                                                      float* __restrict__ delta, double* __restrict__ partial,
+                                                      int nt_max, int lu_max, int uu_max) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int nB = block_floats(c.K), nBp = (nB + 3) & ~3;
+  // multi-view launches: view = blockIdx.y (its own blocks and partial sums)
+  const DevCam cam = cams ? cams[blockIdx.y] : cam1;
+  blocks += (size_t)blockIdx.y * s.n * nBp;
+  partial += (size_t)blockIdx.y * gridDim.x * nw * 3;
   const size_t per_warp = 2 * (size_t)lu_max + 3 * (size_t)uu_max + 32 * (sizeof(GJac) / 4) + 4;
   float* Ls = nullptr;
   float* Y = reinterpret_cast<float*>(smem) + warp * per_warp;
@@ -595,6 +621,8 @@ __global__ void __launch_bounds__(128, 3) k_view_gains(DevScene s, Consts c, Dev
 __global__ void k_reduce_partial(const double* __restrict__ partial, int nblocks, double* out3) {
   __shared__ double sm[3][256];
   const int tid = threadIdx.x;
+  partial += (size_t)blockIdx.x * nblocks * 3;     // one block per view
+  out3 += 3 * blockIdx.x;
   double a[3] = {0.0, 0.0, 0.0};
   for (int i = tid; i < nblocks; i += 256)
     for (int f = 0; f < 3; ++f) a[f] += partial[3 * i + f];
@@ -635,8 +663,9 @@ __global__ void k_final_scores(const double* __restrict__ igc, const double* __r
 }
 
 size_t factors_smem_per_warp(int lmax, int umax) {
-  const size_t per_warp_d = (size_t)lmax * (lmax + 1) / 2 + lmax;
-  const size_t per_warp_f = (size_t)umax * lmax * 2 + (size_t)umax * umax + sizeof(GJac) / 4 + 4;
+  const int ntm = lmax * (lmax + 1) / 2;
+  const size_t per_warp_d = (size_t)ntm + lmax;
+  const size_t per_warp_f = (size_t)umax * lmax * 2 + (size_t)umax * umax + sizeof(GJac) / 4 + ntm + 4;
   return per_warp_d * sizeof(double) + per_warp_f * sizeof(float);
 }
 
@@ -678,7 +707,8 @@ int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams,
   int lmax, umax;
   sizes(c, &lmax, &umax);
   const size_t pw = factors_smem_per_warp(lmax, umax);
-  const int nw = warps_for(pw);
+  int nw = (int)((220 * 1024) / pw);
+  nw = nw < 1 ? 1 : (nw > 8 ? 8 : nw);
   const size_t sm = pw * nw;
   cudaFuncSetAttribute(k_build_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int64_t nblk = (s.n + nw - 1) / nw;
@@ -688,12 +718,21 @@ int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams,
 }
 
 template <int UO>
-void launch_gains_k(const DevScene& s, const Consts& c, const DevCam& cam, const float* blocks,
-                    const Factors& f, float* delta, double* partial, int grid, int nw, size_t sm,
-                    const GainsDims& d, cudaStream_t st) {
+void launch_gains_k(const DevScene& s, const Consts& c, const DevCam& cam, const DevCam* cams, int nv,
+                    const float* blocks, const Factors& f, float* delta, double* partial, int grid, int nw,
+                    size_t sm, const GainsDims& d, cudaStream_t st) {
   cudaFuncSetAttribute(k_view_gains<UO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_view_gains<UO><<<grid, 32 * nw, sm, st>>>(s, c, cam, blocks, f, delta, partial, d.nt_max, d.lu_max,
-                                              d.uu_max);
+  k_view_gains<UO><<<dim3(grid, nv), 32 * nw, sm, st>>>(s, c, cam, cams, blocks, f, delta, partial, d.nt_max,
+                                                        d.lu_max, d.uu_max);
+}
+
+template <class L>
+void dispatch_uo(int K, L&& fn) {
+  const int uo = 6 + K;
+  if (uo <= 24) fn(std::integral_constant<int, 24>{});
+  else if (uo <= 40) fn(std::integral_constant<int, 40>{});
+  else if (uo <= 72) fn(std::integral_constant<int, 72>{});
+  else fn(std::integral_constant<int, 136>{});
 }
 
 int launch_view_gains(const DevScene& s, const Consts& c, const DevCam& cam, const float* blocks,
@@ -707,11 +746,32 @@ int launch_view_gains(const DevScene& s, const Consts& c, const DevCam& cam, con
   int grid = (int)(nblk < nblocks_cap ? nblk : nblocks_cap);
   if (grid < 1) grid = 1;
   *nblocks_used = grid * nw;        // one partial sum per warp
-  const int uo = 6 + c.K;
-  if (uo <= 24) launch_gains_k<24>(s, c, cam, blocks, f, delta, partial, grid, nw, sm, d, st);
-  else if (uo <= 40) launch_gains_k<40>(s, c, cam, blocks, f, delta, partial, grid, nw, sm, d, st);
-  else if (uo <= 72) launch_gains_k<72>(s, c, cam, blocks, f, delta, partial, grid, nw, sm, d, st);
-  else launch_gains_k<136>(s, c, cam, blocks, f, delta, partial, grid, nw, sm, d, st);
+  dispatch_uo(c.K, [&](auto uo) {
+    launch_gains_k<decltype(uo)::value>(s, c, cam, nullptr, 1, blocks, f, delta, partial, grid, nw, sm, d, st);
+  });
+  return 1;
+}
+
+int launch_views_gains(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const float* blocks,
+                       const Factors& f, double* partial, int parts_cap, int* nparts, cudaStream_t st) {
+  const GainsDims d = gains_dims(c);
+  const size_t pw = gains_smem_per_warp(d);
+  const int nw = warps_for(pw);
+  const size_t sm = pw * nw;
+  const int64_t nblk = ((s.n + 31) / 32 + nw - 1) / nw;
+  int grid = (int)(nblk < parts_cap / nw ? nblk : parts_cap / nw);
+  if (grid < 1) grid = 1;
+  *nparts = grid * nw;
+  DevCam dummy{};
+  dispatch_uo(c.K, [&](auto uo) {
+    launch_gains_k<decltype(uo)::value>(s, c, dummy, cams, nv, blocks, f, nullptr, partial, grid, nw, sm, d, st);
+  });
+  return 1;
+}
+
+int launch_reduce_gains_views(const double* partial, int nparts, int nv, double* out3, cudaStream_t st) {
+  if (nv <= 0) return 0;
+  k_reduce_partial<<<nv, 256, 0, st>>>(partial, nparts, out3);
   return 1;
 }
 

@@ -43,6 +43,7 @@ struct DevCam {
   float fx, fy, cx, cy;
   float campos[3];
   int W, H, GX, GY;
+  int TW, TH;          // screen tile size (16 x 16 by default)
 };
 
 struct Consts {
@@ -83,6 +84,9 @@ struct DevProj {
 int launch_scene_prep(const DevScene& s, const Consts& c, int target, cudaStream_t st);
 int launch_project(const DevScene& s, const Consts& c, const DevCam& cam, const DevProj& pr,
                    cudaStream_t st);
+// Projection of every Gaussian into nv views (device camera array); slot v n + g.
+int launch_project_views(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const DevProj& pr,
+                         cudaStream_t st);
 
 struct SortBuffers {
   uint64_t* keys[2];
@@ -102,6 +106,13 @@ int launch_duplicate(const DevProj& pr, int64_t n, int GX, const uint32_t* offse
 // result is in buffer index *which (0 or 1).
 int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaStream_t st);
 int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st);
+// Multi-view binning: keys (global tile << 32 | depth bits) of every (view, Gaussian) slot.
+int launch_duplicate_views(const DevProj& pr, int64_t n, int nv, const DevCam* cams, const uint32_t* tile_base,
+                           const uint32_t* offsets, uint64_t* keys, uint32_t* vals, cudaStream_t st);
+// Work-queue keys: longest tile lists first.
+int launch_queue_keys(const uint2* ranges, int ntiles, uint64_t* keys, uint32_t* vals, cudaStream_t st);
+size_t scan_scratch_elems(int64_t n);
+size_t radix_hist_elems(int64_t count);
 
 struct CompositeArgs {
   DevCam cam;
@@ -118,6 +129,14 @@ struct CompositeArgs {
   float* obj;
   unsigned long long* stats;   // optional work counters (evaluated, blended, flushes)
   int nB;
+  // persistent multi-view form (queue != NULL): items are global tile ids
+  const uint32_t* queue;       // work items, longest lists first
+  int* counter;                // next item (zeroed before the launch)
+  int n_items;
+  const int* tile_view;        // global tile -> view
+  const uint32_t* tile_base;   // view -> first global tile
+  const DevCam* cams;          // per view
+  int64_t n;                   // Gaussians (stride of the per-view block arrays)
 };
 int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st);
 
@@ -135,6 +154,11 @@ int launch_view_gains(const DevScene& s, const Consts& c, const DevCam& cam, con
                       const Factors& f, float* delta, double* partial, int nblocks_cap,
                       int* nblocks_used, cudaStream_t st);
 int launch_reduce_gains(const double* partial, int nblocks, double* out3, cudaStream_t st);
+// All views at once: blocks [nv][n][nBp]; partial sums [nv][nparts][3] with
+// nparts returned; out3 [nv][3].
+int launch_views_gains(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const float* blocks,
+                       const Factors& f, double* partial, int parts_cap, int* nparts, cudaStream_t st);
+int launch_reduce_gains_views(const double* partial, int nparts, int nv, double* out3, cudaStream_t st);
 int launch_final_scores(const double* ig_cand, const double* ig_train, int n_cand, int n_train,
                         const Consts& c, float* out4, int* best, float* best_score, int* err,
                         cudaStream_t st);

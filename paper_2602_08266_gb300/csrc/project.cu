@@ -110,18 +110,18 @@ __device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, floa
   (void)kPi;
 }
 
-__global__ void k_project(DevScene s, Consts c, DevCam cam, DevProj pr) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= s.n) return;
+// Project Gaussian g into camera cam; the records go to slot o of pr.
+__device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, const DevCam& cam, int64_t g,
+                                            const DevProj& pr, size_t o) {
   const float4 ms = s.mu_sig[g];
   const float4 ss = s.scale_skip[g];
   const float4 qq = s.qn[g];
   const float4 ax = s.aux[g];
   const float* R = cam.R;
-  pr.touched[g] = 0u;
-  pr.rect[g] = make_int4(-1, -1, -1, -1);
-  pr.radius[g] = 0.0f;
-  pr.zbits[g] = 0u;
+  pr.touched[o] = 0u;
+  pr.rect[o] = make_int4(-1, -1, -1, -1);
+  pr.radius[o] = 0.0f;
+  pr.zbits[o] = 0u;
   // ---- key path: correctly rounded single precision, fixed order
   const float tx = fa(fa(fa(fm(R[0], ms.x), fm(R[1], ms.y)), fm(R[2], ms.z)), cam.t[0]);
   const float ty = fa(fa(fa(fm(R[3], ms.x), fm(R[4], ms.y)), fm(R[5], ms.z)), cam.t[1]);
@@ -183,9 +183,9 @@ __global__ void k_project(DevScene s, Consts c, DevCam cam, DevProj pr) {
   const float mid = fm(0.5f, fa(a, cc));
   const float lam = fa(mid, __fsqrt_rn(fmaxf(0.1f, fs(fm(mid, mid), det))));
   const float r = ceilf(fm(3.0f, __fsqrt_rn(lam)));
-  const float twf = (float)kTile;
+  const float twf = (float)cam.TW, thf = (float)cam.TH;
   const float fx0 = floorf(fd(fs(mx, r), twf)), fx1 = fa(floorf(fd(fa(mx, r), twf)), 1.0f);
-  const float fy0 = floorf(fd(fs(my, r), twf)), fy1 = fa(floorf(fd(fa(my, r), twf)), 1.0f);
+  const float fy0 = floorf(fd(fs(my, r), thf)), fy1 = fa(floorf(fd(fa(my, r), thf)), 1.0f);
   const int x0 = (int)fminf(fmaxf(fx0, 0.0f), (float)cam.GX);
   const int x1 = (int)fminf(fmaxf(fx1, 0.0f), (float)cam.GX);
   const int y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)cam.GY);
@@ -204,16 +204,37 @@ __global__ void k_project(DevScene s, Consts c, DevCam cam, DevProj pr) {
     for (int k = 0; k < c.nb; ++k) acc += Y[k] * shg[3 * k + ch];
     rgb[ch] = fmaxf(acc, 0.0f);
   }
-  pr.r0[g] = make_float4(mx, my, ss.w, ax.x);
-  pr.r1[g] = make_float4(A, B, C, ms.w);
-  pr.r2[g] = make_float4(rgb[0], rgb[1], rgb[2], tz);
-  pr.rect[g] = make_int4(x0, x1, y0, y1);
-  pr.zbits[g] = __float_as_uint(tz);
-  pr.radius[g] = r;
-  pr.touched[g] = (uint32_t)((x1 - x0) * (y1 - y0));
+  pr.r0[o] = make_float4(mx, my, ss.w, ax.x);
+  pr.r1[o] = make_float4(A, B, C, ms.w);
+  pr.r2[o] = make_float4(rgb[0], rgb[1], rgb[2], tz);
+  pr.rect[o] = make_int4(x0, x1, y0, y1);
+  pr.zbits[o] = __float_as_uint(tz);
+  pr.radius[o] = r;
+  pr.touched[o] = (uint32_t)((x1 - x0) * (y1 - y0));
+}
+
+__global__ void k_project(DevScene s, Consts c, DevCam cam, DevProj pr) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= s.n) return;
+  project_one(s, c, cam, g, pr, (size_t)g);
+}
+
+// All views at once: thread g projects Gaussian g into every view, slot v n + g.
+__global__ void k_project_views(DevScene s, Consts c, const DevCam* __restrict__ cams, int nv, DevProj pr) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= s.n) return;
+  for (int v = 0; v < nv; ++v) project_one(s, c, cams[v], g, pr, (size_t)v * s.n + g);
 }
 
 }  // namespace
+
+int launch_project_views(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const DevProj& pr,
+                         cudaStream_t st) {
+  if (s.n <= 0 || nv <= 0) return 0;
+  const int bs = 128;
+  k_project_views<<<(unsigned)((s.n + bs - 1) / bs), bs, 0, st>>>(s, c, cams, nv, pr);
+  return 1;
+}
 
 int launch_scene_prep(const DevScene& s, const Consts& c, int target, cudaStream_t st) {
   if (s.n <= 0) return 0;

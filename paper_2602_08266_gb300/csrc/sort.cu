@@ -102,6 +102,40 @@ __global__ void k_duplicate(const int4* __restrict__ rect, const uint32_t* __res
     }
 }
 
+// All views: slot v n + g covers the tiles of its rectangle in view v; the key
+// carries the global tile id (first tile of view v + local tile).
+__global__ void k_duplicate_views(const int4* __restrict__ rect, const uint32_t* __restrict__ zbits, int64_t n,
+                                  int nv, const DevCam* __restrict__ cams, const uint32_t* __restrict__ tile_base,
+                                  const uint32_t* __restrict__ offsets, uint64_t* __restrict__ keys,
+                                  uint32_t* __restrict__ vals) {
+  const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (slot >= n * nv) return;
+  const int4 r = rect[slot];
+  if (r.x < 0) return;
+  const int v = (int)(slot / n);
+  const uint32_t g = (uint32_t)(slot - (int64_t)v * n);
+  const int GX = cams[v].GX;
+  const uint32_t base = tile_base[v];
+  uint32_t o = offsets[slot];
+  const uint64_t zb = zbits[slot];
+  for (int ty = r.z; ty < r.w; ++ty)
+    for (int tx = r.x; tx < r.y; ++tx) {
+      keys[o] = ((uint64_t)(base + (uint32_t)(ty * GX + tx)) << 32) | zb;
+      vals[o] = g;
+      ++o;
+    }
+}
+
+// Work-queue keys: longest tile list first, ties by tile id.
+__global__ void k_queue_keys(const uint2* __restrict__ ranges, int ntiles, uint64_t* __restrict__ keys,
+                             uint32_t* __restrict__ vals) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const uint2 r = ranges[t];
+  keys[t] = ((uint64_t)(0xFFFFFFFFu - (r.y - r.x)) << 32) | (uint32_t)t;
+  vals[t] = (uint32_t)t;
+}
+
 constexpr int kRadixThreads = 256;
 constexpr int kRadixRounds = 8;
 constexpr int kRadixTile = kRadixThreads * kRadixRounds;
@@ -224,6 +258,21 @@ int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
   if (count <= 0) return 0;
   k_ranges<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(keys, count, ranges);
+  return 1;
+}
+
+int launch_duplicate_views(const DevProj& pr, int64_t n, int nv, const DevCam* cams, const uint32_t* tile_base,
+                           const uint32_t* offsets, uint64_t* keys, uint32_t* vals, cudaStream_t st) {
+  const int64_t tot = n * nv;
+  if (tot <= 0) return 0;
+  k_duplicate_views<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(pr.rect, pr.zbits, n, nv, cams, tile_base,
+                                                                   offsets, keys, vals);
+  return 1;
+}
+
+int launch_queue_keys(const uint2* ranges, int ntiles, uint64_t* keys, uint32_t* vals, cudaStream_t st) {
+  if (ntiles <= 0) return 0;
+  k_queue_keys<<<(ntiles + 255) / 256, 256, 0, st>>>(ranges, ntiles, keys, vals);
   return 1;
 }
 
