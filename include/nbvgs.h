@@ -74,8 +74,12 @@ typedef struct {
   float t_min;           /* stop a ray before transmittance falls below this (1e-4) */
   float dilation;        /* added to the 2D covariance diagonal, px^2 (0.3) */
   float guard;           /* guard band of the projection Jacobian, x tan(fov/2) (1.3) */
-  int tile_w, tile_h;    /* screen tile; only 16x16 is built */
-  int batched;           /* reserved: 0 = one launch set per view */
+  int tile_w, tile_h;    /* screen tile: 16 x 16 (default) or 32 x 8; 0 x 0 = 16 x 16 until nbv_autotune */
+  int batched;           /* 0: one launch sequence per candidate view; 1: all candidates in one
+                            multi-view launch sequence (one sort, a persistent (view, tile)
+                            compositing launch, one gains launch) replayed as a CUDA graph */
+  int stage;             /* Gaussians the compositing kernel stages in shared memory per round:
+                            32 (default) or 16; only speed depends on it */
 } nbv_config;
 
 typedef struct {
@@ -91,8 +95,9 @@ void nbv_config_default(nbv_config* cfg, int K, int sh_degree);
 /* Create a context bound to the CUDA device current on the calling thread
  * and to `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
  * On success *out owns every device buffer the context allocates later.
- * Errors: NBV_ERR_ARG (bad config: K < 1, sh_degree outside 0..3, tile not
- * 16x16, non-finite or out-of-range constants), NBV_ERR_CUDA. */
+ * Errors: NBV_ERR_ARG (bad config: K < 1 or > 127, sh_degree outside 0..3,
+ * tile not 16x16, 32x8 or 0x0, non-finite or out-of-range constants),
+ * NBV_ERR_CUDA. */
 int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out);
 
 /* Free every device buffer of the context (synchronises its stream). NULL is ignored. */
@@ -114,7 +119,9 @@ int nbv_load_gaussians(nbv_ctx* ctx, int64_t n, const float* means, const float*
                        const float* obj_logits, int ptrs_on_device);
 
 /* Set the training views T (Eqs. 5, 10) or the candidate views C (host
- * array of n cameras, copied). Resets the prepared state for training views.
+ * array of n cameras, copied). New training views reset the prepared state;
+ * passing the cameras the context already holds, byte for byte, changes
+ * nothing (the prepared state and a captured multi-view graph are kept).
  * Errors: NBV_ERR_ARG (n < 0, n > 65535, non-finite pose, width/height not
  * in 1..16384, fx or fy <= 0). */
 int nbv_set_train_views(nbv_ctx* ctx, int n, const nbv_camera* cams);
@@ -200,6 +207,23 @@ int nbv_phase_times(nbv_ctx* ctx, double* ms, int64_t* launches);
  * [0] (pixel, splat) pairs evaluated in the forward pass, [1] pairs blended,
  * [2] (tile, Gaussian) block flushes, [3] compositing launches. Synchronises. */
 int nbv_work_stats(nbv_ctx* ctx, int64_t* out4);
+
+/* Pick the screen tile (16 x 16 or 32 x 8) and the number of Gaussians the
+ * compositing kernel stages in shared memory per round (16 or 32) that
+ * score the current candidate set fastest on the batched path: every
+ * combination prepares and scores once untimed, then once timed with CUDA
+ * events. The choice is kept for this context and remembered for later
+ * contexts with the same K, SH degree and candidate resolutions. A tile
+ * shape decides which Gaussians each tile lists (a Gaussian is listed in
+ * every tile its 3-sigma rectangle touches), so it changes rendered values
+ * slightly; the stage depth changes nothing but speed. Ends with the
+ * context prepared (same target as before, or -1). Synchronises.
+ * Errors: NBV_ERR_STATE (no Gaussians, training or candidate views), those of
+ * nbv_prepare and nbv_score. */
+int nbv_autotune(nbv_ctx* ctx, int* tile_w, int* tile_h, int* stage);
+
+/* The context's tile shape and stage depth. */
+int nbv_get_tiling(const nbv_ctx* ctx, int* tile_w, int* tile_h, int* stage);
 
 /* Largest input of nbv_sort_tile_keys_noalloc (2^20 pairs). */
 #define NBV_NOALLOC_MAX_PAIRS (1 << 20)

@@ -44,7 +44,8 @@ class nbv_config(ctypes.Structure):
                 ("lambda_damp", ctypes.c_float), ("near_z", ctypes.c_float),
                 ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("dilation", ctypes.c_float), ("guard", ctypes.c_float),
-                ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("batched", ctypes.c_int)]
+                ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("batched", ctypes.c_int),
+                ("stage", ctypes.c_int)]
 
 
 class nbv_camera(ctypes.Structure):
@@ -76,6 +77,10 @@ _SIGS = [
     ("nbv_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
     ("nbv_phase_times", ctypes.c_int, [_P, _P, _P]),
     ("nbv_work_stats", ctypes.c_int, [_P, _P]),
+    ("nbv_autotune", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]),
+    ("nbv_get_tiling", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
     ("nbv_sort_tile_keys_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P, _P, _P]),
     ("nbv_last_error", ctypes.c_char_p, [_P]),
     ("nbv_launch_count", ctypes.c_int64, [_P]),
@@ -301,7 +306,8 @@ class NBVScorer:
         total = int(cnt.value)
         dims = self._train if view_set else self._cand
         W, H = int(dims[0][view]), int(dims[1][view])
-        nt = ((W + 15) // 16) * ((H + 15) // 16)
+        tw, th, _ = self.tiling()
+        nt = ((W + tw - 1) // tw) * ((H + th - 1) // th)
         off = torch.empty(nt + 1, dtype=torch.int64, device="cuda")
         ids = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
         self._check(self.lib.nbv_debug_tile_lists(self._h, int(view_set), int(view), _dptr(off),
@@ -327,6 +333,18 @@ class NBVScorer:
         self._check(self.lib.nbv_work_stats(self._h, ctypes.c_void_p(out.ctypes.data)))
         return dict(pairs_evaluated=int(out[0]), pairs_blended=int(out[1]),
                     block_flushes=int(out[2]), composite_launches=int(out[3]))
+
+    def autotune(self):
+        """Pick tile shape and stage depth on the batched path; returns
+        (tile_w, tile_h, stage). Leaves the context prepared."""
+        w, h, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.nbv_autotune(self._h, ctypes.byref(w), ctypes.byref(h), ctypes.byref(g)))
+        return int(w.value), int(h.value), int(g.value)
+
+    def tiling(self):
+        w, h, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.nbv_get_tiling(self._h, ctypes.byref(w), ctypes.byref(h), ctypes.byref(g)))
+        return int(w.value), int(h.value), int(g.value)
 
     def launch_count(self) -> int:
         return int(self.lib.nbv_launch_count(self._h))

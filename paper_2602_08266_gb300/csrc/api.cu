@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "nbv_internal.cuh"
@@ -24,6 +27,8 @@ struct nbv_ctx {
   Consts c;
   cudaStream_t st = nullptr;
   cudaStream_t cap_st = nullptr;   // private stream on which graphs are captured
+  int tw = 16, th = 16;            // screen tile (16 x 16 or 32 x 8)
+  int stage = 32;                  // Gaussians staged per round in the compositing kernel
   int device = 0;
   std::string err;
   bool cuda_dead = false;
@@ -158,7 +163,7 @@ bool finite_cam(const nbv_camera& c) {
          c.height <= 16384;
 }
 
-DevCam to_dev(const nbv_camera& c) {
+DevCam to_dev(const nbv_camera& c, int tw, int th) {
   DevCam d;
   for (int i = 0; i < 9; ++i) d.R[i] = c.R[i];
   for (int i = 0; i < 3; ++i) d.t[i] = c.t[i];
@@ -167,7 +172,7 @@ DevCam to_dev(const nbv_camera& c) {
     d.campos[i] = (float)(-((double)c.R[i] * c.t[0] + (double)c.R[3 + i] * c.t[1] +
                             (double)c.R[6 + i] * c.t[2]));
   d.W = c.width; d.H = c.height;
-  d.TW = kTile; d.TH = kTile;
+  d.TW = tw; d.TH = th;
   d.GX = (c.width + d.TW - 1) / d.TW;
   d.GY = (c.height + d.TH - 1) / d.TH;
   return d;
@@ -225,7 +230,7 @@ struct Phase {
 int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, float* depth,
                 float* alpha, float* obj, bool keep_lists = false) {
   cudaStream_t st = ctx->st;
-  const DevCam dc = to_dev(cam);
+  const DevCam dc = to_dev(cam, ctx->tw, ctx->th);
   const int ntiles = dc.GX * dc.GY;
   DevScene s = dev_scene(ctx);
   {
@@ -278,7 +283,7 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
   a.stats = ctx->prof ? ctx->d_stats : nullptr;
   if (blocks || rgb || depth || alpha || obj) {
     Phase ph(ctx, NBV_PHASE_COMPOSITE);
-    CKR(check_launch(ctx, launch_composite(a, ctx->c, st)));
+    CKR(check_launch(ctx, launch_composite(a, ctx->c, st, ctx->stage)));
     ctx->composite_launches++;
   }
   (void)keep_lists;
@@ -290,7 +295,7 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
 int view_gains(nbv_ctx* ctx, const nbv_camera& cam, const float* blocks, float* delta, double* out3) {
   Phase ph(ctx, NBV_PHASE_GAINS);
   int used = 0;
-  CKR(check_launch(ctx, launch_view_gains(dev_scene(ctx), ctx->c, to_dev(cam), blocks, ctx->F, delta,
+  CKR(check_launch(ctx, launch_view_gains(dev_scene(ctx), ctx->c, to_dev(cam, ctx->tw, ctx->th), blocks, ctx->F, delta,
                                           ctx->partial, ctx->partial_cap, &used, ctx->st)));
   CKR(check_launch(ctx, launch_reduce_gains(ctx->partial, used, out3, ctx->st)));
   return NBV_OK;
@@ -342,7 +347,7 @@ int batched_setup(nbv_ctx* ctx) {
   std::vector<uint32_t> base(nv);
   int64_t nt = 0;
   for (int v = 0; v < nv; ++v) {
-    hc[v] = to_dev(ctx->cand[v]);
+    hc[v] = to_dev(ctx->cand[v], ctx->tw, ctx->th);
     base[v] = (uint32_t)nt;
     nt += (int64_t)hc[v].GX * hc[v].GY;
   }
@@ -427,7 +432,7 @@ int batched_sequence(nbv_ctx* ctx) {
     CK(cudaMemsetAsync(B.counter, 0, sizeof(int), st));
     if (ctx->prof) ctx->composite_launches++;
     CompositeArgs a{};
-    a.cam = B.nv > 0 ? to_dev(ctx->cand[0]) : DevCam{};
+    a.cam = B.nv > 0 ? to_dev(ctx->cand[0], ctx->tw, ctx->th) : DevCam{};
     a.r0 = B.pr.r0; a.r1 = B.pr.r1; a.r2 = B.pr.r2;
     a.p = ctx->p;
     a.vals = svals;
@@ -442,7 +447,7 @@ int batched_sequence(nbv_ctx* ctx) {
     a.tile_base = B.tile_base;
     a.cams = B.cams;
     a.n = n;
-    CKR(check_launch(ctx, launch_composite(a, ctx->c, st)));   // records of view v start at slot v n
+    CKR(check_launch(ctx, launch_composite(a, ctx->c, st, ctx->stage)));   // records of view v start at slot v n
   }
   {
     Phase ph(ctx, NBV_PHASE_GAINS);
@@ -547,14 +552,16 @@ void nbv_config_default(nbv_config* cfg, int K, int sh_degree) {
   cfg->tile_w = 16;
   cfg->tile_h = 16;
   cfg->batched = 0;
+  cfg->stage = 32;
 }
 
 int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   if (!cfg || !out) return NBV_ERR_ARG;
   *out = nullptr;
-  if (cfg->K < 1 || cfg->K > kMaxK || cfg->sh_degree < 0 || cfg->sh_degree > 3 || cfg->tile_w != 16 ||
-      cfg->tile_h != 16)
-    return NBV_ERR_ARG;
+  const bool tile_ok = (cfg->tile_w == 16 && cfg->tile_h == 16) || (cfg->tile_w == 32 && cfg->tile_h == 8) ||
+                       (cfg->tile_w == 0 && cfg->tile_h == 0);
+  if (cfg->K < 1 || cfg->K > kMaxK || cfg->sh_degree < 0 || cfg->sh_degree > 3 || !tile_ok) return NBV_ERR_ARG;
+  if (cfg->stage != 16 && cfg->stage != 32) return NBV_ERR_ARG;
   const float fl[] = {cfg->alpha_obj, cfg->alpha_opa, cfg->beta_d, cfg->beta_o, cfg->lambda_damp,
                       cfg->near_z, cfg->alpha_min, cfg->alpha_max, cfg->t_min, cfg->dilation, cfg->guard};
   for (float v : fl)
@@ -571,6 +578,8 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   c.lam = cfg->lambda_damp; c.near_z = cfg->near_z; c.alpha_min = cfg->alpha_min;
   c.alpha_max = cfg->alpha_max; c.t_min = cfg->t_min; c.dilation = cfg->dilation; c.guard = cfg->guard;
   ctx->nB = block_floats(c.K);
+  if (cfg->tile_w != 0) { ctx->tw = cfg->tile_w; ctx->th = cfg->tile_h; }
+  ctx->stage = cfg->stage;
   ctx->nBp = (ctx->nB + 3) & ~3;
   ctx->st = static_cast<cudaStream_t>(cuda_stream);
   if (cudaGetDevice(&ctx->device) != cudaSuccess ||
@@ -675,7 +684,12 @@ static int set_views(nbv_ctx* ctx, int n, const nbv_camera* cams, std::vector<nb
   return NBV_OK;
 }
 
+static bool same_views(const std::vector<nbv_camera>& a, int n, const nbv_camera* cams) {
+  return (int)a.size() == n && (n == 0 || std::memcmp(a.data(), cams, sizeof(nbv_camera) * n) == 0);
+}
+
 int nbv_set_train_views(nbv_ctx* ctx, int n, const nbv_camera* cams) {
+  if (ctx && same_views(ctx->train, n, cams)) return NBV_OK;
   CKR(set_views(ctx, n, cams, ctx->train));
   batched_drop_graph(ctx);     // the graph reads the training gains buffer
   ctx->prepared = false;
@@ -684,6 +698,7 @@ int nbv_set_train_views(nbv_ctx* ctx, int n, const nbv_camera* cams) {
 }
 
 int nbv_set_candidates(nbv_ctx* ctx, int n, const nbv_camera* cams) {
+  if (ctx && same_views(ctx->cand, n, cams)) return NBV_OK;   // keeps the captured multi-view graph
   CKR(set_views(ctx, n, cams, ctx->cand));
   batched_invalidate(ctx);
   ctx->scored = false;
@@ -705,7 +720,7 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
   }
   CKR(alloc(ctx, &ctx->d_train_cams, (size_t)nt));
   std::vector<DevCam> hc(nt);
-  for (int t = 0; t < nt; ++t) hc[t] = to_dev(ctx->train[t]);
+  for (int t = 0; t < nt; ++t) hc[t] = to_dev(ctx->train[t], ctx->tw, ctx->th);
   CK(cudaMemcpyAsync(ctx->d_train_cams, hc.data(), sizeof(DevCam) * nt, cudaMemcpyHostToDevice, st));
   CKR(grow(ctx, &ctx->train_blocks, &ctx->train_blocks_cap, (size_t)nt * ctx->n * ctx->nBp));
   CK(cudaMemsetAsync(ctx->train_blocks, 0, sizeof(float) * (size_t)nt * ctx->n * ctx->nBp, st));
@@ -820,7 +835,7 @@ int nbv_debug_project(nbv_ctx* ctx, int view_set, int view, int32_t* rect, float
   const std::vector<nbv_camera>& vs = view_set ? ctx->train : ctx->cand;
   if (view < 0 || view >= (int)vs.size()) return fail(ctx, NBV_ERR_ARG, "view out of range");
   cudaStream_t st = ctx->st;
-  CKR(check_launch(ctx, launch_project(dev_scene(ctx), ctx->c, to_dev(vs[view]), ctx->pr, st)));
+  CKR(check_launch(ctx, launch_project(dev_scene(ctx), ctx->c, to_dev(vs[view], ctx->tw, ctx->th), ctx->pr, st)));
   const size_t n = (size_t)ctx->n;
   if (rect) CK(cudaMemcpyAsync(rect, ctx->pr.rect, n * sizeof(int4), cudaMemcpyDeviceToDevice, st));
   if (radius) CK(cudaMemcpyAsync(radius, ctx->pr.radius, n * 4, cudaMemcpyDeviceToDevice, st));
@@ -841,7 +856,7 @@ int nbv_debug_tile_lists(nbv_ctx* ctx, int view_set, int view, int64_t* offsets,
   const int64_t total = (int64_t)*ctx->h_total;
   *count = total;
   if (total > cap || !offsets || !ids) return NBV_OK;
-  const DevCam dc = to_dev(vs[view]);
+  const DevCam dc = to_dev(vs[view], ctx->tw, ctx->th);
   const int ntiles = dc.GX * dc.GY;
   std::vector<uint2> hr(ntiles);
   CK(cudaMemcpyAsync(hr.data(), ctx->sb.ranges, sizeof(uint2) * ntiles, cudaMemcpyDeviceToHost, st));
@@ -896,6 +911,78 @@ int nbv_work_stats(nbv_ctx* ctx, int64_t* out4) {
   out4[0] = (int64_t)h[0]; out4[1] = (int64_t)h[1]; out4[2] = (int64_t)h[2];
   out4[3] = ctx->composite_launches;
   return NBV_OK;
+}
+
+int nbv_get_tiling(const nbv_ctx* ctx, int* tile_w, int* tile_h, int* stage) {
+  if (!ctx) return NBV_ERR_ARG;
+  if (tile_w) *tile_w = ctx->tw;
+  if (tile_h) *tile_h = ctx->th;
+  if (stage) *stage = ctx->stage;
+  return NBV_OK;
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::vector<int>, std::tuple<int, int, int>> g_tune_cache;   // (K, deg, W, H, ...) -> choice
+}  // namespace
+
+int nbv_autotune(nbv_ctx* ctx, int* tile_w, int* tile_h, int* stage) {
+  if (!ctx) return NBV_ERR_ARG;
+  if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
+  if (ctx->n < 1 || ctx->train.empty() || ctx->cand.empty())
+    return fail(ctx, NBV_ERR_STATE, "nbv_autotune needs Gaussians, training and candidate views");
+  std::vector<int> key = {ctx->c.K, ctx->c.deg};
+  for (auto& cm : ctx->cand) { key.push_back(cm.width); key.push_back(cm.height); }
+  const int target = ctx->prepared ? ctx->prepared_target : -1;
+  const bool was_batched = ctx->cfg.batched != 0;
+  int bw = 16, bh = 16, bs = 32;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) { std::tie(bw, bh, bs) = it->second; cached = true; }
+  }
+  if (!cached) {
+    ctx->cfg.batched = 1;
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+    float best = 1e30f;
+    const int shapes[2][2] = {{16, 16}, {32, 8}};
+    const int stages[2] = {32, 16};
+    int rc = NBV_OK;
+    for (int si = 0; si < 2 && rc == NBV_OK; ++si)
+      for (int gi = 0; gi < 2 && rc == NBV_OK; ++gi) {
+        ctx->tw = shapes[si][0]; ctx->th = shapes[si][1]; ctx->stage = stages[gi];
+        batched_invalidate(ctx);
+        rc = nbv_prepare(ctx, target);
+        if (rc == NBV_OK) rc = batched_score(ctx);      // set-up and capture
+        if (rc == NBV_OK) rc = batched_score(ctx);      // warm replay
+        if (rc != NBV_OK) break;
+        cudaEventRecord(e0, ctx->st);
+        rc = batched_score(ctx);
+        cudaEventRecord(e1, ctx->st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(ctx, NBV_ERR_CUDA, "autotune timing"); break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bw = ctx->tw; bh = ctx->th; bs = ctx->stage; }
+      }
+    ctx->pool.push_back(e0);
+    ctx->pool.push_back(e1);
+    ctx->prof = prof;
+    ctx->cfg.batched = was_batched ? 1 : 0;
+    if (rc != NBV_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = std::make_tuple(bw, bh, bs);
+  }
+  ctx->tw = bw; ctx->th = bh; ctx->stage = bs;
+  batched_invalidate(ctx);
+  ctx->prepared = false;
+  ctx->scored = false;
+  if (tile_w) *tile_w = bw;
+  if (tile_h) *tile_h = bh;
+  if (stage) *stage = bs;
+  return nbv_prepare(ctx, target);
 }
 
 const char* nbv_last_error(const nbv_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }

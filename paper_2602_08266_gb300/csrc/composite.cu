@@ -27,7 +27,6 @@
 namespace nbv {
 namespace {
 
-constexpr int kBatch = 32;   // Gaussians staged in shared memory per round
 
 __device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
@@ -61,20 +60,18 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1
 // An FP32 value rounded to TF32 (kept in an FP32 register / word).
 __device__ __forceinline__ float tf32f(float x) { return __uint_as_float(to_tf32(x)); }
 
-// Row strides (floats) of the per-warp contraction buffers: pixel rows of
-// the scalar vector U (3 + 16 * ceil((K + 5) / 16) used) and of the splat
-// geometry vector V (32 used); both = 8 (mod 32) so that fragment loads hit
-// distinct banks.
+// Per-warp contraction buffers are value-major: element (value s, pixel
+// slot) at s * kCS + slot. With kCS = 36 (= 4 mod 32) the per-pixel stores
+// (one value, 32 slots) and the mma fragment loads (value 4 g + slot t) both
+// hit 32 distinct banks. U needs 3 + 16 * ceil((K + 5) / 16) value rows, V 32.
 __host__ __device__ __forceinline__ int u_tiles(int K) { return (K + 5 + 15) / 16; }
-__host__ __device__ __forceinline__ int u_stride(int K) {
-  const int need = 3 + 16 * u_tiles(K);
-  return ((need - 8 + 31) / 32) * 32 + 8;
-}
-constexpr int kVStride = 40;
+__host__ __device__ __forceinline__ int u_rows(int K) { return 3 + 16 * u_tiles(K); }
+constexpr int kCS = 36;
+constexpr int kVRows = 32;
 
 // One 16x16 tile of one view: both passes. blocks_v is the view's block
 // array (NULL: render only).
-template <int KCM>
+template <int KCM, int kBatch>
 __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const Consts& c, const DevCam& cam,
                                                int tile, uint2 rg, float* blocks_v, size_t rec_off,
                                                unsigned char* smem) {
@@ -91,7 +88,11 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
 
   const int tx = tile % cam.GX, ty = tile / cam.GX;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int px = tx * kTile + (tid % kTile), py = ty * kTile + (tid / kTile);
+  // each warp covers an 8 x 4 pixel block (compact footprints keep more of a
+  // warp's lanes inside a splat); 8 warps tile a 16 x 16 or a 32 x 8 tile
+  const int wq = tid >> 5;
+  const int wx = cam.TW >> 3;                 // 8-wide warp blocks per tile row (2 or 4)
+  const int px = tx * cam.TW + 8 * (wq % wx) + (lane & 7), py = ty * cam.TH + 4 * (wq / wx) + (lane >> 3);
   const bool inside = px < cam.W && py < cam.H;
   const float pxc = fa((float)px, 0.5f), pyc = fa((float)py, 0.5f);
 
@@ -187,10 +188,10 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   // pixels of U_s V_c are the structured block entries: two TF32 tensor-core
   // contractions, D_Q = U[0..16)^T V[0..24) and D_X = U[3..)^T V[24..32).
   const int K = c.K;
-  const int SP = u_stride(K), MTB = u_tiles(K);
-  float* Uw = reinterpret_cast<float*>(touched + kBatch) + (size_t)(tid >> 5) * 32 * (SP + kVStride);
-  float* Vw = Uw + 32 * SP;
-  for (int i = lane; i < 32 * (SP + kVStride); i += 32) Uw[i] = 0.0f;
+  const int NU = u_rows(K), MTB = u_tiles(K);
+  float* Uw = reinterpret_cast<float*>(touched + kBatch) + (size_t)(tid >> 5) * kCS * (NU + kVRows);
+  float* Vw = Uw + kCS * NU;
+  for (int i = lane; i < kCS * (NU + kVRows); i += 32) Uw[i] = 0.0f;
   __syncwarp();
   constexpr int MTBM = (KCM + 4 + 15) / 16;
   const int gq = lane >> 2, t4 = lane & 3;
@@ -253,12 +254,11 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       const int nks = (nact + 7) >> 3;
       const int slot = __popc(any & ((1u << lane) - 1u));
       if (lane >= nact && lane < 8 * nks) {       // rows past the last active pixel: zero U
-        float* Uz = Uw + lane * SP;
-        for (int i = 0; i < 8 + K; ++i) Uz[i] = 0.0f;
+        for (int i = 0; i < 8 + K; ++i) Uw[i * kCS + lane] = 0.0f;
       }
       if (act) {
-        float* Ur = Uw + slot * SP;
-        float* Vr = Vw + slot * kVStride;
+        float* Ur = Uw + slot;           // value s at Ur[s * kCS]
+        float* Vr = Vw + slot;
         const bool clamped = pw >= a0.w;
         const float alpha = clamped ? c.alpha_max : a1.w * expf(pw);
         const float inv_om = 1.0f / (1.0f - alpha);
@@ -279,15 +279,18 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
           if (k < KC) {
             const float sk = Ti * pj[k] - Ro[k] * inv_om;
             qo += sk * sk;
-            Ur[6 + k] = tf32f(wa * (sk - s0v));
+            Ur[(6 + k) * kCS] = tf32f(wa * (sk - s0v));
           }
         }
         const float ae2 = ae * ae;
         Ur[0] = tf32f((sr0 * sr0 + sr1 * sr1 + sr2 * sr2) * ae2);
-        Ur[1] = tf32f(sd * sd * ae2);
-        Ur[2] = tf32f(qo * ae2);
-        Ur[3] = tf32f(wa * sr0); Ur[4] = tf32f(wa * sr1); Ur[5] = tf32f(wa * sr2); Ur[6] = tf32f(wa * sd);
-        Ur[7 + K] = tf32f(w * w);
+        Ur[kCS] = tf32f(sd * sd * ae2);
+        Ur[2 * kCS] = tf32f(qo * ae2);
+        Ur[3 * kCS] = tf32f(wa * sr0);
+        Ur[4 * kCS] = tf32f(wa * sr1);
+        Ur[5 * kCS] = tf32f(wa * sr2);
+        Ur[6 * kCS] = tf32f(wa * sd);
+        Ur[(7 + K) * kCS] = tf32f(w * w);
         // splat geometry at this pixel
         const float dx = a0.x - pxc, dy = a0.y - pyc;
         const float v[6] = {-(a1.x * dx + a1.y * dy), -(a1.y * dx + a1.z * dy), -0.5f * dx * dx,
@@ -295,10 +298,10 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
 #pragma unroll
-          for (int n = 0; n <= m; ++n) Vr[m * (m + 1) / 2 + n] = tf32f(v[m] * v[n]);
-          Vr[24 + m] = tf32f(v[m]);
+          for (int n = 0; n <= m; ++n) Vr[(m * (m + 1) / 2 + n) * kCS] = tf32f(v[m] * v[n]);
+          Vr[(24 + m) * kCS] = tf32f(v[m]);
         }
-        Vr[30] = 1.0f;
+        Vr[30 * kCS] = 1.0f;
         // extend the suffix sums with this splat and step T back
         Rr0 += w * a2.x; Rr1 += w * a2.y; Rr2 += w * a2.z; Rd += w * a2.w;
 #pragma unroll
@@ -313,20 +316,23 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       for (int q = 0; q < 3; ++q) dq[q][0] = dq[q][1] = dq[q][2] = dq[q][3] = 0.0f;
 #pragma unroll
       for (int q = 0; q < MTBM; ++q) dxo[q][0] = dxo[q][1] = dxo[q][2] = dxo[q][3] = 0.0f;
+      const uint32_t* Ub = reinterpret_cast<const uint32_t*>(Uw);
+      const uint32_t* Vb = reinterpret_cast<const uint32_t*>(Vw);
       for (int ks = 0; ks < nks; ++ks) {
-        const uint32_t* u0 = reinterpret_cast<const uint32_t*>(Uw + (8 * ks + t4) * SP);
-        const uint32_t* u1 = u0 + 4 * SP;
-        const uint32_t* w0 = reinterpret_cast<const uint32_t*>(Vw + (8 * ks + t4) * kVStride);
-        const uint32_t* w1 = w0 + 4 * kVStride;
-        const uint32_t qa0 = u0[gq], qa1 = u0[gq + 8], qa2 = u1[gq], qa3 = u1[gq + 8];
+        const int c0 = 8 * ks + t4, c1 = c0 + 4;          // pixel slots of this lane's fragments
+        const uint32_t qa0 = Ub[gq * kCS + c0], qa1 = Ub[(gq + 8) * kCS + c0];
+        const uint32_t qa2 = Ub[gq * kCS + c1], qa3 = Ub[(gq + 8) * kCS + c1];
 #pragma unroll
-        for (int nt = 0; nt < 3; ++nt) mma_tf32(dq[nt], qa0, qa1, qa2, qa3, w0[8 * nt + gq], w1[8 * nt + gq]);
-        const uint32_t xb0 = w0[24 + gq], xb1 = w1[24 + gq];
+        for (int nt = 0; nt < 3; ++nt)
+          mma_tf32(dq[nt], qa0, qa1, qa2, qa3, Vb[(8 * nt + gq) * kCS + c0], Vb[(8 * nt + gq) * kCS + c1]);
+        const uint32_t xb0 = Vb[(24 + gq) * kCS + c0], xb1 = Vb[(24 + gq) * kCS + c1];
 #pragma unroll
         for (int mt = 0; mt < MTBM; ++mt)
-          if (mt < MTB)
-            mma_tf32(dxo[mt], u0[3 + 16 * mt + gq], u0[3 + 16 * mt + gq + 8], u1[3 + 16 * mt + gq],
-                     u1[3 + 16 * mt + gq + 8], xb0, xb1);
+          if (mt < MTB) {
+            const int r = 3 + 16 * mt + gq;
+            mma_tf32(dxo[mt], Ub[r * kCS + c0], Ub[(r + 8) * kCS + c0], Ub[r * kCS + c1], Ub[(r + 8) * kCS + c1],
+                     xb0, xb1);
+          }
       }
       __syncwarp();
       // scatter the needed entries of D into the tile's block of splat j
@@ -355,12 +361,12 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   }
 }
 
-template <int KCM>
+template <int KCM, int kBatch>
 __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
     k_composite(CompositeArgs args, Consts c) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (args.queue == nullptr) {                 // one tile of one view per block
-    composite_tile<KCM>(args, c, args.cam, blockIdx.x, args.ranges[blockIdx.x], args.blocks, 0, smem);
+    composite_tile<KCM, kBatch>(args, c, args.cam, blockIdx.x, args.ranges[blockIdx.x], args.blocks, 0, smem);
     return;
   }
   // persistent: (view, tile) items in queue order (longest lists first)
@@ -374,49 +380,56 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
     const uint32_t gt = args.queue[it];
     const int v = args.tile_view[gt];
     const DevCam cam = args.cams[v];
-    composite_tile<KCM>(args, c, cam, (int)(gt - args.tile_base[v]), args.ranges[gt],
+    composite_tile<KCM, kBatch>(args, c, cam, (int)(gt - args.tile_base[v]), args.ranges[gt],
                         args.blocks + (size_t)v * args.n * ((args.nB + 3) & ~3), (size_t)v * args.n, smem);
   }
 }
 
-template <int KCM>
+template <int KCM, int kBatch>
 int launch_k(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
   const int nBp = (a.nB + 3) & ~3;
   const size_t sm = sizeof(float4) * 3 * kBatch + sizeof(int) * kBatch +
                     sizeof(float) * (size_t)kBatch * c.KC + sizeof(float) * (size_t)kBatch * nBp +
                     sizeof(int) * kBatch +
-                    sizeof(float) * (kTilePix / 32) * 32 * (size_t)(u_stride(c.K) + kVStride);
+                    sizeof(float) * (kTilePix / 32) * kCS * (size_t)(u_rows(c.K) + kVRows);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_composite<KCM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_composite<KCM, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   if (a.queue) {
     int per_sm = 1, dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<KCM>, kTilePix, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<KCM, kBatch>, kTilePix, sm);
     if (per_sm < 1) per_sm = 1;
     int grid = nsm * per_sm;
     if (grid > a.n_items) grid = a.n_items;
     if (grid <= 0) return 0;
-    k_composite<KCM><<<grid, kTilePix, sm, st>>>(a, c);
+    k_composite<KCM, kBatch><<<grid, kTilePix, sm, st>>>(a, c);
     return 1;
   }
   const int ntiles = a.cam.GX * a.cam.GY;
   if (ntiles <= 0) return 0;
-  k_composite<KCM><<<ntiles, kTilePix, sm, st>>>(a, c);
+  k_composite<KCM, kBatch><<<ntiles, kTilePix, sm, st>>>(a, c);
   return 1;
 }
 
 }  // namespace
 
-int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
-  if (c.KC <= 8) return launch_k<8>(a, c, st);
-  if (c.KC <= 24) return launch_k<24>(a, c, st);
-  if (c.KC <= 40) return launch_k<40>(a, c, st);
-  if (c.KC <= 72) return launch_k<72>(a, c, st);
-  return launch_k<128>(a, c, st);
+int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage) {
+  if (stage == 16) {
+    if (c.KC <= 8) return launch_k<8, 16>(a, c, st);
+    if (c.KC <= 24) return launch_k<24, 16>(a, c, st);
+    if (c.KC <= 40) return launch_k<40, 16>(a, c, st);
+    if (c.KC <= 72) return launch_k<72, 16>(a, c, st);
+    return launch_k<128, 16>(a, c, st);
+  }
+  if (c.KC <= 8) return launch_k<8, 32>(a, c, st);
+  if (c.KC <= 24) return launch_k<24, 32>(a, c, st);
+  if (c.KC <= 40) return launch_k<40, 32>(a, c, st);
+  if (c.KC <= 72) return launch_k<72, 32>(a, c, st);
+  return launch_k<128, 32>(a, c, st);
 }
 
 }  // namespace nbv

@@ -138,7 +138,8 @@ struct CompositeArgs {
   const DevCam* cams;          // per view
   int64_t n;                   // Gaussians (stride of the per-view block arrays)
 };
-int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st);
+// stage = Gaussians staged in shared memory per round (16 or 32).
+int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage = 32);
 
 struct Factors {
   float* L[3];        // packed lower-triangle Cholesky factor of the scaled H, per output

@@ -36,13 +36,13 @@ def test_config_defaults_are_the_papers():
     assert abs(cfg.alpha_obj - 0.3) < 1e-7 and abs(cfg.alpha_opa - 0.3) < 1e-7
     assert cfg.beta_d == 10.0 and cfg.beta_o == 1.0
     assert abs(cfg.alpha_min - 1 / 255) < 1e-9 and abs(cfg.t_min - 1e-4) < 1e-10
-    assert cfg.tile_w == 16 and cfg.tile_h == 16
+    assert cfg.tile_w == 16 and cfg.tile_h == 16 and cfg.stage == 32 and cfg.batched == 0
 
 
 def test_create_rejects_bad_config_without_gpu():
     P.build()
     lib = P.load_library()
-    for kw in (dict(K=0), dict(sh_degree=4), dict(tile_w=8), dict(lambda_damp=0.0),
+    for kw in (dict(K=0), dict(sh_degree=4), dict(tile_w=8), dict(tile_w=32), dict(stage=24), dict(lambda_damp=0.0),
                dict(alpha_max=1.0)):
         cfg = P.config_default(4, 0)
         for k, v in kw.items():

@@ -311,3 +311,67 @@ def test_batched_matches_per_view_scene_scale_and_recaptures(P):
     b.set_candidates(wl.cand.subset(np.arange(8)))
     gc = b.score_host().astype(np.float64)
     np.testing.assert_allclose(gc, ga[:8], rtol=1e-4)
+
+
+# ------------------------------------------------- tile shape / stage depth
+@pytest.mark.parametrize("batched", [0, 1])
+def test_tile_32x8_parity_tiny(P, batched):
+    """32 x 8 screen tiles: keys, tile lists and renders against the oracle
+    run with the same tile shape (ragged grids), and IG on both paths."""
+    wl = S.make_workload("tiny")
+    wl.cand = _mixed(wl)
+    sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, tile_w=32, tile_h=8, batched=batched)
+    sc.load_scene(wl.scene)
+    sc.set_train_views(wl.train)
+    sc.set_candidates(wl.cand)
+    assert sc.tiling()[:2] == (32, 8)
+    o = O.OracleScene(wl.scene, hyper=O.Hyper(tile_w=32, tile_h=8))
+    for v in range(wl.cand.n):
+        g = sc.debug_project(0, v)
+        r = o.project32(wl.cand, v)
+        np.testing.assert_array_equal(g["rect"].cpu().numpy(), r["rect"])
+        off, ids = sc.debug_tile_lists(0, v)
+        ooff, oids = o.tile_lists(wl.cand, v)
+        np.testing.assert_array_equal(off.cpu().numpy(), ooff)
+        np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+        _compare_render(sc, o, wl.cand, v, wl.scene.K)
+    sc.prepare(-1)
+    ref = o.score(wl.train, wl.cand)
+    for _ in range(2):
+        _check_scores(sc.score_host().astype(np.float64), ref, sc.train_gains().astype(np.float64))
+
+
+def test_stage_depth_changes_nothing_but_speed(P):
+    """Staging 16 instead of 32 Gaussians per shared-memory round leaves the
+    gains equal up to float summation order."""
+    wl = S.make_workload("scene", n_views=6, scale=0.05)
+    out = []
+    for stage in (32, 16):
+        sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=1, stage=stage)
+        sc.load_scene(wl.scene)
+        sc.set_train_views(wl.train)
+        sc.set_candidates(wl.cand)
+        assert sc.tiling()[2] == stage
+        sc.prepare(-1)
+        out.append(sc.score_host().astype(np.float64))
+        sc.close()
+    np.testing.assert_allclose(out[1], out[0], rtol=1e-4)
+
+
+def test_autotune_picks_a_valid_tiling_and_scores_match_oracle(P):
+    wl = S.make_workload("tiny")
+    sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=1)
+    sc.load_scene(wl.scene)
+    sc.set_train_views(wl.train)
+    sc.set_candidates(wl.cand)
+    sc.prepare(-1)
+    tw, th, st = sc.autotune()
+    assert (tw, th) in ((16, 16), (32, 8)) and st in (16, 32)
+    assert sc.tiling() == (tw, th, st)
+    ref = O.OracleScene(wl.scene, hyper=O.Hyper(tile_w=tw, tile_h=th)).score(wl.train, wl.cand)
+    _check_scores(sc.score_host().astype(np.float64), ref, sc.train_gains().astype(np.float64))
+    sc2 = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=1)   # cached choice
+    sc2.load_scene(wl.scene)
+    sc2.set_train_views(wl.train)
+    sc2.set_candidates(wl.cand)
+    assert sc2.autotune() == (tw, th, st)
