@@ -452,8 +452,10 @@ int batched_sequence(nbv_ctx* ctx) {
   {
     Phase ph(ctx, NBV_PHASE_GAINS);
     int nparts = 0;
-    CKR(check_launch(ctx, launch_views_gains(s, ctx->c, B.cams, nv, B.blocks, ctx->F, B.partial, B.parts_cap,
-                                             &nparts, st)));
+    int r = launch_views_gains_gm(s, ctx->c, B.cams, nv, B.blocks, ctx->F, B.partial, B.parts_cap, &nparts, st);
+    if (r < 0)
+      r = launch_views_gains(s, ctx->c, B.cams, nv, B.blocks, ctx->F, B.partial, B.parts_cap, &nparts, st);
+    CKR(check_launch(ctx, r));
     CKR(check_launch(ctx, launch_reduce_gains_views(B.partial, nparts, nv, ctx->ig_cand, st)));
   }
   {
@@ -515,7 +517,6 @@ int ensure_scene_buffers(nbv_ctx* ctx, int64_t n) {
     const int l = f == 0 ? kNG + 3 * nb : (f == 1 ? kNG : kNG + KC);
     ctx->F.l[f] = l;
     CKR(alloc(ctx, &ctx->F.L[f], (size_t)n * l * (l + 1) / 2));
-    CKR(alloc(ctx, &ctx->F.dinv[f], (size_t)n * l));
   }
   ctx->partial_cap = 152 * 16;    // blocks; up to 8 warp partial sums each
   CKR(alloc(ctx, &ctx->partial, (size_t)ctx->partial_cap * 8 * 3));
@@ -605,7 +606,7 @@ void nbv_destroy(nbv_ctx* ctx) {
                   ctx->sb.keys[1], ctx->sb.vals[0], ctx->sb.vals[1], ctx->sb.offsets, ctx->sb.scan_tmp,
                   ctx->sb.hist, ctx->sb.ranges, ctx->blocks, ctx->train_blocks, ctx->partial,
                   ctx->ig_train, ctx->ig_cand, ctx->out4, ctx->d_flags, ctx->d_best_score, ctx->d_err,
-                  ctx->F.L[0], ctx->F.L[1], ctx->F.L[2], ctx->F.dinv[0], ctx->F.dinv[1], ctx->F.dinv[2]};
+                  ctx->F.L[0], ctx->F.L[1], ctx->F.L[2]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->d_stats) cudaFree(ctx->d_stats);

@@ -63,8 +63,9 @@ __device__ __forceinline__ SHC shc() {
 }
 
 // Real SH values and gradients (of the polynomial forms) at direction (x,y,z).
-__device__ void sh_val_grad(int deg, float x, float y, float z, float* Y, float (*G)[3]) {
+__device__ __forceinline__ void sh_val_grad(int deg, float x, float y, float z, float* Y, float (*G)[3]) {
   const SHC k = shc();
+#pragma unroll
   for (int i = 0; i < 16; ++i) { Y[i] = 0.0f; G[i][0] = G[i][1] = G[i][2] = 0.0f; }
   Y[0] = k.c0;
   if (deg < 1) return;
@@ -99,18 +100,25 @@ __device__ void sh_val_grad(int deg, float x, float y, float z, float* Y, float 
 }
 
 // Projection Jacobians of Gaussian g in view cam (values in single precision).
-__device__ void compute_gjac(const DevScene& s, const Consts& c, const DevCam& cam, int64_t g,
-                             GJac& J) {
+// DEG >= 0 fixes the SH degree at compile time (everything stays in
+// registers); DEG = -1 reads it from c.
+template <int DEG>
+__device__ __forceinline__ void compute_gjac_t(const DevScene& s, const Consts& c, const DevCam& cam, int64_t g,
+                                               GJac& J) {
+  const int deg = DEG >= 0 ? DEG : c.deg;
+  const int nb = (deg + 1) * (deg + 1);
   const float4 ms = s.mu_sig[g], ss = s.scale_skip[g], qq = s.qn[g], ax = s.aux[g];
   const float* R = cam.R;
   const float mu[3] = {ms.x, ms.y, ms.z};
   float tc[3];
+#pragma unroll
   for (int i = 0; i < 3; ++i) tc[i] = R[3 * i] * mu[0] + R[3 * i + 1] * mu[1] + R[3 * i + 2] * mu[2] + cam.t[i];
   const float x = tc[0], y = tc[1], z = tc[2];
   const float iz = 1.0f / z, iz2 = iz * iz;
   // mean: d(mx,my)/d t, then * R
   const float dmx[3] = {cam.fx * iz, 0.0f, -cam.fx * x * iz2};
   const float dmy[3] = {0.0f, cam.fy * iz, -cam.fy * y * iz2};
+#pragma unroll
   for (int m = 0; m < 3; ++m) {
     J.Jm[0][m] = dmx[0] * R[m] + dmx[1] * R[3 + m] + dmx[2] * R[6 + m];
     J.Jm[1][m] = dmy[0] * R[m] + dmy[1] * R[3 + m] + dmy[2] * R[6 + m];
@@ -125,6 +133,7 @@ __device__ void compute_gjac(const DevScene& s, const Consts& c, const DevCam& c
   const float j00 = cam.fx * iz, j02 = -cam.fx * xz * iz;
   const float j11 = cam.fy * iz, j12 = -cam.fy * yz * iz;
   float T0[3], T1[3];
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     T0[i] = j00 * R[i] + j02 * R[6 + i];
     T1[i] = j11 * R[3 + i] + j12 * R[6 + i];
@@ -144,11 +153,14 @@ __device__ void compute_gjac(const DevScene& s, const Consts& c, const DevCam& c
                        2.0f * (qx * qz - qw * qy), 2.0f * (qy * qz + qw * qx), 1.0f - 2.0f * (qx * qx + qy * qy)};
   const float s2[3] = {ss.x * ss.x, ss.y * ss.y, ss.z * ss.z};
   float S3[9];
+#pragma unroll
   for (int i = 0; i < 3; ++i)
+#pragma unroll
     for (int j = 0; j < 3; ++j)
       S3[3 * i + j] = Rq[3 * i] * s2[0] * Rq[3 * j] + Rq[3 * i + 1] * s2[1] * Rq[3 * j + 1] +
                       Rq[3 * i + 2] * s2[2] * Rq[3 * j + 2];
   float ST0[3], ST1[3];  // Sigma3 T0^T, Sigma3 T1^T
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
     ST0[i] = S3[3 * i] * T0[0] + S3[3 * i + 1] * T0[1] + S3[3 * i + 2] * T0[2];
     ST1[i] = S3[3 * i] * T1[0] + S3[3 * i + 1] * T1[1] + S3[3 * i + 2] * T1[2];
@@ -166,8 +178,10 @@ __device__ void compute_gjac(const DevScene& s, const Consts& c, const DevCam& c
   };
   // w.r.t. camera-space t, then mu
   float dabc_t[3][3];
+#pragma unroll
   for (int n = 0; n < 3; ++n) {
     float dT0[3], dT1[3];
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
       dT0[i] = dj00[n] * R[i] + dj02[n] * R[6 + i];
       dT1[i] = dj11[n] * R[3 + i] + dj12[n] * R[6 + i];
@@ -178,18 +192,23 @@ __device__ void compute_gjac(const DevScene& s, const Consts& c, const DevCam& c
     const float dc = 2.0f * (dT1[0] * ST1[0] + dT1[1] * ST1[1] + dT1[2] * ST1[2]);
     dconic(da, db, dc, dabc_t[n]);
   }
+#pragma unroll
   for (int m = 0; m < 3; ++m)
+#pragma unroll
     for (int e = 0; e < 3; ++e)
       J.Jc[e][m] = dabc_t[0][e] * R[m] + dabc_t[1][e] * R[3 + m] + dabc_t[2][e] * R[6 + m];
   // w.r.t. log-scales: dSigma3 = 2 s_k^2 r_k r_k^T
   float u0[3], u1[3];   // T0 . r_k, T1 . r_k
+#pragma unroll
   for (int k = 0; k < 3; ++k) {
     u0[k] = T0[0] * Rq[k] + T0[1] * Rq[3 + k] + T0[2] * Rq[6 + k];
     u1[k] = T1[0] * Rq[k] + T1[1] * Rq[3 + k] + T1[2] * Rq[6 + k];
   }
+#pragma unroll
   for (int k = 0; k < 3; ++k) {
     float o[3];
     dconic(2.0f * s2[k] * u0[k] * u0[k], 2.0f * s2[k] * u0[k] * u1[k], 2.0f * s2[k] * u1[k] * u1[k], o);
+#pragma unroll
     for (int e = 0; e < 3; ++e) J.Jc[e][3 + k] = o[e];
   }
   // w.r.t. the normalised quaternion, then the raw one
@@ -199,13 +218,16 @@ __device__ void compute_gjac(const DevScene& s, const Consts& c, const DevCam& c
       {-4.0f * qy, 2.0f * qx, 2.0f * qw, 2.0f * qx, 0.0f, 2.0f * qz, -2.0f * qw, 2.0f * qz, -4.0f * qy},
       {-4.0f * qz, -2.0f * qw, 2.0f * qx, 2.0f * qw, -4.0f * qz, 2.0f * qy, 2.0f * qx, 2.0f * qy, 0.0f}};
   float dq_hat[4][3];
+#pragma unroll
   for (int e = 0; e < 4; ++e) {
     float v0[3], v1[3];
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
       v0[k] = T0[0] * dR[e][k] + T0[1] * dR[e][3 + k] + T0[2] * dR[e][6 + k];
       v1[k] = T1[0] * dR[e][k] + T1[1] * dR[e][3 + k] + T1[2] * dR[e][6 + k];
     }
     float da = 0.0f, db = 0.0f, dc = 0.0f;
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
       da += 2.0f * v0[k] * s2[k] * u0[k];
       db += s2[k] * (v0[k] * u1[k] + u0[k] * v1[k]);
@@ -215,9 +237,12 @@ __device__ void compute_gjac(const DevScene& s, const Consts& c, const DevCam& c
   }
   const float qh[4] = {qw, qx, qy, qz};
   const float inv_n = 1.0f / ax.z;
+#pragma unroll
   for (int i = 0; i < 4; ++i)
+#pragma unroll
     for (int e3 = 0; e3 < 3; ++e3) {
       float acc = 0.0f;
+#pragma unroll
       for (int e = 0; e < 4; ++e) acc += ((e == i ? 1.0f : 0.0f) - qh[e] * qh[i]) * inv_n * dq_hat[e][e3];
       J.Jc[e3][6 + i] = acc;
     }
@@ -227,19 +252,26 @@ __device__ void compute_gjac(const DevScene& s, const Consts& c, const DevCam& c
   const float il = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
   const float d[3] = {dv[0] * il, dv[1] * il, dv[2] * il};
   float G[16][3];
-  sh_val_grad(c.deg, d[0], d[1], d[2], J.Y, G);
-  const float* shg = s.sh + (size_t)g * c.nb * 3;
+  sh_val_grad(deg, d[0], d[1], d[2], J.Y, G);
+  const float* shg = s.sh + (size_t)g * nb * 3;
+#pragma unroll
   for (int ch = 0; ch < 3; ++ch) {
     float val = 0.5f, gr[3] = {0.0f, 0.0f, 0.0f};
-    for (int k = 0; k < c.nb; ++k) {
+#pragma unroll
+    for (int k = 0; k < nb; ++k) {
       const float co = shg[3 * k + ch];
       val += J.Y[k] * co;
       gr[0] += G[k][0] * co; gr[1] += G[k][1] * co; gr[2] += G[k][2] * co;
     }
     J.live[ch] = val < 0.0f ? 0.0f : 1.0f;
     const float gd = gr[0] * d[0] + gr[1] * d[1] + gr[2] * d[2];
+#pragma unroll
     for (int m = 0; m < 3; ++m) J.Jrgb[ch][m] = J.live[ch] * (gr[m] - gd * d[m]) * il;
   }
+}
+
+__device__ void compute_gjac(const DevScene& s, const Consts& c, const DevCam& cam, int64_t g, GJac& J) {
+  compute_gjac_t<-1>(s, c, cam, g, J);
 }
 
 __host__ __device__ __forceinline__ int out_l(int f, const Consts& c) {
@@ -275,7 +307,7 @@ __device__ void build_M(int f, const GJac& J, const Consts& c, const float* p, f
 }
 
 // Dense B (u x u) of output f from the structured block.
-__device__ void build_B(int f, const float* blk, const Consts& c, float* Bm, int lane) {
+__device__ __forceinline__ void build_B(int f, const float* blk, const Consts& c, float* Bm, int lane) {
   const int u = out_u(f, c);
   const int qoff = f == 0 ? kOffQrgb : (f == 1 ? kOffQd : kOffQo);
   const float W2 = blk[kOffW2];
@@ -360,13 +392,10 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
         }
       }
       float* Lg = F.L[f] + (size_t)g * nt;
-      float* dg = F.dinv[f] + (size_t)g * l;
       // damping and Jacobi scaling, in double
       for (int i = lane; i < l; i += 32) {
         const double hii = (double)c.lam + (double)cg * (double)Hf[tri(i, i)];
-        const double di = 1.0 / sqrt(hii);
-        dsc[i] = di;
-        dg[i] = (float)di;
+        dsc[i] = 1.0 / sqrt(hii);
       }
       __syncwarp();
       for (int i = lane; i < nt; i += 32) {
@@ -416,50 +445,54 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
         }
         __syncwarp();
       }
-      for (int i = lane; i < nt; i += 32) Lg[i] = Hf[i];
+      // stored: L~ = L^-1 D^-1/2, so that H^-1 = L~^T L~ and Z = L~ M^T
+      for (int i = lane; i < nt; i += 32) {
+        int r, cc;
+        tri_decode(i, r, cc);
+        Lg[i] = (float)((double)Hf[i] * dsc[cc]);
+      }
       __syncwarp();
     }
   }
 }
 
 // -------------------------------------------------------------- view gains
-// Y = D^-1/2 M^T of output f (l x u, row-major), built by the warp.
-__device__ void build_Y(int f, const GJac& J, const Consts& c, const float* p, const float* dg, float* Y,
-                        int lane) {
+// Y = M^T of output f (l x u, row-major), built by the warp.
+__device__ void build_Y(int f, const GJac& J, const Consts& c, const float* p, float* Y, int lane) {
   const int l = out_l(f, c), u = out_u(f, c);
   for (int i = lane; i < u * l; i += 32) Y[i] = 0.0f;
   __syncwarp();
   if (lane == 0) {
     for (int m = 0; m < 3; ++m) {
-      Y[m * u + 0] = dg[m] * J.Jm[0][m];
-      Y[m * u + 1] = dg[m] * J.Jm[1][m];
+      Y[m * u + 0] = J.Jm[0][m];
+      Y[m * u + 1] = J.Jm[1][m];
     }
     for (int e = 0; e < 3; ++e)
-      for (int k = 0; k < 10; ++k) Y[k * u + 2 + e] = dg[k] * J.Jc[e][k];
-    Y[10 * u + 5] = dg[10] * J.dsig;
+      for (int k = 0; k < 10; ++k) Y[k * u + 2 + e] = J.Jc[e][k];
+    Y[10 * u + 5] = J.dsig;
     if (f == 0) {
       for (int ch = 0; ch < 3; ++ch)
-        for (int m = 0; m < 3; ++m) Y[m * u + 6 + ch] = dg[m] * J.Jrgb[ch][m];
+        for (int m = 0; m < 3; ++m) Y[m * u + 6 + ch] = J.Jrgb[ch][m];
     } else if (f == 1) {
-      for (int m = 0; m < 3; ++m) Y[m * u + 6] = dg[m] * J.Jz[m];
+      for (int m = 0; m < 3; ++m) Y[m * u + 6] = J.Jz[m];
     }
   }
   if (f == 0) {
     for (int i = lane; i < 3 * c.nb; i += 32) {
       const int k = i / 3, ch = i - 3 * k;
-      Y[(kNG + i) * u + 6 + ch] = dg[kNG + i] * J.live[ch] * J.Y[k];
+      Y[(kNG + i) * u + 6 + ch] = J.live[ch] * J.Y[k];
     }
   } else if (f == 2) {
     for (int i = lane; i < c.K * c.KC; i += 32) {   // d p_j / d o_b = p_j (delta_jb - p_b)
       const int j = 1 + i / c.KC, bb = i % c.KC;
-      Y[(kNG + bb) * u + 5 + j] = dg[kNG + bb] * p[j] * ((j == bb ? 1.0f : 0.0f) - p[bb]);
+      Y[(kNG + bb) * u + 5 + j] = p[j] * ((j == bb ? 1.0f : 0.0f) - p[bb]);
     }
   }
   __syncwarp();
 }
 
-// Row i of Z = L^-1 Y for output f with U columns (compile time), using the
-// block sparsity of Y. Ls is L^-1 (packed) in shared memory.
+// Row i of Z = L~ Y for output f with U columns (compile time), using the
+// block sparsity of Y. Ls is L~ (packed lower triangle).
 template <int F, int U>
 __device__ __forceinline__ void z_row(int i, int u, const float* __restrict__ Ls, const float* Y, float* Z) {
   float acc[U];
@@ -495,7 +528,7 @@ __device__ __forceinline__ void z_row(int i, int u, const float* __restrict__ Ls
 }
 
 // log det(I + c W B) for one output; W, B, G are u x u in shared memory.
-__device__ float logdet_IcWB(int u, float cg, const float* W, const float* Bm, float* G, int lane) {
+__device__ __forceinline__ float logdet_IcWB(int u, float cg, const float* W, const float* Bm, float* G, int lane) {
   for (int i = lane; i < u * u; i += 32) {
     const int r = i / u, cc = i - r * u;
     float a = 0.0f;
@@ -542,8 +575,7 @@ __device__ float output_gain(const GJac& J, const Consts& c, const float* p, con
                              float* Bm, float* G, int lane) {
   const int l = out_l(F, c), u = out_u(F, c), nt = l * (l + 1) / 2;
   const float* Lg = Fa.L[F] + (size_t)g * nt;   // rows read straight from global memory (L1)
-  const float* dg = Fa.dinv[F] + (size_t)g * l;
-  build_Y(F, J, c, p, dg, Y, lane);              // ends with __syncwarp
+  build_Y(F, J, c, p, Y, lane);                  // ends with __syncwarp
   for (int i = lane; i < l; i += 32) z_row<F, U>(i, u, Lg, Y, Z);
   __syncwarp();
   for (int i = lane; i < u * (u + 1) / 2; i += 32) {   // W = Z^T Z
@@ -615,6 +647,364 @@ __global__ void __launch_bounds__(128, 3) k_view_gains(DevScene s, Consts c, Dev
   if (lane == 0) {
     double* out = partial + 3 * ((size_t)blockIdx.x * nw + warp);
     out[0] = acc3[0]; out[1] = acc3[1]; out[2] = acc3[2];
+  }
+}
+
+// ------------------------------------ multi-view gains, Gaussian-major
+// One warp per Gaussian and 32 views per pass (lane = view). L~ of the three
+// outputs is staged in the warp's shared memory once per Gaussian and read
+// by broadcast. The colour and depth gains of a (view, Gaussian) run in one
+// lane, in registers:
+//   Z = L~ M^T row by row (M sparse by parameter block), W = Z^T Z,
+//   W = Lw Lw^T (Cholesky; a column with no pivot left is dropped, which
+//   happens exactly when M has a zero row, e.g. a clamped colour channel),
+//   log det(I + c W B) = log det(I + c Lw^T B Lw), the latter SPD with
+//   eigenvalues >= 1, factorised without pivoting; its pivots are 1 + x and
+//   the sum of log1p(x) is the gain.
+// The object gain runs warp-cooperatively per (view, Gaussian): the
+// probability columns of M (d p / d o) do not depend on the view, so
+// Z_p = L~[:, logits] (d p / d o)^T and W_pp = Z_p^T Z_p are formed once per
+// Gaussian; per view only the geometric columns change.
+
+// Packed lower-triangle index with compile-time arguments.
+__host__ __device__ constexpr int ptri(int r, int cc) { return r * (r + 1) / 2 + cc; }
+
+// (Every loop below has a constant trip count, with the triangular bounds
+// as conditions, so that full unrolling leaves only constant indices and the
+// arrays stay in registers.)
+template <int U>
+__device__ __forceinline__ float logdet_lane(float (&Wm)[ptri(U, 0)], const float (&Bm)[ptri(U, 0)], float cg) {
+  // Wm <- Lw (in place)
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    float d = Wm[ptri(j, j)];
+#pragma unroll
+    for (int m = 0; m < U; ++m)
+      if (m < j) d -= Wm[ptri(j, m)] * Wm[ptri(j, m)];
+    const bool live = d > 1e-6f * Wm[ptri(j, j)] && d > 0.0f;
+    const float ljj = live ? sqrtf(d) : 0.0f;
+    const float il = live ? 1.0f / ljj : 0.0f;
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      if (i > j) {
+        float a = Wm[ptri(i, j)];
+#pragma unroll
+        for (int m = 0; m < U; ++m)
+          if (m < j) a -= Wm[ptri(i, m)] * Wm[ptri(j, m)];
+        Wm[ptri(i, j)] = a * il;
+      }
+    }
+    Wm[ptri(j, j)] = ljj;
+  }
+  // X = c Lw^T B Lw (lower triangle), one column of B Lw at a time
+  float X[ptri(U, 0)];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    float t[U];
+#pragma unroll
+    for (int a = 0; a < U; ++a) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int b = 0; b < U; ++b)
+        if (b >= j) acc += (a >= b ? Bm[ptri(a, b)] : Bm[ptri(b, a)]) * Wm[ptri(b, j)];
+      t[a] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      if (i >= j) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < U; ++a)
+          if (a >= i) acc += Wm[ptri(a, i)] * t[a];
+        X[ptri(i, j)] = cg * acc;
+      }
+    }
+  }
+  // Cholesky of I + X with the identity kept apart: pivot = 1 + x
+  float ld = 0.0f;
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    float x = X[ptri(j, j)];
+#pragma unroll
+    for (int m = 0; m < U; ++m)
+      if (m < j) x -= X[ptri(j, m)] * X[ptri(j, m)];
+    x = fmaxf(x, -0.999999f);
+    ld += log1pf(x);
+    const float il = rsqrtf(1.0f + x);
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      if (i > j) {
+        float a = X[ptri(i, j)];
+#pragma unroll
+        for (int m = 0; m < U; ++m)
+          if (m < j) a -= X[ptri(i, m)] * X[ptri(j, m)];
+        X[ptri(i, j)] = a * il;
+      }
+    }
+  }
+  return ld;
+}
+
+// Colour gain of one (view, Gaussian) in one lane. Lt: L~ of the colour
+// output (packed, shared memory, same for every lane).
+template <int DEG>
+__device__ __forceinline__ float rgb_gain_lane(const GJac& J, const float* __restrict__ Lt,
+                                               const float* __restrict__ blk, float cg) {
+  constexpr int NB = (DEG + 1) * (DEG + 1), L = kNG + 3 * NB;
+  float Wm[45];
+#pragma unroll
+  for (int i = 0; i < 45; ++i) Wm[i] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < L; ++i) {
+    const float* Li = Lt + ptri(i, 0);
+    float z[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) z[q] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) {
+      if (k <= i) {
+        const float lk = Li[k];
+        if (k < 3) {
+          z[0] += lk * J.Jm[0][k];
+          z[1] += lk * J.Jm[1][k];
+          z[6] += lk * J.Jrgb[0][k];
+          z[7] += lk * J.Jrgb[1][k];
+          z[8] += lk * J.Jrgb[2][k];
+        }
+        if (k < 10) {
+          z[2] += lk * J.Jc[0][k];
+          z[3] += lk * J.Jc[1][k];
+          z[4] += lk * J.Jc[2][k];
+        } else {
+          z[5] += lk * J.dsig;
+        }
+      }
+    }
+    float sh[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int m = 0; m < NB; ++m)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch)
+        if (kNG + 3 * m + ch <= i) sh[ch] += Li[kNG + 3 * m + ch] * J.Y[m];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) z[6 + ch] += J.live[ch] * sh[ch];
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+      for (int cc = 0; cc < 9; ++cc)
+        if (cc <= r) Wm[ptri(r, cc)] += z[r] * z[cc];
+  }
+  float Bm[45];
+  const float w2 = blk[kOffW2];
+#pragma unroll
+  for (int r = 0; r < 9; ++r)
+#pragma unroll
+    for (int cc = 0; cc < 9; ++cc)
+      if (cc <= r)
+        Bm[ptri(r, cc)] = r < 6 ? blk[kOffQrgb + ptri(r, cc)]
+                                : (cc < 6 ? blk[kOffXrgb + 6 * (r - 6) + cc] : (r == cc ? w2 : 0.0f));
+  return logdet_lane<9>(Wm, Bm, cg);
+}
+
+// Depth gain of one (view, Gaussian) in one lane.
+__device__ __forceinline__ float depth_gain_lane(const GJac& J, const float* __restrict__ Lt,
+                                                 const float* __restrict__ blk, float cg) {
+  float Wm[28];
+#pragma unroll
+  for (int i = 0; i < 28; ++i) Wm[i] = 0.0f;
+#pragma unroll
+  for (int i = 0; i < kNG; ++i) {
+    const float* Li = Lt + ptri(i, 0);
+    float z[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) z[q] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kNG; ++k) {
+      if (k > i) continue;
+      const float lk = Li[k];
+      if (k < 3) {
+        z[0] += lk * J.Jm[0][k];
+        z[1] += lk * J.Jm[1][k];
+        z[6] += lk * J.Jz[k];
+      }
+      if (k < 10) {
+        z[2] += lk * J.Jc[0][k];
+        z[3] += lk * J.Jc[1][k];
+        z[4] += lk * J.Jc[2][k];
+      } else {
+        z[5] += lk * J.dsig;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 7; ++r)
+#pragma unroll
+      for (int cc = 0; cc < 7; ++cc)
+        if (cc <= r) Wm[ptri(r, cc)] += z[r] * z[cc];
+  }
+  float Bm[28];
+#pragma unroll
+  for (int r = 0; r < 7; ++r)
+#pragma unroll
+    for (int cc = 0; cc < 7; ++cc)
+      if (cc <= r) Bm[ptri(r, cc)] = r < 6 ? blk[kOffQd + ptri(r, cc)] : (cc < 6 ? blk[kOffXd + cc] : blk[kOffW2]);
+  return logdet_lane<7>(Wm, Bm, cg);
+}
+
+struct GmLayout {     // per-warp shared memory (floats)
+  int nt0, nt1, nt2;  // packed sizes of L~ per output
+  int l2, u2;         // object output sizes
+  int off_L1, off_L2, off_Yg, off_s, off_Zp, off_Zg, off_W, off_B, off_G, per_warp;
+};
+
+__host__ __device__ inline GmLayout gm_layout(const Consts& c) {
+  GmLayout y{};
+  const int l0 = kNG + 3 * c.nb, l1 = kNG;
+  y.l2 = kNG + c.KC;
+  y.u2 = 6 + c.K;
+  y.nt0 = l0 * (l0 + 1) / 2;
+  y.nt1 = l1 * (l1 + 1) / 2;
+  y.nt2 = y.l2 * (y.l2 + 1) / 2;
+  auto r4 = [](int x) { return (x + 3) & ~3; };
+  y.off_L1 = r4(y.nt0);
+  y.off_L2 = y.off_L1 + r4(y.nt1);
+  y.off_Yg = y.off_L2 + r4(y.nt2);
+  y.off_s = y.off_Yg + 66 * 32;
+  y.off_Zp = y.off_s + r4(y.l2);
+  y.off_Zg = y.off_Zp + r4(y.l2 * c.K);
+  y.off_W = y.off_Zg + r4(y.l2 * 6);
+  y.off_B = y.off_W + r4(y.u2 * y.u2);
+  y.off_G = y.off_B + r4(y.u2 * y.u2);
+  y.per_warp = y.off_G + r4(y.u2 * y.u2);
+  return y;
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256, 1) k_gains_gm(DevScene s, Consts c, const DevCam* __restrict__ cams, int nv,
+                                                    const float* __restrict__ blocks, Factors F,
+                                                    double* __restrict__ partial, int nparts) {
+  extern __shared__ __align__(16) float smf[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const GmLayout y = gm_layout(c);
+  float* base = smf + (size_t)warp * y.per_warp;
+  float* L0 = base;
+  float* L1 = base + y.off_L1;
+  float* L2 = base + y.off_L2;
+  float* Yg = base + y.off_Yg;    // [66][32]: geometric rows of M^T per lane (view)
+  float* srow = base + y.off_s;
+  float* Zp = base + y.off_Zp;    // [l2][K]
+  float* Zg = base + y.off_Zg;    // [l2][6]
+  float* Wo = base + y.off_W;     // [u2][u2]
+  float* Bo = base + y.off_B;
+  float* Go = base + y.off_G;
+  const int nBp = (block_floats(c.K) + 3) & ~3;
+  const int K = c.K, KC = c.KC, l2 = y.l2, u2 = y.u2;
+  const int v0 = 32 * blockIdx.y;
+  const int v = v0 + lane;
+  const bool vok = v < nv;
+  const DevCam* camp = cams + (vok ? v : 0);
+  double acc[3] = {0.0, 0.0, 0.0};
+  const int slot = blockIdx.x * nw + warp;
+  for (int64_t g = slot; g < s.n; g += (int64_t)gridDim.x * nw) {
+    const float cg = s.aux[g].y;
+    if (!(cg > 0.0f)) continue;                        // warp-uniform
+    const float* blk = blocks + ((size_t)v * s.n + g) * nBp;
+    const bool mine = vok && blk[kOffW2] != 0.0f;
+    const unsigned todo_all = __ballot_sync(0xffffffffu, mine);
+    if (todo_all == 0u) continue;
+    // stage L~ of the three outputs
+    {
+      const float* g0 = F.L[0] + (size_t)g * y.nt0;
+      const float* g1 = F.L[1] + (size_t)g * y.nt1;
+      const float* g2 = F.L[2] + (size_t)g * y.nt2;
+      for (int i = lane; i < y.nt0; i += 32) L0[i] = g0[i];
+      for (int i = lane; i < y.nt1; i += 32) L1[i] = g1[i];
+      for (int i = lane; i < y.nt2; i += 32) L2[i] = g2[i];
+    }
+    const float* p = s.p + (size_t)g * KC;
+    __syncwarp();
+    // view-independent object pieces: s_i, Z_p, W_pp (into Wo's lower-right block)
+    for (int i = lane; i < l2; i += 32) {
+      float a = 0.0f;
+      for (int b = 0; kNG + b <= i && b < KC; ++b) a += L2[tri(i, kNG + b)] * p[b];
+      srow[i] = a;
+    }
+    __syncwarp();
+    for (int t = lane; t < l2 * K; t += 32) {
+      const int i = t / K, j = t - i * K;
+      const float lij = (kNG + 1 + j <= i) ? L2[tri(i, kNG + 1 + j)] : 0.0f;
+      Zp[t] = p[1 + j] * (lij - srow[i]);
+    }
+    __syncwarp();
+    for (int t = lane; t < K * K; t += 32) {
+      const int a = t / K, b = t - a * K;
+      if (b > a) continue;
+      float w = 0.0f;
+      for (int i = 0; i < l2; ++i) w += Zp[i * K + a] * Zp[i * K + b];
+      Wo[(6 + a) * u2 + 6 + b] = w;
+      Wo[(6 + b) * u2 + 6 + a] = w;
+    }
+    // per lane: projection Jacobians, geometric rows of M^T for the object pass
+    GJac J;
+    if (mine) {
+      compute_gjac_t<DEG>(s, c, *camp, g, J);
+#pragma unroll
+      for (int q = 0; q < 66; ++q) {
+        const int k = q / 6, cc = q - 6 * (q / 6);
+        float val = 0.0f;
+        if (cc < 2) val = k < 3 ? J.Jm[cc][k] : 0.0f;
+        else if (cc < 5) val = k < 10 ? J.Jc[cc - 2][k] : 0.0f;
+        else val = k == 10 ? J.dsig : 0.0f;
+        Yg[q * 32 + lane] = val;
+      }
+      acc[1] += (double)depth_gain_lane(J, L1, blk, cg);
+      acc[0] += (double)rgb_gain_lane<DEG>(J, L0, blk, cg);
+    }
+    __syncwarp();
+    // object gain, one (view, Gaussian) at a time
+    unsigned todo = todo_all;
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const float* bsrc = blocks + ((size_t)(v0 + src) * s.n + g) * nBp;
+      for (int i = lane; i < l2; i += 32) {           // Z_g = L~[:, :11] M_g^T
+        float zr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        const int kg = i < kNG - 1 ? i : kNG - 1;
+        const float* Li = L2 + tri(i, 0);
+        for (int k = 0; k <= kg; ++k) {
+          const float lk = Li[k];
+#pragma unroll
+          for (int cc = 0; cc < 6; ++cc) zr[cc] += lk * Yg[(6 * k + cc) * 32 + src];
+        }
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) Zg[i * 6 + cc] = zr[cc];
+      }
+      __syncwarp();
+      for (int t = lane; t < 21 + 6 * K; t += 32) {   // W_gg (packed) and W_gp
+        float w = 0.0f;
+        int r, cc;
+        if (t < 21) {
+          tri_decode(t, r, cc);
+          for (int i = 0; i < l2; ++i) w += Zg[i * 6 + r] * Zg[i * 6 + cc];
+        } else {
+          const int q = t - 21;
+          r = q / K;
+          cc = 6 + (q - r * K);
+          for (int i = 0; i < l2; ++i) w += Zg[i * 6 + r] * Zp[i * K + cc - 6];
+        }
+        Wo[r * u2 + cc] = w;
+        Wo[cc * u2 + r] = w;
+      }
+      build_B(2, bsrc, c, Bo, lane);                   // ends with __syncwarp
+      const float d2 = logdet_IcWB(u2, cg, Wo, Bo, Go, lane);
+      if (lane == src) acc[2] += (double)d2;
+    }
+    __syncwarp();
+  }
+  if (vok) {
+    double* out = partial + ((size_t)v * nparts + slot) * 3;
+    out[0] = acc[0];
+    out[1] = acc[1];
+    out[2] = acc[2];
   }
 }
 
@@ -766,6 +1156,38 @@ int launch_views_gains(const DevScene& s, const Consts& c, const DevCam* cams, i
   dispatch_uo(c.K, [&](auto uo) {
     launch_gains_k<decltype(uo)::value>(s, c, dummy, cams, nv, blocks, f, nullptr, partial, grid, nw, sm, d, st);
   });
+  return 1;
+}
+
+int launch_views_gains_gm(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const float* blocks,
+                          const Factors& f, double* partial, int parts_cap, int* nparts, cudaStream_t st) {
+  if (nv <= 0) return 0;
+  const GmLayout y = gm_layout(c);
+  const size_t pw = (size_t)y.per_warp * sizeof(float);
+  int nw = (int)((size_t)(220 * 1024) / pw);
+  if (nw < 1) return -1;                      // does not fit: caller uses the view-major kernel
+  if (nw > 8) nw = 8;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nchunk = (nv + 31) / 32;
+  int grid = (int)((s.n + nw - 1) / nw);
+  const int want = (nsm * 4 + nchunk - 1) / nchunk;   // a few blocks per SM over all chunks
+  if (grid > want) grid = want;
+  if (grid * nw > parts_cap) grid = parts_cap / nw;
+  if (grid < 1) grid = 1;
+  *nparts = grid * nw;
+  const size_t sm = pw * nw;
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kern<<<dim3(grid, nchunk), 32 * nw, sm, st>>>(s, c, cams, nv, blocks, f, partial, *nparts);
+  };
+  switch (c.deg) {
+    case 0: go(k_gains_gm<0>); break;
+    case 1: go(k_gains_gm<1>); break;
+    case 2: go(k_gains_gm<2>); break;
+    default: go(k_gains_gm<3>); break;
+  }
   return 1;
 }
 

@@ -142,8 +142,9 @@ struct CompositeArgs {
 int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage = 32);
 
 struct Factors {
-  float* L[3];        // packed lower-triangle Cholesky factor of the scaled H, per output
-  float* dinv[3];     // D^-1/2 Jacobi scaling per parameter
+  // per output, packed lower triangle of L~ = L^-1 D^-1/2, where D = diag(H)
+  // and D^-1/2 H D^-1/2 = L L^T; hence H^-1 = L~^T L~
+  float* L[3];
   int l[3];
 };
 // Training Hessians: H^f_g = lambda I + c_g sum_t M_t^T B_t M_t, scaled and factorised.
@@ -159,6 +160,11 @@ int launch_reduce_gains(const double* partial, int nblocks, double* out3, cudaSt
 // nparts returned; out3 [nv][3].
 int launch_views_gains(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const float* blocks,
                        const Factors& f, double* partial, int parts_cap, int* nparts, cudaStream_t st);
+// Multi-view gains, Gaussian-major (one warp per Gaussian, lane = view,
+// 32 views per grid row). Writes partial[(v * nparts + slot) * 3 + f].
+// Returns -1 (nothing launched) when its shared memory does not fit.
+int launch_views_gains_gm(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const float* blocks,
+                          const Factors& f, double* partial, int parts_cap, int* nparts, cudaStream_t st);
 int launch_reduce_gains_views(const double* partial, int nparts, int nv, double* out3, cudaStream_t st);
 int launch_final_scores(const double* ig_cand, const double* ig_train, int n_cand, int n_train,
                         const Consts& c, float* out4, int* best, float* best_score, int* err,
