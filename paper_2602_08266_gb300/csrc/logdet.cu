@@ -32,7 +32,6 @@
 namespace nbv {
 namespace {
 
-constexpr int kMaxWarps = 8;
 
 struct GJac {
   float Jm[2][3];    // d(mx,my)/d mu
@@ -281,31 +280,6 @@ __host__ __device__ __forceinline__ int out_u(int f, const Consts& c) {
   return f == 0 ? 9 : (f == 1 ? 7 : 6 + c.K);
 }
 
-// Dense M (u x l, row-major) of output f. Lanes zero it; lane 0 fills it.
-__device__ void build_M(int f, const GJac& J, const Consts& c, const float* p, float* M, int lane) {
-  const int l = out_l(f, c), u = out_u(f, c);
-  for (int i = lane; i < u * l; i += 32) M[i] = 0.0f;
-  __syncwarp();
-  if (lane == 0) {
-    for (int m = 0; m < 3; ++m) { M[0 * l + m] = J.Jm[0][m]; M[1 * l + m] = J.Jm[1][m]; }
-    for (int e = 0; e < 3; ++e)
-      for (int k = 0; k < 10; ++k) M[(2 + e) * l + k] = J.Jc[e][k];
-    M[5 * l + 10] = J.dsig;
-    if (f == 0) {
-      for (int ch = 0; ch < 3; ++ch) {
-        for (int m = 0; m < 3; ++m) M[(6 + ch) * l + m] = J.Jrgb[ch][m];
-        for (int k = 0; k < c.nb; ++k) M[(6 + ch) * l + kNG + 3 * k + ch] = J.live[ch] * J.Y[k];
-      }
-    } else if (f == 1) {
-      for (int m = 0; m < 3; ++m) M[6 * l + m] = J.Jz[m];
-    } else {
-      for (int j = 1; j <= c.K; ++j)      // d p_j / d o_b = p_j (delta_jb - p_b)
-        for (int bb = 0; bb < c.KC; ++bb) M[(5 + j) * l + kNG + bb] = p[j] * ((j == bb ? 1.0f : 0.0f) - p[bb]);
-    }
-  }
-  __syncwarp();
-}
-
 // Dense B (u x u) of output f from the structured block.
 __device__ __forceinline__ void build_B(int f, const float* blk, const Consts& c, float* Bm, int lane) {
   const int u = out_u(f, c);
@@ -337,122 +311,305 @@ __device__ __forceinline__ void tri_decode(int t, int& r, int& cc) {
   cc = t - tri(r, 0);
 }
 
-// One warp per Gaussian: H = lambda I + c_g sum_t M_t^T B_t M_t (single
-// precision sum), Jacobi scaling, Cholesky in double precision (trailing
-// updates spread evenly over the lanes), then L^-1 in single precision
-// (right-looking, also spread evenly), stored packed.
+// Entries of the projection Jacobian M (u x 11) on the geometric parameters
+// (mean, log-scale, quaternion, opacity logit), by row:
+// rows 0-1 mean2D, 2-4 conic, 5 sigma (shared by the three outputs).
+__device__ __forceinline__ float m_geo(const GJac& J, int v, int a) {
+  if (v < 2) return a < 3 ? J.Jm[v][a] : 0.0f;
+  if (v < 5) return a < 10 ? J.Jc[v - 2][a] : 0.0f;
+  return a == 10 ? J.dsig : 0.0f;
+}
+// Entry (u, v) of a 6 x 6 block stored packed lower.
+__device__ __forceinline__ float q6(const float* q, int u, int v) { return u >= v ? q[tri(u, v)] : q[tri(v, u)]; }
+
+// Per-warp shared memory of the factor kernel: doubles (the scaled matrix
+// being factorised and the scaling), then floats.
+struct FactLayout {
+  int l0, l1, l2, nt0, nt1, nt2, ntm, lmax;
+  int d_per_warp;
+  int off_H1, off_H2, off_J, off_GB, off_XG, off_xs, f_per_warp;
+};
+constexpr int kTrainChunk = 8;   // training views whose Jacobians are held at once
+
+FactLayout fact_layout(const Consts& c) {
+  FactLayout y{};
+  y.l0 = kNG + 3 * c.nb;
+  y.l1 = kNG;
+  y.l2 = kNG + c.KC;
+  y.nt0 = y.l0 * (y.l0 + 1) / 2;
+  y.nt1 = y.l1 * (y.l1 + 1) / 2;
+  y.nt2 = y.l2 * (y.l2 + 1) / 2;
+  y.lmax = y.l0 > y.l2 ? y.l0 : y.l2;
+  y.ntm = y.nt0 > y.nt2 ? y.nt0 : y.nt2;
+  y.d_per_warp = y.ntm + y.lmax;
+  auto r4 = [](int x) { return (x + 3) & ~3; };
+  y.off_H1 = r4(y.nt0);
+  y.off_H2 = y.off_H1 + r4(y.nt1);
+  y.off_J = y.off_H2 + r4(y.nt2);
+  y.off_GB = y.off_J + r4(kTrainChunk * (int)(sizeof(GJac) / 4));
+  y.off_XG = y.off_GB + 9 * kNG + 1;
+  y.off_xs = y.off_XG + r4(c.K * kNG);
+  y.f_per_warp = y.off_xs + 12;
+  return y;
+}
+
+// Adds one training view's blocks A = M^T B M of the three outputs to the
+// warp's sums H0 (colour), H1 (depth), H2 (object; geometric-geometric
+// part, plus XG += X_o G for the logit rows, finished per Gaussian), using
+// the block structure of M: geometric rows (mean2D, conic, sigma) over the
+// 11 geometric parameters; colour rows over the mean (view direction) and,
+// channel by channel, over the SH coefficients (live_ch Y_k); the depth row
+// over the mean; the probability rows over the object logits only (view
+// independent).
+__device__ __forceinline__ void add_view_blocks(const GJac& J, const float* __restrict__ blk, const Consts& c,
+                                                float* H0, float* H1, float* H2, float* GB, float* XG,
+                                                int lane) {
+  const float W2 = blk[kOffW2];
+  const int nb = c.nb, K = c.K;
+  // colour: GB = B_rgb M (9 x 11)
+  for (int e = lane; e < 9 * kNG; e += 32) {
+    const int u = e / kNG, a = e - kNG * u;
+    float acc = 0.0f;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+      const float buv = u < 6 ? q6(blk + kOffQrgb, u, v) : blk[kOffXrgb + 6 * (u - 6) + v];
+      acc += buv * m_geo(J, v, a);
+    }
+    if (a < 3) {
+#pragma unroll
+      for (int v = 6; v < 9; ++v) {
+        const float buv = u < 6 ? blk[kOffXrgb + 6 * (v - 6) + u] : (u == v ? W2 : 0.0f);
+        acc += buv * J.Jrgb[v - 6][a];
+      }
+    }
+    GB[e] = acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {   // geometric x geometric
+    int a, b;
+    tri_decode(e, a, b);
+    float acc = 0.0f;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) acc += m_geo(J, v, a) * GB[v * kNG + b];
+    if (a < 3) {
+#pragma unroll
+      for (int v = 6; v < 9; ++v) acc += J.Jrgb[v - 6][a] * GB[v * kNG + b];
+    }
+    H0[e] += acc;
+  }
+  for (int e = lane; e < 3 * nb * kNG; e += 32) {          // SH x geometric
+    const int ish = e / kNG, b = e - kNG * ish;
+    const int k = ish / 3, ch = ish - 3 * k;
+    H0[tri(kNG + ish, b)] += J.live[ch] * J.Y[k] * GB[(6 + ch) * kNG + b];
+  }
+  for (int e = lane; e < 3 * (nb * (nb + 1) / 2); e += 32) {   // SH x SH, same channel only
+    const int ch = e % 3;
+    int k, k2;
+    tri_decode(e / 3, k, k2);
+    H0[tri(kNG + 3 * k + ch, kNG + 3 * k2 + ch)] += W2 * J.live[ch] * J.Y[k] * J.Y[k2];
+  }
+  __syncwarp();
+  // depth: GB = B_d M (7 x 11), H1 = M^T GB
+  for (int e = lane; e < 7 * kNG; e += 32) {
+    const int u = e / kNG, a = e - kNG * u;
+    float acc = 0.0f;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+      const float buv = u < 6 ? q6(blk + kOffQd, u, v) : blk[kOffXd + v];
+      acc += buv * m_geo(J, v, a);
+    }
+    if (a < 3) acc += (u < 6 ? blk[kOffXd + u] : W2) * J.Jz[a];
+    GB[e] = acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {
+    int a, b;
+    tri_decode(e, a, b);
+    float acc = 0.0f;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) acc += m_geo(J, v, a) * GB[v * kNG + b];
+    if (a < 3) acc += J.Jz[a] * GB[6 * kNG + b];
+    H1[e] += acc;
+  }
+  __syncwarp();
+  // object, geometric part: GB = Q_o G (6 x 11), H2 += G^T GB; XG += X_o G (K x 11)
+  for (int e = lane; e < 6 * kNG; e += 32) {
+    const int u = e / kNG, a = e - kNG * u;
+    float acc = 0.0f;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) acc += q6(blk + kOffQo, u, v) * m_geo(J, v, a);
+    GB[e] = acc;
+  }
+  for (int e = lane; e < K * kNG; e += 32) {
+    const int j = e / kNG, a = e - kNG * j;
+    float acc = 0.0f;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) acc += blk[kOffXo + 6 * j + v] * m_geo(J, v, a);
+    XG[e] += acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {
+    int a, b;
+    tri_decode(e, a, b);
+    float acc = 0.0f;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) acc += m_geo(J, v, a) * GB[v * kNG + b];
+    H2[e] += acc;
+  }
+  __syncwarp();
+}
+
+// H = lambda I + c_g Hf (Hf = sum_t A_t, packed, l x l), Jacobi-scaled and
+// Cholesky-factorised in double precision (trailing updates spread over
+// the lanes), the factor inverted in single precision (right-looking), and
+// L~ = L^-1 D^-1/2 stored packed at Lg. Hf is overwritten.
+__device__ void factorise_store(int l, float cg, const Consts& c, float* Hf, double* Hs, double* dsc, float* Lg,
+                                int* err, int lane) {
+  const int nt = l * (l + 1) / 2;
+  for (int i = lane; i < l; i += 32) {
+    const double hii = (double)c.lam + (double)cg * (double)Hf[tri(i, i)];
+    dsc[i] = 1.0 / sqrt(hii);
+  }
+  __syncwarp();
+  for (int i = lane; i < nt; i += 32) {
+    int r, cc;
+    tri_decode(i, r, cc);
+    const double h = (double)cg * (double)Hf[i] + (r == cc ? (double)c.lam : 0.0);
+    Hs[i] = h * dsc[r] * dsc[cc];
+  }
+  __syncwarp();
+  for (int k = 0; k < l; ++k) {
+    const double dkk = Hs[tri(k, k)];
+    if (!(dkk > 0.0) && lane == 0) atomicExch(err, 1);
+    const double Lkk = sqrt(fmax(dkk, 1e-300));
+    const double iL = 1.0 / Lkk;
+    __syncwarp();
+    if (lane == 0) Hs[tri(k, k)] = Lkk;
+    for (int i = k + 1 + lane; i < l; i += 32) Hs[tri(i, k)] *= iL;
+    __syncwarp();
+    const int m = l - k - 1;                       // trailing triangle of size m
+    const int tot = m * (m + 1) / 2;
+    if (lane < tot) {
+      int ii, jj;
+      tri_decode(lane, ii, jj);
+      for (int t = lane; t < tot; t += 32) {
+        const int i = k + 1 + ii, j = k + 1 + jj;
+        Hs[tri(i, j)] -= Hs[tri(i, k)] * Hs[tri(j, k)];
+        jj += 32;
+        while (jj > ii) { jj -= ii + 1; ++ii; }
+      }
+    }
+    __syncwarp();
+  }
+  // X = L^-1, right-looking:
+  //   X_kk = 1 / L_kk,  X_kj = -X_kk acc_kj (j < k),  acc_ij += L_ik X_kj (i > k, j <= k)
+  for (int i = lane; i < nt; i += 32) Hf[i] = 0.0f;
+  __syncwarp();
+  for (int k = 0; k < l; ++k) {
+    const float xkk = (float)(1.0 / Hs[tri(k, k)]);
+    for (int j = lane; j < k; j += 32) Hf[tri(k, j)] = -xkk * Hf[tri(k, j)];
+    if (lane == 0) Hf[tri(k, k)] = xkk;
+    __syncwarp();
+    const int rows = l - 1 - k, cols = k + 1, tot = rows * cols;
+    for (int t = lane; t < tot; t += 32) {
+      const int i = k + 1 + t / cols, j = t - (t / cols) * cols;
+      Hf[tri(i, j)] += (float)Hs[tri(i, k)] * Hf[tri(k, j)];
+    }
+    __syncwarp();
+  }
+  // stored: L~ = L^-1 D^-1/2, so that H^-1 = L~^T L~ and Z = L~ M^T
+  for (int i = lane; i < nt; i += 32) {
+    int r, cc;
+    tri_decode(i, r, cc);
+    Lg[i] = (float)((double)Hf[i] * dsc[cc]);
+  }
+  __syncwarp();
+}
+
+// One warp per Gaussian: the projection Jacobians of up to 8 training views
+// at once (one lane each), the structured sums of the three outputs' blocks
+// over the training views, then each output's training Hessian
+// H = lambda I + c_g sum_t M_t^T B_t M_t factorised (Eqs. 6, 9; C_g = c_g I).
 __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__ cams,
-                                const float* __restrict__ blocks, int n_train, Factors F,
-                                int* err, int lmax, int umax) {
+                                const float* __restrict__ blocks, int n_train, Factors F, int* err,
+                                FactLayout y) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int nB = block_floats(c.K), nBp = (nB + 3) & ~3;
-  const int ntm = lmax * (lmax + 1) / 2;
-  const size_t per_warp_d = (size_t)ntm + lmax;
-  const size_t per_warp_f = (size_t)umax * lmax * 2 + (size_t)umax * umax + sizeof(GJac) / 4 + ntm + 4;
-  double* Hs = reinterpret_cast<double*>(smem) + warp * per_warp_d;
-  double* dsc = Hs + ntm;                              // 1 / sqrt(H_ii)
-  float* fbase = reinterpret_cast<float*>(reinterpret_cast<double*>(smem) + nw * per_warp_d) +
-                 warp * per_warp_f;
-  float* M = fbase;
-  float* BM = M + umax * lmax;
-  float* Bm = BM + umax * lmax;
-  GJac* J = reinterpret_cast<GJac*>(Bm + umax * umax);
-  float* Hf = reinterpret_cast<float*>(J + 1);         // ntm floats
+  const int nBp = (block_floats(c.K) + 3) & ~3;
+  double* Hs = reinterpret_cast<double*>(smem) + (size_t)warp * y.d_per_warp;
+  double* dsc = Hs + y.ntm;
+  float* fb = reinterpret_cast<float*>(reinterpret_cast<double*>(smem) + (size_t)nw * y.d_per_warp) +
+              (size_t)warp * y.f_per_warp;
+  float* H0 = fb;
+  float* H1 = fb + y.off_H1;
+  float* H2 = fb + y.off_H2;
+  GJac* Jw = reinterpret_cast<GJac*>(fb + y.off_J);
+  float* GB = fb + y.off_GB;
+  float* XG = fb + y.off_XG;
+  float* xs = fb + y.off_xs;
+  const int K = c.K, KC = c.KC;
   for (int64_t g = (int64_t)blockIdx.x * nw + warp; g < s.n; g += (int64_t)gridDim.x * nw) {
     const float cg = s.aux[g].y;
-    const float* p = s.p + (size_t)g * c.KC;
-    for (int f = 0; f < 3; ++f) {
-      const int l = out_l(f, c), u = out_u(f, c), nt = l * (l + 1) / 2;
-      for (int i = lane; i < nt; i += 32) Hf[i] = 0.0f;
-      __syncwarp();
-      if (cg > 0.0f) {
-        for (int t = 0; t < n_train; ++t) {
-          const float* blk = blocks + ((size_t)t * s.n + g) * nBp;
-          if (blk[kOffW2] == 0.0f) continue;   // not seen in this view
-          if (lane == 0) compute_gjac(s, c, cams[t], g, *J);
-          __syncwarp();
-          build_M(f, *J, c, p, M, lane);
-          build_B(f, blk, c, Bm, lane);
-          for (int i = lane; i < u * l; i += 32) {      // BM = B M
-            const int r = i / l, cc = i - r * l;
-            float acc = 0.0f;
-            for (int k = 0; k < u; ++k) acc += Bm[r * u + k] * M[k * l + cc];
-            BM[i] = acc;
-          }
-          __syncwarp();
-          for (int i = lane; i < nt; i += 32) {         // H += M^T (B M)
-            int r, cc;
-            tri_decode(i, r, cc);
-            float acc = 0.0f;
-            for (int k = 0; k < u; ++k) acc += M[k * l + r] * BM[k * l + cc];
-            Hf[i] += acc;
-          }
-          __syncwarp();
+    const float* p = s.p + (size_t)g * KC;
+    for (int i = lane; i < y.nt0; i += 32) H0[i] = 0.0f;
+    for (int i = lane; i < y.nt1; i += 32) H1[i] = 0.0f;
+    for (int i = lane; i < y.nt2; i += 32) H2[i] = 0.0f;
+    for (int i = lane; i < K * kNG; i += 32) XG[i] = 0.0f;
+    float w2sum = 0.0f;
+    __syncwarp();
+    if (cg > 0.0f) {
+      for (int t0 = 0; t0 < n_train; t0 += kTrainChunk) {
+        const int t = t0 + lane;
+        bool seen = false;
+        if (lane < kTrainChunk && t < n_train) {
+          seen = blocks[((size_t)t * s.n + g) * nBp + kOffW2] != 0.0f;
+          if (seen) compute_gjac(s, c, cams[t], g, Jw[lane]);
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, seen);
+        __syncwarp();
+        while (todo) {
+          const int src = __ffs(todo) - 1;
+          todo &= todo - 1;
+          const float* blk = blocks + ((size_t)(t0 + src) * s.n + g) * nBp;
+          w2sum += blk[kOffW2];
+          add_view_blocks(Jw[src], blk, c, H0, H1, H2, GB, XG, lane);
         }
       }
-      float* Lg = F.L[f] + (size_t)g * nt;
-      // damping and Jacobi scaling, in double
-      for (int i = lane; i < l; i += 32) {
-        const double hii = (double)c.lam + (double)cg * (double)Hf[tri(i, i)];
-        dsc[i] = 1.0 / sqrt(hii);
+      // object logit rows: d p_j / d o_b = p_j (delta_jb - p_b) (view independent),
+      // B_pp = W2 (I + 1 1^T):
+      //   A[o_b][geo a] = sum_j P_jb XG[j][a] = p_b (XG[b][a] [b >= 1] - sum_j p_j XG[j][a])
+      //   A[o_b][o_b'] = sum_t W2_t (P^T P + cs cs^T)[b][b'],  cs_b = p_b ([b >= 1] - (1 - p_0))
+      for (int a = lane; a < kNG; a += 32) {
+        float acc = 0.0f;
+        for (int j = 1; j <= K; ++j) acc += p[j] * XG[(j - 1) * kNG + a];
+        xs[a] = acc;
       }
       __syncwarp();
-      for (int i = lane; i < nt; i += 32) {
-        int r, cc;
-        tri_decode(i, r, cc);
-        const double h = (double)cg * (double)Hf[i] + (r == cc ? (double)c.lam : 0.0);
-        Hs[i] = h * dsc[r] * dsc[cc];
+      for (int e = lane; e < KC * kNG; e += 32) {
+        const int b = e / kNG, a = e - kNG * b;
+        const float xb = b >= 1 ? XG[(b - 1) * kNG + a] : 0.0f;
+        H2[tri(kNG + b, a)] += p[b] * (xb - xs[a]);
       }
-      __syncwarp();
-      // Cholesky of the scaled matrix (diagonal 1), double precision
-      for (int k = 0; k < l; ++k) {
-        const double dkk = Hs[tri(k, k)];
-        if (!(dkk > 0.0) && lane == 0) atomicExch(err, 1);
-        const double Lkk = sqrt(fmax(dkk, 1e-300));
-        const double iL = 1.0 / Lkk;
-        __syncwarp();
-        if (lane == 0) Hs[tri(k, k)] = Lkk;
-        for (int i = k + 1 + lane; i < l; i += 32) Hs[tri(i, k)] *= iL;
-        __syncwarp();
-        const int m = l - k - 1;                       // trailing triangle of size m
-        const int tot = m * (m + 1) / 2;
-        if (lane < tot) {
-          int ii, jj;
-          tri_decode(lane, ii, jj);
-          for (int t = lane; t < tot; t += 32) {
-            const int i = k + 1 + ii, j = k + 1 + jj;
-            Hs[tri(i, j)] -= Hs[tri(i, k)] * Hs[tri(j, k)];
-            jj += 32;
-            while (jj > ii) { jj -= ii + 1; ++ii; }
-          }
-        }
-        __syncwarp();
-      }
-      // X = L^-1 in single precision, right-looking:
-      //   X_kk = 1 / L_kk,  X_kj = -X_kk acc_kj (j < k),  acc_ij += L_ik X_kj (i > k, j <= k)
-      for (int i = lane; i < nt; i += 32) Hf[i] = 0.0f;
-      __syncwarp();
-      for (int k = 0; k < l; ++k) {
-        const float xkk = (float)(1.0 / Hs[tri(k, k)]);
-        for (int j = lane; j < k; j += 32) Hf[tri(k, j)] = -xkk * Hf[tri(k, j)];
-        if (lane == 0) Hf[tri(k, k)] = xkk;
-        __syncwarp();
-        const int rows = l - 1 - k, cols = k + 1, tot = rows * cols;
-        for (int t = lane; t < tot; t += 32) {
-          const int i = k + 1 + t / cols, j = t - (t / cols) * cols;
-          Hf[tri(i, j)] += (float)Hs[tri(i, k)] * Hf[tri(k, j)];
-        }
-        __syncwarp();
-      }
-      // stored: L~ = L^-1 D^-1/2, so that H^-1 = L~^T L~ and Z = L~ M^T
-      for (int i = lane; i < nt; i += 32) {
-        int r, cc;
-        tri_decode(i, r, cc);
-        Lg[i] = (float)((double)Hf[i] * dsc[cc]);
+      float s2 = 0.0f;
+      for (int j = 1; j <= K; ++j) s2 += p[j] * p[j];
+      const float one_m_p0 = 1.0f - p[0];
+      for (int e = lane; e < KC * (KC + 1) / 2; e += 32) {
+        int b, b2;
+        tri_decode(e, b, b2);
+        const float pb = p[b], pb2 = p[b2];
+        float pp = pb * pb2 * s2;
+        if (b >= 1) pp -= pb * pb * pb2;
+        if (b2 >= 1) pp -= pb2 * pb2 * pb;
+        if (b == b2 && b >= 1) pp += pb * pb;
+        const float csb = pb * ((b >= 1 ? 1.0f : 0.0f) - one_m_p0);
+        const float csb2 = pb2 * ((b2 >= 1 ? 1.0f : 0.0f) - one_m_p0);
+        H2[tri(kNG + b, kNG + b2)] += w2sum * (pp + csb * csb2);
       }
       __syncwarp();
     }
+    factorise_store(y.l0, cg, c, H0, Hs, dsc, F.L[0] + (size_t)g * y.nt0, err, lane);
+    factorise_store(y.l1, cg, c, H1, Hs, dsc, F.L[1] + (size_t)g * y.nt1, err, lane);
+    factorise_store(y.l2, cg, c, H2, Hs, dsc, F.L[2] + (size_t)g * y.nt2, err, lane);
   }
 }
 
@@ -1052,13 +1209,6 @@ __global__ void k_final_scores(const double* __restrict__ igc, const double* __r
   *best_score = bs;
 }
 
-size_t factors_smem_per_warp(int lmax, int umax) {
-  const int ntm = lmax * (lmax + 1) / 2;
-  const size_t per_warp_d = (size_t)ntm + lmax;
-  const size_t per_warp_f = (size_t)umax * lmax * 2 + (size_t)umax * umax + sizeof(GJac) / 4 + ntm + 4;
-  return per_warp_d * sizeof(double) + per_warp_f * sizeof(float);
-}
-
 struct GainsDims { int nt_max, lu_max, uu_max; };
 
 GainsDims gains_dims(const Consts& c) {
@@ -1087,23 +1237,18 @@ int warps_for(size_t per_warp) {
 
 }  // namespace
 
-static void sizes(const Consts& c, int* lmax, int* umax) {
-  *lmax = kNG + 3 * c.nb > kNG + c.KC ? kNG + 3 * c.nb : kNG + c.KC;
-  *umax = 9 > 6 + c.K ? 9 : 6 + c.K;
-}
 
 int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams, const float* blocks,
                          int n_train, const Factors& f, int* d_err, cudaStream_t st) {
-  int lmax, umax;
-  sizes(c, &lmax, &umax);
-  const size_t pw = factors_smem_per_warp(lmax, umax);
+  const FactLayout y = fact_layout(c);
+  const size_t pw = (size_t)y.d_per_warp * sizeof(double) + (size_t)y.f_per_warp * sizeof(float);
   int nw = (int)((220 * 1024) / pw);
   nw = nw < 1 ? 1 : (nw > 8 ? 8 : nw);
   const size_t sm = pw * nw;
   cudaFuncSetAttribute(k_build_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int64_t nblk = (s.n + nw - 1) / nw;
   const int grid = (int)(nblk < 152 * 32 ? nblk : 152 * 32);
-  k_build_factors<<<grid, 32 * nw, sm, st>>>(s, c, cams, blocks, n_train, f, d_err, lmax, umax);
+  k_build_factors<<<grid, 32 * nw, sm, st>>>(s, c, cams, blocks, n_train, f, d_err, y);
   return 1;
 }
 
