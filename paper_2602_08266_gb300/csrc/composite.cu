@@ -174,6 +174,8 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   if (inside) atomicMax(&s_last_max, (int)last);
   __syncthreads();
   const uint32_t last_max = (uint32_t)s_last_max;
+  // splats at or past every pixel of this warp's last blended one are skipped warp-wide
+  const uint32_t wlast = __reduce_max_sync(0xffffffffu, inside ? last : rg.x);
   const float Tf = T;
   float Rr0 = 0.0f, Rr1 = 0.0f, Rr2 = 0.0f, Rd = 0.0f;
   float Ro[KCM];
@@ -240,6 +242,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
     __syncthreads();
     for (int j = nj - 1; j >= 0; --j) {
       const uint32_t idx = start + j;
+      if (idx >= wlast) continue;
       bool act = false;
       const float4 a0 = s0[j], a1 = s1[j], a2 = s2[j];
       float pw = 0.0f;

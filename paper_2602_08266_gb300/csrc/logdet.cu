@@ -459,6 +459,16 @@ __device__ __forceinline__ void add_view_blocks(const GJac& J, const float* __re
   __syncwarp();
 }
 
+// x^-1/2 in double precision by Newton's iteration y <- y (3 - x y^2) / 2,
+// started from the single-precision estimate (two steps: about 2^-22 ->
+// 2^-44 -> below double rounding). x must lie in the normal float range.
+__device__ __forceinline__ double rsqrt_d(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);
+  y = y * (1.5 - 0.5 * x * y * y);
+  return y;
+}
+
 // H = lambda I + c_g Hf (Hf = sum_t A_t, packed, l x l), Jacobi-scaled and
 // Cholesky-factorised in double precision (trailing updates spread over
 // the lanes), the factor inverted in single precision (right-looking), and
@@ -468,7 +478,7 @@ __device__ void factorise_store(int l, float cg, const Consts& c, float* Hf, dou
   const int nt = l * (l + 1) / 2;
   for (int i = lane; i < l; i += 32) {
     const double hii = (double)c.lam + (double)cg * (double)Hf[tri(i, i)];
-    dsc[i] = 1.0 / sqrt(hii);
+    dsc[i] = rsqrt_d(hii);
   }
   __syncwarp();
   for (int i = lane; i < nt; i += 32) {
@@ -478,13 +488,13 @@ __device__ void factorise_store(int l, float cg, const Consts& c, float* Hf, dou
     Hs[i] = h * dsc[r] * dsc[cc];
   }
   __syncwarp();
+  // the diagonal slot keeps 1 / L_kk (all the inversion below needs of it)
   for (int k = 0; k < l; ++k) {
     const double dkk = Hs[tri(k, k)];
     if (!(dkk > 0.0) && lane == 0) atomicExch(err, 1);
-    const double Lkk = sqrt(fmax(dkk, 1e-300));
-    const double iL = 1.0 / Lkk;
+    const double iL = rsqrt_d(fmax(dkk, 1e-30));
     __syncwarp();
-    if (lane == 0) Hs[tri(k, k)] = Lkk;
+    if (lane == 0) Hs[tri(k, k)] = iL;
     for (int i = k + 1 + lane; i < l; i += 32) Hs[tri(i, k)] *= iL;
     __syncwarp();
     const int m = l - k - 1;                       // trailing triangle of size m
@@ -506,14 +516,23 @@ __device__ void factorise_store(int l, float cg, const Consts& c, float* Hf, dou
   for (int i = lane; i < nt; i += 32) Hf[i] = 0.0f;
   __syncwarp();
   for (int k = 0; k < l; ++k) {
-    const float xkk = (float)(1.0 / Hs[tri(k, k)]);
+    const float xkk = (float)Hs[tri(k, k)];
     for (int j = lane; j < k; j += 32) Hf[tri(k, j)] = -xkk * Hf[tri(k, j)];
     if (lane == 0) Hf[tri(k, k)] = xkk;
     __syncwarp();
-    const int rows = l - 1 - k, cols = k + 1, tot = rows * cols;
-    for (int t = lane; t < tot; t += 32) {
-      const int i = k + 1 + t / cols, j = t - (t / cols) * cols;
-      Hf[tri(i, j)] += (float)Hs[tri(i, k)] * Hf[tri(k, j)];
+    const int rows = l - 1 - k, cols = k + 1;
+    if (rows >= cols) {                       // lanes over the rows below k
+      for (int i = k + 1 + lane; i < l; i += 32) {
+        const float lik = (float)Hs[tri(i, k)];
+        float* Xi = Hf + tri(i, 0);
+        const float* Xk = Hf + tri(k, 0);
+        for (int j = 0; j <= k; ++j) Xi[j] += lik * Xk[j];
+      }
+    } else {                                  // lanes over the columns up to k
+      for (int j = lane; j <= k; j += 32) {
+        const float xkj = Hf[tri(k, j)];
+        for (int i = k + 1; i < l; ++i) Hf[tri(i, j)] += (float)Hs[tri(i, k)] * xkj;
+      }
     }
     __syncwarp();
   }
