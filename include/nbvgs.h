@@ -176,7 +176,10 @@ int nbv_debug_project(nbv_ctx* ctx, int view_set, int view, int32_t* rect, float
 /* Sorted tile lists of one view: *count receives the number of (tile,
  * Gaussian) entries; if count <= cap, offsets [ntiles+1] and ids [count]
  * (device arrays) receive the per-tile ranges and Gaussian ids in blend
- * order. Synchronises. */
+ * order. view_set 0 / 1 bins the candidate / training view on its own;
+ * view_set 2 returns candidate `view` as the last multi-view score binned it
+ * (NBV_ERR_STATE when no multi-view score ran since the inputs changed).
+ * Synchronises. */
 int nbv_debug_tile_lists(nbv_ctx* ctx, int view_set, int view, int64_t* offsets, int32_t* ids,
                          int64_t cap, int64_t* count);
 

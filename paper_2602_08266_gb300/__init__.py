@@ -299,12 +299,15 @@ class NBVScorer:
         return out
 
     def debug_tile_lists(self, view_set: int, view: int):
+        """(offsets [ntiles+1], Gaussian ids) of one view's tile lists.
+        view_set 0 / 1: candidate / training view binned on its own; 2: the
+        candidate as the last multi-view score binned it."""
         torch = self.torch
         cnt = ctypes.c_int64(0)
         self._check(self.lib.nbv_debug_tile_lists(self._h, int(view_set), int(view), None, None, 0,
                                                   ctypes.byref(cnt)))
         total = int(cnt.value)
-        dims = self._train if view_set else self._cand
+        dims = self._train if view_set == 1 else self._cand
         W, H = int(dims[0][view]), int(dims[1][view])
         tw, th, _ = self.tiling()
         nt = ((W + tw - 1) // tw) * ((H + th - 1) // th)

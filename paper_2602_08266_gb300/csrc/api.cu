@@ -95,7 +95,12 @@ struct nbv_ctx {
     DevProj pr{};                   // [nv][n] records
     uint32_t* offsets = nullptr;    // [nv n + 1]
     uint32_t* scan_tmp = nullptr;
-    SortBuffers sb{};               // entries
+    SortBuffers db{};               // depth order of the (view, Gaussian) slots
+    uint32_t* tcount = nullptr;     // [nv n] tiles touched, in depth order
+    const uint32_t* svals = nullptr;  // sorted Gaussian ids of the last multi-view pass
+    std::vector<uint32_t> h_base;     // first global tile of each view
+    uint32_t* doffsets = nullptr;   // [nv n + 1] their exclusive scan
+    SortBuffers sb{};               // entries (32-bit tile keys, stored in the 64-bit arrays)
     SortBuffers qb{};               // work queue
     uint2* ranges = nullptr;        // [ntiles]
     int* counter = nullptr;
@@ -353,6 +358,8 @@ int batched_setup(nbv_ctx* ctx) {
   }
   if (nt >= (int64_t(1) << 31)) return fail(ctx, NBV_ERR_ARG, "too many tiles in the candidate set");
   B.ntiles = (int)nt;
+  B.h_base = base;
+  B.svals = nullptr;
   std::vector<int> tv((size_t)nt);
   for (int v = 0; v < nv; ++v)
     for (int64_t t = 0; t < (int64_t)hc[v].GX * hc[v].GY; ++t) tv[base[v] + t] = v;
@@ -368,6 +375,12 @@ int batched_setup(nbv_ctx* ctx) {
   CKR(alloc(ctx, &B.pr.touched, slots)); CKR(alloc(ctx, &B.pr.radius, slots));
   CKR(alloc(ctx, &B.offsets, slots + 1));
   CKR(alloc(ctx, &B.scan_tmp, scan_scratch_elems((int64_t)slots + 1)));
+  CKR(alloc(ctx, &B.db.keys[0], slots)); CKR(alloc(ctx, &B.db.keys[1], slots));
+  CKR(alloc(ctx, &B.db.vals[0], slots)); CKR(alloc(ctx, &B.db.vals[1], slots));
+  CKR(alloc(ctx, &B.db.hist, radix_hist_elems((int64_t)slots)));
+  B.db.cap = slots;
+  CKR(alloc(ctx, &B.tcount, slots));
+  CKR(alloc(ctx, &B.doffsets, slots + 1));
   CKR(alloc(ctx, &B.ranges, (size_t)nt));
   CKR(alloc(ctx, &B.counter, 1));
   CKR(alloc(ctx, &B.blocks, slots * ctx->nBp));
@@ -410,18 +423,27 @@ int batched_sequence(nbv_ctx* ctx) {
     CKR(check_launch(ctx, launch_project_views(s, ctx->c, B.cams, nv, B.pr, st)));
   }
   uint32_t* qv = nullptr;
-  const uint64_t* skeys = nullptr;
   const uint32_t* svals = nullptr;
   {
     Phase ph(ctx, NBV_PHASE_SORT);
-    CKR(check_launch(ctx, launch_scan_u32(B.pr.touched, B.offsets, (int64_t)slots, B.scan_tmp, st)));
-    CKR(check_launch(ctx, launch_duplicate_views(B.pr, n, nv, B.cams, B.tile_base, B.offsets, B.sb.keys[0],
-                                                 B.sb.vals[0], st)));
+    // (view, depth bits) order of the slots first (the slots are in view-major,
+    // Gaussian-index order and every pass is stable), then the entries
+    // duplicated in that order and sorted stably on the tile id alone: each
+    // tile's list comes out in (depth bits, Gaussian index) order
+    CKR(check_launch(ctx, launch_depth_keys(B.pr.zbits, n, nv, B.db.keys[0], B.db.vals[0], st)));
+    int dw = 0;
+    CKR(check_launch(ctx, launch_radix_sort(B.db, (int64_t)slots, 31 + bits_for(nv), &dw, st)));
+    const uint32_t* order = B.db.vals[dw];
+    CKR(check_launch(ctx, launch_gather_touched(B.pr.touched, order, (int64_t)slots, B.tcount, st)));
+    CKR(check_launch(ctx, launch_scan_u32(B.tcount, B.doffsets, (int64_t)slots, B.scan_tmp, st)));
+    uint32_t* k32[2] = {reinterpret_cast<uint32_t*>(B.sb.keys[0]), reinterpret_cast<uint32_t*>(B.sb.keys[1])};
+    CKR(check_launch(ctx, launch_duplicate_sorted(B.pr.rect, order, n, nv, B.cams, B.tile_base, B.doffsets, k32[0],
+                                                  B.sb.vals[0], st)));
     int which = 0;
-    CKR(check_launch(ctx, launch_radix_sort(B.sb, B.total, 32 + bits_for(B.ntiles), &which, st)));
-    skeys = B.sb.keys[which];
+    CKR(check_launch(ctx, launch_radix_sort32(k32, B.sb.vals, B.sb.hist, B.total, bits_for(B.ntiles), &which, st)));
     svals = B.sb.vals[which];
-    CKR(check_launch(ctx, launch_ranges(skeys, B.total, B.ranges, B.ntiles, st)));
+    B.svals = svals;
+    CKR(check_launch(ctx, launch_ranges32(k32[which], B.total, B.ranges, B.ntiles, st)));
     CKR(check_launch(ctx, launch_queue_keys(B.ranges, B.ntiles, B.qb.keys[0], B.qb.vals[0], st)));
     int qw = 0;
     CKR(check_launch(ctx, launch_radix_sort(B.qb, B.ntiles, 32 + bits_for(B.ntiles), &qw, st)));
@@ -516,7 +538,8 @@ int ensure_scene_buffers(nbv_ctx* ctx, int64_t n) {
   for (int f = 0; f < 3; ++f) {
     const int l = f == 0 ? kNG + 3 * nb : (f == 1 ? kNG : kNG + KC);
     ctx->F.l[f] = l;
-    CKR(alloc(ctx, &ctx->F.L[f], (size_t)n * l * (l + 1) / 2));
+    const size_t per = f == 0 ? (size_t)rgb_L_size(nb) : (size_t)l * (l + 1) / 2;
+    CKR(alloc(ctx, &ctx->F.L[f], (size_t)n * per));
   }
   ctx->partial_cap = 152 * 16;    // blocks; up to 8 warp partial sums each
   CKR(alloc(ctx, &ctx->partial, (size_t)ctx->partial_cap * 8 * 3));
@@ -616,7 +639,8 @@ void nbv_destroy(nbv_ctx* ctx) {
     void* bp[] = {B.cams, B.tile_base, B.tile_view, B.pr.r0, B.pr.r1, B.pr.r2, B.pr.rect, B.pr.zbits,
                   B.pr.touched, B.pr.radius, B.offsets, B.scan_tmp, B.sb.keys[0], B.sb.keys[1], B.sb.vals[0],
                   B.sb.vals[1], B.sb.hist, B.qb.keys[0], B.qb.keys[1], B.qb.vals[0], B.qb.vals[1], B.qb.hist,
-                  B.ranges, B.counter, B.blocks, B.partial};
+                  B.ranges, B.counter, B.blocks, B.partial, B.db.keys[0], B.db.keys[1], B.db.vals[0],
+                  B.db.vals[1], B.db.hist, B.tcount, B.doffsets};
     for (void* q : bp)
       if (q) cudaFree(q);
   }
@@ -846,10 +870,43 @@ int nbv_debug_project(nbv_ctx* ctx, int view_set, int view, int32_t* rect, float
   return NBV_OK;
 }
 
+namespace {
+// Tile lists of candidate `view` as the last multi-view pass binned them.
+int debug_batched_lists(nbv_ctx* ctx, int view, int64_t* offsets, int32_t* ids, int64_t cap, int64_t* count) {
+  auto& B = ctx->bt;
+  if (!B.ready || !B.svals) return fail(ctx, NBV_ERR_STATE, "no multi-view pass since the last change");
+  if (view < 0 || view >= B.nv) return fail(ctx, NBV_ERR_ARG, "view out of range");
+  cudaStream_t st = ctx->st;
+  const DevCam dc = to_dev(ctx->cand[view], ctx->tw, ctx->th);
+  const int ntiles = dc.GX * dc.GY;
+  std::vector<uint2> hr(ntiles);
+  CK(cudaMemcpyAsync(hr.data(), B.ranges + B.h_base[view], sizeof(uint2) * ntiles, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<int64_t> ho(ntiles + 1);
+  int64_t run = 0, first = -1;
+  for (int t = 0; t < ntiles; ++t) {
+    ho[t] = run;
+    if (hr[t].y > hr[t].x) {
+      if (first < 0) first = hr[t].x;
+      if ((int64_t)hr[t].x != first + run) return fail(ctx, NBV_ERR_CUDA, "tile ranges of a view are not contiguous");
+    }
+    run += (int64_t)(hr[t].y - hr[t].x);
+  }
+  ho[ntiles] = run;
+  *count = run;
+  if (run > cap || !offsets || !ids) return NBV_OK;
+  CK(cudaMemcpyAsync(offsets, ho.data(), sizeof(int64_t) * (ntiles + 1), cudaMemcpyHostToDevice, st));
+  if (run > 0) CK(cudaMemcpyAsync(ids, B.svals + first, sizeof(int32_t) * run, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return NBV_OK;
+}
+}  // namespace
+
 int nbv_debug_tile_lists(nbv_ctx* ctx, int view_set, int view, int64_t* offsets, int32_t* ids,
                          int64_t cap, int64_t* count) {
   if (!ctx || !count) return NBV_ERR_ARG;
   if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "no Gaussians");
+  if (view_set == 2) return debug_batched_lists(ctx, view, offsets, ids, cap, count);
   const std::vector<nbv_camera>& vs = view_set ? ctx->train : ctx->cand;
   if (view < 0 || view >= (int)vs.size()) return fail(ctx, NBV_ERR_ARG, "view out of range");
   CKR(render_view(ctx, vs[view], nullptr, nullptr, nullptr, nullptr, nullptr));

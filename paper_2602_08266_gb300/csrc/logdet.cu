@@ -327,7 +327,7 @@ __device__ __forceinline__ float q6(const float* q, int u, int v) { return u >= 
 struct FactLayout {
   int l0, l1, l2, nt0, nt1, nt2, ntm, lmax;
   int d_per_warp;
-  int off_H1, off_H2, off_J, off_GB, off_XG, off_xs, f_per_warp;
+  int off_H1, off_H2, off_J, off_GB, off_XG, off_xs, off_E, off_T, f_per_warp;
 };
 constexpr int kTrainChunk = 8;   // training views whose Jacobians are held at once
 
@@ -349,7 +349,9 @@ FactLayout fact_layout(const Consts& c) {
   y.off_GB = y.off_J + r4(kTrainChunk * (int)(sizeof(GJac) / 4));
   y.off_XG = y.off_GB + 9 * kNG + 1;
   y.off_xs = y.off_XG + r4(c.K * kNG);
-  y.f_per_warp = y.off_xs + 12;
+  y.off_E = y.off_xs + 12;
+  y.off_T = y.off_E + 68;
+  y.f_per_warp = y.off_T + r4(kNG * 3 * c.nb);
   return y;
 }
 
@@ -469,10 +471,68 @@ __device__ __forceinline__ double rsqrt_d(double x) {
   return y;
 }
 
+// Cholesky factorisation of a packed lower n x n matrix in double precision,
+// in place, trailing updates spread over the lanes. The diagonal slot keeps
+// 1 / L_kk (all that the inversion needs of it); a non-positive pivot sets
+// *err.
+__device__ void chol_packed_d(double* P, int n, int* err, int lane) {
+  for (int k = 0; k < n; ++k) {
+    const double dkk = P[tri(k, k)];
+    if (!(dkk > 0.0) && lane == 0) atomicExch(err, 1);
+    const double iL = rsqrt_d(fmax(dkk, 1e-30));
+    __syncwarp();
+    if (lane == 0) P[tri(k, k)] = iL;
+    for (int i = k + 1 + lane; i < n; i += 32) P[tri(i, k)] *= iL;
+    __syncwarp();
+    const int m = n - k - 1;                       // trailing triangle of size m
+    const int tot = m * (m + 1) / 2;
+    if (lane < tot) {
+      int ii, jj;
+      tri_decode(lane, ii, jj);
+      for (int t = lane; t < tot; t += 32) {
+        const int i = k + 1 + ii, j = k + 1 + jj;
+        P[tri(i, j)] -= P[tri(i, k)] * P[tri(j, k)];
+        jj += 32;
+        while (jj > ii) { jj -= ii + 1; ++ii; }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// X = L^-1 (packed lower) from the factor chol_packed_d left, right-looking:
+//   X_kk = 1 / L_kk,  X_kj = -X_kk acc_kj (j < k),  acc_ij += L_ik X_kj (i > k, j <= k)
+template <typename TX>
+__device__ void inv_lower(const double* L, TX* X, int n, int lane) {
+  const int nt = n * (n + 1) / 2;
+  for (int i = lane; i < nt; i += 32) X[i] = (TX)0;
+  __syncwarp();
+  for (int k = 0; k < n; ++k) {
+    const TX xkk = (TX)L[tri(k, k)];
+    for (int j = lane; j < k; j += 32) X[tri(k, j)] = -xkk * X[tri(k, j)];
+    if (lane == 0) X[tri(k, k)] = xkk;
+    __syncwarp();
+    const int rows = n - 1 - k, cols = k + 1;
+    if (rows >= cols) {                       // lanes over the rows below k
+      for (int i = k + 1 + lane; i < n; i += 32) {
+        const TX lik = (TX)L[tri(i, k)];
+        TX* Xi = X + tri(i, 0);
+        const TX* Xk = X + tri(k, 0);
+        for (int j = 0; j <= k; ++j) Xi[j] += lik * Xk[j];
+      }
+    } else {                                  // lanes over the columns up to k
+      for (int j = lane; j <= k; j += 32) {
+        const TX xkj = X[tri(k, j)];
+        for (int i = k + 1; i < n; ++i) X[tri(i, j)] += (TX)L[tri(i, k)] * xkj;
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // H = lambda I + c_g Hf (Hf = sum_t A_t, packed, l x l), Jacobi-scaled and
-// Cholesky-factorised in double precision (trailing updates spread over
-// the lanes), the factor inverted in single precision (right-looking), and
-// L~ = L^-1 D^-1/2 stored packed at Lg. Hf is overwritten.
+// Cholesky-factorised in double precision, the factor inverted in single
+// precision, and L~ = L^-1 D^-1/2 stored packed at Lg. Hf is overwritten.
 __device__ void factorise_store(int l, float cg, const Consts& c, float* Hf, double* Hs, double* dsc, float* Lg,
                                 int* err, int lane) {
   const int nt = l * (l + 1) / 2;
@@ -488,59 +548,93 @@ __device__ void factorise_store(int l, float cg, const Consts& c, float* Hf, dou
     Hs[i] = h * dsc[r] * dsc[cc];
   }
   __syncwarp();
-  // the diagonal slot keeps 1 / L_kk (all the inversion below needs of it)
-  for (int k = 0; k < l; ++k) {
-    const double dkk = Hs[tri(k, k)];
-    if (!(dkk > 0.0) && lane == 0) atomicExch(err, 1);
-    const double iL = rsqrt_d(fmax(dkk, 1e-30));
-    __syncwarp();
-    if (lane == 0) Hs[tri(k, k)] = iL;
-    for (int i = k + 1 + lane; i < l; i += 32) Hs[tri(i, k)] *= iL;
-    __syncwarp();
-    const int m = l - k - 1;                       // trailing triangle of size m
-    const int tot = m * (m + 1) / 2;
-    if (lane < tot) {
-      int ii, jj;
-      tri_decode(lane, ii, jj);
-      for (int t = lane; t < tot; t += 32) {
-        const int i = k + 1 + ii, j = k + 1 + jj;
-        Hs[tri(i, j)] -= Hs[tri(i, k)] * Hs[tri(j, k)];
-        jj += 32;
-        while (jj > ii) { jj -= ii + 1; ++ii; }
-      }
-    }
-    __syncwarp();
-  }
-  // X = L^-1, right-looking:
-  //   X_kk = 1 / L_kk,  X_kj = -X_kk acc_kj (j < k),  acc_ij += L_ik X_kj (i > k, j <= k)
-  for (int i = lane; i < nt; i += 32) Hf[i] = 0.0f;
-  __syncwarp();
-  for (int k = 0; k < l; ++k) {
-    const float xkk = (float)Hs[tri(k, k)];
-    for (int j = lane; j < k; j += 32) Hf[tri(k, j)] = -xkk * Hf[tri(k, j)];
-    if (lane == 0) Hf[tri(k, k)] = xkk;
-    __syncwarp();
-    const int rows = l - 1 - k, cols = k + 1;
-    if (rows >= cols) {                       // lanes over the rows below k
-      for (int i = k + 1 + lane; i < l; i += 32) {
-        const float lik = (float)Hs[tri(i, k)];
-        float* Xi = Hf + tri(i, 0);
-        const float* Xk = Hf + tri(k, 0);
-        for (int j = 0; j <= k; ++j) Xi[j] += lik * Xk[j];
-      }
-    } else {                                  // lanes over the columns up to k
-      for (int j = lane; j <= k; j += 32) {
-        const float xkj = Hf[tri(k, j)];
-        for (int i = k + 1; i < l; ++i) Hf[tri(i, j)] += (float)Hs[tri(i, k)] * xkj;
-      }
-    }
-    __syncwarp();
-  }
-  // stored: L~ = L^-1 D^-1/2, so that H^-1 = L~^T L~ and Z = L~ M^T
+  chol_packed_d(Hs, l, err, lane);
+  inv_lower<float>(Hs, Hf, l, lane);
   for (int i = lane; i < nt; i += 32) {
     int r, cc;
     tri_decode(i, r, cc);
     Lg[i] = (float)((double)Hf[i] * dsc[cc]);
+  }
+  __syncwarp();
+}
+
+// The colour output, factorised by blocks with the parameters ordered
+// [SH of channel 0, 1, 2 | geometric]: the three SH blocks are independent
+// (nb x nb each), so H~ = L L^T needs their Cholesky factors L_c, the
+// coupling L_gS = H~_gS L_S^-T and the factor of the geometric Schur
+// complement H~_gg - L_gS L_gS^T, all in double precision (3 nb^3 / 6 +
+// 11 * 3 nb^2 / 2 + ... operations instead of (11 + 3 nb)^3 / 6). L^-1 is
+// stored as A_c = L_c^-1, C_c = -E L_gS,c A_c, E = L_gg^-1 (see Factors),
+// each column scaled by D^-1/2. H0 holds the natural packed sum (SH (k, ch)
+// at 11 + 3 k + ch) and is only read; Ef (66) and Tf (33 nb) are float scratch.
+__device__ void factorise_rgb_store(int nb, float cg, const Consts& c, const float* H0, double* Hs, double* dsc,
+                                    float* Ef, float* Tf, float* Lg, int* err, int lane) {
+  const int T = nb * (nb + 1) / 2, n3 = 3 * nb;
+  const double lam = c.lam, cgd = cg;
+  for (int i = lane; i < kNG + n3; i += 32) dsc[i] = rsqrt_d(lam + cgd * (double)H0[tri(i, i)]);
+  __syncwarp();
+  double* A = Hs;               // 3 packed nb-triangles: A_c = L_c^-1
+  double* LgS = A + 3 * T;      // 11 x 3nb
+  double* S = LgS + kNG * n3;   // packed 11-triangle
+  double* X = S + kNG * (kNG + 1) / 2;   // packed nb-triangle
+  for (int ch = 0; ch < 3; ++ch) {
+    for (int e = lane; e < T; e += 32) {
+      int k, k2;
+      tri_decode(e, k, k2);
+      const int a = kNG + 3 * k + ch, b = kNG + 3 * k2 + ch;
+      X[e] = (cgd * (double)H0[tri(a, b)] + (k == k2 ? lam : 0.0)) * dsc[a] * dsc[b];
+    }
+    __syncwarp();
+    chol_packed_d(X, nb, err, lane);
+    inv_lower<double>(X, A + ch * T, nb, lane);
+  }
+  // L_gS[r][(c, k)] = sum_{k2 <= k} H~[g_r][(c, k2)] A_c[k][k2]
+  for (int e = lane; e < kNG * n3; e += 32) {
+    const int r = e / n3, q = e - r * n3, ch = q / nb, k = q - ch * nb;
+    const double* Ak = A + ch * T + tri(k, 0);
+    double acc = 0.0;
+    for (int k2 = 0; k2 <= k; ++k2) {
+      const int b = kNG + 3 * k2 + ch;
+      acc += (double)H0[tri(b, r)] * dsc[b] * Ak[k2];
+    }
+    LgS[e] = cgd * acc * dsc[r];
+  }
+  __syncwarp();
+  for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {
+    int r, r2;
+    tri_decode(e, r, r2);
+    double acc = (cgd * (double)H0[e] + (r == r2 ? lam : 0.0)) * dsc[r] * dsc[r2];
+    for (int q = 0; q < n3; ++q) acc -= LgS[r * n3 + q] * LgS[r2 * n3 + q];
+    S[e] = acc;
+  }
+  __syncwarp();
+  chol_packed_d(S, kNG, err, lane);
+  inv_lower<float>(S, Ef, kNG, lane);
+  for (int e = lane; e < kNG * n3; e += 32) {          // T_c = L_gS,c A_c
+    const int r = e / n3, q = e - r * n3, ch = q / nb, k = q - ch * nb;
+    float acc = 0.0f;
+    for (int k2 = k; k2 < nb; ++k2) acc += (float)LgS[r * n3 + ch * nb + k2] * (float)A[ch * T + tri(k2, k)];
+    Tf[e] = acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < 3 * T; e += 32) {
+    const int ch = e / T, q = e - ch * T;
+    int k, k2;
+    tri_decode(q, k, k2);
+    Lg[e] = (float)(A[e] * dsc[kNG + 3 * k2 + ch]);
+  }
+  float* Lc = Lg + rgb_off_C(nb);
+  for (int e = lane; e < kNG * n3; e += 32) {
+    const int r = e / n3, q = e - r * n3, ch = q / nb, k = q - ch * nb;
+    float acc = 0.0f;
+    for (int r2 = 0; r2 <= r; ++r2) acc += Ef[tri(r, r2)] * Tf[r2 * n3 + q];
+    Lc[e] = (float)(-(double)acc * dsc[kNG + 3 * k + ch]);
+  }
+  float* Le = Lg + rgb_off_E(nb);
+  for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {
+    int r, r2;
+    tri_decode(e, r, r2);
+    Le[e] = (float)((double)Ef[e] * dsc[r2]);
   }
   __syncwarp();
 }
@@ -626,7 +720,8 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
       }
       __syncwarp();
     }
-    factorise_store(y.l0, cg, c, H0, Hs, dsc, F.L[0] + (size_t)g * y.nt0, err, lane);
+    factorise_rgb_store(c.nb, cg, c, H0, Hs, dsc, fb + y.off_E, fb + y.off_T,
+                        F.L[0] + (size_t)g * rgb_L_size(c.nb), err, lane);
     factorise_store(y.l1, cg, c, H1, Hs, dsc, F.L[1] + (size_t)g * y.nt1, err, lane);
     factorise_store(y.l2, cg, c, H2, Hs, dsc, F.L[2] + (size_t)g * y.nt2, err, lane);
   }
@@ -745,15 +840,72 @@ __device__ __forceinline__ float logdet_IcWB(int u, float cg, const float* W, co
   return ld;
 }
 
+// Z = L~ M^T of the colour output (rows in the factor's order: SH of
+// channel 0, 1, 2, then geometric; 9 columns), from the block form of L~
+// (see Factors): an SH row of channel ch has one nonzero, in column 6 + ch.
+__device__ __forceinline__ void z_geo_rgb_row(const GJac& J, const float* Er, const float* Cr, int r, int nb,
+                                              float (&z)[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) z[q] = 0.0f;
+  for (int k = 0; k <= r; ++k) {
+    const float lk = Er[k];
+    if (k < 3) {
+      z[0] += lk * J.Jm[0][k];
+      z[1] += lk * J.Jm[1][k];
+      z[6] += lk * J.Jrgb[0][k];
+      z[7] += lk * J.Jrgb[1][k];
+      z[8] += lk * J.Jrgb[2][k];
+    }
+    if (k < 10) {
+      z[2] += lk * J.Jc[0][k];
+      z[3] += lk * J.Jc[1][k];
+      z[4] += lk * J.Jc[2][k];
+    } else {
+      z[5] += lk * J.dsig;
+    }
+  }
+  for (int ch = 0; ch < 3; ++ch) {
+    float t = 0.0f;
+    for (int k = 0; k < nb; ++k) t += Cr[ch * nb + k] * J.Y[k];
+    z[6 + ch] += J.live[ch] * t;
+  }
+}
+
+__device__ void z_rgb_warp(const GJac& J, const float* Lt, int nb, float* Z, int lane) {
+  const int n3 = 3 * nb, l = kNG + n3, T = rgb_tri_nb(nb);
+  for (int i = lane; i < l * 9; i += 32) Z[i] = 0.0f;
+  __syncwarp();
+  for (int row = lane; row < l; row += 32) {
+    if (row < n3) {
+      const int ch = row / nb, k = row - ch * nb;
+      const float* Ak = Lt + ch * T + tri(k, 0);
+      float a = 0.0f;
+      for (int k2 = 0; k2 <= k; ++k2) a += Ak[k2] * J.Y[k2];
+      Z[row * 9 + 6 + ch] = J.live[ch] * a;
+    } else {
+      const int r = row - n3;
+      float z[9];
+      z_geo_rgb_row(J, Lt + rgb_off_E(nb) + tri(r, 0), Lt + rgb_off_C(nb) + r * n3, r, nb, z);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Z[row * 9 + q] = z[q];
+    }
+  }
+  __syncwarp();
+}
+
 template <int F, int U>
 __device__ float output_gain(const GJac& J, const Consts& c, const float* p, const Factors& Fa, int64_t g,
                              const float* blk, float cg, float* Ls, float* Y, float* Z, float* W,
                              float* Bm, float* G, int lane) {
   const int l = out_l(F, c), u = out_u(F, c), nt = l * (l + 1) / 2;
-  const float* Lg = Fa.L[F] + (size_t)g * nt;   // rows read straight from global memory (L1)
-  build_Y(F, J, c, p, Y, lane);                  // ends with __syncwarp
-  for (int i = lane; i < l; i += 32) z_row<F, U>(i, u, Lg, Y, Z);
-  __syncwarp();
+  if (F == 0) {
+    z_rgb_warp(J, Fa.L[0] + (size_t)g * rgb_L_size(c.nb), c.nb, Z, lane);   // ends with __syncwarp
+  } else {
+    const float* Lg = Fa.L[F] + (size_t)g * nt;   // rows read straight from global memory (L1)
+    build_Y(F, J, c, p, Y, lane);                  // ends with __syncwarp
+    for (int i = lane; i < l; i += 32) z_row<F, U>(i, u, Lg, Y, Z);
+    __syncwarp();
+  }
   for (int i = lane; i < u * (u + 1) / 2; i += 32) {   // W = Z^T Z
     int r = (int)((sqrtf(8.0f * i + 1.0f) - 1.0f) * 0.5f);
     while (tri(r + 1, 0) <= i) ++r;
@@ -921,25 +1073,42 @@ __device__ __forceinline__ float logdet_lane(float (&Wm)[ptri(U, 0)], const floa
   return ld;
 }
 
-// Colour gain of one (view, Gaussian) in one lane. Lt: L~ of the colour
-// output (packed, shared memory, same for every lane).
+// Colour gain of one (view, Gaussian) in one lane. Lt: the block form of
+// L~ of the colour output (see Factors; shared memory, same for every lane).
 template <int DEG>
 __device__ __forceinline__ float rgb_gain_lane(const GJac& J, const float* __restrict__ Lt,
                                                const float* __restrict__ blk, float cg) {
-  constexpr int NB = (DEG + 1) * (DEG + 1), L = kNG + 3 * NB;
+  constexpr int NB = (DEG + 1) * (DEG + 1), TN = NB * (NB + 1) / 2, N3 = 3 * NB;
+  const float* Cm = Lt + 3 * TN;
+  const float* Em = Cm + kNG * N3;
   float Wm[45];
 #pragma unroll
   for (int i = 0; i < 45; ++i) Wm[i] = 0.0f;
+  // SH rows: channel ch only, W[6 + ch][6 + ch] += live_ch |A_ch Y|^2
 #pragma unroll
-  for (int i = 0; i < L; ++i) {
-    const float* Li = Lt + ptri(i, 0);
+  for (int ch = 0; ch < 3; ++ch) {
+    float ss = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      float a = 0.0f;
+#pragma unroll
+      for (int k2 = 0; k2 < NB; ++k2)
+        if (k2 <= k) a += Lt[ch * TN + ptri(k, k2)] * J.Y[k2];
+      ss += a * a;
+    }
+    Wm[ptri(6 + ch, 6 + ch)] += J.live[ch] * ss;
+  }
+  // geometric rows
+#pragma unroll
+  for (int r = 0; r < kNG; ++r) {
+    const float* Er = Em + ptri(r, 0);
     float z[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) z[q] = 0.0f;
 #pragma unroll
     for (int k = 0; k < kNG; ++k) {
-      if (k <= i) {
-        const float lk = Li[k];
+      if (k <= r) {
+        const float lk = Er[k];
         if (k < 3) {
           z[0] += lk * J.Jm[0][k];
           z[1] += lk * J.Jm[1][k];
@@ -956,19 +1125,18 @@ __device__ __forceinline__ float rgb_gain_lane(const GJac& J, const float* __res
         }
       }
     }
-    float sh[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int m = 0; m < NB; ++m)
+    for (int ch = 0; ch < 3; ++ch) {
+      float t = 0.0f;
 #pragma unroll
-      for (int ch = 0; ch < 3; ++ch)
-        if (kNG + 3 * m + ch <= i) sh[ch] += Li[kNG + 3 * m + ch] * J.Y[m];
+      for (int k = 0; k < NB; ++k) t += Cm[r * N3 + ch * NB + k] * J.Y[k];
+      z[6 + ch] += J.live[ch] * t;
+    }
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) z[6 + ch] += J.live[ch] * sh[ch];
-#pragma unroll
-    for (int r = 0; r < 9; ++r)
+    for (int rr = 0; rr < 9; ++rr)
 #pragma unroll
       for (int cc = 0; cc < 9; ++cc)
-        if (cc <= r) Wm[ptri(r, cc)] += z[r] * z[cc];
+        if (cc <= rr) Wm[ptri(rr, cc)] += z[rr] * z[cc];
   }
   float Bm[45];
   const float w2 = blk[kOffW2];
@@ -1037,7 +1205,8 @@ __host__ __device__ inline GmLayout gm_layout(const Consts& c) {
   const int l0 = kNG + 3 * c.nb, l1 = kNG;
   y.l2 = kNG + c.KC;
   y.u2 = 6 + c.K;
-  y.nt0 = l0 * (l0 + 1) / 2;
+  y.nt0 = rgb_L_size(c.nb);
+  (void)l0;
   y.nt1 = l1 * (l1 + 1) / 2;
   y.nt2 = y.l2 * (y.l2 + 1) / 2;
   auto r4 = [](int x) { return (x + 3) & ~3; };

@@ -104,11 +104,21 @@ int launch_duplicate(const DevProj& pr, int64_t n, int GX, const uint32_t* offse
                      uint32_t* vals, cudaStream_t st);
 // Stable LSD radix sort of (keys, vals) on the low `bits` key bits; the
 // result is in buffer index *which (0 or 1).
+// Stable LSD radix sort of 32-bit keys (8 bits a pass) over `bits` bits,
+// ping-ponging between keys[0/1], vals[0/1]; *which = the buffer holding the result.
+int launch_radix_sort32(uint32_t* keys[2], uint32_t* vals[2], uint32_t* hist, int64_t count, int bits, int* which,
+                        cudaStream_t st);
+// Multi-view depth order: keys (view << 31 | 31 low z bits), vals = slot v n + g.
+int launch_depth_keys(const uint32_t* zbits, int64_t n, int nv, uint64_t* keys, uint32_t* vals, cudaStream_t st);
+int launch_gather_touched(const uint32_t* touched, const uint32_t* order, int64_t m, uint32_t* out, cudaStream_t st);
+// Entries of the slots in `order`: 32-bit global tile keys and Gaussian indices.
+int launch_duplicate_sorted(const int4* rect, const uint32_t* order, int64_t n, int nv, const DevCam* cams,
+                            const uint32_t* tile_base, const uint32_t* offsets, uint32_t* keys, uint32_t* vals,
+                            cudaStream_t st);
+int launch_ranges32(const uint32_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st);
 int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaStream_t st);
 int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st);
-// Multi-view binning: keys (global tile << 32 | depth bits) of every (view, Gaussian) slot.
-int launch_duplicate_views(const DevProj& pr, int64_t n, int nv, const DevCam* cams, const uint32_t* tile_base,
-                           const uint32_t* offsets, uint64_t* keys, uint32_t* vals, cudaStream_t st);
+
 // Work-queue keys: longest tile lists first.
 int launch_queue_keys(const uint2* ranges, int ntiles, uint64_t* keys, uint32_t* vals, cudaStream_t st);
 size_t scan_scratch_elems(int64_t n);
@@ -142,11 +152,21 @@ struct CompositeArgs {
 int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage = 32);
 
 struct Factors {
-  // per output, packed lower triangle of L~ = L^-1 D^-1/2, where D = diag(H)
-  // and D^-1/2 H D^-1/2 = L L^T; hence H^-1 = L~^T L~
+  // per output, L~ = L^-1 D^-1/2, where D = diag(H) and D^-1/2 H D^-1/2 =
+  // L L^T; hence H^-1 = L~^T L~. Depth and object: packed lower triangle.
+  // Colour: the SH coefficients of different channels never meet in H (the
+  // colour-colour part of the 2D block is W2 I_3), so with the parameters
+  // ordered [SH of channel 0, 1, 2 | the 11 geometric ones] L^-1 is
+  //   [[A_0, 0, 0, 0], [0, A_1, 0, 0], [0, 0, A_2, 0], [C_0, C_1, C_2, E]]
+  // and is stored as A_0..A_2 (packed nb-triangles), C (11 x 3 nb, row-major,
+  // column c nb + k), E (packed 11-triangle); see rgb_L_size.
   float* L[3];
   int l[3];
 };
+__host__ __device__ inline int rgb_tri_nb(int nb) { return nb * (nb + 1) / 2; }
+__host__ __device__ inline int rgb_off_C(int nb) { return 3 * rgb_tri_nb(nb); }
+__host__ __device__ inline int rgb_off_E(int nb) { return 3 * rgb_tri_nb(nb) + kNG * 3 * nb; }
+__host__ __device__ inline int rgb_L_size(int nb) { return rgb_off_E(nb) + kNG * (kNG + 1) / 2; }
 // Training Hessians: H^f_g = lambda I + c_g sum_t M_t^T B_t M_t, scaled and factorised.
 int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams, const float* blocks,
                          int n_train, const Factors& f, int* d_err, cudaStream_t st);

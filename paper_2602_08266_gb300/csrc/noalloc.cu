@@ -19,7 +19,8 @@ int launch_radix_pass(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, 
 namespace {
 
 constexpr int64_t kMaxPairs = NBV_NOALLOC_MAX_PAIRS;
-// radix histograms for kMaxPairs keys: 2 x 256 x ceil(kMaxPairs / 2048) words
+// radix histograms for kMaxPairs keys: 2 x 256 x ceil(kMaxPairs / 2048) words (the
+// radix tile holds at least 2048 keys)
 // plus the block sums of their scan (ceil(. / 4096) + 64 words)
 constexpr int64_t kBlocks = (kMaxPairs + 2047) / 2048;
 constexpr int64_t kHistWords = 2 * 256 * kBlocks + (256 * kBlocks + 4095) / 4096 + 64;

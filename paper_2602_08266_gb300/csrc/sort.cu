@@ -102,30 +102,6 @@ __global__ void k_duplicate(const int4* __restrict__ rect, const uint32_t* __res
     }
 }
 
-// All views: slot v n + g covers the tiles of its rectangle in view v; the key
-// carries the global tile id (first tile of view v + local tile).
-__global__ void k_duplicate_views(const int4* __restrict__ rect, const uint32_t* __restrict__ zbits, int64_t n,
-                                  int nv, const DevCam* __restrict__ cams, const uint32_t* __restrict__ tile_base,
-                                  const uint32_t* __restrict__ offsets, uint64_t* __restrict__ keys,
-                                  uint32_t* __restrict__ vals) {
-  const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (slot >= n * nv) return;
-  const int4 r = rect[slot];
-  if (r.x < 0) return;
-  const int v = (int)(slot / n);
-  const uint32_t g = (uint32_t)(slot - (int64_t)v * n);
-  const int GX = cams[v].GX;
-  const uint32_t base = tile_base[v];
-  uint32_t o = offsets[slot];
-  const uint64_t zb = zbits[slot];
-  for (int ty = r.z; ty < r.w; ++ty)
-    for (int tx = r.x; tx < r.y; ++tx) {
-      keys[o] = ((uint64_t)(base + (uint32_t)(ty * GX + tx)) << 32) | zb;
-      vals[o] = g;
-      ++o;
-    }
-}
-
 // Work-queue keys: longest tile list first, ties by tile id.
 __global__ void k_queue_keys(const uint2* __restrict__ ranges, int ntiles, uint64_t* __restrict__ keys,
                              uint32_t* __restrict__ vals) {
@@ -137,11 +113,12 @@ __global__ void k_queue_keys(const uint2* __restrict__ ranges, int ntiles, uint6
 }
 
 constexpr int kRadixThreads = 256;
-constexpr int kRadixRounds = 8;
+constexpr int kRadixRounds = 11;   // tile of 2816 keys: the staging fits the 48 KB of static shared memory
 constexpr int kRadixTile = kRadixThreads * kRadixRounds;
 
-__global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
-                             uint32_t* __restrict__ ghist, int nblocks) {
+template <typename K>
+__global__ void k_radix_hist(const K* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ ghist,
+                             int nblocks) {
   __shared__ uint32_t h[256];
   const int tid = threadIdx.x;
   h[tid] = 0;
@@ -156,27 +133,53 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int s
   ghist[(int64_t)tid * nblocks + blockIdx.x] = h[tid];
 }
 
-__global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n,
-                                int shift, const uint32_t* __restrict__ gscan, int nblocks) {
+// One stable counting pass over a tile of kRadixTile keys: every element's
+// place among the tile's elements of its digit (in input order) is ranked
+// round by round (warp match + per-warp counts), the tile is rearranged by
+// digit in shared memory, and written out in that order, so that each
+// digit's elements leave as one contiguous run.
+template <typename K>
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const K* __restrict__ kin,
+                                                                 const uint32_t* __restrict__ vin,
+                                                                 K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                                 int64_t n, int shift,
+                                                                 const uint32_t* __restrict__ ghist,
+                                                                 const uint32_t* __restrict__ gscan, int nblocks) {
   __shared__ uint32_t cnt[kRadixThreads / 32][256];
-  __shared__ uint32_t run[256];
+  __shared__ uint32_t run[256], lstart[256], gbase[256], wsum[kRadixThreads / 32];
+  __shared__ K sk[kRadixTile];
+  __shared__ uint32_t sv[kRadixTile];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  run[tid] = gscan[(int64_t)tid * nblocks + blockIdx.x];
+  // tile-local start of each digit: exclusive scan of this tile's counts
+  const uint32_t myc = ghist[(int64_t)tid * nblocks + blockIdx.x];
+  uint32_t x = myc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (int w = 0; w < wid; ++w) pre += wsum[w];
+  lstart[tid] = pre + x - myc;
+  gbase[tid] = gscan[(int64_t)tid * nblocks + blockIdx.x];
+  run[tid] = 0;
   const unsigned lt = (1u << lane) - 1u;
   const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  const int tile_n = (int)((n - base) < kRadixTile ? (n - base) : kRadixTile);
   for (int r = 0; r < kRadixRounds; ++r) {
 #pragma unroll
     for (int w = 0; w < kRadixThreads / 32; ++w) cnt[w][tid] = 0;
     __syncthreads();
-    const int64_t i = base + r * kRadixThreads + tid;
-    const bool valid = i < n;
-    uint64_t key = 0;
+    const int li = r * kRadixThreads + tid;
+    const bool valid = li < tile_n;
+    K key = 0;
     uint32_t val = 0;
     int digit = 256;
     if (valid) {
-      key = kin[i];
-      val = vin[i];
+      key = kin[base + li];
+      val = vin[base + li];
       digit = (int)((key >> shift) & 255u);
     }
     const unsigned peers = __match_any_sync(0xffffffffu, digit);
@@ -184,18 +187,96 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const uint32_t
     if (valid && lrank == 0) cnt[wid][digit] = (uint32_t)__popc(peers);
     __syncthreads();
     if (valid) {
-      uint32_t off = run[digit] + (uint32_t)lrank;
-      for (int w = 0; w < wid; ++w) off += cnt[w][digit];
-      kout[off] = key;
-      vout[off] = val;
+      uint32_t pos = lstart[digit] + run[digit] + (uint32_t)lrank;
+      for (int w = 0; w < wid; ++w) pos += cnt[w][digit];
+      sk[pos] = key;
+      sv[pos] = val;
     }
     __syncthreads();
     uint32_t add = 0;
 #pragma unroll
     for (int w = 0; w < kRadixThreads / 32; ++w) add += cnt[w][tid];
     run[tid] += add;
-    __syncthreads();
   }
+  __syncthreads();
+  for (int i = tid; i < tile_n; i += kRadixThreads) {
+    const K key = sk[i];
+    const int d = (int)((key >> shift) & 255u);
+    const uint32_t o = gbase[d] + (uint32_t)i - lstart[d];
+    kout[o] = key;
+    vout[o] = sv[i];
+  }
+}
+
+// Depth keys of every (view, Gaussian) slot: (view << 31) | the low 31 bits
+// of the float bits of camera z (z > near > 0, so the sign bit is clear for
+// every slot that has entries); value = the slot.
+__global__ void k_depth_keys(const uint32_t* __restrict__ zbits, int64_t n, int nv, uint64_t* __restrict__ keys,
+                             uint32_t* __restrict__ vals) {
+  const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (slot >= n * nv) return;
+  const uint64_t v = (uint64_t)(slot / n);
+  keys[slot] = (v << 31) | (uint64_t)(zbits[slot] & 0x7FFFFFFFu);
+  vals[slot] = (uint32_t)slot;
+}
+
+__global__ void k_gather_touched(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order,
+                                 int64_t m, uint32_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) out[i] = touched[order[i]];
+}
+
+// Slots in depth order (per view): each emits its tiles (global tile id,
+// 32-bit key) and its Gaussian index, so that a stable sort on the tile id
+// alone leaves every tile's entries in (depth bits, Gaussian index) order.
+__global__ void k_duplicate_sorted(const int4* __restrict__ rect, const uint32_t* __restrict__ order, int64_t n,
+                                   int64_t m, const DevCam* __restrict__ cams,
+                                   const uint32_t* __restrict__ tile_base, const uint32_t* __restrict__ offsets,
+                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const uint32_t slot = order[i];
+  const int4 r = rect[slot];
+  if (r.x < 0) return;
+  const int v = (int)(slot / (uint64_t)n);
+  const uint32_t g = (uint32_t)(slot - (uint64_t)v * n);
+  const int GX = cams[v].GX;
+  const uint32_t base = tile_base[v];
+  uint32_t o = offsets[i];
+  for (int ty = r.z; ty < r.w; ++ty)
+    for (int tx = r.x; tx < r.y; ++tx) {
+      keys[o] = base + (uint32_t)(ty * GX + tx);
+      vals[o] = g;
+      ++o;
+    }
+}
+
+__global__ void k_ranges32(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t t = keys[i];
+  if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
+  if (i == n - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+}
+
+template <typename K>
+int radix_passes(K* keys[2], uint32_t* vals[2], uint32_t* hist, int64_t count, int bits, int* which,
+                 cudaStream_t st) {
+  *which = 0;
+  if (count <= 1) return 0;
+  const int nblocks = (int)((count + kRadixTile - 1) / kRadixTile);
+  int l = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    const int src = *which, dst = 1 - src;
+    k_radix_hist<K><<<nblocks, kRadixThreads, 0, st>>>(keys[src], count, shift, hist, nblocks);
+    const int64_t hn = 256LL * nblocks;
+    l += 1 + scan_rec(hist, hist + hn, hn, hist + 2 * hn, st);
+    k_radix_scatter<K><<<nblocks, kRadixThreads, 0, st>>>(keys[src], vals[src], keys[dst], vals[dst], count, shift,
+                                                          hist, hist + hn, nblocks);
+    ++l;
+    *which = dst;
+  }
+  return l;
 }
 
 __global__ void k_ranges(const uint64_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
@@ -223,22 +304,43 @@ int launch_duplicate(const DevProj& pr, int64_t n, int GX, const uint32_t* offse
 }
 
 int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaStream_t st) {
-  *which = 0;
-  if (count <= 1) return 0;
-  const int nblocks = (int)((count + kRadixTile - 1) / kRadixTile);
-  int l = 0;
-  for (int shift = 0; shift < bits; shift += 8) {
-    const int src = *which, dst = 1 - src;
-    k_radix_hist<<<nblocks, kRadixThreads, 0, st>>>(b.keys[src], count, shift, b.hist, nblocks);
-    const int64_t hn = 256LL * nblocks;
-    l += 1 + scan_rec(b.hist, b.hist + hn, hn, b.hist + 2 * hn, st);
-    k_radix_scatter<<<nblocks, kRadixThreads, 0, st>>>(b.keys[src], b.vals[src], b.keys[dst],
-                                                       b.vals[dst], count, shift, b.hist + hn,
-                                                       nblocks);
-    ++l;
-    *which = dst;
-  }
-  return l;
+  return radix_passes<uint64_t>(b.keys, b.vals, b.hist, count, bits, which, st);
+}
+
+int launch_radix_sort32(uint32_t* keys[2], uint32_t* vals[2], uint32_t* hist, int64_t count, int bits, int* which,
+                        cudaStream_t st) {
+  return radix_passes<uint32_t>(keys, vals, hist, count, bits, which, st);
+}
+
+int launch_depth_keys(const uint32_t* zbits, int64_t n, int nv, uint64_t* keys, uint32_t* vals, cudaStream_t st) {
+  const int64_t m = n * nv;
+  if (m <= 0) return 0;
+  k_depth_keys<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(zbits, n, nv, keys, vals);
+  return 1;
+}
+
+int launch_gather_touched(const uint32_t* touched, const uint32_t* order, int64_t m, uint32_t* out,
+                          cudaStream_t st) {
+  if (m <= 0) return 0;
+  k_gather_touched<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(touched, order, m, out);
+  return 1;
+}
+
+int launch_duplicate_sorted(const int4* rect, const uint32_t* order, int64_t n, int nv, const DevCam* cams,
+                            const uint32_t* tile_base, const uint32_t* offsets, uint32_t* keys, uint32_t* vals,
+                            cudaStream_t st) {
+  const int64_t m = n * nv;
+  if (m <= 0) return 0;
+  k_duplicate_sorted<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, order, n, m, cams, tile_base, offsets, keys,
+                                                                  vals);
+  return 1;
+}
+
+int launch_ranges32(const uint32_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st) {
+  cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
+  if (count <= 0) return 0;
+  k_ranges32<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(keys, count, ranges);
+  return 1;
 }
 
 // One stable radix pass on the 8 key bits at `shift`, from (kin, vin) to
@@ -248,9 +350,10 @@ int launch_radix_pass(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, 
   if (count <= 0) return 0;
   const int nblocks = (int)((count + kRadixTile - 1) / kRadixTile);
   const int64_t hn = 256LL * nblocks;
-  k_radix_hist<<<nblocks, kRadixThreads, 0, st>>>(kin, count, shift, hist, nblocks);
+  k_radix_hist<uint64_t><<<nblocks, kRadixThreads, 0, st>>>(kin, count, shift, hist, nblocks);
   int l = 1 + scan_rec(hist, hist + hn, hn, hist + 2 * hn, st);
-  k_radix_scatter<<<nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, count, shift, hist + hn, nblocks);
+  k_radix_scatter<uint64_t><<<nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, count, shift, hist, hist + hn,
+                                                               nblocks);
   return l + 1;
 }
 
@@ -258,15 +361,6 @@ int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
   if (count <= 0) return 0;
   k_ranges<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(keys, count, ranges);
-  return 1;
-}
-
-int launch_duplicate_views(const DevProj& pr, int64_t n, int nv, const DevCam* cams, const uint32_t* tile_base,
-                           const uint32_t* offsets, uint64_t* keys, uint32_t* vals, cudaStream_t st) {
-  const int64_t tot = n * nv;
-  if (tot <= 0) return 0;
-  k_duplicate_views<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(pr.rect, pr.zbits, n, nv, cams, tile_base,
-                                                                   offsets, keys, vals);
   return 1;
 }
 

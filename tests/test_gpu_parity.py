@@ -375,3 +375,26 @@ def test_autotune_picks_a_valid_tiling_and_scores_match_oracle(P):
     sc2.set_train_views(wl.train)
     sc2.set_candidates(wl.cand)
     assert sc2.autotune() == (tw, th, st)
+
+
+@pytest.mark.parametrize("name,n_views,views", [("tiny", 8, None), ("scene", 6, (0, 5))])
+def test_batched_tile_lists_bit_exact(P, name, n_views, views):
+    """The multi-view binning (depth order of all (view, Gaussian) slots,
+    duplication in that order, stable sort on the 32-bit tile id) gives
+    every candidate exactly the oracle's (depth bits, index) lists."""
+    wl = S.make_workload(name, n_views=n_views)
+    if name == "tiny":
+        wl.cand = _mixed(wl)
+    sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=1)
+    sc.load_scene(wl.scene)
+    sc.set_train_views(wl.train)
+    sc.set_candidates(wl.cand)
+    sc.prepare(-1)
+    sc.score_host()
+    o = O.OracleScene(wl.scene)
+    for v in (views if views is not None else range(wl.cand.n)):
+        off, ids = sc.debug_tile_lists(2, v)
+        ooff, oids = o.tile_lists(wl.cand, v)
+        np.testing.assert_array_equal(off.cpu().numpy(), ooff)
+        np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    sc.close()
