@@ -36,7 +36,7 @@ SMS = 152
 FP32_LANES = 128
 
 
-def parse():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--views", type=int, default=None, help="override the candidate count (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true", help="keep 16x16 tiles, stage 32")
     ap.add_argument("--only", default=None, choices=[None, "plain", "batched"], help="time one path only")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_info():
@@ -140,6 +140,32 @@ def fp32_peak_tflops(clock_mhz):
     return SMS * FP32_LANES * 2 * clock_mhz * 1e6 / 1e12
 
 
+# ------------------------------------------------------- multi-rank helpers
+def rank_candidates(S, np, wl, rank, world):
+    """Every rank scores its own candidate set (weak scaling): rank 0 keeps
+    the workload's cameras, rank r > 0 draws the same number on the same
+    sphere from seed 1000 + r."""
+    if world <= 1 or rank == 0:
+        return wl.cand
+    return S.sphere_cameras(np.random.default_rng(1000 + rank), wl.cand.n, 0.6,
+                            int(wl.cand.width[0]), int(wl.cand.height[0]), float(wl.cand.fx[0]))
+
+
+def max_over_ranks(torch, value, world, device):
+    """The largest of the ranks' values (the step time the job is judged by)."""
+    if world <= 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(views_per_rank, world, steps, total_ms):
+    """Whole-job views per second: the units every rank processed over the
+    slowest rank's time."""
+    return views_per_rank * world * steps / (total_ms / 1e3)
+
+
 # ---------------------------------------------------------- our GPU arm
 def run_ours(args):
     import numpy as np
@@ -159,10 +185,7 @@ def run_ours(args):
     P.load_library()
 
     wl = S.make_workload(args.workload, seed=0, n_views=args.views)
-    # every rank scores its own candidate set (weak scaling)
-    if world > 1:
-        wl.cand = S.sphere_cameras(np.random.default_rng(1000 + rank), wl.cand.n, 0.6,
-                                   int(wl.cand.width[0]), int(wl.cand.height[0]), float(wl.cand.fx[0]))
+    wl.cand = rank_candidates(S, np, wl, rank, world)
     dev = torch.device("cuda", local)
     sc_arrays = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
                  (wl.scene.means, wl.scene.log_scales, wl.scene.quats, wl.scene.opacity,
@@ -225,11 +248,7 @@ def run_ours(args):
         stats = scorer.work_stats()
         scorer.set_profiling(False)
         scorer.close()
-        total_ms = sum(times)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(torch, sum(times), world, dev)
         return dict(total=total_ms, launches=launches, phases=phases, stats=stats, clocks=ck, best=best,
                     tiling=tiling)
 
@@ -243,7 +262,7 @@ def run_ours(args):
     prof = measure(True, profile=True)
     # the per-view path (one launch sequence per candidate), profiled
     plain = measure(False, profile=True)
-    value = views / (head["total"] / 1e3)
+    value = job_throughput(wl.cand.n, world, args.steps, head["total"])
 
     # roofline of the dominant kernel (the fused compositing + information kernel)
     peak = fp32_peak_tflops(2070.0)
@@ -400,7 +419,7 @@ def run_reference(args):
 
 
 def main():
-    args = parse()
+    args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     else:
