@@ -260,6 +260,83 @@ const char* nbv_last_error(const nbv_ctx* ctx);
 /* Number of kernel launches the context issued so far. */
 int64_t nbv_launch_count(const nbv_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Learned candidate pre-scoring (a pattern layered on the method; the paper
+ * scores every candidate exactly). A per-view descriptor of the projected
+ * Gaussians feeds a 3-layer MLP (BF16 weights and activations, FP32
+ * accumulation on the tensor cores) trained on the exact normalised scores
+ * (Eq. 11) that nbv_score produces; nbv_score_pruned keeps the candidates
+ * it ranks highest and scores only those exactly.
+ * ---------------------------------------------------------------------- */
+
+/* Descriptor length: 4 x 64 image-grid cells + 128 object bins. */
+#define NBV_DESC_DIM 384
+
+/* Descriptors of every candidate into `out` (DEVICE float [n_cand][384]):
+ * for each Gaussian whose centre projects in front of the near plane and
+ * inside the image, with opacity sigma, confidence c_g (Eq. 7 / 12, as the
+ * last nbv_prepare set it), camera depth z and training observation
+ * o_g = sum over the training views and their pixels of w^2 (w = alpha T):
+ *   [0, 64)    sum sigma over an 8 x 8 grid of image cells,
+ *   [64, 128)  sum c_g sigma per cell,
+ *   [128, 192) sum c_g sigma / z per cell,
+ *   [192, 256) sum c_g sigma / (1 + o_g) per cell,
+ *   [256, 384) sum c_g sigma per most-probable object id (0..K),
+ * each feature then mapped to log(1 + s x) with s = 64 / n for the cell
+ * features and (K + 1) / n for the object bins (n = number of Gaussians).
+ * Cells: floor(8 mx / W), floor(8 my / H) of the projected centre, computed
+ * in single precision. Errors: NBV_ERR_STATE (no prepare), NBV_ERR_ARG. */
+int nbv_descriptors(nbv_ctx* ctx, float* out);
+
+typedef struct nbv_mlp nbv_mlp;
+
+/* An MLP d_in -> width -> width -> 1 with ReLU (width a multiple of 16,
+ * <= 256; d_in <= 4096), He-uniform initial weights drawn from `seed`
+ * (splitmix64), zero biases. Parameters (FP32, flattened in this order):
+ * W1 [width][d_in], b1 [width], W2 [width][width], b2 [width], w3 [width],
+ * b3. Runs on `cuda_stream`. */
+int nbv_mlp_create(int d_in, int width, uint64_t seed, void* cuda_stream, nbv_mlp** out);
+void nbv_mlp_destroy(nbv_mlp* mlp);
+int64_t nbv_mlp_num_params(const nbv_mlp* mlp);
+/* Copy the FP32 parameters to / from a DEVICE array of nbv_mlp_num_params. */
+int nbv_mlp_get_params(nbv_mlp* mlp, float* out);
+int nbv_mlp_set_params(nbv_mlp* mlp, const float* in);
+/* y [rows] = MLP(x [rows][d_in]), DEVICE arrays. The input, the weights and
+ * the hidden activations are rounded to BF16; products accumulate in FP32.
+ * Synchronises. Errors: NBV_ERR_TIMEOUT if a tensor-core wait gave up. */
+int nbv_mlp_forward(nbv_mlp* mlp, const float* x, int rows, float* y);
+/* Gradient of the mean squared error mean_m (y_m - t_m)^2 over the
+ * parameters (DEVICE float [num_params], same order), by the hand-written
+ * backward: the two hidden layers' input and weight gradients are tensor-core
+ * products of the BF16 activations; biases and the head reduce in double.
+ * *loss (host) receives the loss before the step. Synchronises. */
+int nbv_mlp_gradients(nbv_mlp* mlp, const float* x, const float* t, int rows, float* grads, double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) of
+ * learning rate lr on the mean squared error of this batch; loss may be
+ * NULL (then the call does not synchronise). */
+int nbv_mlp_train_step(nbv_mlp* mlp, const float* x, const float* t, int rows, float lr, double* loss);
+
+/* D [M][N] (row stride ldd, FP32) = sum_k A(m, k) B(n, k) with BF16
+ * A(m, k) = A[m a_sm + k a_sk], B(n, k) = B[n b_sn + k b_sk] (DEVICE
+ * arrays; the strides express any transposition), on tcgen05 tensor cores
+ * with tensor-memory accumulators. *d_err (DEVICE int, may be NULL) is set
+ * if a bounded wait for the tensor cores gave up. Asynchronous. */
+int nbv_gemm_bf16(const uint16_t* A, int64_t a_sm, int64_t a_sk, const uint16_t* B, int64_t b_sn, int64_t b_sk,
+                  float* D, int64_t ldd, int M, int N, int K, int* d_err, void* cuda_stream);
+
+/* Pre-score every candidate with the MLP over its descriptor, keep the
+ * `keep` highest predictions (ties to the lower index) and score only those
+ * exactly (nbv_score's path); pred (DEVICE [n_cand], may be NULL) receives
+ * the predictions, kept (HOST int [keep]) the kept candidate indices in
+ * descending prediction order, exact (HOST float [keep][4], may be NULL)
+ * their exact rows as nbv_score gives them, *best / *best_score the
+ * argmax among the kept ones (an index into the full candidate list). The
+ * context's candidate set is unchanged on return. Synchronises.
+ * Errors: NBV_ERR_ARG (keep < 1, MLP input size not NBV_DESC_DIM), NBV_ERR_STATE
+ * (no prepare), those of nbv_score. */
+int nbv_score_pruned(nbv_ctx* ctx, nbv_mlp* mlp, int keep, float* pred, int* kept, float* exact, int* best,
+                     float* best_score);
+
 #ifdef __cplusplus
 }
 #endif

@@ -832,6 +832,32 @@ void orc_render(void* h, const float* cam, const int* wh, double* rgb, double* d
   }
 }
 
+// Per Gaussian, the sum over the view's pixels of w^2 = (alpha T)^2 of its
+// blended splats (how strongly the view observes it).
+void orc_view_w2(void* h, const float* cam, const int* wh, double* w2) {
+  Scene* s = static_cast<Scene*>(h);
+  ViewData v;
+  build_view(*s, read_cam(cam, wh), v, true);
+  const int W = wh[0], H = wh[1];
+  for (int64_t g = 0; g < s->n; ++g) w2[g] = 0.0;
+#pragma omp parallel
+  {
+    PixelOut o;
+    std::vector<double> acc(s->n, 0.0);
+#pragma omp for schedule(dynamic, 4)
+    for (int py = 0; py < H; ++py)
+      for (int px = 0; px < W; ++px) {
+        composite_pixel(*s, v, px, py, o);
+        for (const Step& st : o.steps) {
+          const double w = st.alpha * st.T;
+          acc[st.g] += w * w;
+        }
+      }
+#pragma omp critical
+    for (int64_t g = 0; g < s->n; ++g) w2[g] += acc[g];
+  }
+}
+
 // Jacobian blocks A^f_g of one view for the Gaussians with mask[g] != 0
 // (mask may be NULL for all), written densely in the order of g.
 void orc_view_blocks(void* h, const float* cam, const int* wh, const uint8_t* mask, double* Ar,

@@ -51,6 +51,8 @@ def _load():
     lib.orc_confidence.argtypes = [P, P]
     lib.orc_project32.argtypes = [P, P, P, P, P, P, P, P]
     lib.orc_project64.argtypes = [P, P, P, P]
+    lib.orc_view_w2.restype = None
+    lib.orc_view_w2.argtypes = [P, P, P, P]
     lib.orc_tile_lists.restype = i64
     lib.orc_tile_lists.argtypes = [P, P, P, P, P, i64]
     lib.orc_render.argtypes = [P, P, P, P, P, P, P, P, P]
@@ -168,6 +170,13 @@ class OracleScene:
         c = np.zeros(self.n, np.float64)
         self.lib.orc_confidence(self._h, _ptr(c))
         return c
+
+    def view_w2(self, cams, i):
+        """Per Gaussian, sum over view i's pixels of (alpha T)^2."""
+        c, wh = cam_arrays(cams, i)
+        w2 = np.zeros(self.n, np.float64)
+        self.lib.orc_view_w2(self._h, _ptr(c), _ptr(wh), _ptr(w2))
+        return w2
 
     def project32(self, cams, i):
         c, wh = cam_arrays(cams, i)

@@ -82,6 +82,20 @@ _SIGS = [
     ("nbv_get_tiling", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
     ("nbv_sort_tile_keys_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P, _P, _P]),
+    ("nbv_descriptors", ctypes.c_int, [_P, _P]),
+    ("nbv_mlp_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.POINTER(_P)]),
+    ("nbv_mlp_destroy", None, [_P]),
+    ("nbv_mlp_num_params", ctypes.c_int64, [_P]),
+    ("nbv_mlp_get_params", ctypes.c_int, [_P, _P]),
+    ("nbv_mlp_set_params", ctypes.c_int, [_P, _P]),
+    ("nbv_mlp_forward", ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    ("nbv_mlp_gradients", ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
+    ("nbv_mlp_train_step", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_float,
+                                          ctypes.POINTER(ctypes.c_double)]),
+    ("nbv_gemm_bf16", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int64, _P,
+                                     ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+    ("nbv_score_pruned", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_float)]),
     ("nbv_last_error", ctypes.c_char_p, [_P]),
     ("nbv_launch_count", ctypes.c_int64, [_P]),
 ]
@@ -351,3 +365,114 @@ class NBVScorer:
 
     def launch_count(self) -> int:
         return int(self.lib.nbv_launch_count(self._h))
+
+    # ------------------------------------------------- learned pre-scoring
+    DESC_DIM = 384
+
+    def descriptors(self):
+        """[n_cand, 384] per-candidate descriptors (after prepare)."""
+        out = self.torch.empty((max(self.n_cand, 1), self.DESC_DIM), device="cuda")
+        self._check(self.lib.nbv_descriptors(self._h, _dptr(out)))
+        self.torch.cuda.synchronize()
+        return out[:self.n_cand]
+
+    def score_pruned(self, mlp, keep: int):
+        """MLP pre-scores every candidate, the `keep` best are scored
+        exactly; returns dict(pred, kept, exact, best, best_score)."""
+        n = self.n_cand
+        keep = max(1, min(int(keep), n))
+        pred = self.torch.empty(max(n, 1), device="cuda")
+        kept = np.zeros(keep, np.int32)
+        exact = np.zeros((keep, 4), np.float32)
+        best, bs = ctypes.c_int(), ctypes.c_float()
+        self._check(self.lib.nbv_score_pruned(self._h, mlp._h, keep, _dptr(pred),
+                                              ctypes.c_void_p(kept.ctypes.data),
+                                              ctypes.c_void_p(exact.ctypes.data), ctypes.byref(best),
+                                              ctypes.byref(bs)))
+        return dict(pred=pred[:n], kept=kept, exact=exact, best=int(best.value), best_score=float(bs.value))
+
+
+class MLP:
+    """The learned candidate scorer (nbv_mlp): d_in -> width -> width -> 1,
+    BF16 tensor-core layers, trained with the library's own backward and Adam."""
+
+    def __init__(self, d_in: int = 384, width: int = 256, seed: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self.lib.nbv_mlp_create(int(d_in), int(width), ctypes.c_uint64(int(seed)),
+                                     ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if rc != NBV_OK:
+            raise NBVError(rc, "nbv_mlp_create failed")
+        self._h = h
+        self.d_in, self.width = int(d_in), int(width)
+        self.P = int(self.lib.nbv_mlp_num_params(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.nbv_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != NBV_OK:
+            raise NBVError(rc, what)
+
+    def get_params(self):
+        out = self.torch.empty(self.P, device="cuda")
+        self._check(self.lib.nbv_mlp_get_params(self._h, _dptr(out)), "get_params")
+        self.torch.cuda.synchronize()
+        return out
+
+    def set_params(self, p):
+        p = p.detach().float().contiguous().cuda()
+        self._check(self.lib.nbv_mlp_set_params(self._h, _dptr(p)), "set_params")
+        self.torch.cuda.synchronize()
+
+    def forward(self, x):
+        x = x.detach().float().contiguous()
+        y = self.torch.empty(max(x.shape[0], 1), device="cuda")
+        self._check(self.lib.nbv_mlp_forward(self._h, _dptr(x), int(x.shape[0]), _dptr(y)), "forward")
+        return y[:x.shape[0]]
+
+    def gradients(self, x, t):
+        x = x.detach().float().contiguous()
+        t = t.detach().float().contiguous()
+        g = self.torch.empty(self.P, device="cuda")
+        loss = ctypes.c_double()
+        self._check(self.lib.nbv_mlp_gradients(self._h, _dptr(x), _dptr(t), int(x.shape[0]), _dptr(g),
+                                               ctypes.byref(loss)), "gradients")
+        return g, float(loss.value)
+
+    def train_step(self, x, t, lr: float, want_loss: bool = True):
+        loss = ctypes.c_double()
+        rc = self.lib.nbv_mlp_train_step(self._h, _dptr(x), _dptr(t), int(x.shape[0]), ctypes.c_float(lr),
+                                         ctypes.byref(loss) if want_loss else None)
+        self._check(rc, "train_step")
+        return float(loss.value) if want_loss else None
+
+
+def gemm_bf16(A, a_strides, B, b_strides, M, N, K):
+    """D [M, N] float32 = sum_k A(m, k) B(n, k) on the tensor cores; A and B
+    are bfloat16 CUDA tensors addressed with the given (row, k) strides."""
+    import torch
+    lib = load_library()
+    D = torch.empty((M, N), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib.nbv_gemm_bf16(_dptr(A), a_strides[0], a_strides[1], _dptr(B), b_strides[0], b_strides[1], _dptr(D),
+                           N, M, N, K, _dptr(err), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != NBV_OK:
+        raise NBVError(rc, "nbv_gemm_bf16")
+    torch.cuda.synchronize()
+    if int(err.item()) != 0:
+        raise NBVError(-5, "tensor-core wait gave up")
+    return D

@@ -4,6 +4,7 @@
 //   -> per-Gaussian log-det gains -> reduction -> scores.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -85,6 +86,11 @@ struct nbv_ctx {
 
   // batched multi-view scoring (cfg.batched): buffers sized once per
   // (scene, candidate set), the whole score captured in a CUDA graph
+  DevCam* d_desc_cams = nullptr;  // candidate cameras for the descriptors
+  float* desc_raw = nullptr;
+  float* desc = nullptr;
+  float* d_pred = nullptr;
+  size_t desc_cap = 0;             // candidates the descriptor buffers hold
   struct Batched {
     bool ready = false;             // buffers sized for the current scene / candidates
     int nv = 0, ntiles = 0;
@@ -647,6 +653,8 @@ void nbv_destroy(nbv_ctx* ctx) {
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   if (ctx->h_total) cudaFreeHost(ctx->h_total);
+  for (void* p : {(void*)ctx->d_desc_cams, (void*)ctx->desc_raw, (void*)ctx->desc, (void*)ctx->d_pred})
+    if (p) cudaFree(p);
   if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   delete ctx;
 }
@@ -968,6 +976,80 @@ int nbv_work_stats(nbv_ctx* ctx, int64_t* out4) {
   }
   out4[0] = (int64_t)h[0]; out4[1] = (int64_t)h[1]; out4[2] = (int64_t)h[2];
   out4[3] = ctx->composite_launches;
+  return NBV_OK;
+}
+
+
+namespace {
+int ensure_desc(nbv_ctx* ctx, int nc) {
+  if ((size_t)nc <= ctx->desc_cap) return NBV_OK;
+  for (void* p : {(void*)ctx->d_desc_cams, (void*)ctx->desc_raw, (void*)ctx->desc, (void*)ctx->d_pred})
+    if (p) cudaFree(p);
+  ctx->d_desc_cams = nullptr; ctx->desc_raw = nullptr; ctx->desc = nullptr; ctx->d_pred = nullptr;
+  ctx->desc_cap = 0;
+  CKR(alloc(ctx, &ctx->d_desc_cams, (size_t)nc));
+  CKR(alloc(ctx, &ctx->desc_raw, (size_t)nc * NBV_DESC_DIM));
+  CKR(alloc(ctx, &ctx->desc, (size_t)nc * NBV_DESC_DIM));
+  CKR(alloc(ctx, &ctx->d_pred, (size_t)nc));
+  ctx->desc_cap = (size_t)nc;
+  return NBV_OK;
+}
+}  // namespace
+
+int nbv_descriptors(nbv_ctx* ctx, float* out) {
+  if (!ctx || !out) return NBV_ERR_ARG;
+  if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
+  if (!ctx->prepared) return fail(ctx, NBV_ERR_STATE, "nbv_descriptors before nbv_prepare");
+  const int nc = (int)ctx->cand.size();
+  if (nc == 0) return NBV_OK;
+  CKR(ensure_desc(ctx, nc));
+  std::vector<DevCam> hc(nc);
+  for (int v = 0; v < nc; ++v) hc[v] = to_dev(ctx->cand[v], ctx->tw, ctx->th);
+  CK(cudaMemcpyAsync(ctx->d_desc_cams, hc.data(), sizeof(DevCam) * nc, cudaMemcpyHostToDevice, ctx->st));
+  CKR(check_launch(ctx, launch_descriptors(dev_scene(ctx), ctx->c, ctx->d_desc_cams, nc, ctx->train_blocks,
+                                           (int)ctx->train.size(), ctx->nBp, ctx->desc_raw, out, ctx->st)));
+  CK(cudaStreamSynchronize(ctx->st));   // the host copy of the cameras above
+  return NBV_OK;
+}
+
+int nbv_score_pruned(nbv_ctx* ctx, nbv_mlp* mlp, int keep, float* pred, int* kept, float* exact, int* best,
+                     float* best_score) {
+  if (!ctx || !mlp || keep < 1 || !kept || !best || !best_score) return NBV_ERR_ARG;
+  if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
+  if (!ctx->prepared) return fail(ctx, NBV_ERR_STATE, "nbv_score_pruned before nbv_prepare");
+  const int nc = (int)ctx->cand.size();
+  if (nc == 0) return fail(ctx, NBV_ERR_STATE, "no candidates");
+  if (keep > nc) keep = nc;
+  CKR(ensure_desc(ctx, nc));
+  CKR(nbv_descriptors(ctx, ctx->desc));
+  const int rc = nbv_mlp_forward(mlp, ctx->desc, nc, ctx->d_pred);
+  if (rc != NBV_OK) return fail(ctx, rc, "MLP forward failed (input size must be NBV_DESC_DIM)");
+  std::vector<float> hp(nc);
+  CK(cudaMemcpy(hp.data(), ctx->d_pred, sizeof(float) * nc, cudaMemcpyDeviceToHost));
+  if (pred) CK(cudaMemcpy(pred, ctx->d_pred, sizeof(float) * nc, cudaMemcpyDeviceToDevice));
+  std::vector<int> order(nc);
+  for (int i = 0; i < nc; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hp[a] > hp[b]; });
+  std::vector<nbv_camera> full = ctx->cand, sub(keep);
+  for (int i = 0; i < keep; ++i) {
+    kept[i] = order[i];
+    sub[i] = full[order[i]];
+  }
+  CKR(nbv_set_candidates(ctx, keep, sub.data()));
+  std::vector<float> h4((size_t)keep * 4);
+  int src = nbv_score(ctx, h4.data(), 0);
+  const int rs = nbv_set_candidates(ctx, nc, full.data());
+  if (src != NBV_OK) return src;
+  if (rs != NBV_OK) return rs;
+  int bi = -1;
+  float bs = 0.0f;
+  for (int i = 0; i < keep; ++i) {
+    const float v = h4[(size_t)4 * i + 3];
+    if (bi < 0 || v > bs || (v == bs && kept[i] < bi)) { bi = kept[i]; bs = v; }
+  }
+  if (exact) std::memcpy(exact, h4.data(), sizeof(float) * 4 * keep);
+  *best = bi;
+  *best_score = bs;
   return NBV_OK;
 }
 
