@@ -46,6 +46,7 @@ def parse_args(argv=None):
     ap.add_argument("--target", type=int, default=-1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned pre-scoring measurement")
     ap.add_argument("--views", type=int, default=None, help="override the candidate count (profiling runs)")
     ap.add_argument("--no-autotune", action="store_true", help="keep 16x16 tiles, stage 32")
     ap.add_argument("--only", default=None, choices=[None, "plain", "batched"], help="time one path only")
@@ -313,6 +314,8 @@ def run_ours(args):
 
     if not args.no_e2e:
         result["e2e"] = e2e_host(args, P, wl, torch, np, head["tiling"])
+    if not args.no_surrogate and args.workload == "scene" and args.views is None:
+        result["surrogate"] = surrogate_eval(args, P, S, torch, np, per_view["value"] / world, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -320,6 +323,73 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+def surrogate_eval(args, P, S, torch, np, per_view_rate, dev):
+    """The learned pre-scoring on scene-scale workloads: labels from the exact
+    path on 48 seeded training scenes (256 candidates each), 400 Adam steps on
+    exp(2 z) / 4 of the per-scene standardised scores, then on 4 unseen scenes
+    with 512 candidates each: the exact best among all 512 (multi-view path)
+    against the best of the 64 the network keeps (nbv_score_pruned), and the
+    pruned step's throughput (prepare + descriptors + MLP + exact scoring of
+    the 64 kept), CUDA events, L2 flushed between steps."""
+    from paper_2602_08266_gb300 import surrogate as SG
+    t0 = time.perf_counter()
+    xs, zs = [], []
+    for s in range(48):
+        wl = S.make_workload("scene", seed=5000 + s, n_views=256)
+        x, z, _ = SG.scene_labels(P, wl)
+        xs.append(x)
+        zs.append(z)
+    X, Y = torch.cat(xs), SG.rank_target(torch.cat(zs))
+    t_labels = time.perf_counter() - t0
+    mlp = P.MLP(448, 256, seed=7)
+    t1 = time.perf_counter()
+    losses = SG.train(mlp, X, Y, steps=400, batch=512, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    keep, ncand, trials = 64, 512, 4
+    agree = 0
+    ratios = []
+    times = []
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for s in range(trials):
+        wl = S.make_workload("scene", seed=9000 + s, n_views=ncand)
+        sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=1)
+        sc.load_scene(wl.scene)
+        sc.set_train_views(wl.train)
+        sc.set_candidates(wl.cand)
+        sc.prepare(-1)
+        full = sc.score_host().astype(np.float64)
+        best_exact = int(np.argmax(full[:, 3]))
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sc.prepare(-1)
+            r = sc.score_pruned(mlp, keep)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        agree += int(r["best"] == best_exact)
+        ratios.append(float(full[r["best"], 3] / full[best_exact, 3]))
+        sc.close()
+    mlp.close()
+    ms = float(np.mean(times))
+    value = ncand / (ms / 1e3)
+    return {"value": round(value, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
+            "candidates_per_step": ncand, "kept": keep,
+            "top1_agreement": f"{agree}/{trials}",
+            "chosen_over_best_exact_score": [round(x, 4) for x in ratios],
+            "speedup_vs_per_view_path": round(value / per_view_rate, 2) if per_view_rate else None,
+            "train": {"scenes": 48, "labels": int(X.shape[0]), "steps": 400, "first_loss": round(losses[0], 4),
+                      "last_loss": round(losses[-1], 4), "label_s": round(t_labels, 1),
+                      "train_s": round(t_train, 1)},
+            "path": "per-view descriptors + BF16 tcgen05 MLP over all candidates, exact multi-view scoring "
+                    "of the 64 kept; step includes prepare"}
 
 
 def e2e_host(args, P, wl, torch, np, tiling):

@@ -80,6 +80,9 @@ typedef struct {
                             compositing launch, one gains launch) replayed as a CUDA graph */
   int stage;             /* Gaussians the compositing kernel stages in shared memory per round:
                             32 (default) or 16; only speed depends on it */
+  int max_batch_views;   /* batched path: candidates per multi-view pass (0 = as many as keep the
+                            per-(view, Gaussian) state under 32 GB); larger sets run in chunks,
+                            eagerly, and only a single-chunk set is replayed as a CUDA graph */
 } nbv_config;
 
 typedef struct {
@@ -269,23 +272,30 @@ int64_t nbv_launch_count(const nbv_ctx* ctx);
  * it ranks highest and scores only those exactly.
  * ---------------------------------------------------------------------- */
 
-/* Descriptor length: 4 x 64 image-grid cells + 128 object bins. */
-#define NBV_DESC_DIM 384
+/* Descriptor length: 6 x 64 image-grid cells + 56 object bins + 8 totals. */
+#define NBV_DESC_DIM 448
 
-/* Descriptors of every candidate into `out` (DEVICE float [n_cand][384]):
+/* Descriptors of every candidate into `out` (DEVICE float [n_cand][448]):
  * for each Gaussian whose centre projects in front of the near plane and
  * inside the image, with opacity sigma, confidence c_g (Eq. 7 / 12, as the
- * last nbv_prepare set it), camera depth z and training observation
- * o_g = sum over the training views and their pixels of w^2 (w = alpha T):
+ * last nbv_prepare set it), camera depth z, training observation
+ * o_g = sum over the training views and their pixels of w^2 (w = alpha T)
+ * and angular novelty nu = 1 - max over the training cameras of the cosine
+ * between the directions from the camera centres to the Gaussian:
  *   [0, 64)    sum sigma over an 8 x 8 grid of image cells,
  *   [64, 128)  sum c_g sigma per cell,
  *   [128, 192) sum c_g sigma / z per cell,
  *   [192, 256) sum c_g sigma / (1 + o_g) per cell,
- *   [256, 384) sum c_g sigma per most-probable object id (0..K),
- * each feature then mapped to log(1 + s x) with s = 64 / n for the cell
- * features and (K + 1) / n for the object bins (n = number of Gaussians).
- * Cells: floor(8 mx / W), floor(8 my / H) of the projected centre, computed
- * in single precision. Errors: NBV_ERR_STATE (no prepare), NBV_ERR_ARG. */
+ *   [256, 320) sum c_g sigma nu per cell,
+ *   [320, 384) sum c_g sigma nu^2 per cell,
+ *   [384, 440) sum c_g sigma per most-probable object id (ids >= 55 share bin 55),
+ *   [440, 448) view totals of c_g sigma nu, c_g sigma [nu > 0.1],
+ *              c_g sigma [nu > 0.3], c_g sigma sqrt(nu), sigma, c_g sigma,
+ *              c_g sigma / (1 + o_g), c_g sigma / z,
+ * each feature then mapped to log(1 + s x) with s = 64 / n (cells), (K + 1) / n
+ * (object bins) or 1 / n (totals), n = number of Gaussians. Cells:
+ * floor(8 mx / W), floor(8 my / H) of the projected centre, computed in
+ * single precision. Errors: NBV_ERR_STATE (no prepare), NBV_ERR_ARG. */
 int nbv_descriptors(nbv_ctx* ctx, float* out);
 
 typedef struct nbv_mlp nbv_mlp;

@@ -7,11 +7,16 @@ path never imports this module.
 
 Descriptor: for every Gaussian whose centre projects in front of the near
 plane and inside the image, with opacity sigma, confidence c (Eq. 7 / 12),
-camera depth z and training observation o (sum over the training views'
-pixels of w^2, w = alpha T), sums over an 8 x 8 grid of image cells of
-sigma, c sigma, c sigma / z and c sigma / (1 + o), and sums of c sigma per
-most probable object id; then log(1 + s x) with s = 64 / n (cells) or
-(K + 1) / n (objects). The centre,
+camera depth z, training observation o (sum over the training views'
+pixels of w^2, w = alpha T) and angular novelty nu (1 - the largest cosine
+between the direction from the candidate's centre to the Gaussian and the
+directions from the training cameras' centres), sums over an 8 x 8 grid of
+image cells of sigma, c sigma, c sigma / z, c sigma / (1 + o), c sigma nu,
+c sigma nu^2; sums of c sigma per most probable object id (56 bins, larger
+ids in the last); view totals of c sigma nu, c sigma [nu > 0.1],
+c sigma [nu > 0.3], c sigma sqrt(nu), sigma, c sigma, c sigma / (1 + o),
+c sigma / z; then log(1 + s x) with s = 64 / n (cells), (K + 1) / n
+(objects) or 1 / n (totals). The centre,
 the cell and the in-image test are the discrete decisions; they are taken
 in single precision in one fixed order of correctly rounded operations
 (numpy float32 arithmetic, no fused multiply-add), the sums in double.
@@ -26,7 +31,7 @@ from __future__ import annotations
 
 import numpy as np
 
-DESC_DIM = 384
+DESC_DIM = 448
 
 
 def bf16(a):
@@ -36,20 +41,33 @@ def bf16(a):
     return u.astype(np.uint32).view(np.float32)
 
 
-def descriptors(scene, cams, conf, obs=None, near=0.2):
-    """[n_views, 384] descriptors (see the module docstring). conf: c_g per
+def _centres(cams):
+    """Camera centres -R^T t (double)."""
+    R = np.asarray(cams.R, np.float64).reshape(cams.n, 3, 3)
+    t = np.asarray(cams.t, np.float64).reshape(cams.n, 3)
+    return -np.einsum("nji,nj->ni", R, t)
+
+
+def descriptors(scene, cams, conf, obs=None, train=None, near=0.2):
+    """[n_views, 448] descriptors (see the module docstring). conf: c_g per
     Gaussian (float64), as the oracle's confidence gives it; obs: the
-    training observation per Gaussian (zero when None)."""
+    training observation per Gaussian (zero when None); train: the training
+    cameras (novelty 1 when None)."""
     f32 = np.float32
     n, K = scene.n, scene.K
     mu = np.asarray(scene.means, f32)
+    mu64 = mu.astype(np.float64)
     sig = (1.0 / (1.0 + np.exp(-np.asarray(scene.opacity, np.float64).reshape(n)))).astype(f32)
     c = np.asarray(conf, np.float64).astype(f32)
     logits = np.asarray(scene.obj_logits, np.float64).reshape(n, K + 1)
-    ids = np.minimum(np.argmax(logits, axis=1), 127)          # lowest id on ties
-    cs = (c * sig).astype(f32)
-    o = np.zeros(n, np.float32) if obs is None else np.asarray(obs, np.float64).astype(f32)
-    nov = (cs / (f32(1.0) + o).astype(f32)).astype(f32)
+    ids = np.minimum(np.argmax(logits, axis=1), 55)          # lowest id on ties
+    cs = (c * sig).astype(f32).astype(np.float64)
+    o = np.zeros(n) if obs is None else np.asarray(obs, np.float64)
+    cov = cs / (1.0 + o)
+    if train is not None:
+        dt = mu64[None] - _centres(train).astype(np.float32).astype(np.float64)[:, None]
+        dt /= np.linalg.norm(dt, axis=2, keepdims=True)
+    cv = _centres(cams).astype(np.float32).astype(np.float64)
     out = np.zeros((cams.n, DESC_DIM), np.float64)
     for v in range(cams.n):
         R = np.asarray(cams.R[v], f32).reshape(3, 3)
@@ -70,13 +88,23 @@ def descriptors(scene, cams, conf, obs=None, near=0.2):
         ix = np.minimum(7, np.floor(((f32(8.0) * mx).astype(f32) / W).astype(f32))).astype(np.int64)
         iy = np.minimum(7, np.floor(((f32(8.0) * my).astype(f32) / H).astype(f32))).astype(np.int64)
         cell = (iy * 8 + ix)[ok]
+        if train is not None:
+            d = mu64 - cv[v]
+            d /= np.linalg.norm(d, axis=1, keepdims=True)
+            nu = np.maximum(0.0, 1.0 - np.max(np.einsum("tnk,nk->tn", dt, d), axis=0))
+        else:
+            nu = np.ones(n)
+        csz = (cs.astype(f32) / tz).astype(f32).astype(np.float64)
         h = np.zeros(DESC_DIM, np.float64)
-        np.add.at(h, cell, sig[ok].astype(np.float64))
-        np.add.at(h, 64 + cell, cs[ok].astype(np.float64))
-        np.add.at(h, 128 + cell, (cs[ok] / tz[ok]).astype(f32).astype(np.float64))
-        np.add.at(h, 192 + cell, nov[ok].astype(np.float64))
-        np.add.at(h, 256 + ids[ok], cs[ok].astype(np.float64))
-        scale = np.where(np.arange(DESC_DIM) < 256, 64.0 / n, (K + 1) / n)
+        w = [sig.astype(np.float64), cs, csz, cov, cs * nu, cs * nu * nu]
+        for b, wb in enumerate(w):
+            np.add.at(h, 64 * b + cell, wb[ok])
+        np.add.at(h, 384 + ids[ok], cs[ok])
+        tot = [cs * nu, cs * (nu > 0.1), cs * (nu > 0.3), cs * np.sqrt(nu), sig.astype(np.float64), cs, cov, csz]
+        for b, wb in enumerate(tot):
+            h[440 + b] = wb[ok].sum()
+        f = np.arange(DESC_DIM)
+        scale = np.where(f < 384, 64.0 / n, np.where(f < 440, (K + 1) / n, 1.0 / n))
         out[v] = np.log1p(h * scale)
     return out
 

@@ -45,7 +45,7 @@ class nbv_config(ctypes.Structure):
                 ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("dilation", ctypes.c_float), ("guard", ctypes.c_float),
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("batched", ctypes.c_int),
-                ("stage", ctypes.c_int)]
+                ("stage", ctypes.c_int), ("max_batch_views", ctypes.c_int)]
 
 
 class nbv_camera(ctypes.Structure):
@@ -367,10 +367,10 @@ class NBVScorer:
         return int(self.lib.nbv_launch_count(self._h))
 
     # ------------------------------------------------- learned pre-scoring
-    DESC_DIM = 384
+    DESC_DIM = 448
 
     def descriptors(self):
-        """[n_cand, 384] per-candidate descriptors (after prepare)."""
+        """[n_cand, 448] per-candidate descriptors (after prepare)."""
         out = self.torch.empty((max(self.n_cand, 1), self.DESC_DIM), device="cuda")
         self._check(self.lib.nbv_descriptors(self._h, _dptr(out)))
         self.torch.cuda.synchronize()
@@ -396,7 +396,7 @@ class MLP:
     """The learned candidate scorer (nbv_mlp): d_in -> width -> width -> 1,
     BF16 tensor-core layers, trained with the library's own backward and Adam."""
 
-    def __init__(self, d_in: int = 384, width: int = 256, seed: int = 0, stream=None):
+    def __init__(self, d_in: int = 448, width: int = 256, seed: int = 0, stream=None):
         import torch
         self.torch = torch
         self.lib = load_library()

@@ -93,6 +93,7 @@ struct nbv_ctx {
   size_t desc_cap = 0;             // candidates the descriptor buffers hold
   struct Batched {
     bool ready = false;             // buffers sized for the current scene / candidates
+    int v0 = 0;                     // first candidate of the views this state covers
     int nv = 0, ntiles = 0;
     int64_t total = 0;              // (view, tile, Gaussian) entries
     DevCam* cams = nullptr;
@@ -344,21 +345,23 @@ void batched_drop_graph(nbv_ctx* ctx) {
 void batched_invalidate(nbv_ctx* ctx) {
   batched_drop_graph(ctx);
   ctx->bt.ready = false;
+  ctx->bt.svals = nullptr;
 }
 
 // Size every buffer of the multi-view path: camera tables, records, and the
 // entry count (one eager projection + scan, one host read-back).
-int batched_setup(nbv_ctx* ctx) {
+int batched_setup(nbv_ctx* ctx, int v0, int nv) {
   auto& B = ctx->bt;
   cudaStream_t st = ctx->st;
-  const int nv = (int)ctx->cand.size();
   const int64_t n = ctx->n;
+  const int nc = (int)ctx->cand.size();
+  B.v0 = v0;
   B.nv = nv;
   std::vector<DevCam> hc(nv);
   std::vector<uint32_t> base(nv);
   int64_t nt = 0;
   for (int v = 0; v < nv; ++v) {
-    hc[v] = to_dev(ctx->cand[v], ctx->tw, ctx->th);
+    hc[v] = to_dev(ctx->cand[v0 + v], ctx->tw, ctx->th);
     base[v] = (uint32_t)nt;
     nt += (int64_t)hc[v].GX * hc[v].GY;
   }
@@ -392,8 +395,8 @@ int batched_setup(nbv_ctx* ctx) {
   CKR(alloc(ctx, &B.blocks, slots * ctx->nBp));
   B.parts_cap = 152 * 16 * 4;
   CKR(alloc(ctx, &B.partial, (size_t)nv * B.parts_cap * 3));
-  CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)(nv > 0 ? nv : 1) * 3));
-  CKR(grow(ctx, &ctx->out4, &ctx->out4_cap, (size_t)(nv > 0 ? nv : 1) * 4));
+  CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)(nc > 0 ? nc : 1) * 3));
+  CKR(grow(ctx, &ctx->out4, &ctx->out4_cap, (size_t)(nc > 0 ? nc : 1) * 4));
   // queue sort buffers
   CKR(alloc(ctx, &B.qb.keys[0], (size_t)nt)); CKR(alloc(ctx, &B.qb.keys[1], (size_t)nt));
   CKR(alloc(ctx, &B.qb.vals[0], (size_t)nt)); CKR(alloc(ctx, &B.qb.vals[1], (size_t)nt));
@@ -416,7 +419,7 @@ int batched_setup(nbv_ctx* ctx) {
 
 // The whole multi-view score, enqueued on the context stream (captured into
 // a graph by batched_score).
-int batched_sequence(nbv_ctx* ctx) {
+int batched_sequence(nbv_ctx* ctx, bool final_scores) {
   auto& B = ctx->bt;
   cudaStream_t st = ctx->st;
   const int nv = B.nv;
@@ -460,7 +463,7 @@ int batched_sequence(nbv_ctx* ctx) {
     CK(cudaMemsetAsync(B.counter, 0, sizeof(int), st));
     if (ctx->prof) ctx->composite_launches++;
     CompositeArgs a{};
-    a.cam = B.nv > 0 ? to_dev(ctx->cand[0], ctx->tw, ctx->th) : DevCam{};
+    a.cam = B.nv > 0 ? to_dev(ctx->cand[B.v0], ctx->tw, ctx->th) : DevCam{};
     a.r0 = B.pr.r0; a.r1 = B.pr.r1; a.r2 = B.pr.r2;
     a.p = ctx->p;
     a.vals = svals;
@@ -484,24 +487,53 @@ int batched_sequence(nbv_ctx* ctx) {
     if (r < 0)
       r = launch_views_gains(s, ctx->c, B.cams, nv, B.blocks, ctx->F, B.partial, B.parts_cap, &nparts, st);
     CKR(check_launch(ctx, r));
-    CKR(check_launch(ctx, launch_reduce_gains_views(B.partial, nparts, nv, ctx->ig_cand, st)));
+    CKR(check_launch(ctx, launch_reduce_gains_views(B.partial, nparts, nv, ctx->ig_cand + 3 * (size_t)B.v0, st)));
   }
-  {
+  if (final_scores) {
     Phase ph(ctx, NBV_PHASE_SCORE);
-    CKR(check_launch(ctx, launch_final_scores(ctx->ig_cand, ctx->ig_train, nv, (int)ctx->train.size(), ctx->c,
-                                              ctx->out4, ctx->d_flags, ctx->d_best_score, ctx->d_flags + 1, st)));
+    CKR(check_launch(ctx, launch_final_scores(ctx->ig_cand, ctx->ig_train, (int)ctx->cand.size(),
+                                              (int)ctx->train.size(), ctx->c, ctx->out4, ctx->d_flags,
+                                              ctx->d_best_score, ctx->d_flags + 1, st)));
   }
   return NBV_OK;
+}
+
+// Candidates per multi-view pass: all of them unless their per-(view,
+// Gaussian) state (blocks, records, binning slots) would pass 32 GB, or the
+// configuration caps it.
+int batched_chunk(const nbv_ctx* ctx) {
+  const int nc = (int)ctx->cand.size();
+  const double per_view = (double)ctx->n * ((double)ctx->nBp * 4.0 + 128.0);
+  int chunk = (int)std::max(1.0, std::floor(32.0e9 / std::max(per_view, 1.0)));
+  if (ctx->cfg.max_batch_views > 0) chunk = std::min(chunk, ctx->cfg.max_batch_views);
+  return std::max(1, std::min(chunk, std::max(nc, 1)));
 }
 
 int batched_score(nbv_ctx* ctx) {
   auto& B = ctx->bt;
   cudaStream_t st = ctx->st;
-  if (!B.ready) {
+  const int nc = (int)ctx->cand.size();
+  const int chunk = batched_chunk(ctx);
+  if (nc > chunk) {
+    // candidate chunks one after the other, each set up and run eagerly; the
+    // final normalisation over all of them at the end
     batched_drop_graph(ctx);
-    CKR(batched_setup(ctx));
+    for (int v0 = 0; v0 < nc; v0 += chunk) {
+      B.ready = false;
+      CKR(batched_setup(ctx, v0, std::min(chunk, nc - v0)));
+      CKR(batched_sequence(ctx, false));
+    }
+    B.ready = false;
+    Phase ph(ctx, NBV_PHASE_SCORE);
+    CKR(check_launch(ctx, launch_final_scores(ctx->ig_cand, ctx->ig_train, nc, (int)ctx->train.size(), ctx->c,
+                                              ctx->out4, ctx->d_flags, ctx->d_best_score, ctx->d_flags + 1, st)));
+    return NBV_OK;
   }
-  if (ctx->prof) return batched_sequence(ctx);   // timed phase by phase, not replayed
+  if (!B.ready || B.v0 != 0 || B.nv != nc) {
+    batched_drop_graph(ctx);
+    CKR(batched_setup(ctx, 0, nc));
+  }
+  if (ctx->prof) return batched_sequence(ctx, true);   // timed phase by phase, not replayed
   if (!B.exec) {
     // capture on the private stream (the caller's stream may be the legacy
     // default stream, which cannot be captured)
@@ -513,7 +545,7 @@ int batched_score(nbv_ctx* ctx) {
     ctx->st = ctx->cap_st;
     const int64_t l0 = ctx->launches;
     CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
-    const int rc = batched_sequence(ctx);
+    const int rc = batched_sequence(ctx, true);
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(ctx->st, &g);
     if (rc != NBV_OK) { if (g) cudaGraphDestroy(g); return rc; }
@@ -583,6 +615,7 @@ void nbv_config_default(nbv_config* cfg, int K, int sh_degree) {
   cfg->tile_h = 16;
   cfg->batched = 0;
   cfg->stage = 32;
+  cfg->max_batch_views = 0;
 }
 
 int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
@@ -592,6 +625,7 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
                        (cfg->tile_w == 0 && cfg->tile_h == 0);
   if (cfg->K < 1 || cfg->K > kMaxK || cfg->sh_degree < 0 || cfg->sh_degree > 3 || !tile_ok) return NBV_ERR_ARG;
   if (cfg->stage != 16 && cfg->stage != 32) return NBV_ERR_ARG;
+  if (cfg->max_batch_views < 0) return NBV_ERR_ARG;
   const float fl[] = {cfg->alpha_obj, cfg->alpha_opa, cfg->beta_d, cfg->beta_o, cfg->lambda_damp,
                       cfg->near_z, cfg->alpha_min, cfg->alpha_max, cfg->t_min, cfg->dilation, cfg->guard};
   for (float v : fl)
@@ -773,7 +807,7 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (herr) return fail(ctx, NBV_ERR_CUDA, "training block not positive definite");
+  if (herr) return fail(ctx, NBV_ERR_CUDA, "non-finite training Hessian");
   ctx->prepared = true;
   ctx->prepared_target = target_obj;
   return NBV_OK;
@@ -882,13 +916,15 @@ namespace {
 // Tile lists of candidate `view` as the last multi-view pass binned them.
 int debug_batched_lists(nbv_ctx* ctx, int view, int64_t* offsets, int32_t* ids, int64_t cap, int64_t* count) {
   auto& B = ctx->bt;
-  if (!B.ready || !B.svals) return fail(ctx, NBV_ERR_STATE, "no multi-view pass since the last change");
-  if (view < 0 || view >= B.nv) return fail(ctx, NBV_ERR_ARG, "view out of range");
+  if (!B.svals || B.nv < 1) return fail(ctx, NBV_ERR_STATE, "no multi-view pass since the last change");
+  if (view < 0 || view >= (int)ctx->cand.size()) return fail(ctx, NBV_ERR_ARG, "view out of range");
+  const int lv = view - B.v0;
+  if (lv < 0 || lv >= B.nv) return fail(ctx, NBV_ERR_STATE, "view not in the last multi-view chunk");
   cudaStream_t st = ctx->st;
   const DevCam dc = to_dev(ctx->cand[view], ctx->tw, ctx->th);
   const int ntiles = dc.GX * dc.GY;
   std::vector<uint2> hr(ntiles);
-  CK(cudaMemcpyAsync(hr.data(), B.ranges + B.h_base[view], sizeof(uint2) * ntiles, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hr.data(), B.ranges + B.h_base[lv], sizeof(uint2) * ntiles, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   std::vector<int64_t> ho(ntiles + 1);
   int64_t run = 0, first = -1;
@@ -1006,8 +1042,9 @@ int nbv_descriptors(nbv_ctx* ctx, float* out) {
   std::vector<DevCam> hc(nc);
   for (int v = 0; v < nc; ++v) hc[v] = to_dev(ctx->cand[v], ctx->tw, ctx->th);
   CK(cudaMemcpyAsync(ctx->d_desc_cams, hc.data(), sizeof(DevCam) * nc, cudaMemcpyHostToDevice, ctx->st));
-  CKR(check_launch(ctx, launch_descriptors(dev_scene(ctx), ctx->c, ctx->d_desc_cams, nc, ctx->train_blocks,
-                                           (int)ctx->train.size(), ctx->nBp, ctx->desc_raw, out, ctx->st)));
+  CKR(check_launch(ctx, launch_descriptors(dev_scene(ctx), ctx->c, ctx->d_desc_cams, nc, ctx->d_train_cams,
+                                           (int)ctx->train.size(), ctx->train_blocks, ctx->nBp, ctx->desc_raw,
+                                           out, ctx->st)));
   CK(cudaStreamSynchronize(ctx->st));   // the host copy of the cameras above
   return NBV_OK;
 }

@@ -473,12 +473,20 @@ __device__ __forceinline__ double rsqrt_d(double x) {
 
 // Cholesky factorisation of a packed lower n x n matrix in double precision,
 // in place, trailing updates spread over the lanes. The diagonal slot keeps
-// 1 / L_kk (all that the inversion needs of it); a non-positive pivot sets
-// *err.
-__device__ void chol_packed_d(double* P, int n, int* err, int lane) {
+// 1 / L_kk (all that the inversion needs of it).
+// The matrix is a Jacobi-scaled damped Hessian D^-1/2 (lambda I + A) D^-1/2
+// with A positive semi-definite, so every pivot is at least lambda / H_kk =
+// lambda dk[k stride]^2 (dk: the scaling D^-1/2). Rounding in the single-
+// precision sums of A can push a pivot of a nearly unobserved direction
+// below that bound, even below zero; such a pivot is raised to the bound.
+// A non-finite pivot sets *err.
+__device__ void chol_packed_d(double* P, int n, int* err, int lane, double lam, const double* dk, int stride) {
   for (int k = 0; k < n; ++k) {
-    const double dkk = P[tri(k, k)];
-    if (!(dkk > 0.0) && lane == 0) atomicExch(err, 1);
+    double dkk = P[tri(k, k)];
+    if (!isfinite(dkk) && lane == 0) atomicExch(err, 1);
+    const double dd = dk[k * stride];
+    const double floor_k = lam * dd * dd;
+    if (!(dkk >= floor_k)) dkk = floor_k;
     const double iL = rsqrt_d(fmax(dkk, 1e-30));
     __syncwarp();
     if (lane == 0) P[tri(k, k)] = iL;
@@ -548,7 +556,7 @@ __device__ void factorise_store(int l, float cg, const Consts& c, float* Hf, dou
     Hs[i] = h * dsc[r] * dsc[cc];
   }
   __syncwarp();
-  chol_packed_d(Hs, l, err, lane);
+  chol_packed_d(Hs, l, err, lane, (double)c.lam, dsc, 1);
   inv_lower<float>(Hs, Hf, l, lane);
   for (int i = lane; i < nt; i += 32) {
     int r, cc;
@@ -585,7 +593,7 @@ __device__ void factorise_rgb_store(int nb, float cg, const Consts& c, const flo
       X[e] = (cgd * (double)H0[tri(a, b)] + (k == k2 ? lam : 0.0)) * dsc[a] * dsc[b];
     }
     __syncwarp();
-    chol_packed_d(X, nb, err, lane);
+    chol_packed_d(X, nb, err, lane, lam, dsc + kNG + ch, 3);
     inv_lower<double>(X, A + ch * T, nb, lane);
   }
   // L_gS[r][(c, k)] = sum_{k2 <= k} H~[g_r][(c, k2)] A_c[k][k2]
@@ -608,7 +616,7 @@ __device__ void factorise_rgb_store(int nb, float cg, const Consts& c, const flo
     S[e] = acc;
   }
   __syncwarp();
-  chol_packed_d(S, kNG, err, lane);
+  chol_packed_d(S, kNG, err, lane, lam, dsc, 1);   // the Schur complement is >= lambda D_g^-1 too
   inv_lower<float>(S, Ef, kNG, lane);
   for (int e = lane; e < kNG * n3; e += 32) {          // T_c = L_gS,c A_c
     const int r = e / n3, q = e - r * n3, ch = q / nb, k = q - ch * nb;

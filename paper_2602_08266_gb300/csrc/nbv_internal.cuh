@@ -104,10 +104,10 @@ int launch_duplicate(const DevProj& pr, int64_t n, int GX, const uint32_t* offse
                      uint32_t* vals, cudaStream_t st);
 // Stable LSD radix sort of (keys, vals) on the low `bits` key bits; the
 // result is in buffer index *which (0 or 1).
-// Candidate descriptors [nv][384] (raw: scratch of the same size); tblocks:
-// the training views' blocks [n_train][n][nBp] (their W2 entries are read).
-int launch_descriptors(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const float* tblocks,
-                       int n_train, int nBp, float* raw, float* out, cudaStream_t st);
+// Candidate descriptors [nv][448] (raw: scratch of the same size); tcams: the
+// training cameras; tblocks: their blocks [n_train][n][nBp] (W2 entries read).
+int launch_descriptors(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const DevCam* tcams,
+                       int n_train, const float* tblocks, int nBp, float* raw, float* out, cudaStream_t st);
 // Stable LSD radix sort of 32-bit keys (8 bits a pass) over `bits` bits,
 // ping-ponging between keys[0/1], vals[0/1]; *which = the buffer holding the result.
 int launch_radix_sort32(uint32_t* keys[2], uint32_t* vals[2], uint32_t* hist, int64_t count, int bits, int* which,

@@ -13,7 +13,7 @@ import numpy as np
 
 
 def scene_labels(P, wl, target=-1, **cfg):
-    """(descriptors [n_cand, 384], standardised exact totals [n_cand], raw
+    """(descriptors [n_cand, 448], standardised exact totals [n_cand], raw
     totals [n_cand]) of one workload, as CUDA tensors."""
     sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=1, **cfg)
     try:
@@ -27,6 +27,13 @@ def scene_labels(P, wl, target=-1, **cfg):
         sc.close()
     z = (y - y.mean()) / (y.std() + 1e-12)
     return x, z, y
+
+
+def rank_target(z):
+    """Training target from standardised scores: exp(2 z) / 4 spends the
+    network's accuracy on the high-gain candidates that pruning must keep."""
+    import torch
+    return (torch.exp(2.0 * z) / 4.0).contiguous()
 
 
 def train(mlp, X, Y, steps=400, batch=512, lr=2e-3, seed=0):

@@ -54,11 +54,13 @@ def test_descriptors_match_oracle(P, name, target, scale):
     d = sc.descriptors().cpu().numpy().astype(np.float64)
     o = O.OracleScene(wl.scene, target=target)
     obs = sum(o.view_w2(wl.train, t) for t in range(wl.train.n))
-    want = SO.descriptors(wl.scene, wl.cand, o.confidence(), obs)
-    exact = np.r_[0:192, 256:384]          # cells and object bins: same decisions, sums in another order
+    want = SO.descriptors(wl.scene, wl.cand, o.confidence(), obs, wl.train)
+    exact = np.r_[0:192, 384:440]          # cells and object bins: same decisions, sums in another order
     np.testing.assert_allclose(d[:, exact], want[:, exact], rtol=2e-5, atol=1e-6)
-    # the training-coverage block: the kernel's w^2 sums come from its TF32 contraction
-    np.testing.assert_allclose(d[:, 192:256], want[:, 192:256], rtol=2e-3, atol=1e-5)
+    # the training-coverage blocks: the kernel's w^2 sums come from its TF32
+    # contraction; the novelty (1 - cos) from single-precision directions
+    np.testing.assert_allclose(d[:, 192:384], want[:, 192:384], rtol=2e-3, atol=2e-4)
+    np.testing.assert_allclose(d[:, 440:], want[:, 440:], rtol=2e-3, atol=2e-4)
     sc.close()
 
 
@@ -108,8 +110,8 @@ def test_pruned_scoring_gain(P):
         x, z, _ = SG.scene_labels(P, wl)
         xs.append(x)
         zs.append(z)
-    X, Y = torch.cat(xs), torch.cat(zs)
-    mlp = P.MLP(384, 256, seed=3)
+    X, Y = torch.cat(xs), SG.rank_target(torch.cat(zs))
+    mlp = P.MLP(448, 256, seed=3)
     losses = SG.train(mlp, X, Y, steps=600, batch=512, lr=1e-3)
     assert losses[-1] < 0.8 * losses[0]
     hit = agree = 0

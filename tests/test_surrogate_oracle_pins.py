@@ -37,15 +37,31 @@ def test_descriptor_hand_worked():
     logits[1, 1] = 5.0
     scene = types.SimpleNamespace(n=4, K=K, means=means, opacity=rho, obj_logits=logits)
     conf = np.array([2.0, 4.0, 7.0, 9.0])
-    raw = np.zeros(384)
+    # a training camera at the candidate's own pose (novelty 0 for every
+    # Gaussian) and one on the opposite side (novelty 2 - (1 - cos) ...)
+    raw = np.zeros(448)
     raw[36], raw[9] = 0.5, 0.75                                       # sigma
     raw[64 + 36], raw[64 + 9] = 1.0, 3.0                              # c sigma
     raw[128 + 36], raw[128 + 9] = 1.0, 3.0                            # c sigma / z (z = 1)
     raw[192 + 36], raw[192 + 9] = 1.0 / 2.0, 3.0 / 4.0                # c sigma / (1 + o)
-    raw[256 + 2], raw[256 + 1] = 1.0, 3.0                             # per object id
-    scale = np.where(np.arange(384) < 256, 64 / 4, (K + 1) / 4)
-    d = SO.descriptors(scene, _cam(), conf, obs=np.array([1.0, 3.0, 0.0, 0.0]))[0]
+    raw[384 + 2], raw[384 + 1] = 1.0, 3.0                             # per object id
+    raw[444], raw[445], raw[446], raw[447] = 1.25, 4.0, 1.25, 4.0      # totals: sigma, c sigma, cov, /z
+    f = np.arange(448)
+    scale = np.where(f < 384, 64 / 4, np.where(f < 440, (K + 1) / 4, 1 / 4))
+    d = SO.descriptors(scene, _cam(), conf, obs=np.array([1.0, 3.0, 0.0, 0.0]), train=_cam())[0]
     np.testing.assert_allclose(d, np.log1p(raw * scale), rtol=1e-6, atol=1e-12)
+    # novelty: a training camera on the far side of the scene (centre (0, 0, 1)
+    # looking along -z) sees the centre Gaussian from the opposite direction
+    far = _cam()
+    far.R = np.diag([1.0, -1.0, -1.0]).astype(np.float32)[None]
+    far.t = np.array([[0, 0, 1]], np.float32)
+    d2 = SO.descriptors(scene, _cam(), conf, train=far)[0]
+    # Gaussian 0: directions (0,0,1) vs (0,0,-1): nu = 2; Gaussian 1 at
+    # (-.25,-.25,0): cosine of (-.25,-.25,1) with (-.25,-.25,-1), nu = 1 - (1/8 - 1)/(1 + 1/8)
+    nu1 = 1 - (0.125 - 1) / 1.125
+    assert np.expm1(d2[256 + 36]) / 16 == pytest.approx(2.0 * 1.0, rel=1e-6)
+    assert np.expm1(d2[256 + 9]) / 16 == pytest.approx(3.0 * nu1, rel=1e-6)
+    assert np.expm1(d2[320 + 9]) / 16 == pytest.approx(3.0 * nu1 ** 2, rel=1e-6)
 
 
 def _params(d_in, width, rng, scale=0.5):
