@@ -81,8 +81,9 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   float4* s1 = s0 + kBatch;
   float4* s2 = s1 + kBatch;
   int* sid = reinterpret_cast<int*>(s2 + kBatch);
-  float* sp = reinterpret_cast<float*>(sid + kBatch);            // [kBatch][KC]
-  float* acc = sp + kBatch * KC;                                  // [kBatch][nBp]
+  const int KCP = (KC + 1) & ~1;                                  // even row stride: float2 loads
+  float* sp = reinterpret_cast<float*>(sid + kBatch);            // [kBatch][KCP]
+  float* acc = sp + kBatch * KCP;                                 // [kBatch][nBp]
   int* touched = reinterpret_cast<int*>(acc + kBatch * nBp);      // [kBatch]
   __shared__ int s_last_max;
 
@@ -98,9 +99,9 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
 
   // ------------------------------------------------------------- pass 1
   float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
-  float O[KCM];
+  float2 O2[KCM / 2];                       // object channels in pairs (packed f32x2 FMA)
 #pragma unroll
-  for (int k = 0; k < KCM; ++k) O[k] = 0.0f;
+  for (int q = 0; q < KCM / 2; ++q) O2[q] = make_float2(0.0f, 0.0f);
   uint32_t last = rg.x;     // one past the list index of the last blended splat
   bool done = !inside;
   uint32_t n_eval = 0, n_blend = 0;
@@ -114,9 +115,9 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       s2[tid] = args.r2[rec_off + g];
       sid[tid] = (int)g;
     }
-    for (int i = tid; i < (int)nj * KC; i += kTilePix) {
-      const int j = i / KC, k = i - j * KC;
-      sp[i] = args.p[(size_t)args.vals[start + j] * KC + k];
+    for (int i = tid; i < (int)nj * KCP; i += kTilePix) {
+      const int j = i / KCP, k = i - j * KCP;
+      sp[i] = k < KC ? args.p[(size_t)args.vals[start + j] * KC + k] : 0.0f;
     }
     __syncthreads();
     if (!done) {
@@ -131,9 +132,11 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         const float w = alpha * T;
         const float4 a2 = s2[j];
         C0 += w * a2.x; C1 += w * a2.y; C2 += w * a2.z; D += w * a2.w;
+        const float2 w2 = make_float2(w, w);
+        const float2* pj2 = reinterpret_cast<const float2*>(sp + j * KCP);
 #pragma unroll
-        for (int k = 0; k < KCM; ++k)
-          if (k < KC) O[k] += w * sp[j * KC + k];
+        for (int q = 0; q < KCM / 2; ++q)
+          if (2 * q < KC) O2[q] = __ffma2_rn(w2, pj2[q], O2[q]);
         T = tt;
         last = start + j + 1;
         ++n_blend;
@@ -160,10 +163,10 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       float sum = 0.0f;
 #pragma unroll
       for (int k = 0; k < KCM; ++k)
-        if (k < KC) sum += O[k];
+        if (k < KC) sum += (k & 1) ? O2[k >> 1].y : O2[k >> 1].x;
 #pragma unroll
       for (int k = 0; k < KCM; ++k)
-        if (k < KC) args.obj[pix * KC + k] = O[k] + (k == 0 ? 1.0f - sum : 0.0f);
+        if (k < KC) args.obj[pix * KC + k] = ((k & 1) ? O2[k >> 1].y : O2[k >> 1].x) + (k == 0 ? 1.0f - sum : 0.0f);
     }
   }
   if (blocks_v == nullptr) return;
@@ -178,9 +181,9 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   const uint32_t wlast = __reduce_max_sync(0xffffffffu, inside ? last : rg.x);
   const float Tf = T;
   float Rr0 = 0.0f, Rr1 = 0.0f, Rr2 = 0.0f, Rd = 0.0f;
-  float Ro[KCM];
+  float2 Ro2[KCM / 2];                      // object suffix sums in pairs
 #pragma unroll
-  for (int k = 0; k < KCM; ++k) Ro[k] = 0.0f;
+  for (int q = 0; q < KCM / 2; ++q) Ro2[q] = make_float2(0.0f, 0.0f);
   float Tb = T;   // transmittance after the splat being visited
   // Per-warp contraction buffers: row = pixel (lane). U holds the pixel's
   // scalars [q_rgb a^2, q_d a^2, q_o a^2 | w s_c a (3), w s_D a, w (s_j - s_0) a
@@ -234,9 +237,9 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       sid[tid] = (int)g;
       touched[tid] = 0;
     }
-    for (int i = tid; i < nj * KC; i += kTilePix) {
-      const int j = i / KC, k = i - j * KC;
-      sp[i] = args.p[(size_t)args.vals[start + j] * KC + k];
+    for (int i = tid; i < nj * KCP; i += kTilePix) {
+      const int j = i / KCP, k = i - j * KCP;
+      sp[i] = k < KC ? args.p[(size_t)args.vals[start + j] * KC + k] : 0.0f;
     }
     for (int i = tid; i < nj * nBp; i += kTilePix) acc[i] = 0.0f;
     __syncthreads();
@@ -274,17 +277,27 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         const float sr1 = Ti * a2.y - Rr1 * inv_om;
         const float sr2 = Ti * a2.z - Rr2 * inv_om;
         const float sd = Ti * a2.w - Rd * inv_om;
-        const float* pj = sp + j * KC;
-        const float s0v = Ti * pj[0] - (Ro[0] + Tf) * inv_om;   // residual channel
-        float qo = s0v * s0v;
+        const float2* pj2 = reinterpret_cast<const float2*>(sp + j * KCP);
+        // s_k = T_i p_k - R_k / (1 - alpha), two channels per packed FMA; the
+        // residual channel 0 also carries -T_final / (1 - alpha)
+        const float2 Ti2 = make_float2(Ti, Ti), ni2 = make_float2(-inv_om, -inv_om);
+        float2 s01 = __ffma2_rn(Ti2, pj2[0], __fmul2_rn(Ro2[0], ni2));
+        s01.x -= Tf * inv_om;
+        const float s0v = s01.x;
+        const float2 wa2 = make_float2(wa, wa), off2 = make_float2(-wa * s0v, -wa * s0v);
+        float2 qo2 = make_float2(s0v * s0v, s01.y * s01.y);
+        if (KC > 1) Ur[7 * kCS] = tf32f(fmaf(wa, s01.y, -wa * s0v));
 #pragma unroll
-        for (int k = 1; k < KCM; ++k) {
-          if (k < KC) {
-            const float sk = Ti * pj[k] - Ro[k] * inv_om;
-            qo += sk * sk;
-            Ur[(6 + k) * kCS] = tf32f(wa * (sk - s0v));
+        for (int q = 1; q < KCM / 2; ++q) {
+          if (2 * q < KC) {
+            const float2 sk2 = __ffma2_rn(Ti2, pj2[q], __fmul2_rn(Ro2[q], ni2));
+            qo2 = __ffma2_rn(sk2, sk2, qo2);
+            const float2 u2 = __ffma2_rn(wa2, sk2, off2);
+            Ur[(6 + 2 * q) * kCS] = tf32f(u2.x);
+            if (2 * q + 1 < KC) Ur[(7 + 2 * q) * kCS] = tf32f(u2.y);
           }
         }
+        const float qo = qo2.x + qo2.y;
         const float ae2 = ae * ae;
         Ur[0] = tf32f((sr0 * sr0 + sr1 * sr1 + sr2 * sr2) * ae2);
         Ur[kCS] = tf32f(sd * sd * ae2);
@@ -307,9 +320,10 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         Vr[30 * kCS] = 1.0f;
         // extend the suffix sums with this splat and step T back
         Rr0 += w * a2.x; Rr1 += w * a2.y; Rr2 += w * a2.z; Rd += w * a2.w;
+        const float2 w2 = make_float2(w, w);
 #pragma unroll
-        for (int k = 0; k < KCM; ++k)
-          if (k < KC) Ro[k] += w * pj[k];
+        for (int q = 0; q < KCM / 2; ++q)
+          if (2 * q < KC) Ro2[q] = __ffma2_rn(w2, pj2[q], Ro2[q]);
         Tb = Ti;
       }
       if (lane == 0) touched[j] = 1;
@@ -392,7 +406,7 @@ template <int KCM, int kBatch>
 int launch_k(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
   const int nBp = (a.nB + 3) & ~3;
   const size_t sm = sizeof(float4) * 3 * kBatch + sizeof(int) * kBatch +
-                    sizeof(float) * (size_t)kBatch * c.KC + sizeof(float) * (size_t)kBatch * nBp +
+                    sizeof(float) * (size_t)kBatch * ((c.KC + 1) & ~1) + sizeof(float) * (size_t)kBatch * nBp +
                     sizeof(int) * kBatch +
                     sizeof(float) * (kTilePix / 32) * kCS * (size_t)(u_rows(c.K) + kVRows);
   static bool attr_set = false;
