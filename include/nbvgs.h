@@ -264,6 +264,29 @@ const char* nbv_last_error(const nbv_ctx* ctx);
 int64_t nbv_launch_count(const nbv_ctx* ctx);
 
 /* ------------------------------------------------------------------------
+ * Differentiable rendering for the map refinement of the NBV loop (a pattern
+ * layered on the method: the paper refines the map with its reconstruction
+ * losses, Eqs. 3-4).
+ * ---------------------------------------------------------------------- */
+
+/* Render any camera (host struct) into DEVICE buffers like nbv_render. */
+int nbv_render_view(nbv_ctx* ctx, const nbv_camera* cam, float* rgb, float* depth, float* alpha, float* obj);
+
+/* Backward pass of the rasterizer (Eqs. 1-2) for one camera: given DEVICE
+ * gradients of a loss with respect to the rendered colour [H][W][3], depth
+ * [H][W], opacity [H][W] and object channels [H][W][K+1] (any may be NULL:
+ * zero), ADD the gradients with respect to the loaded Gaussians' raw
+ * parameters to the DEVICE arrays g_means [n][3], g_log_scales [n][3],
+ * g_quats [n][4] (unnormalised), g_opacity [n] (logit), g_sh [n][(d+1)^2][3]
+ * and g_obj_logits [n][K+1]. The forward pass is recomputed per tile (no
+ * per-pixel lists are kept); a splat clamped at alpha_max passes no gradient
+ * to its geometry or opacity; decisions (culling, tiles, the 1/255 and 1e-4
+ * cut-offs) are held fixed. Asynchronous on the context stream. */
+int nbv_render_backward(nbv_ctx* ctx, const nbv_camera* cam, const float* g_rgb, const float* g_depth,
+                        const float* g_alpha, const float* g_obj, float* g_means, float* g_log_scales,
+                        float* g_quats, float* g_opacity, float* g_sh, float* g_obj_logits);
+
+/* ------------------------------------------------------------------------
  * Learned candidate pre-scoring (a pattern layered on the method; the paper
  * scores every candidate exactly). A per-view descriptor of the projected
  * Gaussians feeds a 3-layer MLP (BF16 weights and activations, FP32

@@ -82,6 +82,8 @@ _SIGS = [
     ("nbv_get_tiling", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int)]),
     ("nbv_sort_tile_keys_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, _P, _P, _P]),
+    ("nbv_render_view", ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("nbv_render_backward", ctypes.c_int, [_P, _P] + [_P] * 10),
     ("nbv_descriptors", ctypes.c_int, [_P, _P]),
     ("nbv_mlp_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, _P, ctypes.POINTER(_P)]),
     ("nbv_mlp_destroy", None, [_P]),
@@ -267,6 +269,36 @@ class NBVScorer:
         self._check(self.lib.nbv_render(self._h, int(cand), _dptr(out["rgb"]), _dptr(out["depth"]),
                                         _dptr(out["alpha"]), _dptr(out["obj"])))
         return {k: v for k, v in out.items() if v is not None}
+
+    def render_camera(self, cams, i: int):
+        """Render camera i of `cams` (any camera set): dict of device tensors."""
+        torch = self.torch
+        _, arr = _cams_struct(cams)
+        W, H = int(cams.width[i]), int(cams.height[i])
+        dev = torch.device("cuda")
+        out = dict(rgb=torch.empty((H, W, 3), device=dev), depth=torch.empty((H, W), device=dev),
+                   alpha=torch.empty((H, W), device=dev), obj=torch.empty((H, W, self.K + 1), device=dev))
+        self._check(self.lib.nbv_render_view(self._h, ctypes.byref(arr[i]), _dptr(out["rgb"]), _dptr(out["depth"]),
+                                             _dptr(out["alpha"]), _dptr(out["obj"])))
+        return out
+
+    def render_backward(self, cams, i: int, g_rgb=None, g_depth=None, g_alpha=None, g_obj=None, grads=None):
+        """Add the gradients of the loaded Gaussians' raw parameters for the
+        given output gradients of camera i (device tensors, any may be None)
+        to `grads` (created zero when None); returns grads."""
+        torch = self.torch
+        n, nb, KC = self.n, (self.deg + 1) ** 2, self.K + 1
+        if grads is None:
+            z = lambda *s: torch.zeros(s, device="cuda")
+            grads = dict(means=z(n, 3), log_scales=z(n, 3), quats=z(n, 4), opacity=z(n), sh=z(n, nb, 3),
+                         obj_logits=z(n, KC))
+        _, arr = _cams_struct(cams)
+        c = lambda t: None if t is None else t.detach().float().contiguous()
+        keep = [c(g_rgb), c(g_depth), c(g_alpha), c(g_obj)]
+        self._check(self.lib.nbv_render_backward(
+            self._h, ctypes.byref(arr[i]), *[_dptr(t) for t in keep],
+            *[_dptr(grads[k]) for k in ("means", "log_scales", "quats", "opacity", "sh", "obj_logits")]))
+        return grads
 
     def score(self, out=None):
         """[n_cand, 4] device tensor: IG_rgb, IG_d, IG_o (Eq. 5 per output)

@@ -86,6 +86,8 @@ struct nbv_ctx {
 
   // batched multi-view scoring (cfg.batched): buffers sized once per
   // (scene, candidate set), the whole score captured in a CUDA graph
+  float* gacc = nullptr;           // backward: per-Gaussian gradients of the projected quantities
+  size_t gacc_cap = 0;
   DevCam* d_desc_cams = nullptr;  // candidate cameras for the descriptors
   float* desc_raw = nullptr;
   float* desc = nullptr;
@@ -687,7 +689,8 @@ void nbv_destroy(nbv_ctx* ctx) {
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   if (ctx->h_total) cudaFreeHost(ctx->h_total);
-  for (void* p : {(void*)ctx->d_desc_cams, (void*)ctx->desc_raw, (void*)ctx->desc, (void*)ctx->d_pred})
+  for (void* p : {(void*)ctx->d_desc_cams, (void*)ctx->desc_raw, (void*)ctx->desc, (void*)ctx->d_pred,
+                  (void*)ctx->gacc})
     if (p) cudaFree(p);
   if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   delete ctx;
@@ -1087,6 +1090,44 @@ int nbv_score_pruned(nbv_ctx* ctx, nbv_mlp* mlp, int keep, float* pred, int* kep
   if (exact) std::memcpy(exact, h4.data(), sizeof(float) * 4 * keep);
   *best = bi;
   *best_score = bs;
+  return NBV_OK;
+}
+
+
+int nbv_render_view(nbv_ctx* ctx, const nbv_camera* cam, float* rgb, float* depth, float* alpha, float* obj) {
+  if (!ctx || !cam) return NBV_ERR_ARG;
+  if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
+  if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "nbv_render_view: no Gaussians");
+  if (!finite_cam(*cam)) return fail(ctx, NBV_ERR_ARG, "bad camera");
+  return render_view(ctx, *cam, nullptr, rgb, depth, alpha, obj);
+}
+
+int nbv_render_backward(nbv_ctx* ctx, const nbv_camera* cam, const float* g_rgb, const float* g_depth,
+                        const float* g_alpha, const float* g_obj, float* g_means, float* g_log_scales,
+                        float* g_quats, float* g_opacity, float* g_sh, float* g_obj_logits) {
+  if (!ctx || !cam || !g_means || !g_log_scales || !g_quats || !g_opacity || !g_sh || !g_obj_logits)
+    return NBV_ERR_ARG;
+  if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
+  if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "nbv_render_backward: no Gaussians");
+  if (!finite_cam(*cam)) return fail(ctx, NBV_ERR_ARG, "bad camera");
+  // projection and binning of the view (the lists the backward pass walks)
+  CKR(render_view(ctx, *cam, nullptr, nullptr, nullptr, nullptr, nullptr));
+  const int gw = backward_width(ctx->c);
+  CKR(grow(ctx, &ctx->gacc, &ctx->gacc_cap, (size_t)ctx->n * gw));
+  cudaStream_t st = ctx->st;
+  CK(cudaMemsetAsync(ctx->gacc, 0, sizeof(float) * (size_t)ctx->n * gw, st));
+  BackwardArgs a{};
+  a.cam = to_dev(*cam, ctx->tw, ctx->th);
+  a.r0 = ctx->pr.r0; a.r1 = ctx->pr.r1; a.r2 = ctx->pr.r2;
+  a.p = ctx->p;
+  a.vals = ctx->sb.vals[0];
+  a.ranges = ctx->sb.ranges;
+  a.g_rgb = g_rgb; a.g_depth = g_depth; a.g_alpha = g_alpha; a.g_obj = g_obj;
+  a.gacc = ctx->gacc;
+  a.gw = gw;
+  CKR(check_launch(ctx, launch_render_backward(a, ctx->c, st)));
+  CKR(check_launch(ctx, launch_project_backward(dev_scene(ctx), ctx->c, a.cam, ctx->gacc, gw, ctx->pr.rect, g_means,
+                                                g_log_scales, g_quats, g_opacity, g_sh, g_obj_logits, st)));
   return NBV_OK;
 }
 

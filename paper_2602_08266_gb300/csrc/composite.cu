@@ -32,15 +32,6 @@ __device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); 
 __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
 
-// Splat exponent at a pixel centre: the decision quantity, fixed order.
-__device__ __forceinline__ float splat_power(float mx, float my, float A, float B, float C, float pxc,
-                                             float pyc) {
-  const float dx = fs(mx, pxc), dy = fs(my, pyc);
-  const float dxx = fm(dx, dx), dyy = fm(dy, dy), dxy = fm(dx, dy);
-  const float q = fa(fm(A, dxx), fm(C, dyy));
-  return fs(fm(-0.5f, q), fm(B, dxy));
-}
-
 // TF32 tensor-core helpers (warp-level mma.sync, FP32 accumulation).
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;

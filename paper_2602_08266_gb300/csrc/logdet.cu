@@ -1405,6 +1405,50 @@ __global__ void k_final_scores(const double* __restrict__ igc, const double* __r
   *best_score = bs;
 }
 
+// Gradients of the raw parameters of each projected Gaussian from the
+// gradients of its projected quantities (one thread per Gaussian): the
+// transpose of the projection Jacobian M applied to
+// (mean2D, conic, sigma, colour, z), and the softmax Jacobian to the
+// probability gradients.
+__global__ void k_project_backward(DevScene s, Consts c, DevCam cam, const float* __restrict__ gacc, int gw,
+                                   const int4* __restrict__ rect, float* __restrict__ g_mu,
+                                   float* __restrict__ g_logs, float* __restrict__ g_q, float* __restrict__ g_rho,
+                                   float* __restrict__ g_sh, float* __restrict__ g_obj) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= s.n || rect[g].x < 0) return;
+  const float* a = gacc + (size_t)g * gw;
+  bool any = false;
+  for (int q = 0; q < gw; ++q) any |= a[q] != 0.0f;
+  if (!any) return;
+  GJac J;
+  compute_gjac(s, c, cam, g, J);
+  const float gm0 = a[0], gm1 = a[1], gcon[3] = {a[2], a[3], a[4]}, gsig = a[5];
+  const float gcol[3] = {a[6], a[7], a[8]}, gz = a[9];
+  for (int m = 0; m < 3; ++m) {
+    float v = J.Jm[0][m] * gm0 + J.Jm[1][m] * gm1 + J.Jz[m] * gz;
+    for (int e = 0; e < 3; ++e) v += J.Jc[e][m] * gcon[e];
+    for (int ch = 0; ch < 3; ++ch) v += J.Jrgb[ch][m] * gcol[ch];
+    g_mu[3 * g + m] += v;
+  }
+  for (int k = 0; k < 3; ++k) {
+    float v = 0.0f;
+    for (int e = 0; e < 3; ++e) v += J.Jc[e][3 + k] * gcon[e];
+    g_logs[3 * g + k] += v;
+  }
+  for (int i = 0; i < 4; ++i) {
+    float v = 0.0f;
+    for (int e = 0; e < 3; ++e) v += J.Jc[e][6 + i] * gcon[e];
+    g_q[4 * g + i] += v;
+  }
+  g_rho[g] += J.dsig * gsig;
+  for (int k = 0; k < c.nb; ++k)
+    for (int ch = 0; ch < 3; ++ch) g_sh[((size_t)g * c.nb + k) * 3 + ch] += J.live[ch] * J.Y[k] * gcol[ch];
+  const float* p = s.p + (size_t)g * c.KC;
+  float pg = 0.0f;
+  for (int k = 1; k < c.KC; ++k) pg += p[k] * a[10 + k];
+  for (int b = 0; b < c.KC; ++b) g_obj[(size_t)g * c.KC + b] += p[b] * ((b >= 1 ? a[10 + b] : 0.0f) - pg);
+}
+
 struct GainsDims { int nt_max, lu_max, uu_max; };
 
 GainsDims gains_dims(const Consts& c) {
@@ -1529,6 +1573,15 @@ int launch_views_gains_gm(const DevScene& s, const Consts& c, const DevCam* cams
     case 2: go(k_gains_gm<2>); break;
     default: go(k_gains_gm<3>); break;
   }
+  return 1;
+}
+
+int launch_project_backward(const DevScene& s, const Consts& c, const DevCam& cam, const float* gacc, int gw,
+                            const int4* rect, float* g_means, float* g_logs, float* g_quats, float* g_rho,
+                            float* g_sh, float* g_obj, cudaStream_t st) {
+  if (s.n <= 0) return 0;
+  k_project_backward<<<(unsigned)((s.n + 127) / 128), 128, 0, st>>>(s, c, cam, gacc, gw, rect, g_means, g_logs,
+                                                                    g_quats, g_rho, g_sh, g_obj);
   return 1;
 }
 

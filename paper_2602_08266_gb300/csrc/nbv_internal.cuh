@@ -128,6 +128,17 @@ int launch_queue_keys(const uint2* ranges, int ntiles, uint64_t* keys, uint32_t*
 size_t scan_scratch_elems(int64_t n);
 size_t radix_hist_elems(int64_t count);
 
+// Splat exponent at a pixel centre, p = -(A dx^2 + C dy^2)/2 - B dx dy with
+// (dx, dy) = mean2D - pixel centre: the quantity the alpha decisions compare,
+// computed by correctly rounded operations in one fixed order (shared by the
+// forward pass and the backward pass's recomputation).
+__device__ __forceinline__ float splat_power(float mx, float my, float A, float B, float C, float pxc, float pyc) {
+  const float dx = __fsub_rn(mx, pxc), dy = __fsub_rn(my, pyc);
+  const float dxx = __fmul_rn(dx, dx), dyy = __fmul_rn(dy, dy), dxy = __fmul_rn(dx, dy);
+  const float q = __fadd_rn(__fmul_rn(A, dxx), __fmul_rn(C, dyy));
+  return __fsub_rn(__fmul_rn(-0.5f, q), __fmul_rn(B, dxy));
+}
+
 struct CompositeArgs {
   DevCam cam;
   const float4* r0;
@@ -154,6 +165,32 @@ struct CompositeArgs {
 };
 // stage = Gaussians staged in shared memory per round (16 or 32).
 int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage = 32);
+
+// Backward pass of the rasterizer for one view (backward.cu): per-pixel
+// output gradients in, per-Gaussian gradients of the projected quantities
+// out, gacc[g][gw] += {u (mean2D, A, B, C, sigma), rgb (3), z, p_0..p_K}.
+struct BackwardArgs {
+  DevCam cam;
+  const float4* r0;
+  const float4* r1;
+  const float4* r2;
+  const float* p;
+  const uint32_t* vals;
+  const uint2* ranges;
+  const float* g_rgb;      // [H][W][3] or NULL
+  const float* g_depth;    // [H][W] or NULL
+  const float* g_alpha;    // [H][W] or NULL
+  const float* g_obj;      // [H][W][K+1] or NULL
+  float* gacc;             // [n][gw]
+  int gw;
+};
+int backward_width(const Consts& c);
+int launch_render_backward(const BackwardArgs& a, const Consts& c, cudaStream_t st);
+// Chain rule through the projection (logdet.cu): gradients of the raw
+// parameters += M^T gacc for every projected Gaussian of the view.
+int launch_project_backward(const DevScene& s, const Consts& c, const DevCam& cam, const float* gacc, int gw,
+                            const int4* rect, float* g_means, float* g_logs, float* g_quats, float* g_rho,
+                            float* g_sh, float* g_obj, cudaStream_t st);
 
 struct Factors {
   // per output, L~ = L^-1 D^-1/2, where D = diag(H) and D^-1/2 H D^-1/2 =
