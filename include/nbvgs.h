@@ -83,6 +83,12 @@ typedef struct {
   int max_batch_views;   /* batched path: candidates per multi-view pass (0 = as many as keep the
                             per-(view, Gaussian) state under 32 GB); larger sets run in chunks,
                             eagerly, and only a single-chunk set is replayed as a CUDA graph */
+  int criterion;         /* per-Gaussian information criterion of Eq. 6's block-diagonal form:
+                            0 (default) log det(H_T + c A_v) - log det H_T, the paper's;
+                            1 tr(H_T^-1 c A_v), its first-order term (an expected-information
+                              criterion in the manner of FisherRF);
+                            2 tr(c A_v), T-optimality (no training prior).
+                            Normalisation (Eq. 10) and weighting (Eq. 11) are unchanged */
 } nbv_config;
 
 typedef struct {

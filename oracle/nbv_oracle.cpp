@@ -108,6 +108,7 @@ struct Hyper {
   float alpha_obj, alpha_opa, beta_d, beta_o, lambda;
   float near_z, alpha_min, alpha_max, t_min, dilation, guard;
   int tile_w, tile_h;
+  int crit;   // 0: log det (Eq. 6); 1: tr(H_T^-1 c A_v); 2: tr(c A_v) (T-optimality)
 };
 
 struct Cam32 {
@@ -690,14 +691,14 @@ static void alloc_blocks(const Scene& s, Blocks& B, const uint8_t* mask) {
 extern "C" {
 
 // Scene set-up (A0). hp = {alpha_obj, alpha_opa, beta_d, beta_o, lambda, near,
-// alpha_min, alpha_max, t_min, dilation, guard, tile_w, tile_h}.
+// alpha_min, alpha_max, t_min, dilation, guard, tile_w, tile_h, criterion}.
 void* orc_scene_create(int64_t n, int K, int sh_degree, const float* means, const float* log_scales,
                        const float* quats, const float* opacity, const float* sh, const float* obj,
                        const float* hp, int target) {
   Scene* s = new Scene();
   s->n = n; s->K = K; s->deg = sh_degree; s->nb = (sh_degree + 1) * (sh_degree + 1); s->target = target;
   s->hp = Hyper{hp[0], hp[1], hp[2], hp[3], hp[4], hp[5], hp[6], hp[7], hp[8], hp[9], hp[10],
-                (int)hp[11], (int)hp[12]};
+                (int)hp[11], (int)hp[12], (int)hp[13]};
   const int KC = K + 1;
   s->mu.assign(means, means + 3 * n);
   s->logs.assign(log_scales, log_scales + 3 * n);
@@ -913,7 +914,37 @@ static int prepare_state(Scene* s, int n_train, const float* tcams, const int* t
   return bad ? -2 : 0;
 }
 
-// IG_f(T, v) = sum_g [log det(H_T,g + c_g A_v,g) - log det H_T,g] (Eqs. 5, 6, 9).
+// trace(H^-1 A) for symmetric positive definite H (l x l): H = L L^T by
+// Cholesky, X = L^-1 A L^-T by two triangular solves, trace of X.
+static double trace_solve(const double* Hg, const double* A, int l) {
+  std::vector<double> L(Hg, Hg + (size_t)l * l), Y((size_t)l * l);
+  logdet_spd(L, l);                                   // leaves the factor in the lower triangle
+  // Y = L^-1 A (column by column)
+  for (int c = 0; c < l; ++c)
+    for (int i = 0; i < l; ++i) {
+      double x = A[i * l + c];
+      for (int k = 0; k < i; ++k) x -= L[i * l + k] * Y[k * l + c];
+      Y[i * l + c] = x / L[i * l + i];
+    }
+  // trace(L^-1 A L^-T) = sum_i (L^-1 Y^T)_ii with Y^T = A L^-T ... = sum over i of row i of
+  // L^-1 applied to column i of Y^T: solve L z = (row i of Y)^T and take z_i
+  double tr = 0.0;
+  std::vector<double> z(l);
+  for (int i = 0; i < l; ++i) {
+    for (int r = 0; r < l; ++r) {
+      double x = Y[i * l + r];
+      for (int k = 0; k < r; ++k) x -= L[r * l + k] * z[k];
+      z[r] = x / L[r * l + r];
+    }
+    tr += z[i];
+  }
+  return tr;
+}
+
+// IG_f(T, v) = sum_g [log det(H_T,g + c_g A_v,g) - log det H_T,g] (Eqs. 5, 6, 9),
+// or, for the criterion variants, sum_g tr(H_T,g^-1 c_g A_v,g) (the first-order
+// term of that log det: an expected-information criterion in the manner of
+// FisherRF) or sum_g tr(c_g A_v,g) (T-optimality).
 static int score_view(Scene* s, const Cam32& c, double* out3, double* dg, int row_stride) {
   const int ls[3] = {NG + 3 * s->nb, NG, NG + s->K + 1};
   ViewData v;
@@ -933,6 +964,16 @@ static int score_view(Scene* s, const Cam32& c, double* out3, double* dg, int ro
       bool zero = true;
       for (int i = 0; i < l * l && zero; ++i) zero = (A[i] == 0.0);
       if (zero || s->conf[g] == 0.0) { dl[3 * g + f] = 0.0; continue; }
+      if (s->hp.crit == 2) {
+        double tr = 0.0;
+        for (int i = 0; i < l; ++i) tr += A[i * l + i];
+        dl[3 * g + f] = s->conf[g] * tr;
+        continue;
+      }
+      if (s->hp.crit == 1) {
+        dl[3 * g + f] = s->conf[g] * trace_solve(&s->H[f][(size_t)g * l * l], A, l);
+        continue;
+      }
       std::vector<double> M(s->H[f].begin() + (size_t)g * l * l, s->H[f].begin() + (size_t)(g + 1) * l * l);
       for (int i = 0; i < l * l; ++i) M[i] += s->conf[g] * A[i];
       double ld = logdet_spd(M, l);

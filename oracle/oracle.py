@@ -94,11 +94,12 @@ class Hyper:
     guard: float = 1.3
     tile_w: int = 16
     tile_h: int = 16
+    crit: int = 0          # 0 log det (Eq. 6), 1 tr(H_T^-1 c A), 2 tr(c A)
 
     def array(self):
         return np.array([self.alpha_obj, self.alpha_opa, self.beta_d, self.beta_o, self.lam,
                          self.near, self.alpha_min, self.alpha_max, self.t_min, self.dilation,
-                         self.guard, self.tile_w, self.tile_h], np.float32)
+                         self.guard, self.tile_w, self.tile_h, self.crit], np.float32)
 
 
 def cam_arrays(cams, i):

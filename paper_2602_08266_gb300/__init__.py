@@ -45,7 +45,7 @@ class nbv_config(ctypes.Structure):
                 ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("dilation", ctypes.c_float), ("guard", ctypes.c_float),
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("batched", ctypes.c_int),
-                ("stage", ctypes.c_int), ("max_batch_views", ctypes.c_int)]
+                ("stage", ctypes.c_int), ("max_batch_views", ctypes.c_int), ("criterion", ctypes.c_int)]
 
 
 class nbv_camera(ctypes.Structure):

@@ -618,6 +618,7 @@ void nbv_config_default(nbv_config* cfg, int K, int sh_degree) {
   cfg->batched = 0;
   cfg->stage = 32;
   cfg->max_batch_views = 0;
+  cfg->criterion = 0;
 }
 
 int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
@@ -628,6 +629,7 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   if (cfg->K < 1 || cfg->K > kMaxK || cfg->sh_degree < 0 || cfg->sh_degree > 3 || !tile_ok) return NBV_ERR_ARG;
   if (cfg->stage != 16 && cfg->stage != 32) return NBV_ERR_ARG;
   if (cfg->max_batch_views < 0) return NBV_ERR_ARG;
+  if (cfg->criterion < 0 || cfg->criterion > 2) return NBV_ERR_ARG;
   const float fl[] = {cfg->alpha_obj, cfg->alpha_opa, cfg->beta_d, cfg->beta_o, cfg->lambda_damp,
                       cfg->near_z, cfg->alpha_min, cfg->alpha_max, cfg->t_min, cfg->dilation, cfg->guard};
   for (float v : fl)
@@ -643,6 +645,7 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   c.alpha_obj = cfg->alpha_obj; c.alpha_opa = cfg->alpha_opa; c.beta_d = cfg->beta_d; c.beta_o = cfg->beta_o;
   c.lam = cfg->lambda_damp; c.near_z = cfg->near_z; c.alpha_min = cfg->alpha_min;
   c.alpha_max = cfg->alpha_max; c.t_min = cfg->t_min; c.dilation = cfg->dilation; c.guard = cfg->guard;
+  c.crit = cfg->criterion;
   ctx->nB = block_floats(c.K);
   if (cfg->tile_w != 0) { ctx->tw = cfg->tile_w; ctx->th = cfg->tile_h; }
   ctx->stage = cfg->stage;

@@ -728,6 +728,35 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
       }
       __syncwarp();
     }
+    if (c.crit == 2) {
+      // T-optimality has no training prior: the gains read L~ = I
+      float* L0g = F.L[0] + (size_t)g * rgb_L_size(c.nb);
+      const int T = rgb_tri_nb(c.nb);
+      for (int i = lane; i < rgb_L_size(c.nb); i += 32) {
+        float v = 0.0f;
+        if (i < 3 * T) {
+          int k, k2;
+          tri_decode(i % T, k, k2);
+          v = k == k2 ? 1.0f : 0.0f;
+        } else if (i >= rgb_off_E(c.nb)) {
+          int r, r2;
+          tri_decode(i - rgb_off_E(c.nb), r, r2);
+          v = r == r2 ? 1.0f : 0.0f;
+        }
+        L0g[i] = v;
+      }
+      for (int f = 1; f < 3; ++f) {
+        const int nt = f == 1 ? y.nt1 : y.nt2;
+        float* Lg = F.L[f] + (size_t)g * nt;
+        for (int i = lane; i < nt; i += 32) {
+          int r, r2;
+          tri_decode(i, r, r2);
+          Lg[i] = r == r2 ? 1.0f : 0.0f;
+        }
+      }
+      __syncwarp();
+      continue;
+    }
     factorise_rgb_store(c.nb, cg, c, H0, Hs, dsc, fb + y.off_E, fb + y.off_T,
                         F.L[0] + (size_t)g * rgb_L_size(c.nb), err, lane);
     factorise_store(y.l1, cg, c, H1, Hs, dsc, F.L[1] + (size_t)g * y.nt1, err, lane);
@@ -807,7 +836,17 @@ __device__ __forceinline__ void z_row(int i, int u, const float* __restrict__ Ls
 }
 
 // log det(I + c W B) for one output; W, B, G are u x u in shared memory.
-__device__ __forceinline__ float logdet_IcWB(int u, float cg, const float* W, const float* Bm, float* G, int lane) {
+__device__ __forceinline__ float logdet_IcWB(int u, float cg, const float* W, const float* Bm, float* G, int lane,
+                                             int crit = 0) {
+  if (crit != 0) {   // trace criteria: c tr(W B)
+    float t = 0.0f;
+    for (int i = lane; i < u * u; i += 32) {
+      const int r = i / u, cc = i - r * u;
+      t += W[r * u + cc] * Bm[cc * u + r];
+    }
+    for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return cg * t;
+  }
   for (int i = lane; i < u * u; i += 32) {
     const int r = i / u, cc = i - r * u;
     float a = 0.0f;
@@ -925,7 +964,7 @@ __device__ float output_gain(const GJac& J, const Consts& c, const float* p, con
     W[cc * u + r] = a;
   }
   build_B(F, blk, c, Bm, lane);                  // ends with __syncwarp
-  return logdet_IcWB(u, cg, W, Bm, G, lane);
+  return logdet_IcWB(u, cg, W, Bm, G, lane, c.crit);
 }
 
 template <int UO>
@@ -1009,7 +1048,17 @@ __host__ __device__ constexpr int ptri(int r, int cc) { return r * (r + 1) / 2 +
 // as conditions, so that full unrolling leaves only constant indices and the
 // arrays stay in registers.)
 template <int U>
-__device__ __forceinline__ float logdet_lane(float (&Wm)[ptri(U, 0)], const float (&Bm)[ptri(U, 0)], float cg) {
+__device__ __forceinline__ float logdet_lane(float (&Wm)[ptri(U, 0)], const float (&Bm)[ptri(U, 0)], float cg,
+                                             int crit = 0) {
+  if (crit != 0) {   // trace criteria: c tr(W B) (W and B symmetric, packed)
+    float t = 0.0f;
+#pragma unroll
+    for (int r = 0; r < U; ++r)
+#pragma unroll
+      for (int cc = 0; cc < U; ++cc)
+        if (cc <= r) t += (cc == r ? 1.0f : 2.0f) * Wm[ptri(r, cc)] * Bm[ptri(r, cc)];
+    return cg * t;
+  }
   // Wm <- Lw (in place)
 #pragma unroll
   for (int j = 0; j < U; ++j) {
@@ -1085,7 +1134,7 @@ __device__ __forceinline__ float logdet_lane(float (&Wm)[ptri(U, 0)], const floa
 // L~ of the colour output (see Factors; shared memory, same for every lane).
 template <int DEG>
 __device__ __forceinline__ float rgb_gain_lane(const GJac& J, const float* __restrict__ Lt,
-                                               const float* __restrict__ blk, float cg) {
+                                               const float* __restrict__ blk, float cg, int crit) {
   constexpr int NB = (DEG + 1) * (DEG + 1), TN = NB * (NB + 1) / 2, N3 = 3 * NB;
   const float* Cm = Lt + 3 * TN;
   const float* Em = Cm + kNG * N3;
@@ -1155,12 +1204,12 @@ __device__ __forceinline__ float rgb_gain_lane(const GJac& J, const float* __res
       if (cc <= r)
         Bm[ptri(r, cc)] = r < 6 ? blk[kOffQrgb + ptri(r, cc)]
                                 : (cc < 6 ? blk[kOffXrgb + 6 * (r - 6) + cc] : (r == cc ? w2 : 0.0f));
-  return logdet_lane<9>(Wm, Bm, cg);
+  return logdet_lane<9>(Wm, Bm, cg, crit);
 }
 
 // Depth gain of one (view, Gaussian) in one lane.
 __device__ __forceinline__ float depth_gain_lane(const GJac& J, const float* __restrict__ Lt,
-                                                 const float* __restrict__ blk, float cg) {
+                                                 const float* __restrict__ blk, float cg, int crit) {
   float Wm[28];
 #pragma unroll
   for (int i = 0; i < 28; ++i) Wm[i] = 0.0f;
@@ -1199,7 +1248,7 @@ __device__ __forceinline__ float depth_gain_lane(const GJac& J, const float* __r
 #pragma unroll
     for (int cc = 0; cc < 7; ++cc)
       if (cc <= r) Bm[ptri(r, cc)] = r < 6 ? blk[kOffQd + ptri(r, cc)] : (cc < 6 ? blk[kOffXd + cc] : blk[kOffW2]);
-  return logdet_lane<7>(Wm, Bm, cg);
+  return logdet_lane<7>(Wm, Bm, cg, crit);
 }
 
 struct GmLayout {     // per-warp shared memory (floats)
@@ -1309,8 +1358,8 @@ __global__ void __launch_bounds__(256, 1) k_gains_gm(DevScene s, Consts c, const
         else val = k == 10 ? J.dsig : 0.0f;
         Yg[q * 32 + lane] = val;
       }
-      acc[1] += (double)depth_gain_lane(J, L1, blk, cg);
-      acc[0] += (double)rgb_gain_lane<DEG>(J, L0, blk, cg);
+      acc[1] += (double)depth_gain_lane(J, L1, blk, cg, c.crit);
+      acc[0] += (double)rgb_gain_lane<DEG>(J, L0, blk, cg, c.crit);
     }
     __syncwarp();
     // object gain, one (view, Gaussian) at a time
@@ -1348,7 +1397,7 @@ __global__ void __launch_bounds__(256, 1) k_gains_gm(DevScene s, Consts c, const
         Wo[cc * u2 + r] = w;
       }
       build_B(2, bsrc, c, Bo, lane);                   // ends with __syncwarp
-      const float d2 = logdet_IcWB(u2, cg, Wo, Bo, Go, lane);
+      const float d2 = logdet_IcWB(u2, cg, Wo, Bo, Go, lane, c.crit);
       if (lane == src) acc[2] += (double)d2;
     }
     __syncwarp();

@@ -50,6 +50,7 @@ struct Consts {
   int K, KC, deg, nb;
   float alpha_obj, alpha_opa, beta_d, beta_o, lam;
   float near_z, alpha_min, alpha_max, t_min, dilation, guard;
+  int crit;   // 0: log det (Eq. 6); 1: tr(H_T^-1 c A); 2: tr(c A) (T-optimality)
 };
 
 // Scene on the device (structure of arrays).

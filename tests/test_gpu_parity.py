@@ -117,16 +117,16 @@ def test_render_parity_scene_scale_one_view(P):
 
 
 # ------------------------------------------------------------------- IG
-def _check_scores(gpu4, ref, train_gpu=None):
+def _check_scores(gpu4, ref, train_gpu=None, rtol=IG_RTOL):
     igc = ref["ig_cand"]
-    np.testing.assert_allclose(gpu4[:, :3], igc, rtol=IG_RTOL, atol=0)
+    np.testing.assert_allclose(gpu4[:, :3], igc, rtol=rtol, atol=0)
     if train_gpu is not None:
-        np.testing.assert_allclose(train_gpu, ref["ig_train"], rtol=IG_RTOL, atol=0)
+        np.testing.assert_allclose(train_gpu, ref["ig_train"], rtol=rtol, atol=0)
     tot = ref["score"]
-    np.testing.assert_allclose(gpu4[:, 3], tot, rtol=IG_RTOL)
+    np.testing.assert_allclose(gpu4[:, 3], tot, rtol=rtol)
     order = np.argsort(-tot)
     best_g = int(np.argmax(gpu4[:, 3]))
-    if len(tot) > 1 and (tot[order[0]] - tot[order[1]]) > IG_RTOL * abs(tot[order[0]]):
+    if len(tot) > 1 and (tot[order[0]] - tot[order[1]]) > 2 * rtol * abs(tot[order[0]]):
         assert best_g == ref["best"]
 
 
@@ -424,3 +424,22 @@ def test_batched_chunks_match_single_pass(P):
         np.testing.assert_allclose(o, out[0], rtol=1e-5)
     ref = O.OracleScene(wl.scene).score(wl.train, wl.cand)
     _check_scores(out[2], ref)
+
+
+@pytest.mark.parametrize("crit,batched,target", [(1, 0, -1), (1, 1, 2), (2, 0, -1), (2, 1, -1)])
+def test_criterion_variants_parity(P, crit, batched, target):
+    """tr(H_T^-1 c A) (crit 1) and T-optimality tr(c A) (crit 2) on the
+    per-view and multi-view paths against the oracle. Both are linear in the
+    2D blocks, whose entries carry the TF32 rounding of the tensor-core
+    contraction (2^-11 relative per product) without the compression of the
+    logarithm; the bound is 5e-3 relative instead of the log-det's 1e-4."""
+    wl = S.make_workload("tiny")
+    wl.cand = _mixed(wl)
+    sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=batched, criterion=crit)
+    sc.load_scene(wl.scene)
+    sc.set_train_views(wl.train)
+    sc.set_candidates(wl.cand)
+    sc.prepare(target)
+    ref = O.OracleScene(wl.scene, hyper=O.Hyper(crit=crit), target=target).score(wl.train, wl.cand)
+    _check_scores(sc.score_host().astype(np.float64), ref, sc.train_gains().astype(np.float64), rtol=5e-3)
+    sc.close()

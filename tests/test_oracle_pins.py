@@ -464,3 +464,24 @@ def test_invariants_on_tiny_workload():
         m = r["alpha"] > 1e-6
         zd = r["depth"][m] / r["alpha"][m]
         assert zd.min() > 0.2 and zd.max() < 1.2
+
+
+@pytest.mark.parametrize("crit", [1, 2])
+def test_criterion_variants_closed_form_single_training_view(crit):
+    """The criterion variants on T = {t}, candidate = t: per Gaussian
+    tr(H_T^-1 c A) = sum_i c mu_i / (lambda + c mu_i) (crit 1) and
+    tr(c A) = sum_i c mu_i (crit 2) over the eigenvalues of A_t; the
+    normalised score is again exactly 1 + beta_d + beta_o."""
+    wl = S.make_workload("tiny")
+    sc = wl.scene.subset(np.arange(300))
+    o = O.OracleScene(sc, hyper=O.Hyper(crit=crit))
+    train = wl.train.subset([2])
+    res = o.score(train, train, delta_view=0)
+    c = o.confidence()
+    lam32 = float(np.float32(o.hyper.lam))
+    for f, A in enumerate(o.view_blocks(train, 0)):
+        mu = np.maximum(np.linalg.eigvalsh(A), 0.0)
+        cm = c[:, None] * mu
+        per = (cm / (lam32 + cm)).sum(1) if crit == 1 else cm.sum(1)
+        np.testing.assert_allclose(res["delta"][:, f], per, rtol=1e-8, atol=1e-10)
+    assert abs(res["score"][0] - 12.0) < 1e-10
