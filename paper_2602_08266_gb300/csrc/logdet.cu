@@ -1251,6 +1251,100 @@ __device__ __forceinline__ float depth_gain_lane(const GJac& J, const float* __r
   return logdet_lane<7>(Wm, Bm, cg, crit);
 }
 
+// Object gain of one (view, Gaussian), rows in registers: lane r < u holds
+// row r of G = I + c W B (u = 6 + K <= UO <= 32), formed from W (shared,
+// u x u) and the structured block B = [[Q, X^T], [X, W2 (I + 1 1^T)]]:
+//   G[r][c<6]  = c (sum_{k<6} W[r][k] Q[k][c] + sum_j W[r][6+j] X[j][c])
+//   G[r][6+j]  = c (sum_{k<6} W[r][k] X[j][k] + W2 (W[r][6+j] + sum_i W[r][6+i]))
+// (plus the identity), then log|det G| by Gaussian elimination with partial
+// pivoting across the lanes: the pivot row is found by a warp arg-max and
+// broadcast by shuffles, rows already used as pivots drop out (no swaps).
+// Qs: Q (6 x 6, full), Xs: X (K x 6) in shared memory.
+template <int UO>
+__device__ __forceinline__ float obj_logdet_rows(int u, int K, float cg, float w2, const float* W, const float* Qs,
+                                                 const float* Xs, int lane, int crit) {
+  const int r = lane;
+  const bool row = r < u;
+  float wr[UO];
+#pragma unroll
+  for (int k = 0; k < UO; ++k) wr[k] = (row && k < u) ? W[r * u + k] : 0.0f;
+  if (crit != 0) {   // trace criteria: c tr(W B) = c sum_r sum_k W[r][k] B[k][r], row r's share
+    float br = 0.0f;
+    if (row) {
+      if (r < 6) {
+#pragma unroll
+        for (int k = 0; k < UO; ++k)
+          if (k < u) br += wr[k] * (k < 6 ? Qs[k * 6 + r] : Xs[(k - 6) * 6 + r]);
+      } else {
+        const int j = r - 6;
+        float sw = 0.0f;
+#pragma unroll
+        for (int k = 6; k < UO; ++k)
+          if (k < u) sw += wr[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) br += wr[k] * Xs[j * 6 + k];
+        float wrr = 0.0f;
+#pragma unroll
+        for (int k = 6; k < UO; ++k)
+          if (k == r) wrr = wr[k];
+        br += w2 * (wrr + sw);
+      }
+    }
+    for (int o = 16; o >= 1; o >>= 1) br += __shfl_xor_sync(0xffffffffu, br, o);
+    return cg * br;
+  }
+  float sw = 0.0f;
+#pragma unroll
+  for (int k = 6; k < UO; ++k) sw += wr[k];
+  float g[UO];
+#pragma unroll
+  for (int cc = 0; cc < 6; ++cc) {
+    float a = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a += wr[k] * Qs[k * 6 + cc];
+#pragma unroll
+    for (int j = 0; j < UO - 6; ++j)
+      if (j < K) a += wr[6 + j] * Xs[j * 6 + cc];
+    g[cc] = (r == cc ? 1.0f : 0.0f) + cg * a;
+  }
+#pragma unroll
+  for (int j = 0; j < UO - 6; ++j) {
+    float a = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a += wr[k] * Xs[j * 6 + k];
+    a += w2 * (wr[6 + j] + sw);
+    g[6 + j] = (r == 6 + j ? 1.0f : 0.0f) + (j < K ? cg * a : 0.0f);
+  }
+  bool done = !row;
+  float ld = 0.0f;
+#pragma unroll
+  for (int k = 0; k < UO; ++k) {
+    if (k < u) {
+      float best = done ? -1.0f : fabsf(g[k]);
+      int bl = r;
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
+      }
+      const float piv = __shfl_sync(0xffffffffu, g[k], bl);
+      ld += logf(fabsf(piv));
+      const bool upd = !done && r != bl;
+      const float f = upd ? g[k] / piv : 0.0f;
+#pragma unroll
+      for (int j = 0; j < UO; ++j) {
+        if (j > k) {
+          const float pj = __shfl_sync(0xffffffffu, g[j], bl);
+          g[j] -= f * pj;
+        }
+      }
+      if (r == bl) done = true;
+    }
+  }
+  return ld;
+}
+
 struct GmLayout {     // per-warp shared memory (floats)
   int nt0, nt1, nt2;  // packed sizes of L~ per output
   int l2, u2;         // object output sizes
@@ -1396,8 +1490,20 @@ __global__ void __launch_bounds__(256, 1) k_gains_gm(DevScene s, Consts c, const
         Wo[r * u2 + cc] = w;
         Wo[cc * u2 + r] = w;
       }
-      build_B(2, bsrc, c, Bo, lane);                   // ends with __syncwarp
-      const float d2 = logdet_IcWB(u2, cg, Wo, Bo, Go, lane, c.crit);
+      float d2;
+      if (u2 <= 32) {
+        // Q (full 6 x 6) and X of this view's block into shared memory
+        for (int i = lane; i < 36 + 6 * K; i += 32)
+          Bo[i] = i < 36 ? q6(bsrc + kOffQo, i / 6, i % 6) : bsrc[kOffXo + i - 36];
+        __syncwarp();
+        const float w2 = bsrc[kOffW2];
+        d2 = u2 <= 24 ? obj_logdet_rows<24>(u2, K, cg, w2, Wo, Bo, Bo + 36, lane, c.crit)
+                      : obj_logdet_rows<32>(u2, K, cg, w2, Wo, Bo, Bo + 36, lane, c.crit);
+        __syncwarp();
+      } else {
+        build_B(2, bsrc, c, Bo, lane);                 // ends with __syncwarp
+        d2 = logdet_IcWB(u2, cg, Wo, Bo, Go, lane, c.crit);
+      }
       if (lane == src) acc[2] += (double)d2;
     }
     __syncwarp();
