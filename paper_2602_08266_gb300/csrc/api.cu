@@ -807,9 +807,26 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
                                                nt, ctx->F, ctx->d_err, st)));
   }
   CKR(grow(ctx, &ctx->ig_train, &ctx->ig_train_cap, (size_t)nt * 3));
-  for (int t = 0; t < nt; ++t)
-    CKR(view_gains(ctx, ctx->train[t], ctx->train_blocks + (size_t)t * ctx->n * ctx->nBp, nullptr,
-                   ctx->ig_train + 3 * t));
+  {
+    // training gains (the normalisers of Eq. 10): all training views in one
+    // multi-view gains launch when its shared memory fits, else view by view
+    Phase ph(ctx, NBV_PHASE_GAINS);
+    const int parts_cap = (ctx->partial_cap * 8) / std::max(nt, 1);
+    int nparts = 0;
+    const int r = parts_cap >= 8
+                      ? launch_views_gains_gm(dev_scene(ctx), ctx->c, ctx->d_train_cams, nt, ctx->train_blocks, ctx->F,
+                                              ctx->partial, parts_cap, &nparts, st)
+                      : -1;
+    if (r >= 0) {
+      CKR(check_launch(ctx, r));
+      CKR(check_launch(ctx, launch_reduce_gains_views(ctx->partial, nparts, nt, ctx->ig_train, st)));
+    }
+    if (r < 0) {
+      for (int t = 0; t < nt; ++t)
+        CKR(view_gains(ctx, ctx->train[t], ctx->train_blocks + (size_t)t * ctx->n * ctx->nBp, nullptr,
+                       ctx->ig_train + 3 * t));
+    }
+  }
   int herr = 0;
   CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
