@@ -325,9 +325,9 @@ __device__ __forceinline__ float q6(const float* q, int u, int v) { return u >= 
 // Per-warp shared memory of the factor kernel: doubles (the scaled matrix
 // being factorised and the scaling), then floats.
 struct FactLayout {
-  int l0, l1, l2, nt0, nt1, nt2, ntm, lmax;
-  int d_per_warp;
-  int off_H1, off_H2, off_J, off_GB, off_XG, off_xs, off_E, off_T, f_per_warp;
+  int l0, l1, l2, nt0, nt1, nt2;
+  int off_A, off_X, off_R, d_per_warp;     // doubles: scaling and floors (2 (l0 + l1 + l2)), then these
+  int off_H1, off_H2, off_J, off_GB, off_XG, off_xs, off_E, off_T, off_col, f_per_warp;
 };
 constexpr int kTrainChunk = 8;   // training views whose Jacobians are held at once
 
@@ -339,9 +339,12 @@ FactLayout fact_layout(const Consts& c) {
   y.nt0 = y.l0 * (y.l0 + 1) / 2;
   y.nt1 = y.l1 * (y.l1 + 1) / 2;
   y.nt2 = y.l2 * (y.l2 + 1) / 2;
-  y.lmax = y.l0 > y.l2 ? y.l0 : y.l2;
-  y.ntm = y.nt0 > y.nt2 ? y.nt0 : y.nt2;
-  y.d_per_warp = y.ntm + y.lmax;
+  const int T = c.nb * (c.nb + 1) / 2, n3 = 3 * c.nb;
+  auto mx = [](int a, int b) { return a > b ? a : b; };
+  y.off_A = 2 * (y.l0 + y.l1 + y.l2);
+  y.off_X = y.off_A + 3 * T;
+  y.off_R = y.off_X + mx(3 * T, kNG * n3);
+  y.d_per_warp = y.off_R + mx(kNG * n3 + kNG * (kNG + 1), y.nt2);
   auto r4 = [](int x) { return (x + 3) & ~3; };
   y.off_H1 = r4(y.nt0);
   y.off_H2 = y.off_H1 + r4(y.nt1);
@@ -351,7 +354,8 @@ FactLayout fact_layout(const Consts& c) {
   y.off_xs = y.off_XG + r4(c.K * kNG);
   y.off_E = y.off_xs + 12;
   y.off_T = y.off_E + 68;
-  y.f_per_warp = y.off_T + r4(kNG * 3 * c.nb);
+  y.off_col = y.off_T + r4(kNG * 3 * c.nb);
+  y.f_per_warp = y.off_col + r4(mx(y.l2, 2 * kNG));
   return y;
 }
 
@@ -471,178 +475,311 @@ __device__ __forceinline__ double rsqrt_d(double x) {
   return y;
 }
 
-// Cholesky factorisation of a packed lower n x n matrix in double precision,
-// in place, trailing updates spread over the lanes. The diagonal slot keeps
-// 1 / L_kk (all that the inversion needs of it).
-// The matrix is a Jacobi-scaled damped Hessian D^-1/2 (lambda I + A) D^-1/2
-// with A positive semi-definite, so every pivot is at least lambda / H_kk =
-// lambda dk[k stride]^2 (dk: the scaling D^-1/2). Rounding in the single-
-// precision sums of A can push a pivot of a nearly unobserved direction
-// below that bound, even below zero; such a pivot is raised to the bound.
-// A non-finite pivot sets *err.
-__device__ void chol_packed_d(double* P, int n, int* err, int lane, double lam, const double* dk, int stride) {
-  for (int k = 0; k < n; ++k) {
-    double dkk = P[tri(k, k)];
-    if (!isfinite(dkk) && lane == 0) atomicExch(err, 1);
-    const double dd = dk[k * stride];
-    const double floor_k = lam * dd * dd;
-    if (!(dkk >= floor_k)) dkk = floor_k;
-    const double iL = rsqrt_d(fmax(dkk, 1e-30));
+// Up to four packed lower matrices that one warp factorises (or inverts)
+// together: the pivots of a step are taken by lanes 0-3 at once and the
+// element updates of all matrices are spread over the warp, so the serial
+// chain of a step is paid once for the set. n = 0 marks an unused slot.
+struct MatSet {
+  double* P0;
+  double* P1;
+  double* P2;
+  double* P3;
+  const double* f0;     // pivot floors by row (see chol_set_d)
+  const double* f1;
+  const double* f2;
+  const double* f3;
+  int n0, n1, n2, n3;
+};
+
+__device__ __forceinline__ double* ms_P(const MatSet& s, int q) {
+  return q == 0 ? s.P0 : (q == 1 ? s.P1 : (q == 2 ? s.P2 : s.P3));
+}
+__device__ __forceinline__ const double* ms_f(const MatSet& s, int q) {
+  return q == 0 ? s.f0 : (q == 1 ? s.f1 : (q == 2 ? s.f2 : s.f3));
+}
+__device__ __forceinline__ int ms_n(const MatSet& s, int q) {
+  return q == 0 ? s.n0 : (q == 1 ? s.n1 : (q == 2 ? s.n2 : s.n3));
+}
+__device__ __forceinline__ int ms_nmax(const MatSet& s) { return max(max(s.n0, s.n1), max(s.n2, s.n3)); }
+
+// Which of four consecutive ranges of sizes c[0..3] the index e falls in;
+// e becomes the offset inside it.
+__device__ __forceinline__ int range_of(const int (&c)[4], int& e) {
+  int q = 0;
+  if (e >= c[0]) {
+    e -= c[0];
+    q = 1;
+    if (e >= c[1]) {
+      e -= c[1];
+      q = 2;
+      if (e >= c[2]) {
+        e -= c[2];
+        q = 3;
+      }
+    }
+  }
+  return q;
+}
+
+// Cholesky factorisation of the set in double precision, in place; the
+// diagonal slot keeps 1 / L_kk (all that the inversion needs of it).
+// Each matrix is a Jacobi-scaled damped Hessian D^-1/2 (lambda I + A) D^-1/2
+// with A positive semi-definite, so pivot k is at least lambda / H_kk (the
+// floor f[k]). Rounding in the single-precision sums of A can push a pivot
+// of a nearly unobserved direction below that bound, even below zero; such a
+// pivot is raised to the bound. A non-finite pivot sets *err.
+__device__ void chol_set_d(const MatSet& s, int* err, int lane) {
+  const int nmax = ms_nmax(s);
+  for (int k = 0; k < nmax; ++k) {
+    if (lane < 4 && k < ms_n(s, lane)) {
+      double* P = ms_P(s, lane);
+      double dkk = P[tri(k, k)];
+      if (!isfinite(dkk)) atomicExch(err, 1);
+      const double fk = ms_f(s, lane)[k];
+      if (!(dkk >= fk)) dkk = fk;
+      P[tri(k, k)] = rsqrt_d(fmax(dkk, 1e-30));
+    }
     __syncwarp();
-    if (lane == 0) P[tri(k, k)] = iL;
-    for (int i = k + 1 + lane; i < n; i += 32) P[tri(i, k)] *= iL;
+    int cs[4], ct[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = max(ms_n(s, q) - k - 1, 0);
+      cs[q] = r;
+      ct[q] = r * (r + 1) / 2;
+    }
+    const int ns = cs[0] + cs[1] + cs[2] + cs[3];
+    for (int e0 = lane; e0 < ns; e0 += 32) {        // column k below the pivot
+      int e = e0;
+      const int q = range_of(cs, e);
+      double* P = ms_P(s, q);
+      P[tri(k + 1 + e, k)] *= P[tri(k, k)];
+    }
     __syncwarp();
-    const int m = n - k - 1;                       // trailing triangle of size m
-    const int tot = m * (m + 1) / 2;
-    if (lane < tot) {
+    const int nt = ct[0] + ct[1] + ct[2] + ct[3];
+    for (int e0 = lane; e0 < nt; e0 += 32) {        // trailing triangles
+      int e = e0;
+      const int q = range_of(ct, e);
+      double* P = ms_P(s, q);
       int ii, jj;
-      tri_decode(lane, ii, jj);
-      for (int t = lane; t < tot; t += 32) {
-        const int i = k + 1 + ii, j = k + 1 + jj;
-        P[tri(i, j)] -= P[tri(i, k)] * P[tri(j, k)];
-        jj += 32;
-        while (jj > ii) { jj -= ii + 1; ++ii; }
-      }
+      tri_decode(e, ii, jj);
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      P[tri(i, j)] -= P[tri(i, k)] * P[tri(j, k)];
     }
     __syncwarp();
   }
 }
 
-// X = L^-1 (packed lower) from the factor chol_packed_d left, right-looking:
-//   X_kk = 1 / L_kk,  X_kj = -X_kk acc_kj (j < k),  acc_ij += L_ik X_kj (i > k, j <= k)
+// X_q = L_q^-1 (packed lower) for the factors chol_set_d left, right-looking:
+//   X_kk = 1 / L_kk,  X_kj = -X_kk acc_kj (j < k),  acc_ij += L_ik X_kj (i > k, j <= k).
+// For single-precision X the column L_.k is converted once per step into
+// col (sum of the set's n floats).
 template <typename TX>
-__device__ void inv_lower(const double* L, TX* X, int n, int lane) {
-  const int nt = n * (n + 1) / 2;
-  for (int i = lane; i < nt; i += 32) X[i] = (TX)0;
+__device__ void inv_set(const MatSet& s, TX* X0, TX* X1, TX* X2, TX* X3, float* col, int lane) {
+  const int nn[4] = {s.n0, s.n1, s.n2, s.n3};
+  int tt[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) tt[q] = nn[q] * (nn[q] + 1) / 2;
+  auto Xq = [&](int q) { return q == 0 ? X0 : (q == 1 ? X1 : (q == 2 ? X2 : X3)); };
+  const int ntot = tt[0] + tt[1] + tt[2] + tt[3];
+  for (int e0 = lane; e0 < ntot; e0 += 32) {
+    int e = e0;
+    const int q = range_of(tt, e);
+    Xq(q)[e] = (TX)0;
+  }
+  auto cb = [&](int q) {                      // offset of matrix q's column in col
+    return q == 0 ? 0 : (q == 1 ? nn[0] : (q == 2 ? nn[0] + nn[1] : nn[0] + nn[1] + nn[2]));
+  };
   __syncwarp();
-  for (int k = 0; k < n; ++k) {
-    const TX xkk = (TX)L[tri(k, k)];
-    for (int j = lane; j < k; j += 32) X[tri(k, j)] = -xkk * X[tri(k, j)];
-    if (lane == 0) X[tri(k, k)] = xkk;
+  const int nmax = ms_nmax(s);
+  for (int k = 0; k < nmax; ++k) {
+    int ca[4], cc[4], cu[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool live = k < nn[q];
+      ca[q] = live ? k + 1 : 0;                 // row k of X
+      cc[q] = live ? nn[q] - k - 1 : 0;         // column k of L below the diagonal
+      cu[q] = cc[q] * (k + 1);                  // updates of the rows below
+    }
+    const int na = ca[0] + ca[1] + ca[2] + ca[3];
+    const int nc = std::is_same<TX, float>::value ? cc[0] + cc[1] + cc[2] + cc[3] : 0;
+    for (int e0 = lane; e0 < na + nc; e0 += 32) {
+      if (e0 < na) {
+        int e = e0;
+        const int q = range_of(ca, e);
+        const TX xkk = (TX)ms_P(s, q)[tri(k, k)];
+        TX* X = Xq(q);
+        X[tri(k, e)] = e == k ? xkk : -xkk * X[tri(k, e)];
+      } else {
+        int e = e0 - na;
+        const int q = range_of(cc, e);
+        col[cb(q) + k + 1 + e] = (float)ms_P(s, q)[tri(k + 1 + e, k)];
+      }
+    }
     __syncwarp();
-    const int rows = n - 1 - k, cols = k + 1;
-    if (rows >= cols) {                       // lanes over the rows below k
-      for (int i = k + 1 + lane; i < n; i += 32) {
-        const TX lik = (TX)L[tri(i, k)];
-        TX* Xi = X + tri(i, 0);
-        const TX* Xk = X + tri(k, 0);
-        for (int j = 0; j <= k; ++j) Xi[j] += lik * Xk[j];
-      }
-    } else {                                  // lanes over the columns up to k
-      for (int j = lane; j <= k; j += 32) {
-        const TX xkj = X[tri(k, j)];
-        for (int i = k + 1; i < n; ++i) X[tri(i, j)] += (TX)L[tri(i, k)] * xkj;
-      }
+    const int nu = cu[0] + cu[1] + cu[2] + cu[3];
+    for (int e0 = lane; e0 < nu; e0 += 32) {
+      int e = e0;
+      const int q = range_of(cu, e);
+      const int i = k + 1 + e / (k + 1), j = e - (i - k - 1) * (k + 1);
+      TX* X = Xq(q);
+      TX lik;
+      if constexpr (std::is_same<TX, float>::value) lik = col[cb(q) + i];
+      else lik = ms_P(s, q)[tri(i, k)];
+      X[tri(i, j)] += lik * X[tri(k, j)];
     }
     __syncwarp();
   }
 }
 
-// H = lambda I + c_g Hf (Hf = sum_t A_t, packed, l x l), Jacobi-scaled and
-// Cholesky-factorised in double precision, the factor inverted in single
-// precision, and L~ = L^-1 D^-1/2 stored packed at Lg. Hf is overwritten.
-__device__ void factorise_store(int l, float cg, const Consts& c, float* Hf, double* Hs, double* dsc, float* Lg,
-                                int* err, int lane) {
-  const int nt = l * (l + 1) / 2;
-  for (int i = lane; i < l; i += 32) {
-    const double hii = (double)c.lam + (double)cg * (double)Hf[tri(i, i)];
-    dsc[i] = rsqrt_d(hii);
-  }
-  __syncwarp();
-  for (int i = lane; i < nt; i += 32) {
-    int r, cc;
-    tri_decode(i, r, cc);
-    const double h = (double)cg * (double)Hf[i] + (r == cc ? (double)c.lam : 0.0);
-    Hs[i] = h * dsc[r] * dsc[cc];
-  }
-  __syncwarp();
-  chol_packed_d(Hs, l, err, lane, (double)c.lam, dsc, 1);
-  inv_lower<float>(Hs, Hf, l, lane);
-  for (int i = lane; i < nt; i += 32) {
-    int r, cc;
-    tri_decode(i, r, cc);
-    Lg[i] = (float)((double)Hf[i] * dsc[cc]);
-  }
-  __syncwarp();
-}
-
-// The colour output, factorised by blocks with the parameters ordered
-// [SH of channel 0, 1, 2 | geometric]: the three SH blocks are independent
-// (nb x nb each), so H~ = L L^T needs their Cholesky factors L_c, the
-// coupling L_gS = H~_gS L_S^-T and the factor of the geometric Schur
-// complement H~_gg - L_gS L_gS^T, all in double precision (3 nb^3 / 6 +
-// 11 * 3 nb^2 / 2 + ... operations instead of (11 + 3 nb)^3 / 6). L^-1 is
-// stored as A_c = L_c^-1, C_c = -E L_gS,c A_c, E = L_gg^-1 (see Factors),
-// each column scaled by D^-1/2. H0 holds the natural packed sum (SH (k, ch)
-// at 11 + 3 k + ch) and is only read; Ef (66) and Tf (33 nb) are float scratch.
-__device__ void factorise_rgb_store(int nb, float cg, const Consts& c, const float* H0, double* Hs, double* dsc,
-                                    float* Ef, float* Tf, float* Lg, int* err, int lane) {
-  const int T = nb * (nb + 1) / 2, n3 = 3 * nb;
+// All three outputs' training factors of one Gaussian, stored in the forms
+// Factors describes. H0, H1, H2: the natural packed sums sum_t A_t of colour
+// (SH (k, ch) at 11 + 3 k + ch), depth and object (floats; H2 and H1 are
+// reused as outputs, H0 as scratch once read). Each H = lambda I + c_g H_sum
+// is Jacobi-scaled, H~ = D^-1/2 H D^-1/2, and Cholesky-factorised in double
+// precision. Colour goes by blocks with the parameters ordered [SH of
+// channel 0, 1, 2 | geometric]: the three SH blocks are independent, so H~ =
+// L L^T needs their factors L_c, the coupling L_gS = H~_gS L_S^-T and the
+// factor of the geometric Schur complement H~_gg - L_gS L_gS^T. Order of
+// work: the SH blocks and the object matrix together, then the Schur
+// complement and the depth matrix together.
+__device__ void factorise_all(const FactLayout& y, float cg, const Consts& c, float* H0, float* H1, float* H2,
+                              double* D, float* fb, float* L0g, float* L1g, float* L2g, int* err, int lane) {
+  const int nb = c.nb, T = nb * (nb + 1) / 2, n3 = 3 * nb, l0 = y.l0, l2 = y.l2, nt2 = y.nt2;
+  const int nd = l0 + kNG + l2;
   const double lam = c.lam, cgd = cg;
-  for (int i = lane; i < kNG + n3; i += 32) dsc[i] = rsqrt_d(lam + cgd * (double)H0[tri(i, i)]);
-  __syncwarp();
-  double* A = Hs;               // 3 packed nb-triangles: A_c = L_c^-1
-  double* LgS = A + 3 * T;      // 11 x 3nb
-  double* S = LgS + kNG * n3;   // packed 11-triangle
-  double* X = S + kNG * (kNG + 1) / 2;   // packed nb-triangle
-  for (int ch = 0; ch < 3; ++ch) {
-    for (int e = lane; e < T; e += 32) {
-      int k, k2;
-      tri_decode(e, k, k2);
-      const int a = kNG + 3 * k + ch, b = kNG + 3 * k2 + ch;
-      X[e] = (cgd * (double)H0[tri(a, b)] + (k == k2 ? lam : 0.0)) * dsc[a] * dsc[b];
+  double* dsc0 = D;                  // D^-1/2 of colour (natural order), depth, object
+  double* dsc1 = D + l0;
+  double* dsc2 = dsc1 + kNG;
+  double* flX = D + nd;              // pivot floors lambda / H_kk: SH blocks [ch][k],
+  double* flS = flX + n3;            // Schur complement, depth, object
+  double* fl1 = flS + kNG;
+  double* fl2 = fl1 + kNG;
+  double* A = D + y.off_A;           // A_c = L_c^-1 (3 packed nb-triangles)
+  double* X = D + y.off_X;           // SH blocks being factorised; then H~_gS rows
+  double* R = D + y.off_R;           // object matrix; then L_gS, Schur complement, depth
+  float* Ef = fb + y.off_E;
+  float* Tf = fb + y.off_T;
+  float* col = fb + y.off_col;
+  for (int i = lane; i < nd; i += 32) {
+    float h;
+    int fi;
+    if (i < l0) {                 // colour: geometric r -> Schur floors, SH (k, ch) -> [ch][k]
+      h = H0[tri(i, i)];
+      fi = i < kNG ? n3 + i : ((i - kNG) % 3) * nb + (i - kNG) / 3;
+    } else {                      // depth and object rows keep their index (l0 = n3 + 11)
+      const int r = i < l0 + kNG ? i - l0 : i - l0 - kNG;
+      h = (i < l0 + kNG ? H1 : H2)[tri(r, r)];
+      fi = i;
     }
-    __syncwarp();
-    chol_packed_d(X, nb, err, lane, lam, dsc + kNG + ch, 3);
-    inv_lower<double>(X, A + ch * T, nb, lane);
-  }
-  // L_gS[r][(c, k)] = sum_{k2 <= k} H~[g_r][(c, k2)] A_c[k][k2]
-  for (int e = lane; e < kNG * n3; e += 32) {
-    const int r = e / n3, q = e - r * n3, ch = q / nb, k = q - ch * nb;
-    const double* Ak = A + ch * T + tri(k, 0);
-    double acc = 0.0;
-    for (int k2 = 0; k2 <= k; ++k2) {
-      const int b = kNG + 3 * k2 + ch;
-      acc += (double)H0[tri(b, r)] * dsc[b] * Ak[k2];
-    }
-    LgS[e] = cgd * acc * dsc[r];
+    const double d = rsqrt_d(lam + cgd * (double)h);
+    D[i] = d;
+    flX[fi] = lam * d * d;
   }
   __syncwarp();
-  for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {
+  for (int e = lane; e < 3 * T; e += 32) {
+    const int ch = e / T;
+    int k, k2;
+    tri_decode(e - ch * T, k, k2);
+    const int a = kNG + 3 * k + ch, b = kNG + 3 * k2 + ch;
+    X[e] = (cgd * (double)H0[tri(a, b)] + (k == k2 ? lam : 0.0)) * dsc0[a] * dsc0[b];
+  }
+  for (int e = lane; e < nt2; e += 32) {
     int r, r2;
     tri_decode(e, r, r2);
-    double acc = (cgd * (double)H0[e] + (r == r2 ? lam : 0.0)) * dsc[r] * dsc[r2];
+    R[e] = (cgd * (double)H2[e] + (r == r2 ? lam : 0.0)) * dsc2[r] * dsc2[r2];
+  }
+  __syncwarp();
+  chol_set_d(MatSet{X, X + T, X + 2 * T, R, flX, flX + nb, flX + 2 * nb, fl2, nb, nb, nb, l2}, err, lane);
+  inv_set<double>(MatSet{X, X + T, X + 2 * T, nullptr, nullptr, nullptr, nullptr, nullptr, nb, nb, nb, 0},
+                  A, A + T, A + 2 * T, (double*)nullptr, col, lane);
+  inv_set<float>(MatSet{R, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, l2, 0, 0, 0},
+                 H2, (float*)nullptr, (float*)nullptr, (float*)nullptr, col, lane);
+  for (int e = lane; e < nt2; e += 32) {             // object: L~ = L^-1 D^-1/2
+    int r, r2;
+    tri_decode(e, r, r2);
+    L2g[e] = (float)((double)H2[e] * dsc2[r2]);
+  }
+  // colour coupling: H~_gS rows, X[r][ch nb + k2] = H(b, r) D^-1/2_b, b = 11 + 3 k2 + ch
+  for (int e = lane; e < kNG * n3; e += 32) {
+    const int r = e / n3, q = e - r * n3, ch = q / nb, k2 = q - ch * nb;
+    const int b = kNG + 3 * k2 + ch;
+    X[e] = (double)H0[tri(b, r)] * dsc0[b];
+  }
+  __syncwarp();
+  // L_gS[r][ch nb + k] = c_g D^-1/2_r sum_{k2 <= k} X[r][ch nb + k2] A_c[k][k2]; each
+  // lane takes k and nb - 1 - k (nb + 1 terms in all, the same count on every lane)
+  double* LgS = R;
+  double* S = R + kNG * n3;
+  double* S1 = S + kNG * (kNG + 1) / 2;
+  const int hp = (nb + 1) / 2;
+  for (int task = lane; task < kNG * 3 * hp; task += 32) {
+    const int r = task / (3 * hp), rem = task - r * 3 * hp, ch = rem / hp, p = rem - ch * hp;
+    const int k1 = p, k2 = nb - 1 - p;
+    const double* hrow = X + r * n3 + ch * nb;
+    const double* Ac = A + ch * T;
+    double acc = 0.0, acc1 = 0.0;
+    for (int it = 0; it <= nb; ++it) {
+      if (it == k1 + 1) {
+        acc1 = acc;
+        acc = 0.0;
+      }
+      const bool first = it <= k1;
+      const int q = first ? it : it - k1 - 1;
+      acc = fma(hrow[q], Ac[tri(first ? k1 : k2, q)], acc);
+    }
+    const double sc = cgd * dsc0[r];
+    LgS[r * n3 + ch * nb + k1] = sc * acc1;
+    LgS[r * n3 + ch * nb + k2] = sc * acc;
+  }
+  __syncwarp();
+  for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {   // H~_gg - L_gS L_gS^T
+    int r, r2;
+    tri_decode(e, r, r2);
+    double acc = (cgd * (double)H0[e] + (r == r2 ? lam : 0.0)) * dsc0[r] * dsc0[r2];
     for (int q = 0; q < n3; ++q) acc -= LgS[r * n3 + q] * LgS[r2 * n3 + q];
     S[e] = acc;
   }
+  for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {   // depth
+    int r, r2;
+    tri_decode(e, r, r2);
+    S1[e] = (cgd * (double)H1[e] + (r == r2 ? lam : 0.0)) * dsc1[r] * dsc1[r2];
+  }
   __syncwarp();
-  chol_packed_d(S, kNG, err, lane, lam, dsc, 1);   // the Schur complement is >= lambda D_g^-1 too
-  inv_lower<float>(S, Ef, kNG, lane);
+  // the Schur complement is >= lambda D_g^-1 too, so its floors are those of the geometric rows
+  chol_set_d(MatSet{S, S1, nullptr, nullptr, flS, fl1, nullptr, nullptr, kNG, kNG, 0, 0}, err, lane);
+  inv_set<float>(MatSet{S, S1, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, kNG, kNG, 0, 0}, Ef, H1,
+                 (float*)nullptr, (float*)nullptr, col, lane);
+  // single-precision copies of A_c and L_gS (H0 is no longer read)
+  float* Af = H0;
+  float* LgSf = H0 + 3 * T;
+  for (int e = lane; e < 3 * T + kNG * n3; e += 32) Af[e] = (float)(e < 3 * T ? A[e] : LgS[e - 3 * T]);
+  __syncwarp();
   for (int e = lane; e < kNG * n3; e += 32) {          // T_c = L_gS,c A_c
     const int r = e / n3, q = e - r * n3, ch = q / nb, k = q - ch * nb;
     float acc = 0.0f;
-    for (int k2 = k; k2 < nb; ++k2) acc += (float)LgS[r * n3 + ch * nb + k2] * (float)A[ch * T + tri(k2, k)];
+    for (int k2 = k; k2 < nb; ++k2) acc += LgSf[r * n3 + ch * nb + k2] * Af[ch * T + tri(k2, k)];
     Tf[e] = acc;
   }
   __syncwarp();
   for (int e = lane; e < 3 * T; e += 32) {
-    const int ch = e / T, q = e - ch * T;
+    const int ch = e / T;
     int k, k2;
-    tri_decode(q, k, k2);
-    Lg[e] = (float)(A[e] * dsc[kNG + 3 * k2 + ch]);
+    tri_decode(e - ch * T, k, k2);
+    L0g[e] = (float)(A[e] * dsc0[kNG + 3 * k2 + ch]);
   }
-  float* Lc = Lg + rgb_off_C(nb);
+  float* Lc = L0g + rgb_off_C(nb);
   for (int e = lane; e < kNG * n3; e += 32) {
     const int r = e / n3, q = e - r * n3, ch = q / nb, k = q - ch * nb;
     float acc = 0.0f;
     for (int r2 = 0; r2 <= r; ++r2) acc += Ef[tri(r, r2)] * Tf[r2 * n3 + q];
-    Lc[e] = (float)(-(double)acc * dsc[kNG + 3 * k + ch]);
+    Lc[e] = (float)(-(double)acc * dsc0[kNG + 3 * k + ch]);
   }
-  float* Le = Lg + rgb_off_E(nb);
+  float* Le = L0g + rgb_off_E(nb);
   for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {
     int r, r2;
     tri_decode(e, r, r2);
-    Le[e] = (float)((double)Ef[e] * dsc[r2]);
+    Le[e] = (float)((double)Ef[e] * dsc0[r2]);
+    L1g[e] = (float)((double)H1[e] * dsc1[r2]);
   }
   __syncwarp();
 }
@@ -657,8 +794,7 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int nBp = (block_floats(c.K) + 3) & ~3;
-  double* Hs = reinterpret_cast<double*>(smem) + (size_t)warp * y.d_per_warp;
-  double* dsc = Hs + y.ntm;
+  double* Dw = reinterpret_cast<double*>(smem) + (size_t)warp * y.d_per_warp;
   float* fb = reinterpret_cast<float*>(reinterpret_cast<double*>(smem) + (size_t)nw * y.d_per_warp) +
               (size_t)warp * y.f_per_warp;
   float* H0 = fb;
@@ -757,10 +893,8 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
       __syncwarp();
       continue;
     }
-    factorise_rgb_store(c.nb, cg, c, H0, Hs, dsc, fb + y.off_E, fb + y.off_T,
-                        F.L[0] + (size_t)g * rgb_L_size(c.nb), err, lane);
-    factorise_store(y.l1, cg, c, H1, Hs, dsc, F.L[1] + (size_t)g * y.nt1, err, lane);
-    factorise_store(y.l2, cg, c, H2, Hs, dsc, F.L[2] + (size_t)g * y.nt2, err, lane);
+    factorise_all(y, cg, c, H0, H1, H2, Dw, fb, F.L[0] + (size_t)g * rgb_L_size(c.nb), F.L[1] + (size_t)g * y.nt1,
+                  F.L[2] + (size_t)g * y.nt2, err, lane);
   }
 }
 
