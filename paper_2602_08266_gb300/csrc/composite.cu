@@ -67,7 +67,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
                                                int tile, uint2 rg, float* blocks_v, size_t rec_off,
                                                unsigned char* smem) {
   const int KC = c.KC;
-  const int nBp = (args.nB + 3) & ~3;
+  const int nB = args.nB, nBp = (nB + 3) & ~3;
   float4* s0 = reinterpret_cast<float4*>(smem);
   float4* s1 = s0 + kBatch;
   float4* s2 = s1 + kBatch;
@@ -250,9 +250,6 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       const int nact = __popc(any);
       const int nks = (nact + 7) >> 3;
       const int slot = __popc(any & ((1u << lane) - 1u));
-      if (lane >= nact && lane < 8 * nks) {       // rows past the last active pixel: zero U
-        for (int i = 0; i < 8 + K; ++i) Uw[i * kCS + lane] = 0.0f;
-      }
       if (act) {
         float* Ur = Uw + slot;           // value s at Ur[s * kCS]
         float* Vr = Vw + slot;
@@ -328,12 +325,16 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       const uint32_t* Vb = reinterpret_cast<const uint32_t*>(Vw);
       for (int ks = 0; ks < nks; ++ks) {
         const int c0 = 8 * ks + t4, c1 = c0 + 4;          // pixel slots of this lane's fragments
+        // slots at or past nact hold an earlier splat's values: their V (the B
+        // operand of both contractions) enters as zero
+        const bool ok0 = c0 < nact, ok1 = c1 < nact;
         const uint32_t qa0 = Ub[gq * kCS + c0], qa1 = Ub[(gq + 8) * kCS + c0];
         const uint32_t qa2 = Ub[gq * kCS + c1], qa3 = Ub[(gq + 8) * kCS + c1];
 #pragma unroll
         for (int nt = 0; nt < 3; ++nt)
-          mma_tf32(dq[nt], qa0, qa1, qa2, qa3, Vb[(8 * nt + gq) * kCS + c0], Vb[(8 * nt + gq) * kCS + c1]);
-        const uint32_t xb0 = Vb[(24 + gq) * kCS + c0], xb1 = Vb[(24 + gq) * kCS + c1];
+          mma_tf32(dq[nt], qa0, qa1, qa2, qa3, ok0 ? Vb[(8 * nt + gq) * kCS + c0] : 0u,
+                   ok1 ? Vb[(8 * nt + gq) * kCS + c1] : 0u);
+        const uint32_t xb0 = ok0 ? Vb[(24 + gq) * kCS + c0] : 0u, xb1 = ok1 ? Vb[(24 + gq) * kCS + c1] : 0u;
 #pragma unroll
         for (int mt = 0; mt < MTBM; ++mt)
           if (mt < MTB) {
@@ -343,16 +344,23 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
           }
       }
       __syncwarp();
-      // scatter the needed entries of D into the tile's block of splat j
-      float* accj = acc + j * nBp;
+      // scatter D into the tile's block of splat j: the needed fragment
+      // entries are staged at their block offsets in the (now free) V buffer,
+      // then added with one atomic per block entry, 32 consecutive entries
+      // per warp instruction (half the atomics of adding from the fragments)
+      float* stage = Vw;
 #pragma unroll
       for (int q = 0; q < 6; ++q)
-        if (eq[q] >= 0) atomicAdd(&accj[eq[q]], dq[q >> 1][q & 1]);
+        if (eq[q] >= 0) stage[eq[q]] = dq[q >> 1][q & 1];
 #pragma unroll
       for (int mt = 0; mt < MTBM; ++mt)
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-          if (ex[mt][i] >= 0) atomicAdd(&accj[ex[mt][i]], dxo[mt][i]);
+          if (ex[mt][i] >= 0) stage[ex[mt][i]] = dxo[mt][i];
+      __syncwarp();
+      float* accj = acc + j * nBp;
+      for (int e = lane; e < nB; e += 32) atomicAdd(&accj[e], stage[e]);
+      __syncwarp();
     }
     __syncthreads();
     // flush the tile's share of each touched Gaussian's block
