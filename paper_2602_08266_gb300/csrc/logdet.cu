@@ -1393,7 +1393,10 @@ __device__ __forceinline__ float depth_gain_lane(const GJac& J, const float* __r
 // (plus the identity), then log|det G| by Gaussian elimination with partial
 // pivoting across the lanes: the pivot row is found by a warp arg-max and
 // broadcast by shuffles, rows already used as pivots drop out (no swaps).
-// Qs: Q (6 x 6, full), Xs: X (K x 6) in shared memory.
+// After each step every row shifts left by one column, so the pivot column
+// is always g[0] and the step is a loop body of its own (compact code: this
+// runs once per (view, Gaussian), and fully unrolled steps overflow the
+// instruction cache). Qs: Q (6 x 6, full), Xs: X (K x 6) in shared memory.
 template <int UO>
 __device__ __forceinline__ float obj_logdet_rows(int u, int K, float cg, float w2, const float* W, const float* Qs,
                                                  const float* Xs, int lane, int crit) {
@@ -1431,15 +1434,18 @@ __device__ __forceinline__ float obj_logdet_rows(int u, int K, float cg, float w
 #pragma unroll
   for (int k = 6; k < UO; ++k) sw += wr[k];
   float g[UO];
+  {
+    // G[r][c < 6]: one pass over k (rows of [Q; X]), W[r][k] read from shared memory
+    float a[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    const float* Wr = W + (row ? r : 0) * u;
+    for (int k = 0; k < u; ++k) {
+      const float wk = row ? Wr[k] : 0.0f;
+      const float* bk = k < 6 ? Qs + k * 6 : Xs + (k - 6) * 6;
 #pragma unroll
-  for (int cc = 0; cc < 6; ++cc) {
-    float a = 0.0f;
+      for (int cc = 0; cc < 6; ++cc) a[cc] += wk * bk[cc];
+    }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) a += wr[k] * Qs[k * 6 + cc];
-#pragma unroll
-    for (int j = 0; j < UO - 6; ++j)
-      if (j < K) a += wr[6 + j] * Xs[j * 6 + cc];
-    g[cc] = (r == cc ? 1.0f : 0.0f) + cg * a;
+    for (int cc = 0; cc < 6; ++cc) g[cc] = (r == cc ? 1.0f : 0.0f) + cg * a[cc];
   }
 #pragma unroll
   for (int j = 0; j < UO - 6; ++j) {
@@ -1451,30 +1457,33 @@ __device__ __forceinline__ float obj_logdet_rows(int u, int K, float cg, float w
   }
   bool done = !row;
   float ld = 0.0f;
+  for (int k = 0; k < u; ++k) {
+    float best = done ? -1.0f : fabsf(g[0]);
+    int bl = r;
 #pragma unroll
-  for (int k = 0; k < UO; ++k) {
-    if (k < u) {
-      float best = done ? -1.0f : fabsf(g[k]);
-      int bl = r;
+    for (int o = 16; o >= 1; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
+    }
+    const float piv = __shfl_sync(0xffffffffu, g[0], bl);
+    ld += logf(fabsf(piv));
+    const bool upd = !done && r != bl;
+    const float f = upd ? g[0] / piv : 0.0f;
+    const int live = u - k - 1;                 // columns right of the pivot (warp-uniform)
 #pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-        if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
-      }
-      const float piv = __shfl_sync(0xffffffffu, g[k], bl);
-      ld += logf(fabsf(piv));
-      const bool upd = !done && r != bl;
-      const float f = upd ? g[k] / piv : 0.0f;
+    for (int j0 = 0; j0 < UO - 1; j0 += 4) {
+      if (j0 < live) {
 #pragma unroll
-      for (int j = 0; j < UO; ++j) {
-        if (j > k) {
-          const float pj = __shfl_sync(0xffffffffu, g[j], bl);
-          g[j] -= f * pj;
+        for (int jj = 0; jj < 4; ++jj) {
+          if (j0 + jj < UO - 1) {
+            const float pj = __shfl_sync(0xffffffffu, g[j0 + jj + 1], bl);
+            g[j0 + jj] = g[j0 + jj + 1] - f * pj;
+          }
         }
       }
-      if (r == bl) done = true;
     }
+    if (r == bl) done = true;
   }
   return ld;
 }
