@@ -1458,18 +1458,15 @@ __device__ __forceinline__ float obj_logdet_rows(int u, int K, float cg, float w
   bool done = !row;
   float ld = 0.0f;
   for (int k = 0; k < u; ++k) {
-    float best = done ? -1.0f : fabsf(g[0]);
-    int bl = r;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-      if (ob > best || (ob == best && ol < bl)) { best = ob; bl = ol; }
-    }
+    // pivot row: the largest |g[0]| among the rows left, by one warp max over
+    // keys (|g[0]| with its lowest 5 bits replaced by the inverted lane, so
+    // near-ties go to the lower row; |g| >= 0 orders like its bit pattern)
+    const unsigned key = done ? 0u : ((__float_as_uint(fabsf(g[0])) & ~31u) | (unsigned)(31 - r));
+    const int bl = 31 - (int)(__reduce_max_sync(0xffffffffu, key) & 31u);
     const float piv = __shfl_sync(0xffffffffu, g[0], bl);
     ld += logf(fabsf(piv));
     const bool upd = !done && r != bl;
-    const float f = upd ? g[0] / piv : 0.0f;
+    const float f = upd ? g[0] * __frcp_rn(piv) : 0.0f;
     const int live = u - k - 1;                 // columns right of the pivot (warp-uniform)
 #pragma unroll
     for (int j0 = 0; j0 < UO - 1; j0 += 4) {
