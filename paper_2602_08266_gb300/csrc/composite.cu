@@ -32,13 +32,7 @@ __device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); 
 __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
 
-// TF32 tensor-core helpers (warp-level mma.sync, FP32 accumulation).
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
+// TF32 tensor-core helper (warp-level mma.sync, FP32 accumulation).
 __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
   asm volatile(
@@ -48,8 +42,13 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// An FP32 value rounded to TF32 (kept in an FP32 register / word).
-__device__ __forceinline__ float tf32f(float x) { return __uint_as_float(to_tf32(x)); }
+// An FP32 value as a TF32 operand of the contraction. The tensor core reads
+// only the upper 19 bits of a TF32 operand word (sign, exponent, 10 mantissa
+// bits), so adding half a TF32 unit in the last place (bit 12) to the bit
+// pattern makes it read the value rounded to nearest, ties away from zero,
+// which is what cvt.rna.tf32.f32 produces, for a single integer add. Finite
+// x only (all U and V entries are).
+__device__ __forceinline__ float tf32f(float x) { return __uint_as_float(__float_as_uint(x) + 0x1000u); }
 
 // Per-warp contraction buffers are value-major: element (value s, pixel
 // slot) at s * kCS + slot. With kCS = 36 (= 4 mod 32) the per-pixel stores
@@ -96,6 +95,10 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   uint32_t last = rg.x;     // one past the list index of the last blended splat
   bool done = !inside;
   uint32_t n_eval = 0, n_blend = 0;
+  // colour, depth and object sums only when an image is asked for (the
+  // information pass needs only the final transmittance and list ends)
+  const bool want_cd = args.rgb != nullptr || args.depth != nullptr;
+  const bool want_o = args.obj != nullptr;
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
     if (__syncthreads_count(done) == kTilePix) break;
     const uint32_t nj = min((uint32_t)kBatch, rg.y - start);
@@ -103,12 +106,14 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       const uint32_t g = args.vals[start + tid];
       s0[tid] = args.r0[rec_off + g];
       s1[tid] = args.r1[rec_off + g];
-      s2[tid] = args.r2[rec_off + g];
+      if (want_cd) s2[tid] = args.r2[rec_off + g];
       sid[tid] = (int)g;
     }
-    for (int i = tid; i < (int)nj * KCP; i += kTilePix) {
-      const int j = i / KCP, k = i - j * KCP;
-      sp[i] = k < KC ? args.p[(size_t)args.vals[start + j] * KC + k] : 0.0f;
+    if (want_o) {
+      for (int i = tid; i < (int)nj * KCP; i += kTilePix) {
+        const int j = i / KCP, k = i - j * KCP;
+        sp[i] = k < KC ? args.p[(size_t)args.vals[start + j] * KC + k] : 0.0f;
+      }
     }
     __syncthreads();
     if (!done) {
@@ -121,13 +126,17 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         const float tt = T * (1.0f - alpha);
         if (tt < c.t_min) { done = true; break; }
         const float w = alpha * T;
-        const float4 a2 = s2[j];
-        C0 += w * a2.x; C1 += w * a2.y; C2 += w * a2.z; D += w * a2.w;
-        const float2 w2 = make_float2(w, w);
-        const float2* pj2 = reinterpret_cast<const float2*>(sp + j * KCP);
+        if (want_cd) {
+          const float4 a2 = s2[j];
+          C0 += w * a2.x; C1 += w * a2.y; C2 += w * a2.z; D += w * a2.w;
+        }
+        if (want_o) {
+          const float2 w2 = make_float2(w, w);
+          const float2* pj2 = reinterpret_cast<const float2*>(sp + j * KCP);
 #pragma unroll
-        for (int q = 0; q < KCM / 2; ++q)
-          if (2 * q < KC) O2[q] = __ffma2_rn(w2, pj2[q], O2[q]);
+          for (int q = 0; q < KCM / 2; ++q)
+            if (2 * q < KC) O2[q] = __ffma2_rn(w2, pj2[q], O2[q]);
+        }
         T = tt;
         last = start + j + 1;
         ++n_blend;
