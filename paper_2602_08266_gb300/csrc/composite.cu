@@ -42,6 +42,15 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// Four 8 x 8 tiles of 16-bit pairs from shared memory (one row address per lane).
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const float* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a)
+               : "memory");
+}
+
 // An FP32 value as a TF32 operand of the contraction. The tensor core reads
 // only the upper 19 bits of a TF32 operand word (sign, exponent, 10 mantissa
 // bits), so adding half a TF32 unit in the last place (bit 12) to the bit
@@ -330,26 +339,36 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       for (int q = 0; q < 3; ++q) dq[q][0] = dq[q][1] = dq[q][2] = dq[q][3] = 0.0f;
 #pragma unroll
       for (int q = 0; q < MTBM; ++q) dxo[q][0] = dxo[q][1] = dxo[q][2] = dxo[q][3] = 0.0f;
-      const uint32_t* Ub = reinterpret_cast<const uint32_t*>(Uw);
-      const uint32_t* Vb = reinterpret_cast<const uint32_t*>(Vw);
+      // fragments by ldmatrix (8 x 8 tiles of 16-bit pairs = 8 rows x 4 TF32
+      // words): lane l addresses row l % 8 of tile l / 8. A: tiles (rows
+      // 0-7 | 8-15) x (slots 0-3 | 4-7); V (B, one row per output column):
+      // (rows 0-7 | 8-15, then 16-23 | 24-31) x (slots 0-3 | 4-7)
+      const int i8 = lane & 7, m4 = lane >> 3;
+      const float* aq = Uw + (8 * (m4 & 1) + i8) * kCS + 4 * (m4 >> 1);
+      const float* ax = aq + 3 * kCS;
+      const float* vq = Vw + (8 * (m4 >> 1) + i8) * kCS + 4 * (m4 & 1);
       for (int ks = 0; ks < nks; ++ks) {
         const int c0 = 8 * ks + t4, c1 = c0 + 4;          // pixel slots of this lane's fragments
         // slots at or past nact hold an earlier splat's values: their V (the B
         // operand of both contractions) enters as zero
         const bool ok0 = c0 < nact, ok1 = c1 < nact;
-        const uint32_t qa0 = Ub[gq * kCS + c0], qa1 = Ub[(gq + 8) * kCS + c0];
-        const uint32_t qa2 = Ub[gq * kCS + c1], qa3 = Ub[(gq + 8) * kCS + c1];
-#pragma unroll
-        for (int nt = 0; nt < 3; ++nt)
-          mma_tf32(dq[nt], qa0, qa1, qa2, qa3, ok0 ? Vb[(8 * nt + gq) * kCS + c0] : 0u,
-                   ok1 ? Vb[(8 * nt + gq) * kCS + c1] : 0u);
-        const uint32_t xb0 = ok0 ? Vb[(24 + gq) * kCS + c0] : 0u, xb1 = ok1 ? Vb[(24 + gq) * kCS + c1] : 0u;
+        uint32_t qa[4], vb[4], vc[4];
+        ldsm_x4(qa, aq + 8 * ks);
+        ldsm_x4(vb, vq + 8 * ks);
+        ldsm_x4(vc, vq + 16 * kCS + 8 * ks);
+        const uint32_t b00 = ok0 ? vb[0] : 0u, b01 = ok1 ? vb[1] : 0u;   // columns 0-7
+        const uint32_t b10 = ok0 ? vb[2] : 0u, b11 = ok1 ? vb[3] : 0u;   // 8-15
+        const uint32_t b20 = ok0 ? vc[0] : 0u, b21 = ok1 ? vc[1] : 0u;   // 16-23
+        const uint32_t xb0 = ok0 ? vc[2] : 0u, xb1 = ok1 ? vc[3] : 0u;   // 24-31
+        mma_tf32(dq[0], qa[0], qa[1], qa[2], qa[3], b00, b01);
+        mma_tf32(dq[1], qa[0], qa[1], qa[2], qa[3], b10, b11);
+        mma_tf32(dq[2], qa[0], qa[1], qa[2], qa[3], b20, b21);
 #pragma unroll
         for (int mt = 0; mt < MTBM; ++mt)
           if (mt < MTB) {
-            const int r = 3 + 16 * mt + gq;
-            mma_tf32(dxo[mt], Ub[r * kCS + c0], Ub[(r + 8) * kCS + c0], Ub[r * kCS + c1], Ub[(r + 8) * kCS + c1],
-                     xb0, xb1);
+            uint32_t xa[4];
+            ldsm_x4(xa, ax + 16 * mt * kCS + 8 * ks);
+            mma_tf32(dxo[mt], xa[0], xa[1], xa[2], xa[3], xb0, xb1);
           }
       }
       __syncwarp();
