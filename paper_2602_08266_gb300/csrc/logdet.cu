@@ -343,8 +343,8 @@ FactLayout fact_layout(const Consts& c) {
   auto mx = [](int a, int b) { return a > b ? a : b; };
   y.off_A = 2 * (y.l0 + y.l1 + y.l2);
   y.off_X = y.off_A + 3 * T;
-  y.off_R = y.off_X + mx(3 * T, kNG * n3);
-  y.d_per_warp = y.off_R + mx(kNG * n3 + kNG * (kNG + 1), y.nt2);
+  y.off_R = y.off_X + mx(3 * T, kNG * (n3 + 1));      // coupling rows padded to an odd stride
+  y.d_per_warp = y.off_R + mx(kNG * (n3 + 1) + kNG * (kNG + 1), y.nt2);
   auto r4 = [](int x) { return (x + 3) & ~3; };
   y.off_H1 = r4(y.nt0);
   y.off_H2 = y.off_H1 + r4(y.nt1);
@@ -645,6 +645,7 @@ __device__ void inv_set(const MatSet& s, TX* X0, TX* X1, TX* X2, TX* X3, float* 
 __device__ void factorise_all(const FactLayout& y, float cg, const Consts& c, float* H0, float* H1, float* H2,
                               double* D, float* fb, float* L0g, float* L1g, float* L2g, int* err, int lane) {
   const int nb = c.nb, T = nb * (nb + 1) / 2, n3 = 3 * nb, l0 = y.l0, l2 = y.l2, nt2 = y.nt2;
+  const int n3p = n3 + 1;   // row stride of H~_gS and L_gS: odd, so rows fall in distinct banks
   const int nd = l0 + kNG + l2;
   const double lam = c.lam, cgd = cg;
   double* dsc0 = D;                  // D^-1/2 of colour (natural order), depth, object
@@ -703,19 +704,19 @@ __device__ void factorise_all(const FactLayout& y, float cg, const Consts& c, fl
   for (int e = lane; e < kNG * n3; e += 32) {
     const int r = e / n3, q = e - r * n3, ch = q / nb, k2 = q - ch * nb;
     const int b = kNG + 3 * k2 + ch;
-    X[e] = (double)H0[tri(b, r)] * dsc0[b];
+    X[r * n3p + q] = (double)H0[tri(b, r)] * dsc0[b];
   }
   __syncwarp();
   // L_gS[r][ch nb + k] = c_g D^-1/2_r sum_{k2 <= k} X[r][ch nb + k2] A_c[k][k2]; each
   // lane takes k and nb - 1 - k (nb + 1 terms in all, the same count on every lane)
   double* LgS = R;
-  double* S = R + kNG * n3;
+  double* S = R + kNG * n3p;
   double* S1 = S + kNG * (kNG + 1) / 2;
   const int hp = (nb + 1) / 2;
   for (int task = lane; task < kNG * 3 * hp; task += 32) {
     const int r = task / (3 * hp), rem = task - r * 3 * hp, ch = rem / hp, p = rem - ch * hp;
     const int k1 = p, k2 = nb - 1 - p;
-    const double* hrow = X + r * n3 + ch * nb;
+    const double* hrow = X + r * n3p + ch * nb;
     const double* Ac = A + ch * T;
     double acc = 0.0, acc1 = 0.0;
     for (int it = 0; it <= nb; ++it) {
@@ -728,15 +729,15 @@ __device__ void factorise_all(const FactLayout& y, float cg, const Consts& c, fl
       acc = fma(hrow[q], Ac[tri(first ? k1 : k2, q)], acc);
     }
     const double sc = cgd * dsc0[r];
-    LgS[r * n3 + ch * nb + k1] = sc * acc1;
-    LgS[r * n3 + ch * nb + k2] = sc * acc;
+    LgS[r * n3p + ch * nb + k1] = sc * acc1;
+    LgS[r * n3p + ch * nb + k2] = sc * acc;
   }
   __syncwarp();
   for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {   // H~_gg - L_gS L_gS^T
     int r, r2;
     tri_decode(e, r, r2);
     double acc = (cgd * (double)H0[e] + (r == r2 ? lam : 0.0)) * dsc0[r] * dsc0[r2];
-    for (int q = 0; q < n3; ++q) acc -= LgS[r * n3 + q] * LgS[r2 * n3 + q];
+    for (int q = 0; q < n3; ++q) acc -= LgS[r * n3p + q] * LgS[r2 * n3p + q];
     S[e] = acc;
   }
   for (int e = lane; e < kNG * (kNG + 1) / 2; e += 32) {   // depth
@@ -752,12 +753,12 @@ __device__ void factorise_all(const FactLayout& y, float cg, const Consts& c, fl
   // single-precision copies of A_c and L_gS (H0 is no longer read)
   float* Af = H0;
   float* LgSf = H0 + 3 * T;
-  for (int e = lane; e < 3 * T + kNG * n3; e += 32) Af[e] = (float)(e < 3 * T ? A[e] : LgS[e - 3 * T]);
+  for (int e = lane; e < 3 * T + kNG * n3p; e += 32) Af[e] = (float)(e < 3 * T ? A[e] : LgS[e - 3 * T]);
   __syncwarp();
   for (int e = lane; e < kNG * n3; e += 32) {          // T_c = L_gS,c A_c
     const int r = e / n3, q = e - r * n3, ch = q / nb, k = q - ch * nb;
     float acc = 0.0f;
-    for (int k2 = k; k2 < nb; ++k2) acc += LgSf[r * n3 + ch * nb + k2] * Af[ch * T + tri(k2, k)];
+    for (int k2 = k; k2 < nb; ++k2) acc += LgSf[r * n3p + ch * nb + k2] * Af[ch * T + tri(k2, k)];
     Tf[e] = acc;
   }
   __syncwarp();
