@@ -127,15 +127,22 @@ class Clocks:
 
 # ------------------------------------------------------- roofline numbers
 def composite_flops(stats, K):
-    """Algorithmic FP32 operations of the fused compositing kernel:
-    forward: 11 per evaluated (pixel, splat) pair (the splat exponent) and
-    13 + 2(K+1) per blended pair (alpha, transmittance, colour, depth and
-    K+1 object accumulations); information pass: 266 + 21 K per blended pair
+    """Algorithmic FP32 operations of the fused compositing kernel as the
+    scoring path runs it (no images are written, so the forward pass keeps
+    only what the information pass needs): forward: 11 per evaluated
+    (pixel, splat) pair (the splat exponent) and 5 per blended pair (alpha,
+    transmittance, weight); information pass: 266 + 21 K per blended pair
     (exponent, transmittance recovery, d out / d alpha for 4 + K+1 outputs,
     the structured block contributions and their sums over pixels)."""
-    KC = K + 1
     ev, bl = stats["pairs_evaluated"], stats["pairs_blended"]
-    return 11 * ev + (13 + 2 * KC) * bl + (266 + 21 * K) * bl
+    return 11 * ev + 5 * bl + (266 + 21 * K) * bl
+
+
+# DRAM bytes (read + write) of the compositing kernel per composited view of
+# the scene workload, from one ncu capture of its 8-view launch
+# (dram__bytes_read.sum 192.0 MB + dram__bytes_write.sum 91.9 MB); a launch's
+# traffic is taken as this times the views it covers
+SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW = (192.0e6 + 91.9e6) / 8
 
 
 def fp32_peak_tflops(clock_mhz):
@@ -277,8 +284,12 @@ def run_ours(args):
         return flops, avg_s, flops / avg_s / 1e12
 
     flops_per_launch, avg_launch_s, achieved = comp_roof(prof)
+    traffic = None
+    if args.workload == "scene":
+        views_per_launch = (wl.cand.n + wl.train.n) * args.steps / max(prof["stats"]["composite_launches"], 1)
+        traffic = round(SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW * views_per_launch)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": "k_composite (fused compositing + information blocks, all candidates in one launch)",
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz max SM clock (derived)",
                 "flops_per_launch": flops_per_launch, "avg_launch_ms": round(avg_launch_s * 1e3, 3)}
