@@ -377,11 +377,12 @@ def test_autotune_picks_a_valid_tiling_and_scores_match_oracle(P):
     assert sc2.autotune() == (tw, th, st)
 
 
-@pytest.mark.parametrize("name,n_views,views", [("tiny", 8, None), ("scene", 6, (0, 5))])
+@pytest.mark.parametrize("name,n_views,views", [("tiny", 8, None), ("scene", 6, (0, 5)), ("scene", 64, (0, 37, 63))])
 def test_batched_tile_lists_bit_exact(P, name, n_views, views):
     """The multi-view binning (depth order of all (view, Gaussian) slots,
     duplication in that order, stable sort on the 32-bit tile id) gives
-    every candidate exactly the oracle's (depth bits, index) lists."""
+    every candidate exactly the oracle's (depth bits, index) lists. With 64
+    views at 640x480 the tile ids take 17 bits (a third radix pass)."""
     wl = S.make_workload(name, n_views=n_views)
     if name == "tiny":
         wl.cand = _mixed(wl)
