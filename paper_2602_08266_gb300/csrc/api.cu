@@ -661,6 +661,11 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
     nbv_destroy(ctx);
     return NBV_ERR_CUDA;
   }
+  launch_tri_table_init(ctx->st);
+  if (cudaGetLastError() != cudaSuccess) {
+    nbv_destroy(ctx);
+    return NBV_ERR_CUDA;
+  }
   *out = ctx;
   return NBV_OK;
 }

@@ -303,8 +303,28 @@ __device__ __forceinline__ void build_B(int f, const float* blk, const Consts& c
 }
 
 // --------------------------------------------------------- training factors
-// Decode the linear index t of a packed lower triangle into (row, col).
+// Decode the linear index t of a packed lower triangle into (row, col): a
+// table lookup (row << 16 | col) for every triangle of up to kTriRows rows
+// (all the factors: l <= 11 + 128), computed beyond.
+constexpr int kTriRows = 140;
+constexpr int kTriMax = kTriRows * (kTriRows + 1) / 2;
+__device__ uint32_t g_tri[kTriMax];
+
+__global__ void k_tri_init() {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= kTriMax) return;
+  int r = 0;
+  while (tri(r + 1, 0) <= t) ++r;      // 140 steps at most, once per library context
+  g_tri[t] = ((uint32_t)r << 16) | (uint32_t)(t - tri(r, 0));
+}
+
 __device__ __forceinline__ void tri_decode(int t, int& r, int& cc) {
+  if (t < kTriMax) {
+    const uint32_t v = __ldg(&g_tri[t]);
+    r = (int)(v >> 16);
+    cc = (int)(v & 0xFFFFu);
+    return;
+  }
   r = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
   while (tri(r + 1, 0) <= t) ++r;
   while (tri(r, 0) > t) --r;
@@ -617,10 +637,14 @@ __device__ void inv_set(const MatSet& s, TX* X0, TX* X1, TX* X2, TX* X3, float* 
     }
     __syncwarp();
     const int nu = cu[0] + cu[1] + cu[2] + cu[3];
+    // e / (k + 1) as floor((e + 1/2) / (k + 1)) in single precision: exact for
+    // e < 2^13, k < 140 (the error is below 2^-10, the distance to the next
+    // integer at least 1 / 280)
+    const float rk = 1.0f / (float)(k + 1);
     for (int e0 = lane; e0 < nu; e0 += 32) {
       int e = e0;
       const int q = range_of(cu, e);
-      const int i = k + 1 + e / (k + 1), j = e - (i - k - 1) * (k + 1);
+      const int i = k + 1 + (int)(((float)e + 0.5f) * rk), j = e - (i - k - 1) * (k + 1);
       TX* X = Xq(q);
       TX lik;
       if constexpr (std::is_same<TX, float>::value) lik = col[cb(q) + i];
@@ -1773,6 +1797,11 @@ int warps_for(size_t per_warp) {
 
 }  // namespace
 
+
+int launch_tri_table_init(cudaStream_t st) {
+  k_tri_init<<<(kTriMax + 255) / 256, 256, 0, st>>>();
+  return 1;
+}
 
 int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams, const float* blocks,
                          int n_train, const Factors& f, int* d_err, cudaStream_t st) {

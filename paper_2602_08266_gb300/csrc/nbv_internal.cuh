@@ -210,6 +210,9 @@ __host__ __device__ inline int rgb_off_C(int nb) { return 3 * rgb_tri_nb(nb); }
 __host__ __device__ inline int rgb_off_E(int nb) { return 3 * rgb_tri_nb(nb) + kNG * 3 * nb; }
 __host__ __device__ inline int rgb_L_size(int nb) { return rgb_off_E(nb) + kNG * (kNG + 1) / 2; }
 // Training Hessians: H^f_g = lambda I + c_g sum_t M_t^T B_t M_t, scaled and factorised.
+// Decode table of packed lower-triangle indices used by the factor and gains
+// kernels; launched once when a context is created.
+int launch_tri_table_init(cudaStream_t st);
 int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams, const float* blocks,
                          int n_train, const Factors& f, int* d_err, cudaStream_t st);
 // Per-Gaussian log-det gains of one view: delta [n][3]; per-block partial sums
