@@ -1481,7 +1481,11 @@ __device__ __forceinline__ float obj_logdet_rows(int u, int K, float cg, float w
     g[6 + j] = (r == 6 + j ? 1.0f : 0.0f) + (j < K ? cg * a : 0.0f);
   }
   bool done = !row;
-  float ld = 0.0f;
+  // log |det| = log(mant) + ex log 2: the pivot magnitudes are multiplied into
+  // a mantissa in [1, 2) and their binary exponents summed (one multiply and
+  // a few integer operations per step instead of a logarithm)
+  float mant = 1.0f;
+  int ex = 0;
   for (int k = 0; k < u; ++k) {
     // pivot row: the largest |g[0]| among the rows left, by one warp max over
     // keys (|g[0]| with its lowest 5 bits replaced by the inverted lane, so
@@ -1489,9 +1493,13 @@ __device__ __forceinline__ float obj_logdet_rows(int u, int K, float cg, float w
     const unsigned key = done ? 0u : ((__float_as_uint(fabsf(g[0])) & ~31u) | (unsigned)(31 - r));
     const int bl = 31 - (int)(__reduce_max_sync(0xffffffffu, key) & 31u);
     const float piv = __shfl_sync(0xffffffffu, g[0], bl);
-    ld += logf(fabsf(piv));
+    {
+      const uint32_t b = __float_as_uint(mant * fabsf(piv));
+      ex += (int)((b >> 23) & 0xFFu) - 127;
+      mant = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+    }
     const bool upd = !done && r != bl;
-    const float f = upd ? g[0] * __frcp_rn(piv) : 0.0f;
+    const float f = upd ? __fdividef(g[0], piv) : 0.0f;
     const int live = u - k - 1;                 // columns right of the pivot (warp-uniform)
 #pragma unroll
     for (int j0 = 0; j0 < UO - 1; j0 += 4) {
@@ -1507,7 +1515,7 @@ __device__ __forceinline__ float obj_logdet_rows(int u, int K, float cg, float w
     }
     if (r == bl) done = true;
   }
-  return ld;
+  return logf(mant) + (float)ex * 0.693147180559945309f;
 }
 
 struct GmLayout {     // per-warp shared memory (floats)
