@@ -121,8 +121,10 @@ void nbv_destroy(nbv_ctx* ctx);
  * the call returns after the copy was queued from a staging buffer, so the
  * caller may reuse its memory). Resets any prepared state.
  * Errors: NBV_ERR_ARG (n < 1, NULL, a zero quaternion, a non-finite value),
- * NBV_ERR_OOM, NBV_ERR_CUDA. Validation reads the data on the host; for
- * device pointers it copies them back once (synchronising). */
+ * NBV_ERR_OOM, NBV_ERR_CUDA. Validation runs on the device after the copy
+ * (one synchronisation of the stream); after a load that fails it, the
+ * context holds no usable scene (prepare and render return NBV_ERR_STATE)
+ * until a load succeeds. */
 int nbv_load_gaussians(nbv_ctx* ctx, int64_t n, const float* means, const float* log_scales,
                        const float* quats, const float* opacity, const float* sh,
                        const float* obj_logits, int ptrs_on_device);

@@ -38,6 +38,7 @@ struct nbv_ctx {
 
   // scene
   int64_t n = 0;
+  bool scene_ok = false;        // the last load passed the input check
   float *mu = nullptr, *logs = nullptr, *q = nullptr, *rho = nullptr, *sh = nullptr, *obj = nullptr;
   float4 *mu_sig = nullptr, *scale_skip = nullptr, *qn = nullptr, *aux = nullptr;
   float* p = nullptr;
@@ -69,7 +70,7 @@ struct nbv_ctx {
   size_t ig_train_cap = 0, ig_cand_cap = 0;
   float* out4 = nullptr;
   size_t out4_cap = 0;
-  int* d_flags = nullptr;       // [0] best, [1] empty flag, [2] factor error
+  int* d_flags = nullptr;       // [0] best, [1] empty flag, [2] input check
   float* d_best_score = nullptr;
   bool scored = false;
   int* d_err = nullptr;
@@ -586,12 +587,6 @@ int ensure_scene_buffers(nbv_ctx* ctx, int64_t n) {
   return NBV_OK;
 }
 
-bool check_host_floats(const float* a, size_t m) {
-  for (size_t i = 0; i < m; ++i)
-    if (!std::isfinite(a[i])) return false;
-  return true;
-}
-
 }  // namespace
 
 // ======================================================================== C ABI
@@ -715,40 +710,30 @@ int nbv_load_gaussians(nbv_ctx* ctx, int64_t n, const float* means, const float*
   const size_t sizes[6] = {(size_t)3 * n, (size_t)3 * n, (size_t)4 * n, (size_t)n, (size_t)n * nb * 3,
                            (size_t)n * KC};
   const float* src[6] = {means, log_scales, quats, opacity, sh, obj_logits};
-  // validate on the host (device inputs are read back once for this)
-  std::vector<std::vector<float>> hostcopy;
-  const float* hv[6];
-  if (ptrs_on_device) {
-    hostcopy.resize(6);
-    for (int i = 0; i < 6; ++i) {
-      hostcopy[i].resize(sizes[i]);
-      CK(cudaMemcpyAsync(hostcopy[i].data(), src[i], sizes[i] * 4, cudaMemcpyDeviceToHost, ctx->st));
-      hv[i] = hostcopy[i].data();
-    }
-    CK(cudaStreamSynchronize(ctx->st));
-  } else {
-    for (int i = 0; i < 6; ++i) hv[i] = src[i];
-  }
-  for (int i = 0; i < 6; ++i)
-    if (!check_host_floats(hv[i], sizes[i])) return fail(ctx, NBV_ERR_ARG, "non-finite Gaussian parameter");
-  for (int64_t g = 0; g < n; ++g) {
-    const float* qq = hv[2] + 4 * g;
-    if (qq[0] == 0.0f && qq[1] == 0.0f && qq[2] == 0.0f && qq[3] == 0.0f)
-      return fail(ctx, NBV_ERR_ARG, "zero quaternion");
-  }
   if (n != ctx->n) {
     CKR(ensure_scene_buffers(ctx, n));
     ctx->n = n;
   }
-  float* dst[6] = {ctx->mu, ctx->logs, ctx->q, ctx->rho, ctx->sh, ctx->obj};
-  for (int i = 0; i < 6; ++i)
-    CK(cudaMemcpyAsync(dst[i], src[i], sizes[i] * 4,
-                       ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st));
-  if (!ptrs_on_device) CK(cudaStreamSynchronize(ctx->st));   // the caller may reuse its host memory
+  ctx->scene_ok = false;
   ctx->prepared = false;
   ctx->scored = false;
   ctx->prepared_target = -2;
   batched_invalidate(ctx);
+  float* dst[6] = {ctx->mu, ctx->logs, ctx->q, ctx->rho, ctx->sh, ctx->obj};
+  for (int i = 0; i < 6; ++i)
+    CK(cudaMemcpyAsync(dst[i], src[i], sizes[i] * 4,
+                       ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st));
+  // validation on the device, after the copy; one synchronisation (after which
+  // the caller may also reuse its host memory)
+  int bad = 0;
+  CK(cudaMemsetAsync(ctx->d_flags + 2, 0, sizeof(int), ctx->st));
+  CKR(check_launch(ctx, launch_check_inputs(ctx->mu, ctx->logs, ctx->q, ctx->rho, ctx->sh, ctx->obj, n, nb * 3, KC,
+                                            ctx->d_flags + 2, ctx->st)));
+  CK(cudaMemcpyAsync(&bad, ctx->d_flags + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (bad & 2) return fail(ctx, NBV_ERR_ARG, "zero quaternion");
+  if (bad) return fail(ctx, NBV_ERR_ARG, "non-finite Gaussian parameter");
+  ctx->scene_ok = true;
   CKR(check_launch(ctx, launch_scene_prep(dev_scene(ctx), ctx->c, -1, ctx->st)));
   return NBV_OK;
 }
@@ -786,7 +771,8 @@ int nbv_set_candidates(nbv_ctx* ctx, int n, const nbv_camera* cams) {
 int nbv_prepare(nbv_ctx* ctx, int target_obj) {
   if (!ctx) return NBV_ERR_ARG;
   if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
-  if (ctx->n < 1 || ctx->train.empty()) return fail(ctx, NBV_ERR_STATE, "nbv_prepare: no Gaussians or no training views");
+  if (ctx->n < 1 || !ctx->scene_ok || ctx->train.empty())
+    return fail(ctx, NBV_ERR_STATE, "nbv_prepare: no Gaussians or no training views");
   if (target_obj < -1 || target_obj > ctx->c.K) return fail(ctx, NBV_ERR_ARG, "target_obj out of range");
   cudaStream_t st = ctx->st;
   const int nt = (int)ctx->train.size();
@@ -844,7 +830,7 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
 int nbv_render(nbv_ctx* ctx, int cand, float* rgb, float* depth, float* alpha, float* obj) {
   if (!ctx) return NBV_ERR_ARG;
   if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
-  if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "nbv_render: no Gaussians");
+  if (ctx->n < 1 || !ctx->scene_ok) return fail(ctx, NBV_ERR_STATE, "nbv_render: no Gaussians");
   if (cand < 0 || cand >= (int)ctx->cand.size()) return fail(ctx, NBV_ERR_ARG, "candidate out of range");
   return render_view(ctx, ctx->cand[cand], nullptr, rgb, depth, alpha, obj);
 }
@@ -926,7 +912,7 @@ int nbv_gaussian_gains(nbv_ctx* ctx, int cand, float* delta) {
 int nbv_debug_project(nbv_ctx* ctx, int view_set, int view, int32_t* rect, float* radius,
                       uint32_t* zbits, float* mean2d, float* conic) {
   if (!ctx) return NBV_ERR_ARG;
-  if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "no Gaussians");
+  if (ctx->n < 1 || !ctx->scene_ok) return fail(ctx, NBV_ERR_STATE, "no Gaussians");
   const std::vector<nbv_camera>& vs = view_set ? ctx->train : ctx->cand;
   if (view < 0 || view >= (int)vs.size()) return fail(ctx, NBV_ERR_ARG, "view out of range");
   cudaStream_t st = ctx->st;
@@ -977,7 +963,7 @@ int debug_batched_lists(nbv_ctx* ctx, int view, int64_t* offsets, int32_t* ids, 
 int nbv_debug_tile_lists(nbv_ctx* ctx, int view_set, int view, int64_t* offsets, int32_t* ids,
                          int64_t cap, int64_t* count) {
   if (!ctx || !count) return NBV_ERR_ARG;
-  if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "no Gaussians");
+  if (ctx->n < 1 || !ctx->scene_ok) return fail(ctx, NBV_ERR_STATE, "no Gaussians");
   if (view_set == 2) return debug_batched_lists(ctx, view, offsets, ids, cap, count);
   const std::vector<nbv_camera>& vs = view_set ? ctx->train : ctx->cand;
   if (view < 0 || view >= (int)vs.size()) return fail(ctx, NBV_ERR_ARG, "view out of range");
@@ -1122,7 +1108,7 @@ int nbv_score_pruned(nbv_ctx* ctx, nbv_mlp* mlp, int keep, float* pred, int* kep
 int nbv_render_view(nbv_ctx* ctx, const nbv_camera* cam, float* rgb, float* depth, float* alpha, float* obj) {
   if (!ctx || !cam) return NBV_ERR_ARG;
   if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
-  if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "nbv_render_view: no Gaussians");
+  if (ctx->n < 1 || !ctx->scene_ok) return fail(ctx, NBV_ERR_STATE, "nbv_render_view: no Gaussians");
   if (!finite_cam(*cam)) return fail(ctx, NBV_ERR_ARG, "bad camera");
   return render_view(ctx, *cam, nullptr, rgb, depth, alpha, obj);
 }
@@ -1133,7 +1119,7 @@ int nbv_render_backward(nbv_ctx* ctx, const nbv_camera* cam, const float* g_rgb,
   if (!ctx || !cam || !g_means || !g_log_scales || !g_quats || !g_opacity || !g_sh || !g_obj_logits)
     return NBV_ERR_ARG;
   if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
-  if (ctx->n < 1) return fail(ctx, NBV_ERR_STATE, "nbv_render_backward: no Gaussians");
+  if (ctx->n < 1 || !ctx->scene_ok) return fail(ctx, NBV_ERR_STATE, "nbv_render_backward: no Gaussians");
   if (!finite_cam(*cam)) return fail(ctx, NBV_ERR_ARG, "bad camera");
   // projection and binning of the view (the lists the backward pass walks)
   CKR(render_view(ctx, *cam, nullptr, nullptr, nullptr, nullptr, nullptr));
@@ -1172,7 +1158,7 @@ std::map<std::vector<int>, std::tuple<int, int, int>> g_tune_cache;   // (K, deg
 int nbv_autotune(nbv_ctx* ctx, int* tile_w, int* tile_h, int* stage) {
   if (!ctx) return NBV_ERR_ARG;
   if (ctx->cuda_dead) return fail(ctx, NBV_ERR_CUDA, "context unusable after a CUDA error");
-  if (ctx->n < 1 || ctx->train.empty() || ctx->cand.empty())
+  if (ctx->n < 1 || !ctx->scene_ok || ctx->train.empty() || ctx->cand.empty())
     return fail(ctx, NBV_ERR_STATE, "nbv_autotune needs Gaussians, training and candidate views");
   std::vector<int> key = {ctx->c.K, ctx->c.deg};
   for (auto& cm : ctx->cand) { key.push_back(cm.width); key.push_back(cm.height); }

@@ -83,6 +83,9 @@ struct DevProj {
 // ------------------------------------------------------------ kernels (host wrappers)
 // Each wrapper launches on `st` and returns the number of launches issued.
 int launch_scene_prep(const DevScene& s, const Consts& c, int target, cudaStream_t st);
+// Non-finite parameters (bit 0) and zero quaternions (bit 1) of loaded Gaussians, OR-ed into *flag.
+int launch_check_inputs(const float* mu, const float* logs, const float* q, const float* rho, const float* sh,
+                        const float* obj, int64_t n, int nsh, int KC, int* flag, cudaStream_t st);
 int launch_project(const DevScene& s, const Consts& c, const DevCam& cam, const DevProj& pr,
                    cudaStream_t st);
 // Projection of every Gaussian into nv views (device camera array); slot v n + g.

@@ -236,6 +236,40 @@ int launch_project_views(const DevScene& s, const Consts& c, const DevCam* cams,
   return 1;
 }
 
+namespace {
+// Input check of the n loaded Gaussians: bit 0 of *flag for a non-finite
+// parameter, bit 1 for an all-zero quaternion (OR-ed over the grid).
+__global__ void k_check_inputs(const float* __restrict__ mu, const float* __restrict__ logs,
+                               const float* __restrict__ q, const float* __restrict__ rho,
+                               const float* __restrict__ sh, const float* __restrict__ obj, int64_t n, int nsh,
+                               int KC, int* __restrict__ flag) {
+  int bits = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += stride) {
+    bool ok = true;
+    for (int i = 0; i < 3; ++i) ok = ok && isfinite(mu[3 * g + i]) && isfinite(logs[3 * g + i]);
+    const float q0 = q[4 * g], q1 = q[4 * g + 1], q2 = q[4 * g + 2], q3 = q[4 * g + 3];
+    ok = ok && isfinite(q0) && isfinite(q1) && isfinite(q2) && isfinite(q3) && isfinite(rho[g]);
+    if (q0 == 0.0f && q1 == 0.0f && q2 == 0.0f && q3 == 0.0f) bits |= 2;
+    for (int i = 0; i < nsh; ++i) ok = ok && isfinite(sh[g * nsh + i]);
+    for (int i = 0; i < KC; ++i) ok = ok && isfinite(obj[g * KC + i]);
+    if (!ok) bits |= 1;
+  }
+  bits = __reduce_or_sync(0xffffffffu, bits);
+  if ((threadIdx.x & 31) == 0 && bits != 0) atomicOr(flag, bits);
+}
+}  // namespace
+
+int launch_check_inputs(const float* mu, const float* logs, const float* q, const float* rho, const float* sh,
+                        const float* obj, int64_t n, int nsh, int KC, int* flag, cudaStream_t st) {
+  if (n <= 0) return 0;
+  const int bs = 256;
+  int64_t nb = (n + bs - 1) / bs;
+  if (nb > 152 * 16) nb = 152 * 16;
+  k_check_inputs<<<(unsigned)nb, bs, 0, st>>>(mu, logs, q, rho, sh, obj, n, nsh, KC, flag);
+  return 1;
+}
+
 int launch_scene_prep(const DevScene& s, const Consts& c, int target, cudaStream_t st) {
   if (s.n <= 0) return 0;
   const int bs = 128;
