@@ -12,6 +12,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "nbv_internal.cuh"
@@ -24,6 +25,8 @@ size_t radix_hist_elems(int64_t count);
 using namespace nbv;
 
 struct nbv_ctx {
+  // capacity of every buffer alloc() manages, keyed by the address of its pointer
+  std::unordered_map<const void*, size_t> alloc_caps;
   nbv_config cfg;
   Consts c;
   cudaStream_t st = nullptr;
@@ -165,8 +168,11 @@ int grow(nbv_ctx* ctx, T** ptr, size_t* cap, size_t count) {
 
 template <class T>
 int alloc(nbv_ctx* ctx, T** ptr, size_t count) {
-  size_t cap = 0;
-  if (*ptr) { cudaFree(*ptr); *ptr = nullptr; }
+  // keeps a buffer that is large enough (re-setting a multi-view path of the
+  // same size frees and maps nothing: cudaFree synchronises the device, and
+  // mapping gigabytes takes milliseconds)
+  size_t& cap = ctx->alloc_caps[static_cast<const void*>(ptr)];
+  if (!*ptr) cap = 0;
   return grow(ctx, ptr, &cap, count);
 }
 
