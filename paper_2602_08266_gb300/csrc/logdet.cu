@@ -373,8 +373,18 @@ FactLayout fact_layout(const Consts& c) {
   y.off_XG = y.off_GB + 9 * kNG + 1;
   y.off_xs = y.off_XG + r4(c.K * kNG);
   y.off_E = y.off_xs + 12;
-  y.off_T = y.off_E + 68;
-  y.off_col = y.off_T + r4(kNG * 3 * c.nb);
+  // T_c (11 x 3 nb) lives only inside the factorisation, after the Jacobians
+  // and block scratch of the accumulation are done with: it takes their
+  // space when it fits (one more warp per block at SH degree 3)
+  const int tsz = r4(kNG * 3 * c.nb);
+  int end = y.off_E + 68;
+  if (tsz <= y.off_xs - y.off_J) {
+    y.off_T = y.off_J;
+  } else {
+    y.off_T = end;
+    end += tsz;
+  }
+  y.off_col = end;
   y.f_per_warp = y.off_col + r4(mx(y.l2, 2 * kNG));
   return y;
 }
