@@ -342,6 +342,15 @@ __device__ __forceinline__ float m_geo(const GJac& J, int v, int a) {
 // Entry (u, v) of a 6 x 6 block stored packed lower.
 __device__ __forceinline__ float q6(const float* q, int u, int v) { return u >= v ? q[tri(u, v)] : q[tri(v, u)]; }
 
+// The colour sums H0 are stored by blocks, without the SH entries of
+// different channels (always zero): geometric x geometric (packed 11-triangle,
+// 66), SH (k, ch) x geometric b at 66 + (3 k + ch) 11 + b, and SH x SH of one
+// channel at 66 + 33 nb + ch T + tri(k, k2), T = nb (nb + 1) / 2.
+__host__ __device__ __forceinline__ int h0_sg(int ish, int b) { return kNG * (kNG + 1) / 2 + ish * kNG + b; }
+__host__ __device__ __forceinline__ int h0_ss(int nb, int ch, int k, int k2) {
+  return kNG * (kNG + 1) / 2 + kNG * 3 * nb + ch * (nb * (nb + 1) / 2) + tri(k, k2);
+}
+
 // Per-warp shared memory of the factor kernel: doubles (the scaled matrix
 // being factorised and the scaling), then floats.
 struct FactLayout {
@@ -356,7 +365,7 @@ FactLayout fact_layout(const Consts& c) {
   y.l0 = kNG + 3 * c.nb;
   y.l1 = kNG;
   y.l2 = kNG + c.KC;
-  y.nt0 = y.l0 * (y.l0 + 1) / 2;
+  y.nt0 = rgb_L_size(c.nb);       // the structured colour sums (same count as the stored factor)
   y.nt1 = y.l1 * (y.l1 + 1) / 2;
   y.nt2 = y.l2 * (y.l2 + 1) / 2;
   const int T = c.nb * (c.nb + 1) / 2, n3 = 3 * c.nb;
@@ -436,13 +445,13 @@ __device__ __forceinline__ void add_view_blocks(const GJac& J, const float* __re
   for (int e = lane; e < 3 * nb * kNG; e += 32) {          // SH x geometric
     const int ish = e / kNG, b = e - kNG * ish;
     const int k = ish / 3, ch = ish - 3 * k;
-    H0[tri(kNG + ish, b)] += J.live[ch] * J.Y[k] * GB[(6 + ch) * kNG + b];
+    H0[h0_sg(ish, b)] += J.live[ch] * J.Y[k] * GB[(6 + ch) * kNG + b];
   }
   for (int e = lane; e < 3 * (nb * (nb + 1) / 2); e += 32) {   // SH x SH, same channel only
     const int ch = e % 3;
     int k, k2;
     tri_decode(e / 3, k, k2);
-    H0[tri(kNG + 3 * k + ch, kNG + 3 * k2 + ch)] += W2 * J.live[ch] * J.Y[k] * J.Y[k2];
+    H0[h0_ss(nb, ch, k, k2)] += W2 * J.live[ch] * J.Y[k] * J.Y[k2];
   }
   __syncwarp();
   // depth: GB = B_d M (7 x 11), H1 = M^T GB
@@ -666,9 +675,10 @@ __device__ void inv_set(const MatSet& s, TX* X0, TX* X1, TX* X2, TX* X3, float* 
 }
 
 // All three outputs' training factors of one Gaussian, stored in the forms
-// Factors describes. H0, H1, H2: the natural packed sums sum_t A_t of colour
-// (SH (k, ch) at 11 + 3 k + ch), depth and object (floats; H2 and H1 are
-// reused as outputs, H0 as scratch once read). Each H = lambda I + c_g H_sum
+// Factors describes. H0, H1, H2: the sums sum_t A_t of colour (by blocks,
+// see h0_sg / h0_ss; SH (k, ch) is parameter 11 + 3 k + ch), depth and
+// object (packed; floats; H2 and H1 are reused as outputs, H0 as scratch
+// once read). Each H = lambda I + c_g H_sum
 // is Jacobi-scaled, H~ = D^-1/2 H D^-1/2, and Cholesky-factorised in double
 // precision. Colour goes by blocks with the parameters ordered [SH of
 // channel 0, 1, 2 | geometric]: the three SH blocks are independent, so H~ =
@@ -699,7 +709,7 @@ __device__ void factorise_all(const FactLayout& y, float cg, const Consts& c, fl
     float h;
     int fi;
     if (i < l0) {                 // colour: geometric r -> Schur floors, SH (k, ch) -> [ch][k]
-      h = H0[tri(i, i)];
+      h = i < kNG ? H0[tri(i, i)] : H0[h0_ss(nb, (i - kNG) % 3, (i - kNG) / 3, (i - kNG) / 3)];
       fi = i < kNG ? n3 + i : ((i - kNG) % 3) * nb + (i - kNG) / 3;
     } else {                      // depth and object rows keep their index (l0 = n3 + 11)
       const int r = i < l0 + kNG ? i - l0 : i - l0 - kNG;
@@ -716,7 +726,7 @@ __device__ void factorise_all(const FactLayout& y, float cg, const Consts& c, fl
     int k, k2;
     tri_decode(e - ch * T, k, k2);
     const int a = kNG + 3 * k + ch, b = kNG + 3 * k2 + ch;
-    X[e] = (cgd * (double)H0[tri(a, b)] + (k == k2 ? lam : 0.0)) * dsc0[a] * dsc0[b];
+    X[e] = (cgd * (double)H0[h0_ss(nb, ch, k, k2)] + (k == k2 ? lam : 0.0)) * dsc0[a] * dsc0[b];
   }
   for (int e = lane; e < nt2; e += 32) {
     int r, r2;
@@ -738,7 +748,7 @@ __device__ void factorise_all(const FactLayout& y, float cg, const Consts& c, fl
   for (int e = lane; e < kNG * n3; e += 32) {
     const int r = e / n3, q = e - r * n3, ch = q / nb, k2 = q - ch * nb;
     const int b = kNG + 3 * k2 + ch;
-    X[r * n3p + q] = (double)H0[tri(b, r)] * dsc0[b];
+    X[r * n3p + q] = (double)H0[h0_sg(3 * k2 + ch, r)] * dsc0[b];
   }
   __syncwarp();
   // L_gS[r][ch nb + k] = c_g D^-1/2_r sum_{k2 <= k} X[r][ch nb + k2] A_c[k][k2]; each
@@ -1826,7 +1836,7 @@ int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams,
   const FactLayout y = fact_layout(c);
   const size_t pw = (size_t)y.d_per_warp * sizeof(double) + (size_t)y.f_per_warp * sizeof(float);
   int nw = (int)((220 * 1024) / pw);
-  nw = nw < 1 ? 1 : (nw > 8 ? 8 : nw);
+  nw = nw < 1 ? 1 : (nw > 12 ? 12 : nw);
   const size_t sm = pw * nw;
   cudaFuncSetAttribute(k_build_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int64_t nblk = (s.n + nw - 1) / nw;
