@@ -131,7 +131,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         const float pw = splat_power(a0.x, a0.y, a1.x, a1.y, a1.z, pxc, pyc);
         ++n_eval;
         if (pw > 0.0f || pw < a0.z) continue;
-        const float alpha = (pw >= a0.w) ? c.alpha_max : a1.w * expf(pw);
+        const float alpha = (pw >= a0.w) ? c.alpha_max : a1.w * __expf(pw);
         const float tt = T * (1.0f - alpha);
         if (tt < c.t_min) { done = true; break; }
         const float w = alpha * T;
@@ -272,8 +272,8 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         float* Ur = Uw + slot;           // value s at Ur[s * kCS]
         float* Vr = Vw + slot;
         const bool clamped = pw >= a0.w;
-        const float alpha = clamped ? c.alpha_max : a1.w * expf(pw);
-        const float inv_om = 1.0f / (1.0f - alpha);
+        const float alpha = clamped ? c.alpha_max : a1.w * __expf(pw);
+        const float inv_om = __fdividef(1.0f, 1.0f - alpha);
         const float Ti = Tb * inv_om;
         const float w = alpha * Ti;
         const float ae = clamped ? 0.0f : alpha;
