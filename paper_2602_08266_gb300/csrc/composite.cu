@@ -316,7 +316,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         // splat geometry at this pixel
         const float dx = a0.x - pxc, dy = a0.y - pyc;
         const float v[6] = {-(a1.x * dx + a1.y * dy), -(a1.y * dx + a1.z * dy), -0.5f * dx * dx,
-                            -dx * dy, -0.5f * dy * dy, 1.0f / a1.w};
+                            -dx * dy, -0.5f * dy * dy, __fdividef(1.0f, a1.w)};
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
 #pragma unroll
