@@ -229,26 +229,52 @@ __global__ void k_gather_touched(const uint32_t* __restrict__ touched, const uin
 // Slots in depth order (per view): each emits its tiles (global tile id,
 // 32-bit key) and its Gaussian index, so that a stable sort on the tile id
 // alone leaves every tile's entries in (depth bits, Gaussian index) order.
+// A warp takes 32 consecutive slots (one per lane) and then writes their
+// runs one slot after the other, one entry per lane, so that the stores of a
+// run are contiguous across the warp.
 __global__ void k_duplicate_sorted(const int4* __restrict__ rect, const uint32_t* __restrict__ order, int64_t n,
                                    int64_t m, const DevCam* __restrict__ cams,
                                    const uint32_t* __restrict__ tile_base, const uint32_t* __restrict__ offsets,
                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  const uint32_t slot = order[i];
-  const int4 r = rect[slot];
-  if (r.x < 0) return;
-  const int v = (int)(slot / (uint64_t)n);
-  const uint32_t g = (uint32_t)(slot - (uint64_t)v * n);
-  const int GX = cams[v].GX;
-  const uint32_t base = tile_base[v];
-  uint32_t o = offsets[i];
-  for (int ty = r.z; ty < r.w; ++ty)
-    for (int tx = r.x; tx < r.y; ++tx) {
-      keys[o] = base + (uint32_t)(ty * GX + tx);
-      vals[o] = g;
-      ++o;
+  const int lane = threadIdx.x & 31;
+  int4 r = make_int4(-1, -1, -1, -1);
+  uint32_t g = 0, base = 0, o = 0;
+  int GX = 0;
+  if (i < m) {
+    const uint32_t slot = order[i];
+    r = rect[slot];
+    if (r.x >= 0) {
+      const int v = (int)(slot / (uint64_t)n);
+      g = (uint32_t)(slot - (uint64_t)v * n);
+      GX = cams[v].GX;
+      base = tile_base[v];
+      o = offsets[i];
     }
+  }
+  for (int s = 0; s < 32; ++s) {
+    const int rx = __shfl_sync(0xffffffffu, r.x, s), ry = __shfl_sync(0xffffffffu, r.y, s);
+    const int rz = __shfl_sync(0xffffffffu, r.z, s), rw = __shfl_sync(0xffffffffu, r.w, s);
+    const uint32_t gs = __shfl_sync(0xffffffffu, g, s), bs = __shfl_sync(0xffffffffu, base, s);
+    const uint32_t os = __shfl_sync(0xffffffffu, o, s);
+    const int gx = __shfl_sync(0xffffffffu, GX, s);
+    if (rx < 0) continue;                       // the same for the whole warp
+    const int w = ry - rx, cnt = w * (rw - rz);
+    if (cnt <= 0) continue;
+    // entry t = (ty - rz) w + (tx - rx); lane starts at t = lane, steps by 32
+    int qy = lane / w, qx = lane - qy * w;
+    const int dq = 32 / w, dr = 32 - dq * w;
+    for (int t = lane; t < cnt; t += 32) {
+      keys[os + t] = bs + (uint32_t)((rz + qy) * gx + rx + qx);
+      vals[os + t] = gs;
+      qy += dq;
+      qx += dr;
+      if (qx >= w) {
+        qx -= w;
+        ++qy;
+      }
+    }
+  }
 }
 
 __global__ void k_ranges32(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
