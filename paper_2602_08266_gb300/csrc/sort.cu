@@ -88,18 +88,40 @@ int scan_rec(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaSt
 __global__ void k_duplicate(const int4* __restrict__ rect, const uint32_t* __restrict__ zbits,
                             int64_t n, int GX, const uint32_t* __restrict__ offsets,
                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  // lane per Gaussian, then each Gaussian's run written by the whole warp
+  // (as in k_duplicate_sorted)
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= n) return;
-  const int4 r = rect[g];
-  if (r.x < 0) return;
-  uint32_t o = offsets[g];
-  const uint64_t zb = zbits[g];
-  for (int ty = r.z; ty < r.w; ++ty)
-    for (int tx = r.x; tx < r.y; ++tx) {
-      keys[o] = ((uint64_t)(ty * GX + tx) << 32) | zb;
-      vals[o] = (uint32_t)g;
-      ++o;
+  const int lane = threadIdx.x & 31;
+  int4 r = make_int4(-1, -1, -1, -1);
+  uint32_t o = 0, zb = 0;
+  if (g < n) {
+    r = rect[g];
+    if (r.x >= 0) {
+      o = offsets[g];
+      zb = zbits[g];
     }
+  }
+  const int64_t g0 = g - lane;
+  for (int s = 0; s < 32; ++s) {
+    const int rx = __shfl_sync(0xffffffffu, r.x, s), ry = __shfl_sync(0xffffffffu, r.y, s);
+    const int rz = __shfl_sync(0xffffffffu, r.z, s), rw = __shfl_sync(0xffffffffu, r.w, s);
+    const uint32_t os = __shfl_sync(0xffffffffu, o, s), zs = __shfl_sync(0xffffffffu, zb, s);
+    if (rx < 0) continue;                       // the same for the whole warp
+    const int w = ry - rx, cnt = w * (rw - rz);
+    if (cnt <= 0) continue;
+    int qy = lane / w, qx = lane - qy * w;
+    const int dq = 32 / w, dr = 32 - dq * w;
+    for (int t = lane; t < cnt; t += 32) {
+      keys[os + t] = ((uint64_t)((rz + qy) * GX + rx + qx) << 32) | (uint64_t)zs;
+      vals[os + t] = (uint32_t)(g0 + s);
+      qy += dq;
+      qx += dr;
+      if (qx >= w) {
+        qx -= w;
+        ++qy;
+      }
+    }
+  }
 }
 
 // Work-queue keys: longest tile list first, ties by tile id.
