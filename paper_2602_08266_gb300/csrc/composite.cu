@@ -5,12 +5,12 @@
 // Pass 1 (forward): each pixel walks its tile's depth-sorted list,
 //   alpha = min(alpha_max, sigma exp(p)),  p = -(A dx^2 + C dy^2)/2 - B dx dy,
 // skipping a splat when p > 0 or alpha < alpha_min and stopping before a
-// splat that would take the transmittance below t_min; it accumulates
-// colour, depth D = sum w z, opacity and the K+1 object channels
-// O' = sum w softmax(o), w = alpha T, and writes O = O' + e0 (1 - 1^T O').
-// Both alpha decisions are comparisons of p against per-Gaussian exponent
-// thresholds, with p computed by correctly rounded operations in a fixed
-// order.
+// splat that would take the transmittance below t_min; when an image is
+// asked for it accumulates colour, depth D = sum w z, opacity and the K+1
+// object channels O' = sum w softmax(o), w = alpha T, and writes
+// O = O' + e0 (1 - 1^T O'). Both alpha decisions are comparisons of p
+// against per-Gaussian exponent thresholds, with p computed by correctly
+// rounded operations in a fixed order.
 //
 // Pass 2 (information): the same list is walked back to front over the
 // splats each pixel blended, recovering T_i = T_{i+1} / (1 - alpha_i) and
@@ -19,9 +19,10 @@
 // for every output X (and d O_0 / d alpha_i gets the residual term
 // -T_final / (1 - alpha_i)). Each pixel forms its share of the structured
 // 2D Gauss-Newton block of every splat (layout in nbv_internal.cuh); the
-// block is reduced over the warp with a shuffle transpose-reduce, over the
-// tile in shared memory, and added to the per-Gaussian block in global
-// memory with one vector atomic per 4 floats per (tile, Gaussian).
+// shares are summed over the warp's pixels by TF32 tensor-core products,
+// over the tile's warps in shared memory, and added to the per-Gaussian
+// block in global memory with one vector atomic per 4 floats per
+// (tile, Gaussian).
 #include "nbv_internal.cuh"
 
 namespace nbv {
