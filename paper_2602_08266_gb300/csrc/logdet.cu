@@ -8,9 +8,10 @@
 //
 // Training state (once per NBV step):
 //   H^f_g = lambda I + c_g sum_t M_t^T B_t M_t          (Eqs. 6, 9 with C_g = c_g I)
-// Jacobi-scaled, H~ = D^-1/2 H D^-1/2, Cholesky-factorised, H~ = L L^T, and
-// the factor inverted, all in double precision; L^-1 is kept in single
-// precision.
+// Jacobi-scaled, H~ = D^-1/2 H D^-1/2, and Cholesky-factorised in double
+// precision, H~ = L L^T; L^-1 (the colour SH blocks inverted in double, the
+// other triangles in single precision from the double factor) is kept in
+// single precision.
 //
 // Per view, by Sylvester's determinant identity,
 //   log det(H + c A) - log det H = log det(I_u + c W B),
