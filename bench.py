@@ -140,9 +140,9 @@ def composite_flops(stats, K):
 
 # DRAM bytes (read + write) of the compositing kernel per composited view of
 # the scene workload, from one ncu capture of its 8-view launch
-# (dram__bytes_read.sum 190.7 MB + dram__bytes_write.sum 90.4 MB); a launch's
+# (dram__bytes_read.sum 190.4 MB + dram__bytes_write.sum 90.5 MB); a launch's
 # traffic is taken as this times the views it covers
-SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW = (190.7e6 + 90.4e6) / 8
+SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW = (190.4e6 + 90.5e6) / 8
 
 
 def fp32_peak_tflops(clock_mhz):

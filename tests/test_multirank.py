@@ -87,4 +87,4 @@ def test_composite_flop_count_and_traffic_constant():
     st = {"pairs_evaluated": 1000, "pairs_blended": 10}
     assert bench.composite_flops(st, 16) == 11 * 1000 + 5 * 10 + (266 + 21 * 16) * 10
     assert bench.composite_flops({"pairs_evaluated": 0, "pairs_blended": 0}, 16) == 0
-    assert bench.SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW == pytest.approx((190.7e6 + 90.4e6) / 8)
+    assert bench.SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW == pytest.approx((190.4e6 + 90.5e6) / 8)
