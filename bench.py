@@ -139,10 +139,12 @@ def composite_flops(stats, K):
 
 
 # DRAM bytes (read + write) of the compositing kernel per composited view of
-# the scene workload, from one ncu capture of its 8-view launch
-# (dram__bytes_read.sum 190.4 MB + dram__bytes_write.sum 90.5 MB); a launch's
-# traffic is taken as this times the views it covers
-SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW = (190.4e6 + 90.5e6) / 8
+# the scene workload, from one ncu capture of its 8-view launch; a launch's
+# traffic is taken as this times the views it covers. None while no capture
+# of the current tile lists exists: the last one (190.4 MB read + 90.5 MB
+# written for 8 views) was taken before the ellipse-tile culling shortened
+# the lists, so the roofline reports traffic null.
+SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW = None
 
 
 def fp32_peak_tflops(clock_mhz):
@@ -285,7 +287,7 @@ def run_ours(args):
 
     flops_per_launch, avg_launch_s, achieved = comp_roof(prof)
     traffic = None
-    if args.workload == "scene":
+    if args.workload == "scene" and SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW is not None:
         views_per_launch = (wl.cand.n + wl.train.n) * args.steps / max(prof["stats"]["composite_launches"], 1)
         traffic = round(SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW * views_per_launch)
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),

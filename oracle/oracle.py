@@ -55,6 +55,7 @@ def _load():
     lib.orc_view_w2.argtypes = [P, P, P, P]
     lib.orc_tile_lists.restype = i64
     lib.orc_tile_lists.argtypes = [P, P, P, P, P, i64]
+    lib.orc_cull_check.argtypes = [P, P, P, P]
     lib.orc_render.argtypes = [P, P, P, P, P, P, P, P, P]
     lib.orc_view_blocks.argtypes = [P, P, P, P, P, P, P]
     lib.orc_score.restype = i32
@@ -206,6 +207,14 @@ class OracleScene:
         ids = np.zeros(max(tot, 1), np.int32)
         self.lib.orc_tile_lists(self._h, _ptr(c), _ptr(wh), _ptr(off), _ptr(ids), tot)
         return off, ids[:tot]
+
+    def cull_check(self, cams, i):
+        """Tile culling of view i checked pixel by pixel: rectangle entries,
+        entries kept, and dropped pairs with a passing pixel (must be 0)."""
+        c, wh = cam_arrays(cams, i)
+        cnt = np.zeros(3, np.int64)
+        self.lib.orc_cull_check(self._h, _ptr(c), _ptr(wh), _ptr(cnt))
+        return dict(total=int(cnt[0]), kept=int(cnt[1]), bad=int(cnt[2]))
 
     def render(self, cams, i):
         c, wh = cam_arrays(cams, i)

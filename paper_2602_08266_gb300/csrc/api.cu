@@ -279,7 +279,7 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
   CKR(grow(ctx, &ctx->sb.ranges, &ctx->ranges_cap, (size_t)ntiles));
   {
     Phase ph(ctx, NBV_PHASE_SORT);
-    CKR(check_launch(ctx, launch_duplicate(ctx->pr, ctx->n, dc.GX, ctx->sb.offsets, ctx->sb.keys[0],
+    CKR(check_launch(ctx, launch_duplicate(ctx->pr, ctx->n, dc.GX, dc.TW, dc.TH, ctx->sb.offsets, ctx->sb.keys[0],
                                            ctx->sb.vals[0], st)));
     int tile_bits = 1;
     while ((1 << tile_bits) < ntiles) ++tile_bits;
@@ -455,7 +455,7 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
     CKR(check_launch(ctx, launch_gather_touched(B.pr.touched, order, (int64_t)slots, B.tcount, st)));
     CKR(check_launch(ctx, launch_scan_u32(B.tcount, B.doffsets, (int64_t)slots, B.scan_tmp, st)));
     uint32_t* k32[2] = {reinterpret_cast<uint32_t*>(B.sb.keys[0]), reinterpret_cast<uint32_t*>(B.sb.keys[1])};
-    CKR(check_launch(ctx, launch_duplicate_sorted(B.pr.rect, order, n, nv, B.cams, B.tile_base, B.doffsets, k32[0],
+    CKR(check_launch(ctx, launch_duplicate_sorted(B.pr.rect, B.pr.r0, B.pr.r1, order, n, nv, B.cams, B.tile_base, B.doffsets, k32[0],
                                                   B.sb.vals[0], st)));
     int which = 0;
     CKR(check_launch(ctx, launch_radix_sort32(k32, B.sb.vals, B.sb.hist, B.total, bits_for(B.ntiles), &which, st)));

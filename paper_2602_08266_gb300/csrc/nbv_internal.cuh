@@ -76,7 +76,7 @@ struct DevProj {
   float4* r2;                // {r, g, b, z}
   int4* rect;                // {x0, x1, y0, y1}
   uint32_t* zbits;
-  uint32_t* touched;         // tiles covered (0 = culled)
+  uint32_t* touched;         // tiles of the rectangle that pass tile_hit (0 = culled)
   float* radius;
 };
 
@@ -104,7 +104,7 @@ struct SortBuffers {
 };
 // Exclusive scan of touched into offsets; total written to *d_total (device).
 int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st);
-int launch_duplicate(const DevProj& pr, int64_t n, int GX, const uint32_t* offsets, uint64_t* keys,
+int launch_duplicate(const DevProj& pr, int64_t n, int GX, int TW, int TH, const uint32_t* offsets, uint64_t* keys,
                      uint32_t* vals, cudaStream_t st);
 // Stable LSD radix sort of (keys, vals) on the low `bits` key bits; the
 // result is in buffer index *which (0 or 1).
@@ -120,9 +120,9 @@ int launch_radix_sort32(uint32_t* keys[2], uint32_t* vals[2], uint32_t* hist, in
 int launch_depth_keys(const uint32_t* zbits, int64_t n, int nv, uint64_t* keys, uint32_t* vals, cudaStream_t st);
 int launch_gather_touched(const uint32_t* touched, const uint32_t* order, int64_t m, uint32_t* out, cudaStream_t st);
 // Entries of the slots in `order`: 32-bit global tile keys and Gaussian indices.
-int launch_duplicate_sorted(const int4* rect, const uint32_t* order, int64_t n, int nv, const DevCam* cams,
-                            const uint32_t* tile_base, const uint32_t* offsets, uint32_t* keys, uint32_t* vals,
-                            cudaStream_t st);
+int launch_duplicate_sorted(const int4* rect, const float4* r0, const float4* r1, const uint32_t* order, int64_t n,
+                            int nv, const DevCam* cams, const uint32_t* tile_base, const uint32_t* offsets,
+                            uint32_t* keys, uint32_t* vals, cudaStream_t st);
 int launch_ranges32(const uint32_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st);
 int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaStream_t st);
 int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st);
@@ -132,7 +132,48 @@ int launch_queue_keys(const uint2* ranges, int ntiles, uint64_t* keys, uint32_t*
 size_t scan_scratch_elems(int64_t n);
 size_t radix_hist_elems(int64_t count);
 
-// Splat exponent at a pixel centre, p = -(A dx^2 + C dy^2)/2 - B dx dy with
+// Whether a splat can pass its alpha cut-off at some pixel centre of tile
+// (tx, ty): the minimum over the rectangle of the tile's pixel centres of
+// q(d) = A dx^2 + 2 B dx dy + C dy^2 (d = pixel centre - mean2D; zero when
+// the mean lies inside, else on an edge at the clamped stationary point)
+// against -2 thr (thr = log(alpha_min / sigma), the exponent of the skip
+// test), widened by 2^-8 relative, 2^-8 absolute and 2^-18 of
+// M = A max(dx^2) + C max(dy^2) over the tile. The rounding of q here and of
+// the per-pixel exponent is at most about 24 units of 2^-24 times M (the
+// cross term is at most M/2 for a positive-definite conic), so the widening
+// never drops a tile with a pixel that passes the skip test, however
+// elongated the splat. Correctly rounded single-precision operations in a
+// fixed order; the oracle repeats them, so tile lists agree bit for bit.
+__device__ __forceinline__ bool tile_hit(float A, float B, float C, float mx, float my, float thr, int tx, int ty,
+                                         int TW, int TH) {
+  const float xl = __fsub_rn(__fadd_rn((float)(tx * TW), 0.5f), mx);
+  const float xh = __fsub_rn(__fsub_rn((float)((tx + 1) * TW), 0.5f), mx);
+  const float yl = __fsub_rn(__fadd_rn((float)(ty * TH), 0.5f), my);
+  const float yh = __fsub_rn(__fsub_rn((float)((ty + 1) * TH), 0.5f), my);
+  if (xl <= 0.0f && xh >= 0.0f && yl <= 0.0f && yh >= 0.0f) return true;
+  const float mxx = fmaxf(__fmul_rn(xl, xl), __fmul_rn(xh, xh)), myy = fmaxf(__fmul_rn(yl, yl), __fmul_rn(yh, yh));
+  const float M = __fadd_rn(__fmul_rn(A, mxx), __fmul_rn(C, myy));
+  const float lim = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(-2.0f, thr), 1.00390625f), 0.00390625f),
+                              __fmul_rn(M, 3.814697265625e-06f));
+  const float B2 = __fmul_rn(2.0f, B);
+  float best = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    float dx, dy;
+    if (e < 2) {
+      dx = e == 0 ? xl : xh;
+      dy = fminf(fmaxf(-__fdiv_rn(__fmul_rn(B, dx), C), yl), yh);
+    } else {
+      dy = e == 2 ? yl : yh;
+      dx = fminf(fmaxf(-__fdiv_rn(__fmul_rn(B, dy), A), xl), xh);
+    }
+    const float q = __fadd_rn(__fadd_rn(__fmul_rn(A, __fmul_rn(dx, dx)), __fmul_rn(B2, __fmul_rn(dx, dy))),
+                              __fmul_rn(C, __fmul_rn(dy, dy)));
+    best = fminf(best, q);
+  }
+  return best <= lim;
+}
+
 // (dx, dy) = mean2D - pixel centre: the quantity the alpha decisions compare,
 // computed by correctly rounded operations in one fixed order (shared by the
 // forward pass and the backward pass's recomputation).

@@ -210,7 +210,10 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   pr.rect[o] = make_int4(x0, x1, y0, y1);
   pr.zbits[o] = __float_as_uint(tz);
   pr.radius[o] = r;
-  pr.touched[o] = (uint32_t)((x1 - x0) * (y1 - y0));
+  uint32_t hits = 0;
+  for (int tyi = y0; tyi < y1; ++tyi)
+    for (int txi = x0; txi < x1; ++txi) hits += tile_hit(A, B, C, mx, my, ss.w, txi, tyi, cam.TW, cam.TH) ? 1u : 0u;
+  pr.touched[o] = hits;
 }
 
 __global__ void k_project(DevScene s, Consts c, DevCam cam, DevProj pr) {

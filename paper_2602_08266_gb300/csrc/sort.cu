@@ -85,20 +85,24 @@ int scan_rec(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaSt
   return launches + 1;
 }
 
-__global__ void k_duplicate(const int4* __restrict__ rect, const uint32_t* __restrict__ zbits,
-                            int64_t n, int GX, const uint32_t* __restrict__ offsets,
+// Every Gaussian's entries for the tiles of its rectangle that pass
+// tile_hit, in row order: a lane per Gaussian, then each Gaussian's
+// rectangle walked by the whole warp (32 tiles at a time, the passing ones
+// compacted by a ballot), so that the stores of a run are contiguous.
+__global__ void k_duplicate(DevProj pr, int64_t n, int GX, int TW, int TH, const uint32_t* __restrict__ offsets,
                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  // lane per Gaussian, then each Gaussian's run written by the whole warp
-  // (as in k_duplicate_sorted)
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   int4 r = make_int4(-1, -1, -1, -1);
   uint32_t o = 0, zb = 0;
+  float4 a0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), a1 = a0;
   if (g < n) {
-    r = rect[g];
+    r = pr.rect[g];
     if (r.x >= 0) {
       o = offsets[g];
-      zb = zbits[g];
+      zb = pr.zbits[g];
+      a0 = pr.r0[g];
+      a1 = pr.r1[g];
     }
   }
   const int64_t g0 = g - lane;
@@ -106,14 +110,25 @@ __global__ void k_duplicate(const int4* __restrict__ rect, const uint32_t* __res
     const int rx = __shfl_sync(0xffffffffu, r.x, s), ry = __shfl_sync(0xffffffffu, r.y, s);
     const int rz = __shfl_sync(0xffffffffu, r.z, s), rw = __shfl_sync(0xffffffffu, r.w, s);
     const uint32_t os = __shfl_sync(0xffffffffu, o, s), zs = __shfl_sync(0xffffffffu, zb, s);
+    const float mx = __shfl_sync(0xffffffffu, a0.x, s), my = __shfl_sync(0xffffffffu, a0.y, s);
+    const float thr = __shfl_sync(0xffffffffu, a0.z, s);
+    const float A = __shfl_sync(0xffffffffu, a1.x, s), B = __shfl_sync(0xffffffffu, a1.y, s);
+    const float C = __shfl_sync(0xffffffffu, a1.z, s);
     if (rx < 0) continue;                       // the same for the whole warp
     const int w = ry - rx, cnt = w * (rw - rz);
-    if (cnt <= 0) continue;
     int qy = lane / w, qx = lane - qy * w;
     const int dq = 32 / w, dr = 32 - dq * w;
-    for (int t = lane; t < cnt; t += 32) {
-      keys[os + t] = ((uint64_t)((rz + qy) * GX + rx + qx) << 32) | (uint64_t)zs;
-      vals[os + t] = (uint32_t)(g0 + s);
+    uint32_t wo = os;
+    for (int t0 = 0; t0 < cnt; t0 += 32) {
+      const int tx = rx + qx, ty = rz + qy;
+      const bool hit = t0 + lane < cnt && tile_hit(A, B, C, mx, my, thr, tx, ty, TW, TH);
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const uint32_t at = wo + (uint32_t)__popc(m & ((1u << lane) - 1u));
+        keys[at] = ((uint64_t)(ty * GX + tx) << 32) | (uint64_t)zs;
+        vals[at] = (uint32_t)(g0 + s);
+      }
+      wo += (uint32_t)__popc(m);
       qy += dq;
       qx += dr;
       if (qx >= w) {
@@ -248,13 +263,14 @@ __global__ void k_gather_touched(const uint32_t* __restrict__ touched, const uin
   if (i < m) out[i] = touched[order[i]];
 }
 
-// Slots in depth order (per view): each emits its tiles (global tile id,
-// 32-bit key) and its Gaussian index, so that a stable sort on the tile id
-// alone leaves every tile's entries in (depth bits, Gaussian index) order.
-// A warp takes 32 consecutive slots (one per lane) and then writes their
-// runs one slot after the other, one entry per lane, so that the stores of a
-// run are contiguous across the warp.
-__global__ void k_duplicate_sorted(const int4* __restrict__ rect, const uint32_t* __restrict__ order, int64_t n,
+// Slots in depth order (per view): each emits its tiles that pass tile_hit
+// (global tile id, 32-bit key) and its Gaussian index, so that a stable sort
+// on the tile id alone leaves every tile's entries in (depth bits, Gaussian
+// index) order. A warp takes 32 consecutive slots (one per lane) and then
+// walks their rectangles one slot after the other, 32 tiles at a time, the
+// passing ones compacted by a ballot, so that the stores are contiguous.
+__global__ void k_duplicate_sorted(const int4* __restrict__ rect, const float4* __restrict__ r0,
+                                   const float4* __restrict__ r1, const uint32_t* __restrict__ order, int64_t n,
                                    int64_t m, const DevCam* __restrict__ cams,
                                    const uint32_t* __restrict__ tile_base, const uint32_t* __restrict__ offsets,
                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
@@ -262,7 +278,8 @@ __global__ void k_duplicate_sorted(const int4* __restrict__ rect, const uint32_t
   const int lane = threadIdx.x & 31;
   int4 r = make_int4(-1, -1, -1, -1);
   uint32_t g = 0, base = 0, o = 0;
-  int GX = 0;
+  int GX = 0, TW = 1, TH = 1;
+  float4 a0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), a1 = a0;
   if (i < m) {
     const uint32_t slot = order[i];
     r = rect[slot];
@@ -270,8 +287,12 @@ __global__ void k_duplicate_sorted(const int4* __restrict__ rect, const uint32_t
       const int v = (int)(slot / (uint64_t)n);
       g = (uint32_t)(slot - (uint64_t)v * n);
       GX = cams[v].GX;
+      TW = cams[v].TW;
+      TH = cams[v].TH;
       base = tile_base[v];
       o = offsets[i];
+      a0 = r0[slot];
+      a1 = r1[slot];
     }
   }
   for (int s = 0; s < 32; ++s) {
@@ -280,15 +301,27 @@ __global__ void k_duplicate_sorted(const int4* __restrict__ rect, const uint32_t
     const uint32_t gs = __shfl_sync(0xffffffffu, g, s), bs = __shfl_sync(0xffffffffu, base, s);
     const uint32_t os = __shfl_sync(0xffffffffu, o, s);
     const int gx = __shfl_sync(0xffffffffu, GX, s);
+    const int tw = __shfl_sync(0xffffffffu, TW, s), th = __shfl_sync(0xffffffffu, TH, s);
+    const float mx = __shfl_sync(0xffffffffu, a0.x, s), my = __shfl_sync(0xffffffffu, a0.y, s);
+    const float thr = __shfl_sync(0xffffffffu, a0.z, s);
+    const float A = __shfl_sync(0xffffffffu, a1.x, s), B = __shfl_sync(0xffffffffu, a1.y, s);
+    const float C = __shfl_sync(0xffffffffu, a1.z, s);
     if (rx < 0) continue;                       // the same for the whole warp
     const int w = ry - rx, cnt = w * (rw - rz);
-    if (cnt <= 0) continue;
     // entry t = (ty - rz) w + (tx - rx); lane starts at t = lane, steps by 32
     int qy = lane / w, qx = lane - qy * w;
     const int dq = 32 / w, dr = 32 - dq * w;
-    for (int t = lane; t < cnt; t += 32) {
-      keys[os + t] = bs + (uint32_t)((rz + qy) * gx + rx + qx);
-      vals[os + t] = gs;
+    uint32_t wo = os;
+    for (int t0 = 0; t0 < cnt; t0 += 32) {
+      const int tx = rx + qx, ty = rz + qy;
+      const bool hit = t0 + lane < cnt && tile_hit(A, B, C, mx, my, thr, tx, ty, tw, th);
+      const unsigned mk = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const uint32_t at = wo + (uint32_t)__popc(mk & ((1u << lane) - 1u));
+        keys[at] = bs + (uint32_t)(ty * gx + tx);
+        vals[at] = gs;
+      }
+      wo += (uint32_t)__popc(mk);
       qy += dq;
       qx += dr;
       if (qx >= w) {
@@ -344,10 +377,10 @@ int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
   return l + 1;
 }
 
-int launch_duplicate(const DevProj& pr, int64_t n, int GX, const uint32_t* offsets, uint64_t* keys,
+int launch_duplicate(const DevProj& pr, int64_t n, int GX, int TW, int TH, const uint32_t* offsets, uint64_t* keys,
                      uint32_t* vals, cudaStream_t st) {
   if (n <= 0) return 0;
-  k_duplicate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pr.rect, pr.zbits, n, GX, offsets, keys, vals);
+  k_duplicate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pr, n, GX, TW, TH, offsets, keys, vals);
   return 1;
 }
 
@@ -374,13 +407,13 @@ int launch_gather_touched(const uint32_t* touched, const uint32_t* order, int64_
   return 1;
 }
 
-int launch_duplicate_sorted(const int4* rect, const uint32_t* order, int64_t n, int nv, const DevCam* cams,
-                            const uint32_t* tile_base, const uint32_t* offsets, uint32_t* keys, uint32_t* vals,
-                            cudaStream_t st) {
+int launch_duplicate_sorted(const int4* rect, const float4* r0, const float4* r1, const uint32_t* order, int64_t n,
+                            int nv, const DevCam* cams, const uint32_t* tile_base, const uint32_t* offsets,
+                            uint32_t* keys, uint32_t* vals, cudaStream_t st) {
   const int64_t m = n * nv;
   if (m <= 0) return 0;
-  k_duplicate_sorted<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, order, n, m, cams, tile_base, offsets, keys,
-                                                                  vals);
+  k_duplicate_sorted<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, order, n, m, cams, tile_base, offsets,
+                                                                  keys, vals);
   return 1;
 }
 

@@ -102,8 +102,14 @@ def test_autograd_function_and_refinement(P):
     go = torch.zeros_like(obj)
     go[..., 1] = 3.0
     g = s.render_backward(cams, 0, gr, gd, None, go)
+    # Both calls add the same per-tile terms with float atomics, in an order
+    # that differs from run to run: where the terms cancel, the difference
+    # scales with their magnitudes rather than with the sum, so the absolute
+    # tolerance follows the tensor's largest entry.
     for p, k in zip(params, ("means", "log_scales", "quats", "opacity", "sh", "obj_logits")):
-        torch.testing.assert_close(p.grad.reshape(-1), g[k].reshape(-1), rtol=1e-5, atol=1e-6)
+        ref = g[k].reshape(-1)
+        torch.testing.assert_close(p.grad.reshape(-1), ref, rtol=1e-5,
+                                   atol=1e-6 + 1e-5 * float(ref.abs().max()))
         p.grad = None
     opt = torch.optim.Adam(params, lr=2e-3)
     with torch.no_grad():

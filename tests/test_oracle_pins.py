@@ -282,18 +282,68 @@ def _brute_lists(p32, W, H, tw=16, th=16):
     return lists
 
 
+def _power32(p32, g, px, py):
+    f32 = np.float32
+    dx = f32(p32["mean2d"][g, 0] - f32(f32(px) + f32(0.5)))
+    dy = f32(p32["mean2d"][g, 1] - f32(f32(py) + f32(0.5)))
+    A, B, Cc = p32["conic"][g]
+    return f32(f32(f32(-0.5) * f32(f32(A * f32(dx * dx)) + f32(Cc * f32(dy * dy)))) - f32(B * f32(dx * dy)))
+
+
+def _skip32(sc):
+    sig32 = (1.0 / (1.0 + np.exp(-sc.opacity.astype(np.float64)))).astype(np.float32)
+    return np.log((1.0 / 255.0) / sig32.astype(np.float64)).astype(np.float32)
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_tile_lists_brute_force(seed):
+    """Every tile's list is the (depth bits, index)-ordered list of the
+    Gaussians whose rectangle covers it, less some that pass the skip test at
+    none of the tile's pixels, and keeps every one that passes at some pixel."""
     sc = random_small_scene(seed, n=30, spread=0.12)
     cam = axis_camera(40, 36, 80.0, 0.5)           # 3x3 tiles, ragged right and bottom
     o = O.OracleScene(sc)
     p32 = o.project32(cam, 0)
     off, ids = o.tile_lists(cam, 0)
     lists = _brute_lists(p32, 40, 36)
+    skip = _skip32(sc)
     GX = 3
-    for (px, py), want in lists.items():
+    need = {}
+    for (px, py), cover in lists.items():
         t = (py // 16) * GX + px // 16
-        assert list(ids[off[t]:off[t + 1]]) == want
+        need.setdefault(t, (cover, set()))
+        for g in cover:
+            pw = _power32(p32, g, px, py)
+            if not (pw > 0 or pw < skip[g]):
+                need[t][1].add(g)
+    dropped = 0
+    for t, (cover, passing) in need.items():
+        got = list(ids[off[t]:off[t + 1]])
+        it = iter(cover)
+        assert all(g in it for g in got), "not an ordered sub-list of the covering Gaussians"
+        assert passing <= set(got), "a Gaussian passing the skip test at a pixel was dropped"
+        dropped += len(cover) - len(got)
+    assert dropped > 0                              # the culling is exercised
+
+
+@pytest.mark.parametrize("aniso", [0.25, 2.5])
+def test_tile_culling_never_drops_a_blending_pixel(aniso):
+    """Dropped (Gaussian, tile) pairs checked pixel by pixel, with elongated
+    splats (log-scale spread 2.5: axis ratios beyond 1000) where cancellation
+    in the power is largest."""
+    rng = np.random.default_rng(7)
+    n = 400
+    means = np.stack([rng.uniform(-0.3, 0.3, n), rng.uniform(-0.3, 0.3, n), rng.uniform(-0.1, 0.3, n)], 1)
+    log_scales = rng.normal(np.log(0.01), aniso, (n, 3))
+    q = rng.standard_normal((n, 4)); q /= np.linalg.norm(q, axis=1, keepdims=True)
+    opacity = rng.normal(0.0, 1.5, n)
+    sh = np.zeros((n, 1, 3)); sh[:, 0, :] = 0.8
+    obj = rng.normal(0, 1.0, (n, 2))
+    sc = make_scene(means, log_scales, q, opacity, sh, obj, 1, 0)
+    cam = axis_camera(200, 152, 180.0, 1.0)
+    r = O.OracleScene(sc).cull_check(cam, 0)
+    assert r["bad"] == 0
+    assert 0 < r["kept"] < r["total"]
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])

@@ -26,22 +26,21 @@ def P():
     return P
 
 
-def _keys_from_projection(rect, zbits, W, H):
-    """Duplicate each projected Gaussian over the tiles of its rectangle, in
-    Gaussian-index order, keyed (tile << 32 | depth bits)."""
+def _keys_from_lists(off, ids, zbits, W, H):
+    """The (tile << 32 | depth bits, Gaussian) pairs of the context's tile
+    lists, laid out as duplication emits them: Gaussian-index order, each
+    Gaussian's tiles in row order."""
     GX = (W + 15) // 16
-    keys, vals = [], []
-    for g in np.nonzero(rect[:, 0] >= 0)[0]:
-        x0, x1, y0, y1 = rect[g]
-        for ty in range(y0, y1):
-            for tx in range(x0, x1):
-                keys.append((np.uint64(ty * GX + tx) << np.uint64(32)) | np.uint64(zbits[g]))
-                vals.append(g)
     ntiles = GX * ((H + 15) // 16)
+    tile = np.repeat(np.arange(ntiles, dtype=np.int64), np.diff(off))
+    g = ids.astype(np.int64)
+    perm = np.lexsort((tile, g))
+    tile, g = tile[perm], g[perm]
+    keys = (tile.astype(np.uint64) << np.uint64(32)) | zbits[g].astype(np.uint64)
     bits = 1
     while (1 << bits) < ntiles:
         bits += 1
-    return np.array(keys, np.uint64), np.array(vals, np.int32), 32 + bits
+    return keys, g.astype(np.int32), 32 + bits
 
 
 def _case(P, wl, v):
@@ -50,12 +49,12 @@ def _case(P, wl, v):
     sc.set_train_views(wl.train)
     sc.set_candidates(wl.cand)
     pr = sc.debug_project(0, v)
-    rect = pr["rect"].cpu().numpy()
     zb = pr["zbits"].cpu().numpy().view(np.uint32)
-    _, ids = sc.debug_tile_lists(0, v)
+    off, ids = sc.debug_tile_lists(0, v)
     W, H = int(wl.cand.width[v]), int(wl.cand.height[v])
-    k, val, bits = _keys_from_projection(rect, zb, W, H)
-    return sc, k, val, bits, ids.cpu().numpy()
+    ids = ids.cpu().numpy()
+    k, val, bits = _keys_from_lists(off.cpu().numpy(), ids, zb, W, H)
+    return sc, k, val, bits, ids
 
 
 @pytest.mark.parametrize("name,scale,v", [("tiny", None, 2), ("scene", 0.02, 5)])
