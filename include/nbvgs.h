@@ -187,7 +187,10 @@ int nbv_debug_project(nbv_ctx* ctx, int view_set, int view, int32_t* rect, float
 /* Sorted tile lists of one view: *count receives the number of (tile,
  * Gaussian) entries; if count <= cap, offsets [ntiles+1] and ids [count]
  * (device arrays) receive the per-tile ranges and Gaussian ids in blend
- * order. view_set 0 / 1 bins the candidate / training view on its own;
+ * order. A tile lists the Gaussians whose 3-sigma rectangle covers it and
+ * that can pass the alpha cut-off at one of its pixel centres (the bound
+ * of the tile culling, which drops only tiles without such a pixel, so no
+ * rendered value depends on it). view_set 0 / 1 bins the candidate / training view on its own;
  * view_set 2 returns candidate `view` as the last multi-view score binned it
  * (NBV_ERR_STATE when no multi-view score ran since the inputs changed).
  * Synchronises. */
@@ -229,7 +232,8 @@ int nbv_work_stats(nbv_ctx* ctx, int64_t* out4);
  * events. The choice is kept for this context and remembered for later
  * contexts with the same K, SH degree and candidate resolutions. A tile
  * shape decides which Gaussians each tile lists (a Gaussian is listed in
- * every tile its 3-sigma rectangle touches), so it changes rendered values
+ * the tiles of its 3-sigma rectangle where it can pass the alpha cut-off),
+ * so it changes rendered values
  * slightly; the stage depth changes nothing but speed. Ends with the
  * context prepared (same target as before, or -1). Synchronises.
  * Errors: NBV_ERR_STATE (no Gaussians, training or candidate views), those of

@@ -8,8 +8,10 @@
 // exponent:  sigma e^p < alpha_min  <=>  p < log(alpha_min / sigma).
 //
 // Projection, per (view, Gaussian): camera-space centre, EWA 2D covariance
-// with dilation, conic, 3-sigma radius, tile rectangle and depth key, and
-// the view-dependent colour from the real spherical harmonics.
+// with dilation, conic, 3-sigma radius, tile rectangle and depth key, the
+// number of the rectangle's tiles that pass tile_hit (the entries the
+// duplication will emit), and the view-dependent colour from the real
+// spherical harmonics.
 //
 // The key path (everything that decides culling, the tile rectangle, the
 // depth key and the per-pixel alpha decisions) uses only correctly rounded

@@ -1,7 +1,8 @@
 // Tile binning and depth sort (the rasterizer's second stage).
 //
-// Every projected Gaussian is duplicated once per screen tile its 3-sigma
-// rectangle covers, keyed (tile << 32 | float bits of camera z). A stable
+// Every projected Gaussian is duplicated once per screen tile of its 3-sigma
+// rectangle in which it can pass its alpha cut-off at some pixel centre
+// (tile_hit), keyed (tile << 32 | float bits of camera z). A stable
 // LSD radix sort over the used key bits then orders each tile's entries
 // front to back, ties going to the lower Gaussian index (duplication emits
 // in index order and every pass is stable). Per-tile [start, end) ranges
