@@ -469,6 +469,52 @@ def test_ig_closed_form_single_training_view():
     assert res["best"] == 0
 
 
+def test_ig_general_views_against_dense_slogdet():
+    """Two training views and two other candidates: each Gaussian's gain is
+    log det(H_T + c A_v) - log det(H_T) with H_T = lambda I + c (A_t0 + A_t1)
+    (Eqs. 5, 6, 9), here by LAPACK's LU log-determinant of the dense blocks;
+    a training view is scored as H_T + c A_t (counted twice); the score is
+    sum_f beta_f IG_f(v) / mean_t IG_f(T, t) (Eqs. 10-11)."""
+    wl = S.make_workload("tiny")
+    sc = wl.scene.subset(np.arange(300))
+    o = O.OracleScene(sc)
+    train = wl.train.subset([0, 2])
+    cand = wl.cand.subset([1, 4])
+    c = o.confidence()
+    lam32 = float(np.float32(o.hyper.lam))
+    At = [o.view_blocks(train, t) for t in range(2)]
+    Av = [o.view_blocks(cand, v) for v in range(2)]
+
+    def gains(HT, A):
+        out = np.zeros(sc.n)
+        for g in range(sc.n):
+            s0 = np.linalg.slogdet(HT[g])
+            s1 = np.linalg.slogdet(HT[g] + c[g] * A[g])
+            assert s0[0] > 0 and s1[0] > 0
+            out[g] = s1[1] - s0[1]
+        return out
+
+    igc = np.zeros((2, 3)); igt = np.zeros((2, 3))
+    for f in range(3):
+        l = At[0][f].shape[1]
+        HT = lam32 * np.eye(l)[None] + c[:, None, None] * (At[0][f] + At[1][f])
+        for v in range(2):
+            per = gains(HT, Av[v][f])
+            igc[v, f] = per.sum()
+            if v == 1:
+                res = o.score(train, cand, delta_view=1)
+                np.testing.assert_allclose(res["delta"][:, f], per, rtol=1e-8, atol=1e-10)
+        for t in range(2):
+            igt[t, f] = gains(HT, At[t][f]).sum()
+    res = o.score(train, cand)
+    np.testing.assert_allclose(res["ig_cand"], igc, rtol=1e-9)
+    np.testing.assert_allclose(res["ig_train"], igt, rtol=1e-9)
+    beta = np.array([1.0, o.hyper.beta_d, o.hyper.beta_o])
+    want = (igc / igt.mean(0) * beta).sum(1)
+    np.testing.assert_allclose(res["score"], want, rtol=1e-9)
+    assert res["best"] == int(np.argmax(want))
+
+
 def test_ig_is_sum_of_nonnegative_gains_and_permutation_invariant():
     wl = S.make_workload("tiny")
     sc = wl.scene.subset(np.arange(300))
