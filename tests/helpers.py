@@ -1,4 +1,7 @@
-"""Small scene builders shared by the tests (inputs only, no method arithmetic)."""
+"""Small scene builders and fixture readers shared by the tests (inputs
+only, no method arithmetic)."""
+import os
+
 import numpy as np
 
 import nbv_synth as S
@@ -40,3 +43,21 @@ def random_small_scene(seed, n=6, K=2, deg=1, spread=0.05, depth=0.0):
         sh[:, 1:, :] = rng.normal(0, 0.1, (n, nb - 1, 3))
     obj = rng.normal(0, 1.0, (n, K + 1))
     return make_scene(means, log_scales, q, opacity, sh, obj, K, deg)
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def paper_hyperparameters():
+    """{name: value} from golden/paper_hyperparameters.txt (values printed
+    in the paper, each line with its citation)."""
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_hyperparameters.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, value, cite = line.split(None, 2)
+            assert cite.startswith("Sec."), line
+            out[name] = float(value)
+    return out

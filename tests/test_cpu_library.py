@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2602_08266_gb300 as P
@@ -30,11 +31,12 @@ def test_library_builds_and_exports_every_declared_symbol():
 
 
 def test_config_defaults_are_the_papers():
+    from tests.helpers import paper_hyperparameters
     P.build()
     cfg = P.config_default(16, 3)
     assert cfg.K == 16 and cfg.sh_degree == 3
-    assert abs(cfg.alpha_obj - 0.3) < 1e-7 and abs(cfg.alpha_opa - 0.3) < 1e-7
-    assert cfg.beta_d == 10.0 and cfg.beta_o == 1.0
+    for name, value in paper_hyperparameters().items():
+        assert getattr(cfg, name) == np.float32(value), name
     assert abs(cfg.alpha_min - 1 / 255) < 1e-9 and abs(cfg.t_min - 1e-4) < 1e-10
     assert cfg.tile_w == 16 and cfg.tile_h == 16 and cfg.stage == 32 and cfg.batched == 0
 

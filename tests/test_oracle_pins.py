@@ -69,6 +69,13 @@ def test_sh_degree_l_is_harmonic_polynomial():
 
 
 # ------------------------------------------------------ confidence, Eqs. 7 and 12
+def test_oracle_defaults_are_the_printed_hyperparameters():
+    from tests.helpers import paper_hyperparameters
+    h = O.Hyper()
+    for name, value in paper_hyperparameters().items():
+        assert getattr(h, name) == value, name
+
+
 def test_confidence_eq7_eq12_hand_values():
     # K = 1: logits [0, log 3] -> p = [1/4, 3/4]; rho = 0 -> sigma = 1/2
     sc = make_scene([[0, 0, 0], [0, 0, 0.01], [0, 0, 0.02]], np.full((3, 3), math.log(0.01)),
