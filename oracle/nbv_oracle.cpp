@@ -34,9 +34,13 @@
  *  - Depth output D = sum_i w_i z_i (camera-space z, not normalised).
  *  - Pixel centre at (px+0.5, py+0.5).
  *  - Tie-break of the depth sort: (float bits of z, Gaussian index).
- *  - Discrete decisions (culling, tile rectangle, alpha cut-off, alpha clamp,
- *    transmittance stop) are taken in single precision, the precision the
- *    GPU kernel works in; every value is computed in double. The
+ *  - A tile lists a splat only where the splat can pass its alpha cut-off
+ *    at one of the tile's pixel centres (a conservative bound on the 3-sigma
+ *    rectangle's tiles: no pixel result depends on it).
+ *  - Discrete decisions (culling, tile rectangle, the tile bound, alpha
+ *    cut-off, alpha clamp, transmittance stop) are taken in single
+ *    precision, the precision the GPU kernel works in; every value is
+ *    computed in double. The
  *    single-precision decision path uses only correctly rounded + - * / sqrt
  *    in a fixed order, so a GPU that follows the same order reproduces every
  *    decision except the transmittance stop, whose running product also
