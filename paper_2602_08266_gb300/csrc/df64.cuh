@@ -134,4 +134,16 @@ DF_HD df64 df_rsqrt(df64 x) {
   return y;
 }
 
+// Operators, so that code written for double reads the same in df64.
+DF_HD df64 operator+(df64 a, df64 b) { return df_add(a, b); }
+DF_HD df64 operator-(df64 a, df64 b) { return df_sub(a, b); }
+DF_HD df64 operator-(df64 a) { return df_neg(a); }
+DF_HD df64 operator*(df64 a, df64 b) { return df_mul(a, b); }
+DF_HD df64& operator+=(df64& a, df64 b) { return a = df_add(a, b); }
+DF_HD df64& operator-=(df64& a, df64 b) { return a = df_sub(a, b); }
+DF_HD df64& operator*=(df64& a, df64 b) { return a = df_mul(a, b); }
+DF_HD bool operator>=(df64 a, df64 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+DF_HD bool df_isfinite(df64 a) { return std::isfinite(a.hi) && std::isfinite(a.lo); }
+DF_HD df64 df_max(df64 a, df64 b) { return a >= b ? a : b; }
+
 }  // namespace nbv

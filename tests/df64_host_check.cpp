@@ -14,6 +14,7 @@
 #include "df64.cuh"
 
 using nbv::df64;
+using namespace nbv;   // the df64 operators
 using LD = long double;
 
 static LD val(df64 x) { return (LD)x.hi + (LD)x.lo; }
@@ -122,13 +123,13 @@ int main() {
       inv[k] = nbv::df_rsqrt(P[k * n + k]);
       for (int i = k + 1; i < n; ++i) P[i * n + k] = nbv::df_mul(P[i * n + k], inv[k]);
       for (int i = k + 1; i < n; ++i)
-        for (int j = k + 1; j <= i; ++j) P[i * n + j] = nbv::df_fms(P[i * n + j], P[i * n + k], P[j * n + k]);
+        for (int j = k + 1; j <= i; ++j) P[i * n + j] -= P[i * n + k] * P[j * n + k];   // operator form
     }
     for (int k = 0; k < n; ++k) {
       for (int j = 0; j < k; ++j) X[k * n + j] = nbv::df_neg(nbv::df_mul(inv[k], X[k * n + j]));
       X[k * n + k] = inv[k];
       for (int i = k + 1; i < n; ++i)
-        for (int j = 0; j <= k; ++j) X[i * n + j] = nbv::df_add(X[i * n + j], nbv::df_mul(P[i * n + k], X[k * n + j]));
+        for (int j = 0; j <= k; ++j) X[i * n + j] += P[i * n + k] * X[k * n + j];
     }
     // the same factorisation in plain single precision, to show what the
     // comparison detects
