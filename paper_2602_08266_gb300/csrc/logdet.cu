@@ -1495,10 +1495,14 @@ __device__ __forceinline__ float obj_logdet_rows(int u, int K, float cg, float w
   }
 #pragma unroll
   for (int j = 0; j < UO - 6; ++j) {
+    // Xs holds the K rows of X only: rows j >= K are never read (the
+    // template covers up to UO - 6 of them, past the end of the buffer)
     float a = 0.0f;
+    if (j < K) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) a += wr[k] * Xs[j * 6 + k];
-    a += w2 * (wr[6 + j] + sw);
+      for (int k = 0; k < 6; ++k) a += wr[k] * Xs[j * 6 + k];
+      a += w2 * (wr[6 + j] + sw);
+    }
     g[6 + j] = (r == 6 + j ? 1.0f : 0.0f) + (j < K ? cg * a : 0.0f);
   }
   bool done = !row;
@@ -1841,7 +1845,8 @@ int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams,
   const size_t sm = pw * nw;
   cudaFuncSetAttribute(k_build_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int64_t nblk = (s.n + nw - 1) / nw;
-  const int grid = (int)(nblk < 152 * 32 ? nblk : 152 * 32);
+  const int64_t gcap = (int64_t)device_sm_count() * 32;
+  const int grid = (int)(nblk < gcap ? nblk : gcap);
   k_build_factors<<<grid, 32 * nw, sm, st>>>(s, c, cams, blocks, n_train, f, d_err, y);
   return 1;
 }
@@ -1906,9 +1911,7 @@ int launch_views_gains_gm(const DevScene& s, const Consts& c, const DevCam* cams
   int nw = (int)((size_t)(220 * 1024) / pw);
   if (nw < 1) return -1;                      // does not fit: caller uses the view-major kernel
   if (nw > 8) nw = 8;
-  int dev = 0, nsm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nsm = device_sm_count();
   const int nchunk = (nv + 31) / 32;
   int grid = (int)((s.n + nw - 1) / nw);
   const int want = (nsm * 4 + nchunk - 1) / nchunk;   // a few blocks per SM over all chunks
