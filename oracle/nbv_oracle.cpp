@@ -34,11 +34,10 @@
  *  - Depth output D = sum_i w_i z_i (camera-space z, not normalised).
  *  - Pixel centre at (px+0.5, py+0.5).
  *  - Tie-break of the depth sort: (float bits of z, Gaussian index).
- *  - A tile lists a splat only where the splat can pass its alpha cut-off
- *    at one of the tile's pixel centres (a conservative bound on the 3-sigma
- *    rectangle's tiles: no pixel result depends on it).
- *  - Discrete decisions (culling, tile rectangle, the tile bound, alpha
- *    cut-off, alpha clamp, transmittance stop) are taken in single
+ *  - A tile lists every splat whose 3-sigma rectangle covers it (the plain
+ *    binning rule of 3D Gaussian Splatting; no culling inside the rectangle).
+ *  - Discrete decisions (culling, tile rectangle, alpha cut-off, alpha
+ *    clamp, transmittance stop) are taken in single
  *    precision, the precision the GPU kernel works in; every value is
  *    computed in double. The
  *    single-precision decision path uses only correctly rounded + - * / sqrt
@@ -287,42 +286,6 @@ static inline float power32(const Key32& k, int px, int py) {
   return (-0.5f * qf) - k.B * dxy;
 }
 
-// Whether splat k can pass its skip test (power >= thr) at some pixel centre
-// of tile (tx, ty). Not part of the method: a tile whose every pixel centre
-// fails the skip test gets no blend from the splat, so leaving it off the
-// tile's list changes no pixel. The bound is the minimum of the quadratic
-// q = A dx^2 + 2 B dx dy + C dy^2 (power = -q/2) over the box spanned by the
-// tile's pixel centres: zero when the mean lies inside the box, else the
-// smallest of its four edge minima (each a 1-D convex quadratic, minimised
-// at its stationary point clamped to the edge). The limit -2 thr is widened
-// by 2^-8 relative, 2^-8 absolute and 2^-18 of A max dx^2 + C max dy^2, which
-// exceeds the rounding of both this bound and the per-pixel power. The single-
-// precision operations and their order are fixed so that the tile lists are
-// reproducible bit for bit.
-static bool tile_hit32(const Key32& k, float thr, int tx, int ty, int TW, int TH) {
-  const float xl = ((float)(tx * TW) + 0.5f) - k.mx;
-  const float xh = ((float)((tx + 1) * TW) - 0.5f) - k.mx;
-  const float yl = ((float)(ty * TH) + 0.5f) - k.my;
-  const float yh = ((float)((ty + 1) * TH) - 0.5f) - k.my;
-  if (xl <= 0.0f && xh >= 0.0f && yl <= 0.0f && yh >= 0.0f) return true;
-  const float mxx = std::fmax(xl * xl, xh * xh), myy = std::fmax(yl * yl, yh * yh);
-  const float M = k.A * mxx + k.C * myy;
-  const float lim = ((-2.0f * thr) * 1.00390625f + 0.00390625f) + M * 3.814697265625e-06f;
-  float best = std::numeric_limits<float>::infinity();
-  const float ex[2] = {xl, xh}, ey[2] = {yl, yh};
-  for (int e = 0; e < 2; ++e) {        // vertical edges: dx fixed, dy free
-    const float dx = ex[e];
-    const float dy = std::fmin(std::fmax(-((k.B * dx) / k.C), yl), yh);
-    best = std::fmin(best, (k.A * (dx * dx) + (2.0f * k.B) * (dx * dy)) + k.C * (dy * dy));
-  }
-  for (int e = 0; e < 2; ++e) {        // horizontal edges: dy fixed, dx free
-    const float dy = ey[e];
-    const float dx = std::fmin(std::fmax(-((k.B * dy) / k.A), xl), xh);
-    best = std::fmin(best, (k.A * (dx * dx) + (2.0f * k.B) * (dx * dy)) + k.C * (dy * dy));
-  }
-  return best <= lim;
-}
-
 // ----------------------------------------------- double-precision value path
 struct CamD {
   double R[9], t[3], fx, fy, cx, cy, campos[3];
@@ -461,16 +424,14 @@ static void build_view(const Scene& s, const Cam32& c, ViewData& v, bool with_va
     for (int64_t g = 0; g < s.n; ++g)
       if (v.keys[g].valid) v.recs[g] = value_path(s, g, v.cd);
   }
-  // tile lists: every Gaussian whose rectangle covers the tile and which can
-  // pass its skip test somewhere in it, sorted by (depth bits, Gaussian index)
+  // tile lists: every Gaussian whose rectangle covers the tile, sorted by
+  // (depth bits, Gaussian index)
   v.lists.assign((size_t)v.GX * v.GY, {});
   for (int64_t g = 0; g < s.n; ++g) {
     const Key32& k = v.keys[g];
     if (!k.valid) continue;
     for (int ty = k.y0; ty < k.y1; ++ty)
-      for (int tx = k.x0; tx < k.x1; ++tx)
-        if (tile_hit32(k, s.pw_skip32[g], tx, ty, s.hp.tile_w, s.hp.tile_h))
-          v.lists[(size_t)ty * v.GX + tx].push_back((int32_t)g);
+      for (int tx = k.x0; tx < k.x1; ++tx) v.lists[(size_t)ty * v.GX + tx].push_back((int32_t)g);
   }
   for (auto& L : v.lists)
     std::stable_sort(L.begin(), L.end(), [&](int32_t a, int32_t b) {
@@ -852,31 +813,40 @@ int64_t orc_tile_lists(void* h, const float* cam, const int* wh, int64_t* offset
   return tot;
 }
 
-// Check of the tile culling on one view, pixel by pixel: counts[0] = rectangle
-// entries, counts[1] = entries kept, counts[2] = dropped (Gaussian, tile) pairs
-// with an image pixel whose power passes the skip test (must be 0).
-void orc_cull_check(void* h, const float* cam, const int* wh, int64_t* counts) {
+// The splats of each tile's list that some image pixel of the tile cannot
+// skip: those with 1/255-cut-off exponent thr <= power <= 0 (the skip test of
+// compositing, single precision) at one of the tile's pixel centres inside
+// the image. A list that drops others changes no pixel. Same layout as
+// orc_tile_lists (offsets [ntiles + 1], ids in list order); returns the total.
+int64_t orc_tile_needed(void* h, const float* cam, const int* wh, int64_t* offsets, int32_t* ids, int64_t cap) {
   Scene* s = static_cast<Scene*>(h);
   Cam32 c = read_cam(cam, wh);
+  ViewData v;
+  build_view(*s, c, v, false);
   const int TW = s->hp.tile_w, TH = s->hp.tile_h;
-  int64_t total = 0, kept = 0, bad = 0;
-  for (int64_t g = 0; g < s->n; ++g) {
-    Key32 k = key_path32(*s, g, c);
-    if (!k.valid) continue;
-    for (int ty = k.y0; ty < k.y1; ++ty)
-      for (int tx = k.x0; tx < k.x1; ++tx) {
-        ++total;
-        if (tile_hit32(k, s->pw_skip32[g], tx, ty, TW, TH)) { ++kept; continue; }
-        bool pass = false;
-        for (int py = ty * TH; py < std::min((ty + 1) * TH, c.H) && !pass; ++py)
-          for (int px = tx * TW; px < std::min((tx + 1) * TW, c.W); ++px) {
-            const float pw = power32(k, px, py);
-            if (!(pw > 0.0f) && !(pw < s->pw_skip32[g])) { pass = true; break; }
-          }
-        bad += pass ? 1 : 0;
-      }
+  std::vector<std::vector<int32_t>> need(v.lists.size());
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t t = 0; t < (int64_t)v.lists.size(); ++t) {
+    const int tx = (int)(t % v.GX), ty = (int)(t / v.GX);
+    for (int32_t g : v.lists[t]) {
+      const Key32& k = v.keys[g];
+      bool pass = false;
+      for (int py = ty * TH; py < std::min((ty + 1) * TH, c.H) && !pass; ++py)
+        for (int px = tx * TW; px < std::min((tx + 1) * TW, c.W); ++px) {
+          const float pw = power32(k, px, py);
+          if (!(pw > 0.0f) && !(pw < s->pw_skip32[g])) { pass = true; break; }
+        }
+      if (pass) need[t].push_back(g);
+    }
   }
-  counts[0] = total; counts[1] = kept; counts[2] = bad;
+  int64_t tot = 0;
+  for (size_t t = 0; t < need.size(); ++t) { offsets[t] = tot; tot += (int64_t)need[t].size(); }
+  offsets[need.size()] = tot;
+  if (tot <= cap) {
+    int64_t o = 0;
+    for (auto& L : need) for (int32_t g : L) ids[o++] = g;
+  }
+  return tot;
 }
 
 // Render one view in double precision. obj is [H][W][K+1]; n_contrib and

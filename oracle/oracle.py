@@ -55,7 +55,8 @@ def _load():
     lib.orc_view_w2.argtypes = [P, P, P, P]
     lib.orc_tile_lists.restype = i64
     lib.orc_tile_lists.argtypes = [P, P, P, P, P, i64]
-    lib.orc_cull_check.argtypes = [P, P, P, P]
+    lib.orc_tile_needed.restype = i64
+    lib.orc_tile_needed.argtypes = [P, P, P, P, P, i64]
     lib.orc_render.argtypes = [P, P, P, P, P, P, P, P, P]
     lib.orc_view_blocks.argtypes = [P, P, P, P, P, P, P]
     lib.orc_score.restype = i32
@@ -198,23 +199,26 @@ class OracleScene:
         self.lib.orc_project64(self._h, _ptr(c), _ptr(wh), _ptr(v))
         return v
 
-    def tile_lists(self, cams, i):
+    def _lists(self, fn, cams, i):
         c, wh = cam_arrays(cams, i)
         tw, th = self.hyper.tile_w, self.hyper.tile_h
         nt = ((int(wh[0]) + tw - 1) // tw) * ((int(wh[1]) + th - 1) // th)
         off = np.zeros(nt + 1, np.int64)
-        tot = self.lib.orc_tile_lists(self._h, _ptr(c), _ptr(wh), _ptr(off), None, 0)
+        tot = fn(self._h, _ptr(c), _ptr(wh), _ptr(off), None, 0)
         ids = np.zeros(max(tot, 1), np.int32)
-        self.lib.orc_tile_lists(self._h, _ptr(c), _ptr(wh), _ptr(off), _ptr(ids), tot)
+        fn(self._h, _ptr(c), _ptr(wh), _ptr(off), _ptr(ids), tot)
         return off, ids[:tot]
 
-    def cull_check(self, cams, i):
-        """Tile culling of view i checked pixel by pixel: rectangle entries,
-        entries kept, and dropped pairs with a passing pixel (must be 0)."""
-        c, wh = cam_arrays(cams, i)
-        cnt = np.zeros(3, np.int64)
-        self.lib.orc_cull_check(self._h, _ptr(c), _ptr(wh), _ptr(cnt))
-        return dict(total=int(cnt[0]), kept=int(cnt[1]), bad=int(cnt[2]))
+    def tile_lists(self, cams, i):
+        """Per-tile lists of view i: every splat whose 3-sigma rectangle
+        covers the tile, in (depth bits, index) order (offsets, ids)."""
+        return self._lists(self.lib.orc_tile_lists, cams, i)
+
+    def tile_needed(self, cams, i):
+        """The entries of tile_lists that pass the skip test (1/255 cut-off,
+        power <= 0) at some in-image pixel centre of their tile: those no
+        valid list may drop (offsets, ids, same order)."""
+        return self._lists(self.lib.orc_tile_needed, cams, i)
 
     def render(self, cams, i):
         c, wh = cam_arrays(cams, i)

@@ -304,14 +304,16 @@ def _skip32(sc):
 
 @pytest.mark.parametrize("seed", [0, 1])
 def test_tile_lists_brute_force(seed):
-    """Every tile's list is the (depth bits, index)-ordered list of the
-    Gaussians whose rectangle covers it, less some that pass the skip test at
-    none of the tile's pixels, and keeps every one that passes at some pixel."""
+    """Every tile's list is exactly the (depth bits, index)-ordered list of
+    the Gaussians whose rectangle covers it (the plain binning rule), and the
+    needed sub-list holds exactly those that pass the skip test at one of the
+    tile's in-image pixels."""
     sc = random_small_scene(seed, n=30, spread=0.12)
     cam = axis_camera(40, 36, 80.0, 0.5)           # 3x3 tiles, ragged right and bottom
     o = O.OracleScene(sc)
     p32 = o.project32(cam, 0)
     off, ids = o.tile_lists(cam, 0)
+    noff, nids = o.tile_needed(cam, 0)
     lists = _brute_lists(p32, 40, 36)
     skip = _skip32(sc)
     GX = 3
@@ -325,19 +327,42 @@ def test_tile_lists_brute_force(seed):
                 need[t][1].add(g)
     dropped = 0
     for t, (cover, passing) in need.items():
-        got = list(ids[off[t]:off[t + 1]])
-        it = iter(cover)
-        assert all(g in it for g in got), "not an ordered sub-list of the covering Gaussians"
-        assert passing <= set(got), "a Gaussian passing the skip test at a pixel was dropped"
-        dropped += len(cover) - len(got)
-    assert dropped > 0                              # the culling is exercised
+        assert list(ids[off[t]:off[t + 1]]) == cover
+        assert list(nids[noff[t]:noff[t + 1]]) == [g for g in cover if g in passing]
+        dropped += len(cover) - len(passing)
+    assert dropped > 0                              # some rectangle entries are not needed
+
+
+def _needed_brute(p32, skip, W, H, tw, th):
+    """(tile, Gaussian) pairs whose splat passes the skip test at one of the
+    tile's in-image pixel centres, by evaluating the single-precision power
+    at every pixel of every covered tile (numpy, same operation order)."""
+    f32 = np.float32
+    GX = (W + tw - 1) // tw
+    out = set()
+    px = np.arange(W, dtype=np.float32) + f32(0.5)
+    py = np.arange(H, dtype=np.float32) + f32(0.5)
+    for g in np.nonzero(p32["rect"][:, 0] >= 0)[0]:
+        x0, x1, y0, y1 = p32["rect"][g]
+        mx, my = p32["mean2d"][g]
+        A, B, Cc = p32["conic"][g]
+        xs, ys = px[x0 * tw:min(x1 * tw, W)], py[y0 * th:min(y1 * th, H)]
+        dx = (mx - xs)[None, :].astype(np.float32)
+        dy = (my - ys)[:, None].astype(np.float32)
+        q = (A * (dx * dx)).astype(f32) + (Cc * (dy * dy)).astype(f32)
+        pw = (f32(-0.5) * q).astype(f32) - (B * (dx * dy)).astype(f32)
+        ok = ~((pw > 0) | (pw < skip[g]))
+        for yy, xx in zip(*np.nonzero(ok)):
+            out.add(((y0 * th + yy) // th * GX + (x0 * tw + xx) // tw, int(g)))
+    return out
 
 
 @pytest.mark.parametrize("aniso", [0.25, 2.5])
-def test_tile_culling_never_drops_a_blending_pixel(aniso):
-    """Dropped (Gaussian, tile) pairs checked pixel by pixel, with elongated
-    splats (log-scale spread 2.5: axis ratios beyond 1000) where cancellation
-    in the power is largest."""
+def test_tile_needed_elongated_splats(aniso):
+    """The needed sub-lists against a vectorised per-pixel brute force, with
+    elongated splats (log-scale spread 2.5: axis ratios beyond 1000) where
+    the cancellation in the power is largest and a rectangle holds many
+    tiles its splat never reaches."""
     rng = np.random.default_rng(7)
     n = 400
     means = np.stack([rng.uniform(-0.3, 0.3, n), rng.uniform(-0.3, 0.3, n), rng.uniform(-0.1, 0.3, n)], 1)
@@ -347,10 +372,15 @@ def test_tile_culling_never_drops_a_blending_pixel(aniso):
     sh = np.zeros((n, 1, 3)); sh[:, 0, :] = 0.8
     obj = rng.normal(0, 1.0, (n, 2))
     sc = make_scene(means, log_scales, q, opacity, sh, obj, 1, 0)
-    cam = axis_camera(200, 152, 180.0, 1.0)
-    r = O.OracleScene(sc).cull_check(cam, 0)
-    assert r["bad"] == 0
-    assert 0 < r["kept"] < r["total"]
+    W, H = 200, 152
+    cam = axis_camera(W, H, 180.0, 1.0)
+    o = O.OracleScene(sc)
+    p32 = o.project32(cam, 0)
+    off, ids = o.tile_lists(cam, 0)
+    noff, nids = o.tile_needed(cam, 0)
+    got = {(t, int(g)) for t in range(len(noff) - 1) for g in nids[noff[t]:noff[t + 1]]}
+    assert got == _needed_brute(p32, _skip32(sc), W, H, 16, 16)
+    assert 0 < len(nids) < len(ids)
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
