@@ -89,6 +89,11 @@ typedef struct {
                               criterion in the manner of FisherRF);
                             2 tr(c A_v), T-optimality (no training prior).
                             Normalisation (Eq. 10) and weighting (Eq. 11) are unchanged */
+  int tf32_contraction;  /* arithmetic of the tensor-core sum over pixels of the per-pixel
+                            Gauss-Newton terms (Eqs. 6, 9): 0 (default) error-compensated, each
+                            product as three TF32 products of the operands' high and low parts
+                            (about 21 significant bits, FP32 accumulation); 1 single TF32
+                            products (10-bit operands), faster and about 2^-11 relative per term */
 } nbv_config;
 
 typedef struct {
@@ -263,11 +268,25 @@ int nbv_get_tiling(const nbv_ctx* ctx, int* tile_w, int* tile_h, int* stage);
  * share that array and race; serialise them.
  * The first call on each device looks up the array's device address (set-up,
  * cached per device); make that first call before any stream capture.
+ * A launch error that earlier work left pending on the calling thread is
+ * cleared on entry (cudaGetLastError), so that NBV_ERR_CUDA reports this
+ * call's own launches.
  * Errors: NBV_ERR_ARG (n < 0, n > NBV_NOALLOC_MAX_PAIRS, key_bits outside
- * 1..64, NULL or aliased buffers), NBV_ERR_CUDA. */
+ * 1..64, a NULL buffer, or an output whose bytes overlap an input or the
+ * other output), NBV_ERR_CUDA. */
 int nbv_sort_tile_keys_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, int64_t n,
                                int key_bits, uint64_t* keys_out, uint32_t* vals_out,
                                void* cuda_stream);
+
+/* Largest number of (view, tile, Gaussian) entries one binning pass may
+ * hold (their offsets and tile ranges are 32-bit). 0 restores the default,
+ * 2^32 - 4097. The entries of every pass are counted in 64 bits on the
+ * device before anything is duplicated: the batched path splits a candidate
+ * set whose pass would exceed the limit into smaller multi-view passes (run
+ * eagerly, one after the other); a single view above it fails with
+ * NBV_ERR_ARG and nothing is written. Drops a captured multi-view graph.
+ * Errors: NBV_ERR_ARG (max_entries < 0 or above the default). */
+int nbv_set_entry_limit(nbv_ctx* ctx, int64_t max_entries);
 
 /* Message of the last error on this context (never NULL). */
 const char* nbv_last_error(const nbv_ctx* ctx);

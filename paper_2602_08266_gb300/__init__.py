@@ -45,7 +45,8 @@ class nbv_config(ctypes.Structure):
                 ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("dilation", ctypes.c_float), ("guard", ctypes.c_float),
                 ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("batched", ctypes.c_int),
-                ("stage", ctypes.c_int), ("max_batch_views", ctypes.c_int), ("criterion", ctypes.c_int)]
+                ("stage", ctypes.c_int), ("max_batch_views", ctypes.c_int), ("criterion", ctypes.c_int),
+                ("tf32_contraction", ctypes.c_int)]
 
 
 class nbv_camera(ctypes.Structure):
@@ -98,6 +99,7 @@ _SIGS = [
                                      ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
     ("nbv_score_pruned", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_float)]),
+    ("nbv_set_entry_limit", ctypes.c_int, [_P, ctypes.c_int64]),
     ("nbv_last_error", ctypes.c_char_p, [_P]),
     ("nbv_launch_count", ctypes.c_int64, [_P]),
 ]
@@ -165,6 +167,14 @@ def sort_tile_keys_noalloc(keys_in, vals_in, key_bits, keys_out, vals_out, strea
     (see nbv_sort_tile_keys_noalloc in include/nbvgs.h)."""
     import torch
     lib = load_library()
+    n = int(keys_in.numel())
+    want = ((keys_in, torch.int64), (vals_in, torch.int32), (keys_out, torch.int64), (vals_out, torch.int32))
+    dev = torch.cuda.current_device()
+    for t, dt in want:
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_contiguous() or t.numel() != n:
+            raise NBVError(-1, "sort_tile_keys_noalloc: keys int64 and values int32, contiguous, all of one length")
+        if not t.is_cuda or t.device.index != dev:
+            raise NBVError(-1, "sort_tile_keys_noalloc: every tensor must be on the current CUDA device")
     st = stream if stream is not None else torch.cuda.current_stream()
     rc = lib.nbv_sort_tile_keys_noalloc(ctypes.c_void_p(keys_in.data_ptr()),
                                         ctypes.c_void_p(vals_in.data_ptr()), int(keys_in.numel()),
@@ -320,6 +330,11 @@ class NBVScorer:
         s = ctypes.c_float(0.0)
         self._check(self.lib.nbv_argmax(self._h, ctypes.byref(b), ctypes.byref(s)))
         return int(b.value), float(s.value)
+
+    def set_entry_limit(self, max_entries: int):
+        """Cap the (view, tile, Gaussian) entries of one binning pass (0: the
+        32-bit default); see nbv_set_entry_limit."""
+        self._check(self.lib.nbv_set_entry_limit(self._h, int(max_entries)))
 
     def train_gains(self):
         out = np.zeros((max(self.n_train, 1), 3), np.float32)

@@ -20,7 +20,35 @@
 namespace nbv {
 size_t scan_scratch_elems(int64_t n);
 size_t radix_hist_elems(int64_t count);
+
+int device_sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+    cudaGetLastError();
+    nsm = 1;
+  }
+  cache[dev] = nsm;
+  return nsm;
+}
 }  // namespace nbv
+
+namespace {
+// Entries of one binning pass are offset and ranged in 32-bit integers.
+constexpr int64_t kMaxPassEntries = int64_t(0xFFFFFFFF) - 4096;
+// Internal return code of batched_setup: the pass would hold more entries
+// than the limit (the caller splits the candidates).
+constexpr int kTooManyEntries = 1;
+}  // namespace
 
 using namespace nbv;
 
@@ -56,6 +84,10 @@ struct nbv_ctx {
   // sort
   SortBuffers sb{};
   uint32_t* h_total = nullptr;   // pinned
+  unsigned long long* h_total64 = nullptr;   // pinned: 64-bit entry count of the last pass
+  unsigned long long* d_total64 = nullptr;
+  int64_t entry_limit = kMaxPassEntries;     // entries one binning pass may hold
+  int nsm = 1;                               // SMs of the context's device
   size_t ranges_cap = 0;
 
   // blocks and factors
@@ -123,6 +155,7 @@ struct nbv_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t launches_per_replay = 0;
+    int forced_chunk = 0;           // > 0: the full set was found over the entry limit; views per pass
   } bt;
 };
 
@@ -261,9 +294,17 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
   {
     Phase ph(ctx, NBV_PHASE_SORT);
     CKR(check_launch(ctx, launch_scan_u32(ctx->pr.touched, ctx->sb.offsets, ctx->n, ctx->sb.scan_tmp, st)));
+    CKR(check_launch(ctx, launch_sum_u64(ctx->pr.touched, ctx->n, ctx->d_total64, st)));
     CK(cudaMemcpyAsync(ctx->h_total, ctx->sb.offsets + ctx->n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_total64, ctx->d_total64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   }
   CK(cudaStreamSynchronize(st));
+  // the 64-bit count decides: the 32-bit scan (and every offset after the
+  // wrap) is only valid below the limit
+  if ((int64_t)*ctx->h_total64 > ctx->entry_limit)
+    return fail(ctx, NBV_ERR_ARG, "a view has " + std::to_string(*ctx->h_total64) +
+                                      " (tile, Gaussian) entries, more than one binning pass holds (" +
+                                      std::to_string(ctx->entry_limit) + ")");
   const int64_t total = (int64_t)*ctx->h_total;
   if ((size_t)total > ctx->sb.cap) {
     size_t cap = ctx->sb.cap;
@@ -355,6 +396,7 @@ void batched_invalidate(nbv_ctx* ctx) {
   batched_drop_graph(ctx);
   ctx->bt.ready = false;
   ctx->bt.svals = nullptr;
+  ctx->bt.forced_chunk = 0;
 }
 
 // Size every buffer of the multi-view path: camera tables, records, and the
@@ -402,7 +444,7 @@ int batched_setup(nbv_ctx* ctx, int v0, int nv) {
   CKR(alloc(ctx, &B.ranges, (size_t)nt));
   CKR(alloc(ctx, &B.counter, 1));
   CKR(alloc(ctx, &B.blocks, slots * ctx->nBp));
-  B.parts_cap = 152 * 16 * 4;
+  B.parts_cap = ctx->nsm * 64;      // >= the multi-view gains launch's warps (a few blocks of <= 8 per SM)
   CKR(alloc(ctx, &B.partial, (size_t)nv * B.parts_cap * 3));
   CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)(nc > 0 ? nc : 1) * 3));
   CKR(grow(ctx, &ctx->out4, &ctx->out4_cap, (size_t)(nc > 0 ? nc : 1) * 4));
@@ -414,8 +456,17 @@ int batched_setup(nbv_ctx* ctx, int v0, int nv) {
   // entry count
   CKR(check_launch(ctx, launch_project_views(dev_scene(ctx), ctx->c, B.cams, nv, B.pr, st)));
   CKR(check_launch(ctx, launch_scan_u32(B.pr.touched, B.offsets, (int64_t)slots, B.scan_tmp, st)));
+  CKR(check_launch(ctx, launch_sum_u64(B.pr.touched, (int64_t)slots, ctx->d_total64, st)));
   CK(cudaMemcpyAsync(ctx->h_total, B.offsets + slots, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ctx->h_total64, ctx->d_total64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if ((int64_t)*ctx->h_total64 > ctx->entry_limit) {
+    if (nv == 1)
+      return fail(ctx, NBV_ERR_ARG, "candidate " + std::to_string(v0) + " has " + std::to_string(*ctx->h_total64) +
+                                        " (tile, Gaussian) entries, more than one binning pass holds (" +
+                                        std::to_string(ctx->entry_limit) + ")");
+    return kTooManyEntries;      // nothing was duplicated; the caller splits the views
+  }
   B.total = (int64_t)*ctx->h_total;
   const size_t cap = (size_t)B.total + 1024;
   CKR(alloc(ctx, &B.sb.keys[0], cap)); CKR(alloc(ctx, &B.sb.keys[1], cap));
@@ -514,33 +565,58 @@ int batched_chunk(const nbv_ctx* ctx) {
   const int nc = (int)ctx->cand.size();
   const double per_view = (double)ctx->n * ((double)ctx->nBp * 4.0 + 128.0);
   int chunk = (int)std::max(1.0, std::floor(32.0e9 / std::max(per_view, 1.0)));
+  // slot ids (view n + Gaussian) and the depth keys' view field are 31-bit
+  chunk = (int)std::min<int64_t>(chunk, std::max<int64_t>(1, ((int64_t(1) << 31) - 1) / std::max<int64_t>(ctx->n, 1)));
   if (ctx->cfg.max_batch_views > 0) chunk = std::min(chunk, ctx->cfg.max_batch_views);
   return std::max(1, std::min(chunk, std::max(nc, 1)));
+}
+
+// Candidates [v0, v0 + *nv) as one multi-view pass, set up and run eagerly;
+// *nv is halved until the pass's entries fit the limit.
+int batched_eager_chunk(nbv_ctx* ctx, int v0, int* nv) {
+  auto& B = ctx->bt;
+  for (;;) {
+    B.ready = false;
+    const int r = batched_setup(ctx, v0, *nv);
+    if (r == kTooManyEntries) {
+      *nv = std::max(1, *nv / 2);
+      continue;
+    }
+    CKR(r);
+    return batched_sequence(ctx, false);
+  }
 }
 
 int batched_score(nbv_ctx* ctx) {
   auto& B = ctx->bt;
   cudaStream_t st = ctx->st;
   const int nc = (int)ctx->cand.size();
-  const int chunk = batched_chunk(ctx);
+  int chunk = batched_chunk(ctx);
+  if (B.forced_chunk > 0) chunk = std::min(chunk, B.forced_chunk);
+  if (nc <= chunk && (!B.ready || B.v0 != 0 || B.nv != nc)) {
+    batched_drop_graph(ctx);
+    const int r = batched_setup(ctx, 0, nc);
+    if (r == kTooManyEntries) {
+      B.ready = false;
+      chunk = B.forced_chunk = std::max(1, nc / 2);
+    } else {
+      CKR(r);
+    }
+  }
   if (nc > chunk) {
     // candidate chunks one after the other, each set up and run eagerly; the
     // final normalisation over all of them at the end
     batched_drop_graph(ctx);
-    for (int v0 = 0; v0 < nc; v0 += chunk) {
-      B.ready = false;
-      CKR(batched_setup(ctx, v0, std::min(chunk, nc - v0)));
-      CKR(batched_sequence(ctx, false));
+    for (int v0 = 0; v0 < nc;) {
+      int nv = std::min(chunk, nc - v0);
+      CKR(batched_eager_chunk(ctx, v0, &nv));
+      v0 += nv;
     }
     B.ready = false;
     Phase ph(ctx, NBV_PHASE_SCORE);
     CKR(check_launch(ctx, launch_final_scores(ctx->ig_cand, ctx->ig_train, nc, (int)ctx->train.size(), ctx->c,
                                               ctx->out4, ctx->d_flags, ctx->d_best_score, ctx->d_flags + 1, st)));
     return NBV_OK;
-  }
-  if (!B.ready || B.v0 != 0 || B.nv != nc) {
-    batched_drop_graph(ctx);
-    CKR(batched_setup(ctx, 0, nc));
   }
   if (ctx->prof) return batched_sequence(ctx, true);   // timed phase by phase, not replayed
   if (!B.exec) {
@@ -588,7 +664,7 @@ int ensure_scene_buffers(nbv_ctx* ctx, int64_t n) {
     const size_t per = f == 0 ? (size_t)rgb_L_size(nb) : (size_t)l * (l + 1) / 2;
     CKR(alloc(ctx, &ctx->F.L[f], (size_t)n * per));
   }
-  ctx->partial_cap = 152 * 16;    // blocks; up to 8 warp partial sums each
+  ctx->partial_cap = ctx->nsm * 16;    // blocks; up to 8 warp partial sums each
   CKR(alloc(ctx, &ctx->partial, (size_t)ctx->partial_cap * 8 * 3));
   return NBV_OK;
 }
@@ -620,6 +696,7 @@ void nbv_config_default(nbv_config* cfg, int K, int sh_degree) {
   cfg->stage = 32;
   cfg->max_batch_views = 0;
   cfg->criterion = 0;
+  cfg->tf32_contraction = 0;
 }
 
 int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
@@ -631,6 +708,7 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   if (cfg->stage != 16 && cfg->stage != 32) return NBV_ERR_ARG;
   if (cfg->max_batch_views < 0) return NBV_ERR_ARG;
   if (cfg->criterion < 0 || cfg->criterion > 2) return NBV_ERR_ARG;
+  if (cfg->tf32_contraction != 0 && cfg->tf32_contraction != 1) return NBV_ERR_ARG;
   const float fl[] = {cfg->alpha_obj, cfg->alpha_opa, cfg->beta_d, cfg->beta_o, cfg->lambda_damp,
                       cfg->near_z, cfg->alpha_min, cfg->alpha_max, cfg->t_min, cfg->dilation, cfg->guard};
   for (float v : fl)
@@ -647,6 +725,7 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   c.lam = cfg->lambda_damp; c.near_z = cfg->near_z; c.alpha_min = cfg->alpha_min;
   c.alpha_max = cfg->alpha_max; c.t_min = cfg->t_min; c.dilation = cfg->dilation; c.guard = cfg->guard;
   c.crit = cfg->criterion;
+  c.tf32 = cfg->tf32_contraction;
   ctx->nB = block_floats(c.K);
   if (cfg->tile_w != 0) { ctx->tw = cfg->tile_w; ctx->th = cfg->tile_h; }
   ctx->stage = cfg->stage;
@@ -655,6 +734,8 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   if (cudaGetDevice(&ctx->device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&ctx->h_total), sizeof(uint32_t)) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&ctx->h_total64), sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&ctx->d_total64), sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_flags), 4 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_best_score), sizeof(float)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_err), sizeof(int)) != cudaSuccess) {
@@ -662,6 +743,7 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
     nbv_destroy(ctx);
     return NBV_ERR_CUDA;
   }
+  ctx->nsm = device_sm_count();
   launch_tri_table_init(ctx->st);
   if (cudaGetLastError() != cudaSuccess) {
     nbv_destroy(ctx);
@@ -698,6 +780,8 @@ void nbv_destroy(nbv_ctx* ctx) {
   for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->pool) cudaEventDestroy(e);
   if (ctx->h_total) cudaFreeHost(ctx->h_total);
+  if (ctx->h_total64) cudaFreeHost(ctx->h_total64);
+  if (ctx->d_total64) cudaFree(ctx->d_total64);
   for (void* p : {(void*)ctx->d_desc_cams, (void*)ctx->desc_raw, (void*)ctx->desc, (void*)ctx->d_pred,
                   (void*)ctx->gacc})
     if (p) cudaFree(p);
@@ -1218,6 +1302,15 @@ int nbv_autotune(nbv_ctx* ctx, int* tile_w, int* tile_h, int* stage) {
   if (tile_h) *tile_h = bh;
   if (stage) *stage = bs;
   return nbv_prepare(ctx, target);
+}
+
+int nbv_set_entry_limit(nbv_ctx* ctx, int64_t max_entries) {
+  if (!ctx) return NBV_ERR_ARG;
+  if (max_entries < 0 || max_entries > kMaxPassEntries)
+    return fail(ctx, NBV_ERR_ARG, "entry limit outside 0 .. 2^32 - 4097");
+  ctx->entry_limit = max_entries == 0 ? kMaxPassEntries : max_entries;
+  batched_invalidate(ctx);
+  return NBV_OK;
 }
 
 const char* nbv_last_error(const nbv_ctx* ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }

@@ -19,10 +19,11 @@
 // for every output X (and d O_0 / d alpha_i gets the residual term
 // -T_final / (1 - alpha_i)). Each pixel forms its share of the structured
 // 2D Gauss-Newton block of every splat (layout in nbv_internal.cuh); the
-// shares are summed over the warp's pixels by TF32 tensor-core products,
-// over the tile's warps in shared memory, and added to the per-Gaussian
-// block in global memory with one vector atomic per 4 floats per
-// (tile, Gaussian).
+// shares are summed over the warp's pixels by TF32 tensor-core products
+// (error-compensated by default: three products of high and low parts per
+// term), over the tile's warps in shared memory, and added to the
+// per-Gaussian block in global memory with one vector atomic per 4 floats
+// per (tile, Gaussian).
 #include "nbv_internal.cuh"
 
 namespace nbv {
@@ -60,6 +61,39 @@ __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const float* p) {
 // x only (all U and V entries are).
 __device__ __forceinline__ float tf32f(float x) { return __uint_as_float(__float_as_uint(x) + 0x1000u); }
 
+// A U or V entry as stored for the contraction: the TF32 operand (single
+// products, 10 mantissa bits) or the FP32 value itself, split into two TF32
+// terms when the fragments are loaded (kSplit).
+template <bool kSplit>
+__device__ __forceinline__ float uvst(float x) { return kSplit ? x : tf32f(x); }
+
+// x = hi + lo with hi the TF32 value nearest x (ties away from zero) and lo
+// the exact remainder, itself given to the tensor core rounded to nearest:
+// the error-compensated product a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi
+// (three TF32 products, FP32 accumulation) keeps about 21 bits of each
+// product instead of 10 (Markidis et al., 2018; Ootomo and Yokota, 2022).
+__device__ __forceinline__ void split_tf32(uint32_t x, uint32_t& hi, uint32_t& lo) {
+  hi = (x + 0x1000u) & 0xFFFFE000u;
+  lo = __float_as_uint(__uint_as_float(x) - __uint_as_float(hi)) + 0x1000u;
+}
+
+// d += A B over one k-step, single TF32 products or error-compensated.
+template <bool kSplit>
+__device__ __forceinline__ void mma_k(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  if (!kSplit) {
+    mma_tf32(d, a[0], a[1], a[2], a[3], b0, b1);
+  } else {
+    uint32_t ah[4], al[4], bh0, bl0, bh1, bl1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) split_tf32(a[i], ah[i], al[i]);
+    split_tf32(b0, bh0, bl0);
+    split_tf32(b1, bh1, bl1);
+    mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+  }
+}
+
 // Per-warp contraction buffers are value-major: element (value s, pixel
 // slot) at s * kCS + slot. With kCS = 36 (= 4 mod 32) the per-pixel stores
 // (one value, 32 slots) and the mma fragment loads (value 4 g + slot t) both
@@ -71,7 +105,7 @@ constexpr int kVRows = 32;
 
 // One 16x16 tile of one view: both passes. blocks_v is the view's block
 // array (NULL: render only).
-template <int KCM, int kBatch>
+template <int KCM, int kBatch, bool kSplit>
 __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const Consts& c, const DevCam& cam,
                                                int tile, uint2 rg, float* blocks_v, size_t rec_off,
                                                unsigned char* smem) {
@@ -293,27 +327,27 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         const float s0v = s01.x;
         const float2 wa2 = make_float2(wa, wa), off2 = make_float2(-wa * s0v, -wa * s0v);
         float2 qo2 = make_float2(s0v * s0v, s01.y * s01.y);
-        if (KC > 1) Ur[7 * kCS] = tf32f(fmaf(wa, s01.y, -wa * s0v));
+        if (KC > 1) Ur[7 * kCS] = uvst<kSplit>(fmaf(wa, s01.y, -wa * s0v));
 #pragma unroll
         for (int q = 1; q < KCM / 2; ++q) {
           if (2 * q < KC) {
             const float2 sk2 = __ffma2_rn(Ti2, pj2[q], __fmul2_rn(Ro2[q], ni2));
             qo2 = __ffma2_rn(sk2, sk2, qo2);
             const float2 u2 = __ffma2_rn(wa2, sk2, off2);
-            Ur[(6 + 2 * q) * kCS] = tf32f(u2.x);
-            if (2 * q + 1 < KC) Ur[(7 + 2 * q) * kCS] = tf32f(u2.y);
+            Ur[(6 + 2 * q) * kCS] = uvst<kSplit>(u2.x);
+            if (2 * q + 1 < KC) Ur[(7 + 2 * q) * kCS] = uvst<kSplit>(u2.y);
           }
         }
         const float qo = qo2.x + qo2.y;
         const float ae2 = ae * ae;
-        Ur[0] = tf32f((sr0 * sr0 + sr1 * sr1 + sr2 * sr2) * ae2);
-        Ur[kCS] = tf32f(sd * sd * ae2);
-        Ur[2 * kCS] = tf32f(qo * ae2);
-        Ur[3 * kCS] = tf32f(wa * sr0);
-        Ur[4 * kCS] = tf32f(wa * sr1);
-        Ur[5 * kCS] = tf32f(wa * sr2);
-        Ur[6 * kCS] = tf32f(wa * sd);
-        Ur[(7 + K) * kCS] = tf32f(w * w);
+        Ur[0] = uvst<kSplit>((sr0 * sr0 + sr1 * sr1 + sr2 * sr2) * ae2);
+        Ur[kCS] = uvst<kSplit>(sd * sd * ae2);
+        Ur[2 * kCS] = uvst<kSplit>(qo * ae2);
+        Ur[3 * kCS] = uvst<kSplit>(wa * sr0);
+        Ur[4 * kCS] = uvst<kSplit>(wa * sr1);
+        Ur[5 * kCS] = uvst<kSplit>(wa * sr2);
+        Ur[6 * kCS] = uvst<kSplit>(wa * sd);
+        Ur[(7 + K) * kCS] = uvst<kSplit>(w * w);
         // splat geometry at this pixel
         const float dx = a0.x - pxc, dy = a0.y - pyc;
         const float v[6] = {-(a1.x * dx + a1.y * dy), -(a1.y * dx + a1.z * dy), -0.5f * dx * dx,
@@ -321,8 +355,8 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
 #pragma unroll
-          for (int n = 0; n <= m; ++n) Vr[(m * (m + 1) / 2 + n) * kCS] = tf32f(v[m] * v[n]);
-          Vr[(24 + m) * kCS] = tf32f(v[m]);
+          for (int n = 0; n <= m; ++n) Vr[(m * (m + 1) / 2 + n) * kCS] = uvst<kSplit>(v[m] * v[n]);
+          Vr[(24 + m) * kCS] = uvst<kSplit>(v[m]);
         }
         Vr[30 * kCS] = 1.0f;
         // extend the suffix sums with this splat and step T back
@@ -361,15 +395,15 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         const uint32_t b10 = ok0 ? vb[2] : 0u, b11 = ok1 ? vb[3] : 0u;   // 8-15
         const uint32_t b20 = ok0 ? vc[0] : 0u, b21 = ok1 ? vc[1] : 0u;   // 16-23
         const uint32_t xb0 = ok0 ? vc[2] : 0u, xb1 = ok1 ? vc[3] : 0u;   // 24-31
-        mma_tf32(dq[0], qa[0], qa[1], qa[2], qa[3], b00, b01);
-        mma_tf32(dq[1], qa[0], qa[1], qa[2], qa[3], b10, b11);
-        mma_tf32(dq[2], qa[0], qa[1], qa[2], qa[3], b20, b21);
+        mma_k<kSplit>(dq[0], qa, b00, b01);
+        mma_k<kSplit>(dq[1], qa, b10, b11);
+        mma_k<kSplit>(dq[2], qa, b20, b21);
 #pragma unroll
         for (int mt = 0; mt < MTBM; ++mt)
           if (mt < MTB) {
             uint32_t xa[4];
             ldsm_x4(xa, ax + 16 * mt * kCS + 8 * ks);
-            mma_tf32(dxo[mt], xa[0], xa[1], xa[2], xa[3], xb0, xb1);
+            mma_k<kSplit>(dxo[mt], xa, xb0, xb1);
           }
       }
       __syncwarp();
@@ -406,12 +440,12 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   }
 }
 
-template <int KCM, int kBatch>
+template <int KCM, int kBatch, bool kSplit>
 __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
     k_composite(CompositeArgs args, Consts c) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (args.queue == nullptr) {                 // one tile of one view per block
-    composite_tile<KCM, kBatch>(args, c, args.cam, blockIdx.x, args.ranges[blockIdx.x], args.blocks, 0, smem);
+    composite_tile<KCM, kBatch, kSplit>(args, c, args.cam, blockIdx.x, args.ranges[blockIdx.x], args.blocks, 0, smem);
     return;
   }
   // persistent: (view, tile) items in queue order (longest lists first)
@@ -425,12 +459,12 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
     const uint32_t gt = args.queue[it];
     const int v = args.tile_view[gt];
     const DevCam cam = args.cams[v];
-    composite_tile<KCM, kBatch>(args, c, cam, (int)(gt - args.tile_base[v]), args.ranges[gt],
+    composite_tile<KCM, kBatch, kSplit>(args, c, cam, (int)(gt - args.tile_base[v]), args.ranges[gt],
                         args.blocks + (size_t)v * args.n * ((args.nB + 3) & ~3), (size_t)v * args.n, smem);
   }
 }
 
-template <int KCM, int kBatch>
+template <int KCM, int kBatch, bool kSplit>
 int launch_k(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
   const int nBp = (a.nB + 3) & ~3;
   const size_t sm = sizeof(float4) * 3 * kBatch + sizeof(int) * kBatch +
@@ -439,42 +473,46 @@ int launch_k(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
                     sizeof(float) * (kTilePix / 32) * kCS * (size_t)(u_rows(c.K) + kVRows);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_composite<KCM, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_composite<KCM, kBatch, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   if (a.queue) {
-    int per_sm = 1, dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<KCM, kBatch>, kTilePix, sm);
+    int per_sm = 1;
+    const int nsm = device_sm_count();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<KCM, kBatch, kSplit>, kTilePix, sm);
     if (per_sm < 1) per_sm = 1;
     int grid = nsm * per_sm;
     if (grid > a.n_items) grid = a.n_items;
     if (grid <= 0) return 0;
-    k_composite<KCM, kBatch><<<grid, kTilePix, sm, st>>>(a, c);
+    k_composite<KCM, kBatch, kSplit><<<grid, kTilePix, sm, st>>>(a, c);
     return 1;
   }
   const int ntiles = a.cam.GX * a.cam.GY;
   if (ntiles <= 0) return 0;
-  k_composite<KCM, kBatch><<<ntiles, kTilePix, sm, st>>>(a, c);
+  k_composite<KCM, kBatch, kSplit><<<ntiles, kTilePix, sm, st>>>(a, c);
   return 1;
+}
+
+template <bool kSplit>
+int launch_stage(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage) {
+  if (stage == 16) {
+    if (c.KC <= 8) return launch_k<8, 16, kSplit>(a, c, st);
+    if (c.KC <= 24) return launch_k<24, 16, kSplit>(a, c, st);
+    if (c.KC <= 40) return launch_k<40, 16, kSplit>(a, c, st);
+    if (c.KC <= 72) return launch_k<72, 16, kSplit>(a, c, st);
+    return launch_k<128, 16, kSplit>(a, c, st);
+  }
+  if (c.KC <= 8) return launch_k<8, 32, kSplit>(a, c, st);
+  if (c.KC <= 24) return launch_k<24, 32, kSplit>(a, c, st);
+  if (c.KC <= 40) return launch_k<40, 32, kSplit>(a, c, st);
+  if (c.KC <= 72) return launch_k<72, 32, kSplit>(a, c, st);
+  return launch_k<128, 32, kSplit>(a, c, st);
 }
 
 }  // namespace
 
 int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage) {
-  if (stage == 16) {
-    if (c.KC <= 8) return launch_k<8, 16>(a, c, st);
-    if (c.KC <= 24) return launch_k<24, 16>(a, c, st);
-    if (c.KC <= 40) return launch_k<40, 16>(a, c, st);
-    if (c.KC <= 72) return launch_k<72, 16>(a, c, st);
-    return launch_k<128, 16>(a, c, st);
-  }
-  if (c.KC <= 8) return launch_k<8, 32>(a, c, st);
-  if (c.KC <= 24) return launch_k<24, 32>(a, c, st);
-  if (c.KC <= 40) return launch_k<40, 32>(a, c, st);
-  if (c.KC <= 72) return launch_k<72, 32>(a, c, st);
-  return launch_k<128, 32>(a, c, st);
+  return c.tf32 ? launch_stage<false>(a, c, st, stage) : launch_stage<true>(a, c, st, stage);
 }
 
 }  // namespace nbv

@@ -119,7 +119,7 @@ int launch_descriptors(const DevScene& s, const Consts& c, const DevCam* cams, i
   cudaMemsetAsync(raw, 0, sizeof(float) * (size_t)nv * kDescDim, st);
   const int nchunk = (nv + kViewChunk - 1) / kViewChunk;
   int gx = (int)((s.n + 255) / 256);
-  const int want = (152 * 8 + nchunk - 1) / nchunk;
+  const int want = (device_sm_count() * 8 + nchunk - 1) / nchunk;
   if (gx > want) gx = want;
   if (gx < 1) gx = 1;
   k_descriptor_hist<<<dim3(gx, nchunk), 256, 0, st>>>(s, c.near_z, cams, nv, tcams, n_train, tblocks, nBp, raw);

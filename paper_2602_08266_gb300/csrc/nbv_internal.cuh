@@ -51,6 +51,7 @@ struct Consts {
   float alpha_obj, alpha_opa, beta_d, beta_o, lam;
   float near_z, alpha_min, alpha_max, t_min, dilation, guard;
   int crit;   // 0: log det (Eq. 6); 1: tr(H_T^-1 c A); 2: tr(c A) (T-optimality)
+  int tf32;   // 1: single TF32 products in the information contraction; 0: error-compensated (3 x TF32)
 };
 
 // Scene on the device (structure of arrays).
@@ -80,6 +81,10 @@ struct DevProj {
   float* radius;
 };
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// read once per device); every grid and partial-sum capacity is sized from it.
+int device_sm_count();
+
 // ------------------------------------------------------------ kernels (host wrappers)
 // Each wrapper launches on `st` and returns the number of launches issued.
 int launch_scene_prep(const DevScene& s, const Consts& c, int target, cudaStream_t st);
@@ -102,6 +107,8 @@ struct SortBuffers {
   size_t cap;            // capacity of keys / vals
   size_t scan_tmp_cap, hist_cap;
 };
+// 64-bit sum of n 32-bit counts into *out (device; zeroed on the stream first).
+int launch_sum_u64(const uint32_t* in, int64_t n, unsigned long long* out, cudaStream_t st);
 // Exclusive scan of touched into offsets; total written to *d_total (device).
 int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st);
 int launch_duplicate(const DevProj& pr, int64_t n, int GX, int TW, int TH, const uint32_t* offsets, uint64_t* keys,

@@ -36,6 +36,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
+// Whether the byte ranges [a, a + na) and [b, b + nb) share a byte.
+bool overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
 }  // namespace
 
 extern "C" int nbv_sort_tile_keys_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, int64_t n,
@@ -43,8 +49,17 @@ extern "C" int nbv_sort_tile_keys_noalloc(const uint64_t* keys_in, const uint32_
                                           void* cuda_stream) {
   if (n < 0 || n > kMaxPairs || key_bits < 1 || key_bits > 64) return NBV_ERR_ARG;
   if (n > 0 && (!keys_in || !vals_in || !keys_out || !vals_out)) return NBV_ERR_ARG;
-  if (n > 0 && ((const void*)keys_out == (const void*)keys_in || (const void*)vals_out == (const void*)vals_in))
-    return NBV_ERR_ARG;
+  if (n > 0) {
+    // the outputs may share no byte with the inputs or with each other
+    const size_t kb = sizeof(uint64_t) * (size_t)n, vb = sizeof(uint32_t) * (size_t)n;
+    if (overlap(keys_out, kb, keys_in, kb) || overlap(keys_out, kb, vals_in, vb) ||
+        overlap(vals_out, vb, keys_in, kb) || overlap(vals_out, vb, vals_in, vb) ||
+        overlap(keys_out, kb, vals_out, vb))
+      return NBV_ERR_ARG;
+  }
+  // a launch error left pending by earlier work on this thread is cleared
+  // here, so that the check after this call's launches reports only its own
+  cudaGetLastError();
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NBV_ERR_CUDA;
   void* base = nullptr;

@@ -270,7 +270,8 @@ int launch_check_inputs(const float* mu, const float* logs, const float* q, cons
   if (n <= 0) return 0;
   const int bs = 256;
   int64_t nb = (n + bs - 1) / bs;
-  if (nb > 152 * 16) nb = 152 * 16;
+  const int64_t cap = (int64_t)device_sm_count() * 16;
+  if (nb > cap) nb = cap;
   k_check_inputs<<<(unsigned)nb, bs, 0, st>>>(mu, logs, q, rho, sh, obj, n, nsh, KC, flag);
   return 1;
 }

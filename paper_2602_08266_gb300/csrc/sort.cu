@@ -369,7 +369,28 @@ __global__ void k_ranges(const uint64_t* __restrict__ keys, int64_t n, uint2* __
   if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
 }
 
+// 64-bit sum of n 32-bit counts into *out (zeroed by the caller): the entry
+// count of a binning pass without the wrap of the 32-bit scan.
+__global__ void k_sum_u64(const uint32_t* __restrict__ in, int64_t n, unsigned long long* __restrict__ out) {
+  unsigned long long acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) acc += in[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0) atomicAdd(out, acc);
+}
+
 }  // namespace
+
+int launch_sum_u64(const uint32_t* in, int64_t n, unsigned long long* out, cudaStream_t st) {
+  cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+  if (n <= 0) return 0;
+  int64_t nb = (n + 255) / 256;
+  const int64_t cap = (int64_t)device_sm_count() * 8;
+  if (nb > cap) nb = cap;
+  k_sum_u64<<<(unsigned)nb, 256, 0, st>>>(in, n, out);
+  return 1;
+}
 
 int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st) {
   int l = 0;
