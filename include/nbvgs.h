@@ -90,10 +90,14 @@ typedef struct {
                             2 tr(c A_v), T-optimality (no training prior).
                             Normalisation (Eq. 10) and weighting (Eq. 11) are unchanged */
   int tf32_contraction;  /* arithmetic of the tensor-core sum over pixels of the per-pixel
-                            Gauss-Newton terms (Eqs. 6, 9): 0 (default) error-compensated, each
-                            product as three TF32 products of the operands' high and low parts
-                            (about 21 significant bits, FP32 accumulation); 1 single TF32
-                            products (10-bit operands), faster and about 2^-11 relative per term */
+                            Gauss-Newton terms (Eqs. 6, 9), FP32 accumulation in every case:
+                            1 single TF32 products (10-bit operands, about 2^-11 relative per
+                            term); 2 error-compensated, each product as three TF32 products of
+                            the operands' high and low parts (about 21 significant bits);
+                            0 (default) automatic: 1 for the log-det criterion, whose logarithm
+                            compresses the rounding, 2 for the linear trace criteria.
+                            This applies to the candidates' blocks; the training views' blocks
+                            (summed into the factorised training Hessians) always use 2 */
 } nbv_config;
 
 typedef struct {
@@ -177,8 +181,11 @@ int nbv_train_gains(nbv_ctx* ctx, float* out);
 
 /* Per-Gaussian log-det gains of candidate `cand`, DEVICE array [n][3]: the
  * terms log det(H_T,g + c_g A_c,g) - log det H_T,g whose sum over g is
- * IG_f(T,c) (Sec. III-B.1, block-diagonal determinant). Needs nbv_prepare.
- * Errors: NBV_ERR_STATE, NBV_ERR_ARG. */
+ * IG_f(T,c) (Sec. III-B.1, block-diagonal determinant); 0 for Gaussians with
+ * c_g = 0. The information contraction of this call is error-compensated
+ * whatever tf32_contraction says (single terms are inspected here; the
+ * logarithm of a view sum does not average their rounding). Needs
+ * nbv_prepare. Errors: NBV_ERR_STATE, NBV_ERR_ARG. */
 int nbv_gaussian_gains(nbv_ctx* ctx, int cand, float* delta);
 
 /* Inspection of one view's projection and tile lists (for verification).
@@ -197,7 +204,10 @@ int nbv_debug_project(nbv_ctx* ctx, int view_set, int view, int32_t* rect, float
  * of the tile culling, which drops only tiles without such a pixel, so no
  * rendered value depends on it). view_set 0 / 1 bins the candidate / training view on its own;
  * view_set 2 returns candidate `view` as the last multi-view score binned it
- * (NBV_ERR_STATE when no multi-view score ran since the inputs changed).
+ * (NBV_ERR_STATE when no multi-view score ran since the inputs changed);
+ * with a target object (Eq. 12) that pass lists splats only in the tiles
+ * where a splat of the target can pass its alpha cut-off, the only tiles
+ * whose lists the information gain reads.
  * Synchronises. */
 int nbv_debug_tile_lists(nbv_ctx* ctx, int view_set, int view, int64_t* offsets, int32_t* ids,
                          int64_t cap, int64_t* count);
@@ -211,7 +221,9 @@ enum {
   NBV_PHASE_FACTORS = 4,   /* training Hessians and their factorisation */
   NBV_PHASE_GAINS = 5,     /* per-Gaussian log-det gains and their sums (Eqs. 5-6) */
   NBV_PHASE_SCORE = 6,     /* normalisation, weighting, argmax (Eqs. 10-11) */
-  NBV_NUM_PHASES = 7
+  NBV_PHASE_TRAIN_COMPOSITE = 7, /* compositing + information blocks of the training views (prepare);
+                                    NBV_PHASE_COMPOSITE holds the candidates' launches */
+  NBV_NUM_PHASES = 8
 };
 
 /* Switch per-phase timing on (1) or off (0); either call clears the
@@ -225,10 +237,23 @@ int nbv_set_profiling(nbv_ctx* ctx, int on);
  * profiling was switched on; arrays of NBV_NUM_PHASES. Synchronises. */
 int nbv_phase_times(nbv_ctx* ctx, double* ms, int64_t* launches);
 
-/* Work counters of the compositing kernel since profiling was switched on:
- * [0] (pixel, splat) pairs evaluated in the forward pass, [1] pairs blended,
- * [2] (tile, Gaussian) block flushes, [3] compositing launches. Synchronises. */
-int nbv_work_stats(nbv_ctx* ctx, int64_t* out4);
+/* Work counters of the compositing kernel since profiling was switched on,
+ * for the candidates' launches (which = 0) or the training views' launches
+ * of prepare (which = 1): [0] (pixel, splat) pairs evaluated in the forward
+ * pass, [1] pairs blended, [2] (tile, Gaussian) block flushes, [3] (pixel,
+ * splat) pairs of the information pass (blended pixels of splats with
+ * c_g > 0), [4] compositing launches, [5] (view, tile, Gaussian) entries
+ * of their binning passes. Synchronises. Errors: NBV_ERR_ARG. */
+int nbv_work_stats(nbv_ctx* ctx, int which, int64_t* out6);
+
+/* Throughput of fused multiply-adds on the FP32 pipes of the current device:
+ * a register-resident loop of independent fma.rn.f32 (packed = 0) or
+ * packed fma.rn.f32x2 (packed = 1) chains over (SMs x 8) blocks of 256
+ * threads, timed with CUDA events on cuda_stream after one untimed launch.
+ * *tflops = 2 flops per lane FMA / seconds / 1e12. Synchronises. A
+ * measurement of the roofline's FP32 peak; it computes nothing of the method.
+ * Errors: NBV_ERR_ARG (NULL tflops), NBV_ERR_CUDA. */
+int nbv_measure_fp32_fma(int packed, void* cuda_stream, double* tflops);
 
 /* Pick the screen tile (16 x 16 or 32 x 8) and the number of Gaussians the
  * compositing kernel stages in shared memory per round (16 or 32) that

@@ -77,7 +77,8 @@ _SIGS = [
                                             ctypes.POINTER(ctypes.c_int64)]),
     ("nbv_set_profiling", ctypes.c_int, [_P, ctypes.c_int]),
     ("nbv_phase_times", ctypes.c_int, [_P, _P, _P]),
-    ("nbv_work_stats", ctypes.c_int, [_P, _P]),
+    ("nbv_work_stats", ctypes.c_int, [_P, ctypes.c_int, _P]),
+    ("nbv_measure_fp32_fma", ctypes.c_int, [ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
     ("nbv_autotune", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int)]),
     ("nbv_get_tiling", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -159,6 +160,20 @@ def _cams_struct(cams):
 
 
 NOALLOC_MAX_PAIRS = 1 << 20
+
+
+def measure_fp32_fma(packed: bool = False, stream=None) -> float:
+    """FP32 fused multiply-add throughput of the current device in TFLOP/s
+    (nbv_measure_fp32_fma): the roofline denominator of the compositing
+    kernel, measured rather than derived."""
+    import torch
+    lib = load_library()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double(0.0)
+    rc = lib.nbv_measure_fp32_fma(1 if packed else 0, ctypes.c_void_p(st.cuda_stream), ctypes.byref(out))
+    if rc != NBV_OK:
+        raise NBVError(rc, "nbv_measure_fp32_fma failed")
+    return float(out.value)
 
 
 def sort_tile_keys_noalloc(keys_in, vals_in, key_bits, keys_out, vals_out, stream=None):
@@ -378,7 +393,7 @@ class NBVScorer:
                                                   _dptr(ids), total, ctypes.byref(cnt)))
         return off, ids[:total]
 
-    PHASES = ("prep", "project", "sort", "composite", "factors", "gains", "score")
+    PHASES = ("prep", "project", "sort", "composite", "factors", "gains", "score", "train_composite")
 
     def set_profiling(self, on: bool):
         self._check(self.lib.nbv_set_profiling(self._h, 1 if on else 0))
@@ -391,12 +406,13 @@ class NBVScorer:
                                              ctypes.c_void_p(ln.ctypes.data)))
         return {p: (float(ms[i]), int(ln[i])) for i, p in enumerate(self.PHASES)}
 
-    def work_stats(self):
-        """Compositing work since profiling was switched on."""
-        out = np.zeros(4, np.int64)
-        self._check(self.lib.nbv_work_stats(self._h, ctypes.c_void_p(out.ctypes.data)))
-        return dict(pairs_evaluated=int(out[0]), pairs_blended=int(out[1]),
-                    block_flushes=int(out[2]), composite_launches=int(out[3]))
+    def work_stats(self, training: bool = False):
+        """Compositing work since profiling was switched on: the candidates'
+        launches, or the training views' launches of prepare."""
+        out = np.zeros(6, np.int64)
+        self._check(self.lib.nbv_work_stats(self._h, 1 if training else 0, ctypes.c_void_p(out.ctypes.data)))
+        return dict(pairs_evaluated=int(out[0]), pairs_blended=int(out[1]), block_flushes=int(out[2]),
+                    pairs_information=int(out[3]), composite_launches=int(out[4]), entries=int(out[5]))
 
     def autotune(self):
         """Pick tile shape and stage depth on the batched path; returns

@@ -74,6 +74,12 @@ struct nbv_ctx {
   float4 *mu_sig = nullptr, *scale_skip = nullptr, *qn = nullptr, *aux = nullptr;
   float* p = nullptr;
   int prepared_target = -2;
+  // active set of the last prepare (Gaussians with c_g > 0): blocks, factors
+  // and gains are kept for these only, in slot order
+  int* slot = nullptr;            // [n]
+  int* act = nullptr;             // [n]
+  int64_t n_act = 0;
+  int last_target = -2;           // target of the active set above
 
   // cameras
   std::vector<nbv_camera> train, cand;
@@ -117,8 +123,9 @@ struct nbv_ctx {
   std::vector<cudaEvent_t> pool;
   double acc_ms[NBV_NUM_PHASES] = {0};
   int64_t acc_launch[NBV_NUM_PHASES] = {0};
-  unsigned long long* d_stats = nullptr;   // composite work counters
-  int64_t composite_launches = 0;
+  unsigned long long* d_stats = nullptr;   // composite work counters: [0..3] candidates, [4..7] training
+  int64_t composite_launches[2] = {0, 0};
+  int64_t binned_entries[2] = {0, 0};      // (view, tile, Gaussian) entries of the binning passes
 
   // batched multi-view scoring (cfg.batched): buffers sized once per
   // (scene, candidate set), the whole score captured in a CUDA graph
@@ -138,7 +145,10 @@ struct nbv_ctx {
     uint32_t* tile_base = nullptr;  // [nv]
     int* tile_view = nullptr;       // [ntiles]
     DevProj pr{};                   // [nv][n] records
-    uint32_t* offsets = nullptr;    // [nv n + 1]
+    uint8_t* mark = nullptr;        // [ntiles] tiles an active splat reaches (active subset only)
+    uint32_t* flags = nullptr;      // [nv n] slots that emit entries
+    int64_t m = 0;                  // how many slots emit entries
+    uint32_t* offsets = nullptr;    // [nv n + 1] their positions
     uint32_t* scan_tmp = nullptr;
     SortBuffers db{};               // depth order of the (view, Gaussian) slots
     uint32_t* tcount = nullptr;     // [nv n] tiles touched, in depth order
@@ -239,6 +249,9 @@ DevScene dev_scene(nbv_ctx* ctx) {
   s.sh = ctx->sh; s.obj_raw = ctx->obj;
   s.mu_sig = ctx->mu_sig; s.scale_skip = ctx->scale_skip; s.qn = ctx->qn; s.aux = ctx->aux;
   s.p = ctx->p;
+  s.slot = ctx->slot;
+  s.act = ctx->act;
+  s.n_act = ctx->n_act;
   return s;
 }
 
@@ -282,7 +295,7 @@ struct Phase {
 
 // Project, bin and sort one view; composite it (images and/or IG blocks).
 int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, float* depth,
-                float* alpha, float* obj, bool keep_lists = false) {
+                float* alpha, float* obj, bool compensated = false, bool training = false) {
   cudaStream_t st = ctx->st;
   const DevCam dc = to_dev(cam, ctx->tw, ctx->th);
   const int ntiles = dc.GX * dc.GY;
@@ -306,6 +319,7 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
                                       " (tile, Gaussian) entries, more than one binning pass holds (" +
                                       std::to_string(ctx->entry_limit) + ")");
   const int64_t total = (int64_t)*ctx->h_total;
+  if (ctx->prof) ctx->binned_entries[training ? 1 : 0] += total;
   if ((size_t)total > ctx->sb.cap) {
     size_t cap = ctx->sb.cap;
     size_t want = (size_t)(total * 1.25) + 1024;
@@ -342,13 +356,17 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
   a.blocks = blocks;
   a.rgb = rgb; a.depth = depth; a.alpha = alpha; a.obj = obj;
   a.nB = ctx->nB;
-  a.stats = ctx->prof ? ctx->d_stats : nullptr;
+  a.n = ctx->n;
+  a.slot = ctx->slot;
+  a.n_act = ctx->n_act;
+  a.stats = ctx->prof ? ctx->d_stats + (training ? 4 : 0) : nullptr;
   if (blocks || rgb || depth || alpha || obj) {
-    Phase ph(ctx, NBV_PHASE_COMPOSITE);
-    CKR(check_launch(ctx, launch_composite(a, ctx->c, st, ctx->stage)));
-    ctx->composite_launches++;
+    Phase ph(ctx, training ? NBV_PHASE_TRAIN_COMPOSITE : NBV_PHASE_COMPOSITE);
+    Consts cc = ctx->c;
+    if (compensated) cc.tf32 = 0;
+    CKR(check_launch(ctx, launch_composite(a, cc, st, ctx->stage)));
+    if (ctx->prof) ctx->composite_launches[training ? 1 : 0]++;
   }
-  (void)keep_lists;
   return NBV_OK;
 }
 
@@ -399,8 +417,35 @@ void batched_invalidate(nbv_ctx* ctx) {
   ctx->bt.forced_chunk = 0;
 }
 
+// Projection of every (view, Gaussian) slot, the tile mark of the active
+// subset (when only part of the scene carries a confidence, Eq. 12), every
+// slot's entry count, and the depth keys of the slots that emit entries, in
+// slot order (positions in B.offsets; how many at B.offsets[nv n]).
+int binning_counts(nbv_ctx* ctx, cudaStream_t st) {
+  auto& B = ctx->bt;
+  const int64_t n = ctx->n;
+  const int64_t slots = (int64_t)B.nv * n;
+  const DevScene s = dev_scene(ctx);
+  int l = 0;
+  {
+    Phase ph(ctx, NBV_PHASE_PROJECT);
+    l += launch_project_views(s, ctx->c, B.cams, B.nv, B.pr, st);
+  }
+  Phase ph(ctx, NBV_PHASE_SORT);
+  const uint8_t* mark = nullptr;
+  if (ctx->n_act < n) {
+    l += launch_mark_tiles(B.pr.rect, B.pr.r0, B.pr.r1, ctx->act, ctx->n_act, n, B.nv, B.cams, B.tile_base, B.mark,
+                           B.ntiles, st);
+    mark = B.mark;
+  }
+  l += launch_count_tiles(B.pr.rect, B.pr.r0, B.pr.r1, n, B.nv, B.cams, B.tile_base, mark, B.pr.touched, st);
+  l += launch_compact_depth_keys(B.pr.touched, slots, B.flags, B.offsets, B.scan_tmp, B.pr.zbits, n, B.db.keys[0],
+                                 B.db.vals[0], st);
+  return l;
+}
+
 // Size every buffer of the multi-view path: camera tables, records, and the
-// entry count (one eager projection + scan, one host read-back).
+// entry count (one eager binning count, one host read-back).
 int batched_setup(nbv_ctx* ctx, int v0, int nv) {
   auto& B = ctx->bt;
   cudaStream_t st = ctx->st;
@@ -432,7 +477,9 @@ int batched_setup(nbv_ctx* ctx, int v0, int nv) {
   const size_t slots = (size_t)nv * n;
   CKR(alloc(ctx, &B.pr.r0, slots)); CKR(alloc(ctx, &B.pr.r1, slots)); CKR(alloc(ctx, &B.pr.r2, slots));
   CKR(alloc(ctx, &B.pr.rect, slots)); CKR(alloc(ctx, &B.pr.zbits, slots));
-  CKR(alloc(ctx, &B.pr.touched, slots)); CKR(alloc(ctx, &B.pr.radius, slots));
+  CKR(alloc(ctx, &B.pr.touched, slots));
+  CKR(alloc(ctx, &B.flags, slots));
+  CKR(alloc(ctx, &B.mark, (size_t)nt));
   CKR(alloc(ctx, &B.offsets, slots + 1));
   CKR(alloc(ctx, &B.scan_tmp, scan_scratch_elems((int64_t)slots + 1)));
   CKR(alloc(ctx, &B.db.keys[0], slots)); CKR(alloc(ctx, &B.db.keys[1], slots));
@@ -443,7 +490,7 @@ int batched_setup(nbv_ctx* ctx, int v0, int nv) {
   CKR(alloc(ctx, &B.doffsets, slots + 1));
   CKR(alloc(ctx, &B.ranges, (size_t)nt));
   CKR(alloc(ctx, &B.counter, 1));
-  CKR(alloc(ctx, &B.blocks, slots * ctx->nBp));
+  CKR(alloc(ctx, &B.blocks, (size_t)nv * ctx->n_act * ctx->nBp));
   B.parts_cap = ctx->nsm * 64;      // >= the multi-view gains launch's warps (a few blocks of <= 8 per SM)
   CKR(alloc(ctx, &B.partial, (size_t)nv * B.parts_cap * 3));
   CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)(nc > 0 ? nc : 1) * 3));
@@ -453,9 +500,10 @@ int batched_setup(nbv_ctx* ctx, int v0, int nv) {
   CKR(alloc(ctx, &B.qb.vals[0], (size_t)nt)); CKR(alloc(ctx, &B.qb.vals[1], (size_t)nt));
   CKR(alloc(ctx, &B.qb.hist, radix_hist_elems(nt)));
   B.qb.cap = (size_t)nt;
-  // entry count
-  CKR(check_launch(ctx, launch_project_views(dev_scene(ctx), ctx->c, B.cams, nv, B.pr, st)));
-  CKR(check_launch(ctx, launch_scan_u32(B.pr.touched, B.offsets, (int64_t)slots, B.scan_tmp, st)));
+  // entry count and the number of slots that emit entries (the same on every
+  // replay of the captured pass: they depend only on the scene, the cameras
+  // and the active set, any change of which drops this state)
+  CKR(check_launch(ctx, binning_counts(ctx, st)));
   CKR(check_launch(ctx, launch_sum_u64(B.pr.touched, (int64_t)slots, ctx->d_total64, st)));
   CK(cudaMemcpyAsync(ctx->h_total, B.offsets + slots, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(ctx->h_total64, ctx->d_total64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -467,7 +515,8 @@ int batched_setup(nbv_ctx* ctx, int v0, int nv) {
                                         std::to_string(ctx->entry_limit) + ")");
     return kTooManyEntries;      // nothing was duplicated; the caller splits the views
   }
-  B.total = (int64_t)*ctx->h_total;
+  B.m = (int64_t)*ctx->h_total;
+  B.total = (int64_t)*ctx->h_total64;
   const size_t cap = (size_t)B.total + 1024;
   CKR(alloc(ctx, &B.sb.keys[0], cap)); CKR(alloc(ctx, &B.sb.keys[1], cap));
   CKR(alloc(ctx, &B.sb.vals[0], cap)); CKR(alloc(ctx, &B.sb.vals[1], cap));
@@ -484,29 +533,25 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
   cudaStream_t st = ctx->st;
   const int nv = B.nv;
   const int64_t n = ctx->n;
-  const size_t slots = (size_t)nv * n;
   DevScene s = dev_scene(ctx);
-  CK(cudaMemsetAsync(B.blocks, 0, sizeof(float) * slots * ctx->nBp, st));
-  {
-    Phase ph(ctx, NBV_PHASE_PROJECT);
-    CKR(check_launch(ctx, launch_project_views(s, ctx->c, B.cams, nv, B.pr, st)));
-  }
+  CK(cudaMemsetAsync(B.blocks, 0, sizeof(float) * (size_t)nv * ctx->n_act * ctx->nBp, st));
+  CKR(check_launch(ctx, binning_counts(ctx, st)));
   uint32_t* qv = nullptr;
   const uint32_t* svals = nullptr;
   {
     Phase ph(ctx, NBV_PHASE_SORT);
-    // (view, depth bits) order of the slots first (the slots are in view-major,
-    // Gaussian-index order and every pass is stable), then the entries
-    // duplicated in that order and sorted stably on the tile id alone: each
-    // tile's list comes out in (depth bits, Gaussian index) order
-    CKR(check_launch(ctx, launch_depth_keys(B.pr.zbits, n, nv, B.db.keys[0], B.db.vals[0], st)));
+    // (view, depth bits) order of the slots that emit entries (compacted in
+    // view-major, Gaussian-index order; every pass is stable), then the
+    // entries duplicated in that order and sorted stably on the tile id
+    // alone: each tile's list comes out in (depth bits, Gaussian index) order
     int dw = 0;
-    CKR(check_launch(ctx, launch_radix_sort(B.db, (int64_t)slots, 31 + bits_for(nv), &dw, st)));
+    CKR(check_launch(ctx, launch_radix_sort(B.db, B.m, 31 + bits_for(nv), &dw, st)));
     const uint32_t* order = B.db.vals[dw];
-    CKR(check_launch(ctx, launch_gather_touched(B.pr.touched, order, (int64_t)slots, B.tcount, st)));
-    CKR(check_launch(ctx, launch_scan_u32(B.tcount, B.doffsets, (int64_t)slots, B.scan_tmp, st)));
+    CKR(check_launch(ctx, launch_gather_touched(B.pr.touched, order, B.m, B.tcount, st)));
+    CKR(check_launch(ctx, launch_scan_u32(B.tcount, B.doffsets, B.m, B.scan_tmp, st)));
     uint32_t* k32[2] = {reinterpret_cast<uint32_t*>(B.sb.keys[0]), reinterpret_cast<uint32_t*>(B.sb.keys[1])};
-    CKR(check_launch(ctx, launch_duplicate_sorted(B.pr.rect, B.pr.r0, B.pr.r1, order, n, nv, B.cams, B.tile_base, B.doffsets, k32[0],
+    CKR(check_launch(ctx, launch_duplicate_sorted(B.pr.rect, B.pr.r0, B.pr.r1, order, n, B.m, B.cams, B.tile_base,
+                                                  ctx->n_act < n ? B.mark : nullptr, B.doffsets, k32[0],
                                                   B.sb.vals[0], st)));
     int which = 0;
     CKR(check_launch(ctx, launch_radix_sort32(k32, B.sb.vals, B.sb.hist, B.total, bits_for(B.ntiles), &which, st)));
@@ -521,7 +566,10 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
   {
     Phase ph(ctx, NBV_PHASE_COMPOSITE);
     CK(cudaMemsetAsync(B.counter, 0, sizeof(int), st));
-    if (ctx->prof) ctx->composite_launches++;
+    if (ctx->prof) {
+      ctx->composite_launches[0]++;
+      ctx->binned_entries[0] += B.total;
+    }
     CompositeArgs a{};
     a.cam = B.nv > 0 ? to_dev(ctx->cand[B.v0], ctx->tw, ctx->th) : DevCam{};
     a.r0 = B.pr.r0; a.r1 = B.pr.r1; a.r2 = B.pr.r2;
@@ -538,6 +586,8 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
     a.tile_base = B.tile_base;
     a.cams = B.cams;
     a.n = n;
+    a.slot = ctx->slot;
+    a.n_act = ctx->n_act;
     CKR(check_launch(ctx, launch_composite(a, ctx->c, st, ctx->stage)));   // records of view v start at slot v n
   }
   {
@@ -563,7 +613,7 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
 // configuration caps it.
 int batched_chunk(const nbv_ctx* ctx) {
   const int nc = (int)ctx->cand.size();
-  const double per_view = (double)ctx->n * ((double)ctx->nBp * 4.0 + 128.0);
+  const double per_view = (double)ctx->n * 128.0 + (double)ctx->n_act * (double)ctx->nBp * 4.0;
   int chunk = (int)std::max(1.0, std::floor(32.0e9 / std::max(per_view, 1.0)));
   // slot ids (view n + Gaussian) and the depth keys' view field are 31-bit
   chunk = (int)std::min<int64_t>(chunk, std::max<int64_t>(1, ((int64_t(1) << 31) - 1) / std::max<int64_t>(ctx->n, 1)));
@@ -652,6 +702,7 @@ int ensure_scene_buffers(nbv_ctx* ctx, int64_t n) {
   CKR(alloc(ctx, &ctx->obj, (size_t)n * KC));
   CKR(alloc(ctx, &ctx->mu_sig, n)); CKR(alloc(ctx, &ctx->scale_skip, n)); CKR(alloc(ctx, &ctx->qn, n));
   CKR(alloc(ctx, &ctx->aux, n)); CKR(alloc(ctx, &ctx->p, (size_t)n * KC));
+  CKR(alloc(ctx, &ctx->slot, n)); CKR(alloc(ctx, &ctx->act, n));
   CKR(alloc(ctx, &ctx->pr.r0, n)); CKR(alloc(ctx, &ctx->pr.r1, n)); CKR(alloc(ctx, &ctx->pr.r2, n));
   CKR(alloc(ctx, &ctx->pr.rect, n)); CKR(alloc(ctx, &ctx->pr.zbits, n));
   CKR(alloc(ctx, &ctx->pr.touched, n)); CKR(alloc(ctx, &ctx->pr.radius, n));
@@ -708,7 +759,7 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   if (cfg->stage != 16 && cfg->stage != 32) return NBV_ERR_ARG;
   if (cfg->max_batch_views < 0) return NBV_ERR_ARG;
   if (cfg->criterion < 0 || cfg->criterion > 2) return NBV_ERR_ARG;
-  if (cfg->tf32_contraction != 0 && cfg->tf32_contraction != 1) return NBV_ERR_ARG;
+  if (cfg->tf32_contraction < 0 || cfg->tf32_contraction > 2) return NBV_ERR_ARG;
   const float fl[] = {cfg->alpha_obj, cfg->alpha_opa, cfg->beta_d, cfg->beta_o, cfg->lambda_damp,
                       cfg->near_z, cfg->alpha_min, cfg->alpha_max, cfg->t_min, cfg->dilation, cfg->guard};
   for (float v : fl)
@@ -725,7 +776,9 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   c.lam = cfg->lambda_damp; c.near_z = cfg->near_z; c.alpha_min = cfg->alpha_min;
   c.alpha_max = cfg->alpha_max; c.t_min = cfg->t_min; c.dilation = cfg->dilation; c.guard = cfg->guard;
   c.crit = cfg->criterion;
-  c.tf32 = cfg->tf32_contraction;
+  // automatic: single TF32 products for the log-det criterion (the logarithm
+  // compresses their rounding), error-compensated for the linear trace criteria
+  c.tf32 = cfg->tf32_contraction == 1 || (cfg->tf32_contraction == 0 && cfg->criterion == 0);
   ctx->nB = block_floats(c.K);
   if (cfg->tile_w != 0) { ctx->tw = cfg->tile_w; ctx->th = cfg->tile_h; }
   ctx->stage = cfg->stage;
@@ -762,7 +815,7 @@ void nbv_destroy(nbv_ctx* ctx) {
                   ctx->sb.keys[1], ctx->sb.vals[0], ctx->sb.vals[1], ctx->sb.offsets, ctx->sb.scan_tmp,
                   ctx->sb.hist, ctx->sb.ranges, ctx->blocks, ctx->train_blocks, ctx->partial,
                   ctx->ig_train, ctx->ig_cand, ctx->out4, ctx->d_flags, ctx->d_best_score, ctx->d_err,
-                  ctx->F.L[0], ctx->F.L[1], ctx->F.L[2]};
+                  ctx->F.L[0], ctx->F.L[1], ctx->F.L[2], ctx->slot, ctx->act};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->d_stats) cudaFree(ctx->d_stats);
@@ -770,7 +823,7 @@ void nbv_destroy(nbv_ctx* ctx) {
   {
     auto& B = ctx->bt;
     void* bp[] = {B.cams, B.tile_base, B.tile_view, B.pr.r0, B.pr.r1, B.pr.r2, B.pr.rect, B.pr.zbits,
-                  B.pr.touched, B.pr.radius, B.offsets, B.scan_tmp, B.sb.keys[0], B.sb.keys[1], B.sb.vals[0],
+                  B.pr.touched, B.mark, B.flags, B.offsets, B.scan_tmp, B.sb.keys[0], B.sb.keys[1], B.sb.vals[0],
                   B.sb.vals[1], B.sb.hist, B.qb.keys[0], B.qb.keys[1], B.qb.vals[0], B.qb.vals[1], B.qb.hist,
                   B.ranges, B.counter, B.blocks, B.partial, B.db.keys[0], B.db.keys[1], B.db.vals[0],
                   B.db.vals[1], B.db.hist, B.tcount, B.doffsets};
@@ -871,16 +924,30 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
   {
     Phase ph(ctx, NBV_PHASE_PREP);
     CKR(check_launch(ctx, launch_scene_prep(dev_scene(ctx), ctx->c, target_obj, st)));
+    // the active set (c_g > 0) in Gaussian-index order; the per-view scratch
+    // (touched counts, their scan) holds the flags and slots meanwhile
+    CKR(check_launch(ctx, launch_active_flags(dev_scene(ctx), ctx->pr.touched, st)));
+    CKR(check_launch(ctx, launch_scan_u32(ctx->pr.touched, ctx->sb.offsets, ctx->n, ctx->sb.scan_tmp, st)));
+    CKR(check_launch(ctx, launch_active_scatter(dev_scene(ctx), ctx->pr.touched, ctx->sb.offsets, ctx->slot, ctx->act,
+                                                st)));
+    CK(cudaMemcpyAsync(ctx->h_total, ctx->sb.offsets + ctx->n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   }
+  CK(cudaStreamSynchronize(st));
+  const int64_t n_act = (int64_t)*ctx->h_total;
+  // the multi-view blocks are [view][active slot], and the captured pass's
+  // entry counts depend on the active set
+  if (n_act != ctx->n_act || target_obj != ctx->last_target) batched_invalidate(ctx);
+  ctx->last_target = target_obj;
+  ctx->n_act = n_act;
   CKR(alloc(ctx, &ctx->d_train_cams, (size_t)nt));
   std::vector<DevCam> hc(nt);
   for (int t = 0; t < nt; ++t) hc[t] = to_dev(ctx->train[t], ctx->tw, ctx->th);
   CK(cudaMemcpyAsync(ctx->d_train_cams, hc.data(), sizeof(DevCam) * nt, cudaMemcpyHostToDevice, st));
-  CKR(grow(ctx, &ctx->train_blocks, &ctx->train_blocks_cap, (size_t)nt * ctx->n * ctx->nBp));
-  CK(cudaMemsetAsync(ctx->train_blocks, 0, sizeof(float) * (size_t)nt * ctx->n * ctx->nBp, st));
+  CKR(grow(ctx, &ctx->train_blocks, &ctx->train_blocks_cap, (size_t)nt * ctx->n_act * ctx->nBp));
+  CK(cudaMemsetAsync(ctx->train_blocks, 0, sizeof(float) * (size_t)nt * ctx->n_act * ctx->nBp, st));
   for (int t = 0; t < nt; ++t)
-    CKR(render_view(ctx, ctx->train[t], ctx->train_blocks + (size_t)t * ctx->n * ctx->nBp, nullptr,
-                    nullptr, nullptr, nullptr));
+    CKR(render_view(ctx, ctx->train[t], ctx->train_blocks + (size_t)t * ctx->n_act * ctx->nBp, nullptr,
+                    nullptr, nullptr, nullptr, true, true));   // the factors' sums: error-compensated always
   CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
   {
     Phase ph(ctx, NBV_PHASE_FACTORS);
@@ -904,7 +971,7 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
     }
     if (r < 0) {
       for (int t = 0; t < nt; ++t)
-        CKR(view_gains(ctx, ctx->train[t], ctx->train_blocks + (size_t)t * ctx->n * ctx->nBp, nullptr,
+        CKR(view_gains(ctx, ctx->train[t], ctx->train_blocks + (size_t)t * ctx->n_act * ctx->nBp, nullptr,
                        ctx->ig_train + 3 * t));
     }
   }
@@ -937,7 +1004,7 @@ int nbv_score(nbv_ctx* ctx, float* ig_out, int out_on_device) {
     CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)(nc > 0 ? nc : 1) * 3));
     CKR(grow(ctx, &ctx->out4, &ctx->out4_cap, (size_t)(nc > 0 ? nc : 1) * 4));
     for (int v = 0; v < nc; ++v) {
-      CK(cudaMemsetAsync(ctx->blocks, 0, sizeof(float) * (size_t)ctx->n * ctx->nBp, st));
+      CK(cudaMemsetAsync(ctx->blocks, 0, sizeof(float) * (size_t)ctx->n_act * ctx->nBp, st));
       CKR(render_view(ctx, ctx->cand[v], ctx->blocks, nullptr, nullptr, nullptr, nullptr));
       CKR(view_gains(ctx, ctx->cand[v], ctx->blocks, nullptr, ctx->ig_cand + 3 * v));
     }
@@ -993,8 +1060,10 @@ int nbv_gaussian_gains(nbv_ctx* ctx, int cand, float* delta) {
   if (cand < 0 || cand >= (int)ctx->cand.size()) return fail(ctx, NBV_ERR_ARG, "candidate out of range");
   cudaStream_t st = ctx->st;
   CKR(grow(ctx, &ctx->ig_cand, &ctx->ig_cand_cap, (size_t)ctx->cand.size() * 3));
-  CK(cudaMemsetAsync(ctx->blocks, 0, sizeof(float) * (size_t)ctx->n * ctx->nBp, st));
-  CKR(render_view(ctx, ctx->cand[cand], ctx->blocks, nullptr, nullptr, nullptr, nullptr));
+  CK(cudaMemsetAsync(ctx->blocks, 0, sizeof(float) * (size_t)ctx->n_act * ctx->nBp, st));
+  CK(cudaMemsetAsync(delta, 0, sizeof(float) * 3 * (size_t)ctx->n, st));   // c_g = 0: no gain
+  // single terms are inspected here: error-compensated contraction whatever the mode
+  CKR(render_view(ctx, ctx->cand[cand], ctx->blocks, nullptr, nullptr, nullptr, nullptr, true));
   CKR(view_gains(ctx, ctx->cand[cand], ctx->blocks, delta, ctx->ig_cand + 3 * cand));
   return NBV_OK;
 }
@@ -1088,10 +1157,11 @@ int nbv_set_profiling(nbv_ctx* ctx, int on) {
   for (auto& r : ctx->recs) { ctx->pool.push_back(r.a); ctx->pool.push_back(r.b); }
   ctx->recs.clear();
   for (int i = 0; i < NBV_NUM_PHASES; ++i) { ctx->acc_ms[i] = 0.0; ctx->acc_launch[i] = 0; }
-  ctx->composite_launches = 0;
-  if (!ctx->d_stats) CK(cudaMalloc(reinterpret_cast<void**>(&ctx->d_stats), 4 * sizeof(unsigned long long)));
-  (void)0;                     // the batched path runs eagerly while profiling, from its graph otherwise
-  CK(cudaMemsetAsync(ctx->d_stats, 0, 4 * sizeof(unsigned long long), ctx->st));
+  ctx->composite_launches[0] = ctx->composite_launches[1] = 0;
+  ctx->binned_entries[0] = ctx->binned_entries[1] = 0;
+  if (!ctx->d_stats) CK(cudaMalloc(reinterpret_cast<void**>(&ctx->d_stats), 8 * sizeof(unsigned long long)));
+  // the batched path runs eagerly while profiling, from its graph otherwise
+  CK(cudaMemsetAsync(ctx->d_stats, 0, 8 * sizeof(unsigned long long), ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   ctx->prof = on != 0;
   return NBV_OK;
@@ -1107,15 +1177,17 @@ int nbv_phase_times(nbv_ctx* ctx, double* ms, int64_t* launches) {
   return NBV_OK;
 }
 
-int nbv_work_stats(nbv_ctx* ctx, int64_t* out4) {
-  if (!ctx || !out4) return NBV_ERR_ARG;
+int nbv_work_stats(nbv_ctx* ctx, int which, int64_t* out6) {
+  if (!ctx || !out6 || which < 0 || which > 1) return NBV_ERR_ARG;
   unsigned long long h[4] = {0, 0, 0, 0};
   if (ctx->d_stats) {
-    CK(cudaMemcpyAsync(h, ctx->d_stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(h, ctx->d_stats + 4 * which, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
   }
-  out4[0] = (int64_t)h[0]; out4[1] = (int64_t)h[1]; out4[2] = (int64_t)h[2];
-  out4[3] = ctx->composite_launches;
+  for (int i = 0; i < 4; ++i) out6[i] = (int64_t)h[i];
+  out6[4] = ctx->composite_launches[which];
+  out6[5] = ctx->binned_entries[which];
   return NBV_OK;
 }
 

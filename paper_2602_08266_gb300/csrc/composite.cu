@@ -131,6 +131,26 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   const bool inside = px < cam.W && py < cam.H;
   const float pxc = fa((float)px, 0.5f), pyc = fa((float)py, 0.5f);
 
+  // An information launch over an active subset (a target object, Eq. 12):
+  // the list entries before the first active splat need no information
+  // pass, and a tile without one needs neither pass (a scoring launch
+  // writes no image).
+  __shared__ int s_first;
+  uint32_t first_info = rg.x;
+  if (blocks_v != nullptr && args.n_act < args.n) {
+    if (tid == 0) s_first = (int)rg.y;
+    __syncthreads();
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kTilePix) {
+      const uint32_t i = b0 + tid;
+      if (i < rg.y && args.slot[args.vals[i]] >= 0) atomicMin(&s_first, (int)i);
+      if (__syncthreads_or(s_first < (int)rg.y)) break;
+    }
+    first_info = (uint32_t)s_first;
+    if (first_info >= rg.y && args.rgb == nullptr && args.depth == nullptr && args.alpha == nullptr &&
+        args.obj == nullptr)
+      return;
+  }
+
   // ------------------------------------------------------------- pass 1
   float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
   float2 O2[KCM / 2];                       // object channels in pairs (packed f32x2 FMA)
@@ -229,6 +249,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
 #pragma unroll
   for (int q = 0; q < KCM / 2; ++q) Ro2[q] = make_float2(0.0f, 0.0f);
   float Tb = T;   // transmittance after the splat being visited
+  uint32_t n_ig = 0;  // (pixel, active splat) pairs of the information pass
   // Per-warp contraction buffers: row = pixel (lane). U holds the pixel's
   // scalars [q_rgb a^2, q_d a^2, q_o a^2 | w s_c a (3), w s_D a, w (s_j - s_0) a
   // (K) | w^2] (a = alpha, or 0 when clamped); V holds the splat geometry
@@ -269,8 +290,8 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       }
       ex[mt][i] = e;
     }
-  for (uint32_t end = last_max; end > rg.x;) {
-    const uint32_t start = (end - rg.x > (uint32_t)kBatch) ? end - kBatch : rg.x;
+  for (uint32_t end = last_max; end > first_info;) {
+    const uint32_t start = (end - first_info > (uint32_t)kBatch) ? end - kBatch : first_info;
     const int nj = (int)(end - start);
     __syncthreads();
     if (tid < nj) {
@@ -278,7 +299,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       s0[tid] = args.r0[rec_off + g];
       s1[tid] = args.r1[rec_off + g];
       s2[tid] = args.r2[rec_off + g];
-      sid[tid] = (int)g;
+      sid[tid] = args.slot[g];          // block slot, or -1: only extends the suffix sums
       touched[tid] = 0;
     }
     for (int i = tid; i < nj * KCP; i += kTilePix) {
@@ -299,6 +320,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       }
       const unsigned any = __ballot_sync(0xffffffffu, act);
       if (any == 0u) continue;
+      const bool info = sid[j] >= 0;     // the same for the whole tile
       // active pixels are compacted into the first rows of the warp's buffers
       const int nact = __popc(any);
       const int nks = (nact + 7) >> 3;
@@ -311,6 +333,8 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         const float inv_om = __fdividef(1.0f, 1.0f - alpha);
         const float Ti = Tb * inv_om;
         const float w = alpha * Ti;
+        const float2* pj2 = reinterpret_cast<const float2*>(sp + j * KCP);
+        if (info) {
         const float ae = clamped ? 0.0f : alpha;
         const float wa = w * ae;
         // d out / d alpha_i = T_i x_i - R_i / (1 - alpha_i)
@@ -318,7 +342,6 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         const float sr1 = Ti * a2.y - Rr1 * inv_om;
         const float sr2 = Ti * a2.z - Rr2 * inv_om;
         const float sd = Ti * a2.w - Rd * inv_om;
-        const float2* pj2 = reinterpret_cast<const float2*>(sp + j * KCP);
         // s_k = T_i p_k - R_k / (1 - alpha), two channels per packed FMA; the
         // residual channel 0 also carries -T_final / (1 - alpha)
         const float2 Ti2 = make_float2(Ti, Ti), ni2 = make_float2(-inv_om, -inv_om);
@@ -359,6 +382,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
           Vr[(24 + m) * kCS] = uvst<kSplit>(v[m]);
         }
         Vr[30 * kCS] = 1.0f;
+        }
         // extend the suffix sums with this splat and step T back
         Rr0 += w * a2.x; Rr1 += w * a2.y; Rr2 += w * a2.z; Rd += w * a2.w;
         const float2 w2 = make_float2(w, w);
@@ -367,6 +391,8 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
           if (2 * q < KC) Ro2[q] = __ffma2_rn(w2, pj2[q], Ro2[q]);
         Tb = Ti;
       }
+      if (!info) continue;
+      n_ig += act ? 1u : 0u;
       if (lane == 0) touched[j] = 1;
       __syncwarp();
       float dq[3][4], dxo[MTBM][4];
@@ -438,6 +464,15 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
     }
     end = start;
   }
+  if (args.stats) {
+    __shared__ unsigned long long s_ig;
+    if (tid == 0) s_ig = 0;
+    __syncthreads();
+    const unsigned wsum = __reduce_add_sync(0xffffffffu, n_ig);
+    if (lane == 0 && wsum) atomicAdd(&s_ig, (unsigned long long)wsum);
+    __syncthreads();
+    if (tid == 0 && s_ig) atomicAdd(&args.stats[3], s_ig);
+  }
 }
 
 template <int KCM, int kBatch, bool kSplit>
@@ -460,7 +495,7 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
     const int v = args.tile_view[gt];
     const DevCam cam = args.cams[v];
     composite_tile<KCM, kBatch, kSplit>(args, c, cam, (int)(gt - args.tile_base[v]), args.ranges[gt],
-                        args.blocks + (size_t)v * args.n * ((args.nB + 3) & ~3), (size_t)v * args.n, smem);
+                        args.blocks + (size_t)v * args.n_act * ((args.nB + 3) & ~3), (size_t)v * args.n, smem);
   }
 }
 

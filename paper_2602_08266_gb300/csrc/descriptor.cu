@@ -49,7 +49,9 @@ __global__ void k_descriptor_hist(DevScene s, float near_z, const DevCam* __rest
     int id = __float_as_int(ax.w);          // the most probable object id, stored as int bits
     id = id < 0 ? 0 : (id >= kObjBins ? kObjBins - 1 : id);
     float obs = 0.0f;                       // sum over training views of sum_pixels w^2
-    for (int t = 0; t < n_train; ++t) obs += tblocks[((size_t)t * s.n + g) * nBp + kOffW2];
+    const int sl = s.slot[g];            // training blocks exist for active Gaussians only
+    if (sl >= 0)
+      for (int t = 0; t < n_train; ++t) obs += tblocks[((size_t)t * s.n_act + sl) * nBp + kOffW2];
     const float cov = __fdiv_rn(cs, fa(1.0f, obs));
     for (int q = 0; q < nvc; ++q) {
       const DevCam& c = cams[v0 + q];

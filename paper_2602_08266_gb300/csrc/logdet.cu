@@ -851,7 +851,8 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
   float* XG = fb + y.off_XG;
   float* xs = fb + y.off_xs;
   const int K = c.K, KC = c.KC;
-  for (int64_t g = (int64_t)blockIdx.x * nw + warp; g < s.n; g += (int64_t)gridDim.x * nw) {
+  for (int64_t sl = (int64_t)blockIdx.x * nw + warp; sl < s.n_act; sl += (int64_t)gridDim.x * nw) {
+    const int64_t g = s.act[sl];          // training blocks and factors are stored by active slot
     const float cg = s.aux[g].y;
     const float* p = s.p + (size_t)g * KC;
     for (int i = lane; i < y.nt0; i += 32) H0[i] = 0.0f;
@@ -865,7 +866,7 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
         const int t = t0 + lane;
         bool seen = false;
         if (lane < kTrainChunk && t < n_train) {
-          seen = blocks[((size_t)t * s.n + g) * nBp + kOffW2] != 0.0f;
+          seen = blocks[((size_t)t * s.n_act + sl) * nBp + kOffW2] != 0.0f;
           if (seen) compute_gjac(s, c, cams[t], g, Jw[lane]);
         }
         unsigned todo = __ballot_sync(0xffffffffu, seen);
@@ -873,7 +874,7 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
         while (todo) {
           const int src = __ffs(todo) - 1;
           todo &= todo - 1;
-          const float* blk = blocks + ((size_t)(t0 + src) * s.n + g) * nBp;
+          const float* blk = blocks + ((size_t)(t0 + src) * s.n_act + sl) * nBp;
           w2sum += blk[kOffW2];
           add_view_blocks(Jw[src], blk, c, H0, H1, H2, GB, XG, lane);
         }
@@ -912,7 +913,7 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
     }
     if (c.crit == 2) {
       // T-optimality has no training prior: the gains read L~ = I
-      float* L0g = F.L[0] + (size_t)g * rgb_L_size(c.nb);
+      float* L0g = F.L[0] + (size_t)sl * rgb_L_size(c.nb);
       const int T = rgb_tri_nb(c.nb);
       for (int i = lane; i < rgb_L_size(c.nb); i += 32) {
         float v = 0.0f;
@@ -929,7 +930,7 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
       }
       for (int f = 1; f < 3; ++f) {
         const int nt = f == 1 ? y.nt1 : y.nt2;
-        float* Lg = F.L[f] + (size_t)g * nt;
+        float* Lg = F.L[f] + (size_t)sl * nt;
         for (int i = lane; i < nt; i += 32) {
           int r, r2;
           tri_decode(i, r, r2);
@@ -939,8 +940,8 @@ __global__ void k_build_factors(DevScene s, Consts c, const DevCam* __restrict__
       __syncwarp();
       continue;
     }
-    factorise_all(y, cg, c, H0, H1, H2, Dw, fb, F.L[0] + (size_t)g * rgb_L_size(c.nb), F.L[1] + (size_t)g * y.nt1,
-                  F.L[2] + (size_t)g * y.nt2, err, lane);
+    factorise_all(y, cg, c, H0, H1, H2, Dw, fb, F.L[0] + (size_t)sl * rgb_L_size(c.nb), F.L[1] + (size_t)sl * y.nt1,
+                  F.L[2] + (size_t)sl * y.nt2, err, lane);
   }
 }
 
@@ -1120,15 +1121,16 @@ __device__ void z_rgb_warp(const GJac& J, const float* Lt, int nb, float* Z, int
   __syncwarp();
 }
 
+// fs: the Gaussian's active slot (the row of its training factors).
 template <int F, int U>
-__device__ float output_gain(const GJac& J, const Consts& c, const float* p, const Factors& Fa, int64_t g,
+__device__ float output_gain(const GJac& J, const Consts& c, const float* p, const Factors& Fa, int64_t fs,
                              const float* blk, float cg, float* Ls, float* Y, float* Z, float* W,
                              float* Bm, float* G, int lane) {
   const int l = out_l(F, c), u = out_u(F, c), nt = l * (l + 1) / 2;
   if (F == 0) {
-    z_rgb_warp(J, Fa.L[0] + (size_t)g * rgb_L_size(c.nb), c.nb, Z, lane);   // ends with __syncwarp
+    z_rgb_warp(J, Fa.L[0] + (size_t)fs * rgb_L_size(c.nb), c.nb, Z, lane);   // ends with __syncwarp
   } else {
-    const float* Lg = Fa.L[F] + (size_t)g * nt;   // rows read straight from global memory (L1)
+    const float* Lg = Fa.L[F] + (size_t)fs * nt;   // rows read straight from global memory (L1)
     build_Y(F, J, c, p, Y, lane);                  // ends with __syncwarp
     for (int i = lane; i < l; i += 32) z_row<F, U>(i, u, Lg, Y, Z);
     __syncwarp();
@@ -1157,7 +1159,7 @@ __global__ void __launch_bounds__(128, 3) k_view_gains(DevScene s, Consts c, Dev
   const int nB = block_floats(c.K), nBp = (nB + 3) & ~3;
   // multi-view launches: view = blockIdx.y (its own blocks and partial sums)
   const DevCam cam = cams ? cams[blockIdx.y] : cam1;
-  blocks += (size_t)blockIdx.y * s.n * nBp;
+  blocks += (size_t)blockIdx.y * s.n_act * nBp;
   partial += (size_t)blockIdx.y * gridDim.x * nw * 3;
   const size_t per_warp = 2 * (size_t)lu_max + 3 * (size_t)uu_max + 32 * (sizeof(GJac) / 4) + 4;
   float* Ls = nullptr;
@@ -1168,14 +1170,15 @@ __global__ void __launch_bounds__(128, 3) k_view_gains(DevScene s, Consts c, Dev
   float* G = Bm + uu_max;
   GJac* Jw = reinterpret_cast<GJac*>(G + uu_max);     // one per lane
   double acc3[3] = {0.0, 0.0, 0.0};
-  const int64_t nbatch = (s.n + 31) / 32;
+  const int64_t nbatch = (s.n_act + 31) / 32;
   const int64_t gw = (int64_t)blockIdx.x * nw + warp, nwarps = (int64_t)gridDim.x * nw;
   for (int64_t bt = gw; bt < nbatch; bt += nwarps) {
-    // every lane takes one Gaussian of the batch: contributes? projection Jacobians
-    const int64_t gl = bt * 32 + lane;
+    // every lane takes one active slot of the batch: contributes? projection Jacobians
+    const int64_t sll = bt * 32 + lane;
     bool mine = false;
-    if (gl < s.n) {
-      mine = s.aux[gl].y > 0.0f && blocks[(size_t)gl * nBp + kOffW2] != 0.0f;
+    if (sll < s.n_act) {
+      const int64_t gl = s.act[sll];
+      mine = blocks[(size_t)sll * nBp + kOffW2] != 0.0f;
       if (mine) compute_gjac(s, c, cam, gl, Jw[lane]);
       else if (delta) { delta[3 * gl] = 0.0f; delta[3 * gl + 1] = 0.0f; delta[3 * gl + 2] = 0.0f; }
     }
@@ -1184,14 +1187,15 @@ __global__ void __launch_bounds__(128, 3) k_view_gains(DevScene s, Consts c, Dev
     while (todo) {
       const int src = __ffs(todo) - 1;
       todo &= todo - 1;
-      const int64_t g = bt * 32 + src;
+      const int64_t sl = bt * 32 + src;
+      const int64_t g = s.act[sl];
       const float cg = s.aux[g].y;
-      const float* blk = blocks + (size_t)g * nBp;
+      const float* blk = blocks + (size_t)sl * nBp;
       const float* p = s.p + (size_t)g * c.KC;
       const GJac& J = Jw[src];
-      const float d0 = output_gain<0, 9>(J, c, p, F, g, blk, cg, Ls, Y, Z, W, Bm, G, lane);
-      const float d1 = output_gain<1, 7>(J, c, p, F, g, blk, cg, Ls, Y, Z, W, Bm, G, lane);
-      const float d2 = output_gain<2, UO>(J, c, p, F, g, blk, cg, Ls, Y, Z, W, Bm, G, lane);
+      const float d0 = output_gain<0, 9>(J, c, p, F, sl, blk, cg, Ls, Y, Z, W, Bm, G, lane);
+      const float d1 = output_gain<1, 7>(J, c, p, F, sl, blk, cg, Ls, Y, Z, W, Bm, G, lane);
+      const float d2 = output_gain<2, UO>(J, c, p, F, sl, blk, cg, Ls, Y, Z, W, Bm, G, lane);
       if (lane == 0) {
         if (delta) { delta[3 * g] = d0; delta[3 * g + 1] = d1; delta[3 * g + 2] = d2; }
         acc3[0] += d0; acc3[1] += d1; acc3[2] += d2;
@@ -1598,18 +1602,18 @@ __global__ void __launch_bounds__(256, 1) k_gains_gm(DevScene s, Consts c, const
   const DevCam* camp = cams + (vok ? v : 0);
   double acc[3] = {0.0, 0.0, 0.0};
   const int slot = blockIdx.x * nw + warp;
-  for (int64_t g = slot; g < s.n; g += (int64_t)gridDim.x * nw) {
+  for (int64_t sl = slot; sl < s.n_act; sl += (int64_t)gridDim.x * nw) {
+    const int64_t g = s.act[sl];                       // active: c_g > 0
     const float cg = s.aux[g].y;
-    if (!(cg > 0.0f)) continue;                        // warp-uniform
-    const float* blk = blocks + ((size_t)v * s.n + g) * nBp;
+    const float* blk = blocks + ((size_t)v * s.n_act + sl) * nBp;
     const bool mine = vok && blk[kOffW2] != 0.0f;
     const unsigned todo_all = __ballot_sync(0xffffffffu, mine);
     if (todo_all == 0u) continue;
     // stage L~ of the three outputs
     {
-      const float* g0 = F.L[0] + (size_t)g * y.nt0;
-      const float* g1 = F.L[1] + (size_t)g * y.nt1;
-      const float* g2 = F.L[2] + (size_t)g * y.nt2;
+      const float* g0 = F.L[0] + (size_t)sl * y.nt0;
+      const float* g1 = F.L[1] + (size_t)sl * y.nt1;
+      const float* g2 = F.L[2] + (size_t)sl * y.nt2;
       for (int i = lane; i < y.nt0; i += 32) L0[i] = g0[i];
       for (int i = lane; i < y.nt1; i += 32) L1[i] = g1[i];
       for (int i = lane; i < y.nt2; i += 32) L2[i] = g2[i];
@@ -1659,7 +1663,7 @@ __global__ void __launch_bounds__(256, 1) k_gains_gm(DevScene s, Consts c, const
     while (todo) {
       const int src = __ffs(todo) - 1;
       todo &= todo - 1;
-      const float* bsrc = blocks + ((size_t)(v0 + src) * s.n + g) * nBp;
+      const float* bsrc = blocks + ((size_t)(v0 + src) * s.n_act + sl) * nBp;
       for (int i = lane; i < l2; i += 32) {           // Z_g = L~[:, :11] M_g^T
         float zr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         const int kg = i < kNG - 1 ? i : kNG - 1;
@@ -1844,7 +1848,8 @@ int launch_build_factors(const DevScene& s, const Consts& c, const DevCam* cams,
   nw = nw < 1 ? 1 : (nw > 12 ? 12 : nw);
   const size_t sm = pw * nw;
   cudaFuncSetAttribute(k_build_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int64_t nblk = (s.n + nw - 1) / nw;
+  if (s.n_act <= 0) return 0;
+  const int64_t nblk = (s.n_act + nw - 1) / nw;
   const int64_t gcap = (int64_t)device_sm_count() * 32;
   const int grid = (int)(nblk < gcap ? nblk : gcap);
   k_build_factors<<<grid, 32 * nw, sm, st>>>(s, c, cams, blocks, n_train, f, d_err, y);
@@ -1876,7 +1881,7 @@ int launch_view_gains(const DevScene& s, const Consts& c, const DevCam& cam, con
   const size_t pw = gains_smem_per_warp(d);
   const int nw = warps_for(pw);
   const size_t sm = pw * nw;
-  const int64_t nblk = ((s.n + 31) / 32 + nw - 1) / nw;
+  const int64_t nblk = ((s.n_act + 31) / 32 + nw - 1) / nw;
   int grid = (int)(nblk < nblocks_cap ? nblk : nblocks_cap);
   if (grid < 1) grid = 1;
   *nblocks_used = grid * nw;        // one partial sum per warp
@@ -1892,7 +1897,7 @@ int launch_views_gains(const DevScene& s, const Consts& c, const DevCam* cams, i
   const size_t pw = gains_smem_per_warp(d);
   const int nw = warps_for(pw);
   const size_t sm = pw * nw;
-  const int64_t nblk = ((s.n + 31) / 32 + nw - 1) / nw;
+  const int64_t nblk = ((s.n_act + 31) / 32 + nw - 1) / nw;
   int grid = (int)(nblk < parts_cap / nw ? nblk : parts_cap / nw);
   if (grid < 1) grid = 1;
   *nparts = grid * nw;
@@ -1913,7 +1918,7 @@ int launch_views_gains_gm(const DevScene& s, const Consts& c, const DevCam* cams
   if (nw > 8) nw = 8;
   const int nsm = device_sm_count();
   const int nchunk = (nv + 31) / 32;
-  int grid = (int)((s.n + nw - 1) / nw);
+  int grid = (int)((s.n_act + nw - 1) / nw);
   const int want = (nsm * 4 + nchunk - 1) / nchunk;   // a few blocks per SM over all chunks
   if (grid > want) grid = want;
   if (grid * nw > parts_cap) grid = parts_cap / nw;

@@ -68,6 +68,13 @@ struct DevScene {
   float4* qn;                // normalised quaternion (w,x,y,z)
   float4* aux;               // {power threshold of alpha_max, c_g, |q|, argmax id}
   float* p;                  // softmax(o) [n][KC]
+  // Active set: the Gaussians with c_g > 0 (all of them without a target;
+  // those of the target object under Eq. 12). Information blocks, training
+  // factors and gains exist only for these, in slot order: a Gaussian with
+  // c_g = 0 adds log det(H + 0) - log det H = 0 to every gain.
+  const int* slot;           // [n] slot of Gaussian g, or -1
+  const int* act;            // [n_act] Gaussian of slot s
+  int64_t n_act;
 };
 
 // Per-view projection (structure of arrays).
@@ -88,6 +95,11 @@ int device_sm_count();
 // ------------------------------------------------------------ kernels (host wrappers)
 // Each wrapper launches on `st` and returns the number of launches issued.
 int launch_scene_prep(const DevScene& s, const Consts& c, int target, cudaStream_t st);
+// Active-set flags (c_g > 0) of the n Gaussians into flags; after their
+// exclusive scan `offsets` [n + 1], launch_active_scatter writes slot / act.
+int launch_active_flags(const DevScene& s, uint32_t* flags, cudaStream_t st);
+int launch_active_scatter(const DevScene& s, const uint32_t* flags, const uint32_t* offsets, int* slot, int* act,
+                          cudaStream_t st);
 // Non-finite parameters (bit 0) and zero quaternions (bit 1) of loaded Gaussians, OR-ed into *flag.
 int launch_check_inputs(const float* mu, const float* logs, const float* q, const float* rho, const float* sh,
                         const float* obj, int64_t n, int nsh, int KC, int* flag, cudaStream_t st);
@@ -126,10 +138,25 @@ int launch_radix_sort32(uint32_t* keys[2], uint32_t* vals[2], uint32_t* hist, in
 // Multi-view depth order: keys (view << 31 | 31 low z bits), vals = slot v n + g.
 int launch_depth_keys(const uint32_t* zbits, int64_t n, int nv, uint64_t* keys, uint32_t* vals, cudaStream_t st);
 int launch_gather_touched(const uint32_t* touched, const uint32_t* order, int64_t m, uint32_t* out, cudaStream_t st);
-// Entries of the slots in `order`: 32-bit global tile keys and Gaussian indices.
+// Entries of the m slots in `order` (n Gaussians per view): 32-bit global
+// tile keys and Gaussian indices; with a tile mark, only marked tiles.
 int launch_duplicate_sorted(const int4* rect, const float4* r0, const float4* r1, const uint32_t* order, int64_t n,
-                            int nv, const DevCam* cams, const uint32_t* tile_base, const uint32_t* offsets,
-                            uint32_t* keys, uint32_t* vals, cudaStream_t st);
+                            int64_t m, const DevCam* cams, const uint32_t* tile_base, const uint8_t* mark,
+                            const uint32_t* offsets, uint32_t* keys, uint32_t* vals, cudaStream_t st);
+// mark [ntiles] (global tile ids; zeroed first) = 1 where a splat of the
+// active set passes tile_hit: the only tiles whose lists matter for the
+// information gain when only part of the scene carries a confidence.
+int launch_mark_tiles(const int4* rect, const float4* r0, const float4* r1, const int* act, int64_t n_act, int64_t n,
+                      int nv, const DevCam* cams, const uint32_t* tile_base, uint8_t* mark, int64_t ntiles,
+                      cudaStream_t st);
+// touched [nv n] = entries of every slot (rectangle tiles passing tile_hit,
+// marked ones only when mark != NULL).
+int launch_count_tiles(const int4* rect, const float4* r0, const float4* r1, int64_t n, int nv, const DevCam* cams,
+                       const uint32_t* tile_base, const uint8_t* mark, uint32_t* touched, cudaStream_t st);
+// Depth keys (view << 31 | z bits) and slot values of the slots with
+// touched > 0, in slot order (flags / pos / scan_tmp: scratch of m words).
+int launch_compact_depth_keys(const uint32_t* touched, int64_t m, uint32_t* flags, uint32_t* pos, uint32_t* scan_tmp,
+                              const uint32_t* zbits, int64_t n, uint64_t* keys, uint32_t* vals, cudaStream_t st);
 int launch_ranges32(const uint32_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st);
 int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaStream_t st);
 int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st);
@@ -213,7 +240,9 @@ struct CompositeArgs {
   const int* tile_view;        // global tile -> view
   const uint32_t* tile_base;   // view -> first global tile
   const DevCam* cams;          // per view
-  int64_t n;                   // Gaussians (stride of the per-view block arrays)
+  int64_t n;                   // Gaussians (stride of the per-view record arrays)
+  const int* slot;             // Gaussian -> block slot or -1 (no information block)
+  int64_t n_act;               // active Gaussians (stride of the per-view block arrays)
 };
 // stage = Gaussians staged in shared memory per round (16 or 32).
 int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage = 32);

@@ -112,7 +112,11 @@ __device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, floa
   (void)kPi;
 }
 
-// Project Gaussian g into camera cam; the records go to slot o of pr.
+// Project Gaussian g into camera cam; the records go to slot o of pr. With
+// kCount (one view at a time) also the radius and the number of rectangle
+// tiles that pass tile_hit; the multi-view path counts them in a separate
+// warp-cooperative pass (k_count_tiles).
+template <bool kCount>
 __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, const DevCam& cam, int64_t g,
                                             const DevProj& pr, size_t o) {
   const float4 ms = s.mu_sig[g];
@@ -120,9 +124,11 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   const float4 qq = s.qn[g];
   const float4 ax = s.aux[g];
   const float* R = cam.R;
-  pr.touched[o] = 0u;
+  if (kCount) {
+    pr.touched[o] = 0u;
+    pr.radius[o] = 0.0f;
+  }
   pr.rect[o] = make_int4(-1, -1, -1, -1);
-  pr.radius[o] = 0.0f;
   pr.zbits[o] = 0u;
   // ---- key path: correctly rounded single precision, fixed order
   const float tx = fa(fa(fa(fm(R[0], ms.x), fm(R[1], ms.y)), fm(R[2], ms.z)), cam.t[0]);
@@ -198,37 +204,61 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   const float il = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
   float Y[16];
   sh_eval(c.deg, dv[0] * il, dv[1] * il, dv[2] * il, Y);
+  // SH coefficients as 16-byte vector loads: 3 nb floats per Gaussian start
+  // 16-byte aligned when 3 nb is a multiple of 4 (SH degree 1 and 3)
   const float* shg = s.sh + (size_t)g * c.nb * 3;
-  float rgb[3];
+  float rgb[3] = {0.5f, 0.5f, 0.5f};
+  if ((c.nb * 3) % 4 == 0) {
+    const float4* sh4 = reinterpret_cast<const float4*>(shg);
+    for (int q = 0; q < (c.nb * 3) / 4; ++q) {
+      const float4 v4 = __ldg(sh4 + q);
+      const float e[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-  for (int ch = 0; ch < 3; ++ch) {
-    float acc = 0.5f;
-    for (int k = 0; k < c.nb; ++k) acc += Y[k] * shg[3 * k + ch];
-    rgb[ch] = fmaxf(acc, 0.0f);
+      for (int u = 0; u < 4; ++u) {
+        const int idx = 4 * q + u, k = idx / 3, ch = idx - 3 * k;
+        rgb[ch] += Y[k] * e[u];
+      }
+    }
+  } else {
+    for (int k = 0; k < c.nb; ++k)
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) rgb[ch] += Y[k] * shg[3 * k + ch];
   }
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(rgb[ch], 0.0f);
   pr.r0[o] = make_float4(mx, my, ss.w, ax.x);
   pr.r1[o] = make_float4(A, B, C, ms.w);
   pr.r2[o] = make_float4(rgb[0], rgb[1], rgb[2], tz);
   pr.rect[o] = make_int4(x0, x1, y0, y1);
   pr.zbits[o] = __float_as_uint(tz);
-  pr.radius[o] = r;
-  uint32_t hits = 0;
-  for (int tyi = y0; tyi < y1; ++tyi)
-    for (int txi = x0; txi < x1; ++txi) hits += tile_hit(A, B, C, mx, my, ss.w, txi, tyi, cam.TW, cam.TH) ? 1u : 0u;
-  pr.touched[o] = hits;
+  if (kCount) {
+    pr.radius[o] = r;
+    uint32_t hits = 0;
+    for (int tyi = y0; tyi < y1; ++tyi)
+      for (int txi = x0; txi < x1; ++txi)
+        hits += tile_hit(A, B, C, mx, my, ss.w, txi, tyi, cam.TW, cam.TH) ? 1u : 0u;
+    pr.touched[o] = hits;
+  }
 }
 
 __global__ void k_project(DevScene s, Consts c, DevCam cam, DevProj pr) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= s.n) return;
-  project_one(s, c, cam, g, pr, (size_t)g);
+  project_one<true>(s, c, cam, g, pr, (size_t)g);
 }
 
-// All views at once: thread g projects Gaussian g into every view, slot v n + g.
-__global__ void k_project_views(DevScene s, Consts c, const DevCam* __restrict__ cams, int nv, DevProj pr) {
+// All views at once, one thread per (view, Gaussian): view blockIdx.y, slot
+// v n + g; consecutive threads take consecutive Gaussians of one view, so
+// every record load and store is coalesced and the camera is the block's.
+__global__ void __launch_bounds__(256) k_project_views(DevScene s, Consts c, const DevCam* __restrict__ cams,
+                                                       DevProj pr) {
+  __shared__ DevCam cam;
+  const int v = blockIdx.y;
+  if (threadIdx.x == 0) cam = cams[v];
+  __syncthreads();
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= s.n) return;
-  for (int v = 0; v < nv; ++v) project_one(s, c, cams[v], g, pr, (size_t)v * s.n + g);
+  project_one<false>(s, c, cam, g, pr, (size_t)v * s.n + g);
 }
 
 }  // namespace
@@ -236,8 +266,8 @@ __global__ void k_project_views(DevScene s, Consts c, const DevCam* __restrict__
 int launch_project_views(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const DevProj& pr,
                          cudaStream_t st) {
   if (s.n <= 0 || nv <= 0) return 0;
-  const int bs = 128;
-  k_project_views<<<(unsigned)((s.n + bs - 1) / bs), bs, 0, st>>>(s, c, cams, nv, pr);
+  const int bs = 256;
+  k_project_views<<<dim3((unsigned)((s.n + bs - 1) / bs), (unsigned)nv), bs, 0, st>>>(s, c, cams, pr);
   return 1;
 }
 
@@ -273,6 +303,35 @@ int launch_check_inputs(const float* mu, const float* logs, const float* q, cons
   const int64_t cap = (int64_t)device_sm_count() * 16;
   if (nb > cap) nb = cap;
   k_check_inputs<<<(unsigned)nb, bs, 0, st>>>(mu, logs, q, rho, sh, obj, n, nsh, KC, flag);
+  return 1;
+}
+
+namespace {
+__global__ void k_active_flags(DevScene s, uint32_t* __restrict__ flags) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g < s.n) flags[g] = s.aux[g].y > 0.0f ? 1u : 0u;
+}
+
+__global__ void k_active_scatter(DevScene s, const uint32_t* __restrict__ flags, const uint32_t* __restrict__ off,
+                                 int* __restrict__ slot, int* __restrict__ act) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= s.n) return;
+  const bool on = flags[g] != 0u;
+  slot[g] = on ? (int)off[g] : -1;
+  if (on) act[off[g]] = (int)g;
+}
+}  // namespace
+
+int launch_active_flags(const DevScene& s, uint32_t* flags, cudaStream_t st) {
+  if (s.n <= 0) return 0;
+  k_active_flags<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(s, flags);
+  return 1;
+}
+
+int launch_active_scatter(const DevScene& s, const uint32_t* flags, const uint32_t* offsets, int* slot, int* act,
+                          cudaStream_t st) {
+  if (s.n <= 0) return 0;
+  k_active_scatter<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(s, flags, offsets, slot, act);
   return 1;
 }
 

@@ -273,8 +273,9 @@ __global__ void k_gather_touched(const uint32_t* __restrict__ touched, const uin
 __global__ void k_duplicate_sorted(const int4* __restrict__ rect, const float4* __restrict__ r0,
                                    const float4* __restrict__ r1, const uint32_t* __restrict__ order, int64_t n,
                                    int64_t m, const DevCam* __restrict__ cams,
-                                   const uint32_t* __restrict__ tile_base, const uint32_t* __restrict__ offsets,
-                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                   const uint32_t* __restrict__ tile_base, const uint8_t* __restrict__ mark,
+                                   const uint32_t* __restrict__ offsets, uint32_t* __restrict__ keys,
+                                   uint32_t* __restrict__ vals) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   int4 r = make_int4(-1, -1, -1, -1);
@@ -315,7 +316,8 @@ __global__ void k_duplicate_sorted(const int4* __restrict__ rect, const float4* 
     uint32_t wo = os;
     for (int t0 = 0; t0 < cnt; t0 += 32) {
       const int tx = rx + qx, ty = rz + qy;
-      const bool hit = t0 + lane < cnt && tile_hit(A, B, C, mx, my, thr, tx, ty, tw, th);
+      const bool hit = t0 + lane < cnt && (mark == nullptr || mark[bs + (uint32_t)(ty * gx + tx)] != 0) &&
+                       tile_hit(A, B, C, mx, my, thr, tx, ty, tw, th);
       const unsigned mk = __ballot_sync(0xffffffffu, hit);
       if (hit) {
         const uint32_t at = wo + (uint32_t)__popc(mk & ((1u << lane) - 1u));
@@ -331,6 +333,134 @@ __global__ void k_duplicate_sorted(const int4* __restrict__ rect, const float4* 
       }
     }
   }
+}
+
+// The tiles (global ids) where a splat of the active set can pass its skip
+// test: its rectangle's tiles that pass tile_hit, one lane per active
+// (view, slot) pair, each rectangle walked by the whole warp.
+__global__ void k_mark_tiles(const int4* __restrict__ rect, const float4* __restrict__ r0,
+                             const float4* __restrict__ r1, const int* __restrict__ act, int64_t n_act, int64_t n,
+                             int nv, const DevCam* __restrict__ cams, const uint32_t* __restrict__ tile_base,
+                             uint8_t* __restrict__ mark) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int4 r = make_int4(-1, -1, -1, -1);
+  uint32_t base = 0;
+  int GX = 0, TW = 1, TH = 1;
+  float4 a0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), a1 = a0;
+  if (i < n_act * nv) {
+    const int v = (int)(i / n_act);
+    const size_t slot = (size_t)v * n + act[i - (int64_t)v * n_act];
+    r = rect[slot];
+    if (r.x >= 0) {
+      GX = cams[v].GX; TW = cams[v].TW; TH = cams[v].TH;
+      base = tile_base[v];
+      a0 = r0[slot];
+      a1 = r1[slot];
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  for (int s = 0; s < 32; ++s) {
+    const int rx = __shfl_sync(0xffffffffu, r.x, s), ry = __shfl_sync(0xffffffffu, r.y, s);
+    const int rz = __shfl_sync(0xffffffffu, r.z, s), rw = __shfl_sync(0xffffffffu, r.w, s);
+    const uint32_t bs = __shfl_sync(0xffffffffu, base, s);
+    const int gx = __shfl_sync(0xffffffffu, GX, s);
+    const int tw = __shfl_sync(0xffffffffu, TW, s), th = __shfl_sync(0xffffffffu, TH, s);
+    const float mx = __shfl_sync(0xffffffffu, a0.x, s), my = __shfl_sync(0xffffffffu, a0.y, s);
+    const float thr = __shfl_sync(0xffffffffu, a0.z, s);
+    const float A = __shfl_sync(0xffffffffu, a1.x, s), B = __shfl_sync(0xffffffffu, a1.y, s);
+    const float C = __shfl_sync(0xffffffffu, a1.z, s);
+    if (rx < 0) continue;                       // the same for the whole warp
+    const int w = ry - rx, cnt = w * (rw - rz);
+    // entry t = (ty - rz) w + (tx - rx); lane starts at t = lane, steps by 32
+    int qy = lane / w, qx = lane - qy * w;
+    const int dq = 32 / w, dr = 32 - dq * w;
+    for (int t = lane; t < cnt; t += 32) {
+      const int ty = rz + qy, tx = rx + qx;
+      if (tile_hit(A, B, C, mx, my, thr, tx, ty, tw, th)) mark[bs + (uint32_t)(ty * gx + tx)] = 1;
+      qy += dq;
+      qx += dr;
+      if (qx >= w) {
+        qx -= w;
+        ++qy;
+      }
+    }
+  }
+}
+
+// Entries every (view, Gaussian) slot will emit: its rectangle's tiles that
+// pass tile_hit (and, with a mark, that a splat of the active set reaches).
+// A lane per slot, then each rectangle walked by the whole warp, 32 tiles at
+// a time, the passing ones counted by a ballot.
+__global__ void k_count_tiles(const int4* __restrict__ rect, const float4* __restrict__ r0,
+                              const float4* __restrict__ r1, int64_t n, int nv, const DevCam* __restrict__ cams,
+                              const uint32_t* __restrict__ tile_base, const uint8_t* __restrict__ mark,
+                              uint32_t* __restrict__ touched) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int4 r = make_int4(-1, -1, -1, -1);
+  uint32_t base = 0;
+  int GX = 0, TW = 1, TH = 1;
+  float4 a0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), a1 = a0;
+  if (i < n * nv) {
+    r = rect[i];
+    if (r.x >= 0) {
+      const int v = (int)(i / n);
+      GX = cams[v].GX; TW = cams[v].TW; TH = cams[v].TH;
+      base = tile_base[v];
+      a0 = r0[i];
+      a1 = r1[i];
+    }
+  }
+  uint32_t mine = 0;
+  for (int s = 0; s < 32; ++s) {
+    const int rx = __shfl_sync(0xffffffffu, r.x, s), ry = __shfl_sync(0xffffffffu, r.y, s);
+    const int rz = __shfl_sync(0xffffffffu, r.z, s), rw = __shfl_sync(0xffffffffu, r.w, s);
+    const uint32_t bs = __shfl_sync(0xffffffffu, base, s);
+    const int gx = __shfl_sync(0xffffffffu, GX, s);
+    const int tw = __shfl_sync(0xffffffffu, TW, s), th = __shfl_sync(0xffffffffu, TH, s);
+    const float mx = __shfl_sync(0xffffffffu, a0.x, s), my = __shfl_sync(0xffffffffu, a0.y, s);
+    const float thr = __shfl_sync(0xffffffffu, a0.z, s);
+    const float A = __shfl_sync(0xffffffffu, a1.x, s), B = __shfl_sync(0xffffffffu, a1.y, s);
+    const float C = __shfl_sync(0xffffffffu, a1.z, s);
+    if (rx < 0) continue;                       // the same for the whole warp
+    const int w = ry - rx, cnt = w * (rw - rz);
+    int qy = lane / w, qx = lane - qy * w;
+    const int dq = 32 / w, dr = 32 - dq * w;
+    uint32_t tot = 0;
+    for (int t0 = 0; t0 < cnt; t0 += 32) {
+      const int ty = rz + qy, tx = rx + qx;
+      const bool hit = t0 + lane < cnt && (mark == nullptr || mark[bs + (uint32_t)(ty * gx + tx)] != 0) &&
+                       tile_hit(A, B, C, mx, my, thr, tx, ty, tw, th);
+      tot += (uint32_t)__popc(__ballot_sync(0xffffffffu, hit));
+      qy += dq;
+      qx += dr;
+      if (qx >= w) {
+        qx -= w;
+        ++qy;
+      }
+    }
+    if (lane == s) mine = tot;
+  }
+  if (i < n * nv) touched[i] = mine;
+}
+
+// Multi-view depth order of the slots that emit entries: for every slot
+// with touched > 0, at its place in the exclusive scan `pos` of those flags,
+// the key (view << 31) | the low 31 bits of the float bits of camera z
+// (z > near > 0: the sign bit is clear) and the slot as the value.
+__global__ void k_compact_depth_keys(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ pos,
+                                     const uint32_t* __restrict__ zbits, int64_t n, int64_t m,
+                                     uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (slot >= m || touched[slot] == 0u) return;
+  const uint32_t at = pos[slot];
+  keys[at] = ((uint64_t)(slot / n) << 31) | (uint64_t)(zbits[slot] & 0x7FFFFFFFu);
+  vals[at] = (uint32_t)slot;
+}
+
+__global__ void k_flags_nonzero(const uint32_t* __restrict__ in, int64_t m, uint32_t* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) out[i] = in[i] != 0u ? 1u : 0u;
 }
 
 __global__ void k_ranges32(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
@@ -430,13 +560,39 @@ int launch_gather_touched(const uint32_t* touched, const uint32_t* order, int64_
 }
 
 int launch_duplicate_sorted(const int4* rect, const float4* r0, const float4* r1, const uint32_t* order, int64_t n,
-                            int nv, const DevCam* cams, const uint32_t* tile_base, const uint32_t* offsets,
-                            uint32_t* keys, uint32_t* vals, cudaStream_t st) {
+                            int64_t m, const DevCam* cams, const uint32_t* tile_base, const uint8_t* mark,
+                            const uint32_t* offsets, uint32_t* keys, uint32_t* vals, cudaStream_t st) {
+  if (m <= 0) return 0;
+  k_duplicate_sorted<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, order, n, m, cams, tile_base, mark,
+                                                                  offsets, keys, vals);
+  return 1;
+}
+
+int launch_mark_tiles(const int4* rect, const float4* r0, const float4* r1, const int* act, int64_t n_act, int64_t n,
+                      int nv, const DevCam* cams, const uint32_t* tile_base, uint8_t* mark, int64_t ntiles,
+                      cudaStream_t st) {
+  cudaMemsetAsync(mark, 0, (size_t)ntiles, st);
+  const int64_t m = n_act * nv;
+  if (m <= 0) return 0;
+  k_mark_tiles<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, act, n_act, n, nv, cams, tile_base, mark);
+  return 1;
+}
+
+int launch_count_tiles(const int4* rect, const float4* r0, const float4* r1, int64_t n, int nv, const DevCam* cams,
+                       const uint32_t* tile_base, const uint8_t* mark, uint32_t* touched, cudaStream_t st) {
   const int64_t m = n * nv;
   if (m <= 0) return 0;
-  k_duplicate_sorted<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, order, n, m, cams, tile_base, offsets,
-                                                                  keys, vals);
+  k_count_tiles<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, n, nv, cams, tile_base, mark, touched);
   return 1;
+}
+
+int launch_compact_depth_keys(const uint32_t* touched, int64_t m, uint32_t* flags, uint32_t* pos, uint32_t* scan_tmp,
+                              const uint32_t* zbits, int64_t n, uint64_t* keys, uint32_t* vals, cudaStream_t st) {
+  if (m <= 0) return 0;
+  k_flags_nonzero<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(touched, m, flags);
+  int l = 1 + launch_scan_u32(flags, pos, m, scan_tmp, st);
+  k_compact_depth_keys<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(touched, pos, zbits, n, m, keys, vals);
+  return l + 1;
 }
 
 int launch_ranges32(const uint32_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st) {

@@ -460,8 +460,8 @@ def test_batched_chunks_match_single_pass(P):
 def test_criterion_variants_parity(P, crit, batched, target):
     """tr(H_T^-1 c A) (crit 1) and T-optimality tr(c A) (crit 2) on the
     per-view and multi-view paths against the oracle at 1e-4 relative. Both
-    are linear in the 2D blocks, so they need the default error-compensated
-    contraction (three TF32 products per term)."""
+    are linear in the 2D blocks, so the automatic contraction mode gives
+    them error-compensated products (three TF32 products per term)."""
     wl = S.make_workload("tiny")
     wl.cand = _mixed(wl)
     sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=batched, criterion=crit)
@@ -475,14 +475,14 @@ def test_criterion_variants_parity(P, crit, batched, target):
 
 
 @pytest.mark.parametrize("batched", [0, 1])
-def test_single_tf32_contraction_log_det_parity(P, batched):
-    """The faster single-TF32 contraction (tf32_contraction = 1) still holds
-    the log-det gains (criterion 0) to 1e-4 relative on the tiny workload, and
-    agrees with the default contraction to the same bound."""
+def test_contraction_modes_log_det_parity(P, batched):
+    """The log-det gains (criterion 0) with single TF32 products (mode 1, the
+    automatic choice for this criterion) and with error-compensated products
+    (mode 2): both within 1e-4 relative of the oracle, and of each other."""
     wl = S.make_workload("tiny")
     out = []
-    for fast in (0, 1):
-        sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=batched, tf32_contraction=fast)
+    for mode in (2, 1):
+        sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=batched, tf32_contraction=mode)
         sc.load_scene(wl.scene)
         sc.set_train_views(wl.train)
         sc.set_candidates(wl.cand)
@@ -490,7 +490,8 @@ def test_single_tf32_contraction_log_det_parity(P, batched):
         out.append(sc.score_host().astype(np.float64))
         sc.close()
     ref = O.OracleScene(wl.scene).score(wl.train, wl.cand)
-    _check_scores(out[1], ref)
+    for o in out:
+        _check_scores(o, ref)
     np.testing.assert_allclose(out[1], out[0], rtol=1e-4)
 
 

@@ -78,14 +78,18 @@ def test_reference_arm_is_rank_zero_only(monkeypatch):
     assert buf.getvalue() == ""
 
 
-def test_composite_flop_count_and_traffic_constant():
-    """The roofline's algorithmic count: 11 flops per evaluated pair, 5 per
-    blended pair in the scoring forward pass, 266 + 21 K in the information
-    pass; the per-view DRAM figure, when a capture of the current tile lists
-    provides one, is positive."""
+def test_roofline_work_counts():
+    """The roofline's algorithmic counts: 16 + (K+1) flops per forward pair
+    and 110 + 8 (K+1) per information pair on the FP32 pipes (the scope
+    table's constants), 2 (88 + 6 K) tensor flops per information pair, the
+    projection's bytes (parameters once, 44 B per (view, Gaussian)) and a
+    plain binning sort's bytes (ceil(bits / 8) passes of 2 x 12 B)."""
     sys.path.insert(0, ROOT)
     import bench
-    st = {"pairs_evaluated": 1000, "pairs_blended": 10}
-    assert bench.composite_flops(st, 16) == 11 * 1000 + 5 * 10 + (266 + 21 * 16) * 10
-    assert bench.composite_flops({"pairs_evaluated": 0, "pairs_blended": 0}, 16) == 0
-    assert bench.SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW is None or bench.SCENE_COMPOSITE_DRAM_BYTES_PER_VIEW > 0
+    st = {"pairs_evaluated": 1000, "pairs_information": 10}
+    assert bench.composite_fp32_flops(st, 16) == 1000 * 33 + 10 * 246
+    assert bench.composite_fp32_flops({"pairs_evaluated": 0, "pairs_information": 0}, 16) == 0
+    assert bench.composite_tensor_flops(st, 32) == 10 * 2 * 280
+    assert bench.project_bytes(10, 4, 3) == 10 * 240 + 44 * 40
+    # 256 views (8 bits) and 192,000 tiles (18 bits) + 32 depth bits: 58 bits, 8 passes
+    assert bench.sort_bytes(100, 256, 192_000) == 8 * 24 * 100
