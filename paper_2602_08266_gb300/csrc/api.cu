@@ -89,6 +89,9 @@ struct nbv_ctx {
   DevProj pr{};
   // sort
   SortBuffers sb{};
+  uint2* fwd = nullptr;           // per-view scoring: forward results per (tile, pixel)
+  uint32_t* tile_first = nullptr; // and each tile's first active entry
+  size_t fwd_cap = 0, tile_first_cap = 0;
   uint32_t* h_total = nullptr;   // pinned
   unsigned long long* h_total64 = nullptr;   // pinned: 64-bit entry count of the last pass
   unsigned long long* d_total64 = nullptr;
@@ -111,7 +114,7 @@ struct nbv_ctx {
   size_t ig_train_cap = 0, ig_cand_cap = 0;
   float* out4 = nullptr;
   size_t out4_cap = 0;
-  int* d_flags = nullptr;       // [0] best, [1] empty flag, [2] input check
+  int* d_flags = nullptr;       // [0] best, [1] empty flag, [2] input check, [3] a staging wait gave up
   float* d_best_score = nullptr;
   bool scored = false;
   int* d_err = nullptr;
@@ -146,6 +149,7 @@ struct nbv_ctx {
     int* tile_view = nullptr;       // [ntiles]
     DevProj pr{};                   // [nv][n] records
     uint8_t* mark = nullptr;        // [ntiles] tiles an active splat reaches (active subset only)
+    int4* bbox = nullptr;           // [nv] each view's bounding box of marked tiles
     uint32_t* flags = nullptr;      // [nv n] slots that emit entries
     int64_t m = 0;                  // how many slots emit entries
     uint32_t* offsets = nullptr;    // [nv n + 1] their positions
@@ -158,7 +162,9 @@ struct nbv_ctx {
     SortBuffers sb{};               // entries (32-bit tile keys, stored in the 64-bit arrays)
     SortBuffers qb{};               // work queue
     uint2* ranges = nullptr;        // [ntiles]
-    int* counter = nullptr;
+    uint2* fwd = nullptr;           // [ntiles][256] forward results
+    uint32_t* tile_first = nullptr; // [ntiles]
+    int* counter = nullptr;         // [2] work-queue heads of the forward and information passes
     float* blocks = nullptr;        // [nv][n][nBp]
     double* partial = nullptr;
     int parts_cap = 0;
@@ -334,7 +340,7 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
   CKR(grow(ctx, &ctx->sb.ranges, &ctx->ranges_cap, (size_t)ntiles));
   {
     Phase ph(ctx, NBV_PHASE_SORT);
-    CKR(check_launch(ctx, launch_duplicate(ctx->pr, ctx->n, dc.GX, dc.TW, dc.TH, ctx->sb.offsets, ctx->sb.keys[0],
+    CKR(check_launch(ctx, launch_duplicate(ctx->pr, ctx->n, dc, ctx->sb.offsets, ctx->sb.keys[0],
                                            ctx->sb.vals[0], st)));
     int tile_bits = 1;
     while ((1 << tile_bits) < ntiles) ++tile_bits;
@@ -359,11 +365,21 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
   a.n = ctx->n;
   a.slot = ctx->slot;
   a.n_act = ctx->n_act;
+  a.err = ctx->d_flags + 3;
   a.stats = ctx->prof ? ctx->d_stats + (training ? 4 : 0) : nullptr;
+  const bool scoring = blocks && !rgb && !depth && !alpha && !obj;
+  if (scoring) {
+    // forward pass on its own (lean, high occupancy), then the information pass
+    CKR(grow(ctx, &ctx->fwd, &ctx->fwd_cap, (size_t)ntiles * kTilePix));
+    CKR(grow(ctx, &ctx->tile_first, &ctx->tile_first_cap, (size_t)ntiles));
+    a.fwd = ctx->fwd;
+    a.tile_first = ctx->tile_first;
+  }
   if (blocks || rgb || depth || alpha || obj) {
     Phase ph(ctx, training ? NBV_PHASE_TRAIN_COMPOSITE : NBV_PHASE_COMPOSITE);
     Consts cc = ctx->c;
     if (compensated) cc.tf32 = 0;
+    if (scoring) CKR(check_launch(ctx, launch_forward(a, cc, st)));
     CKR(check_launch(ctx, launch_composite(a, cc, st, ctx->stage)));
     if (ctx->prof) ctx->composite_launches[training ? 1 : 0]++;
   }
@@ -433,12 +449,14 @@ int binning_counts(nbv_ctx* ctx, cudaStream_t st) {
   }
   Phase ph(ctx, NBV_PHASE_SORT);
   const uint8_t* mark = nullptr;
+  const int4* bbox = nullptr;
   if (ctx->n_act < n) {
     l += launch_mark_tiles(B.pr.rect, B.pr.r0, B.pr.r1, ctx->act, ctx->n_act, n, B.nv, B.cams, B.tile_base, B.mark,
-                           B.ntiles, st);
+                           B.ntiles, B.bbox, st);
     mark = B.mark;
+    bbox = B.bbox;
   }
-  l += launch_count_tiles(B.pr.rect, B.pr.r0, B.pr.r1, n, B.nv, B.cams, B.tile_base, mark, B.pr.touched, st);
+  l += launch_count_tiles(B.pr.rect, B.pr.r0, B.pr.r1, n, B.nv, B.cams, B.tile_base, mark, bbox, B.pr.touched, st);
   l += launch_compact_depth_keys(B.pr.touched, slots, B.flags, B.offsets, B.scan_tmp, B.pr.zbits, n, B.db.keys[0],
                                  B.db.vals[0], st);
   return l;
@@ -480,6 +498,7 @@ int batched_setup(nbv_ctx* ctx, int v0, int nv) {
   CKR(alloc(ctx, &B.pr.touched, slots));
   CKR(alloc(ctx, &B.flags, slots));
   CKR(alloc(ctx, &B.mark, (size_t)nt));
+  CKR(alloc(ctx, &B.bbox, (size_t)nv));
   CKR(alloc(ctx, &B.offsets, slots + 1));
   CKR(alloc(ctx, &B.scan_tmp, scan_scratch_elems((int64_t)slots + 1)));
   CKR(alloc(ctx, &B.db.keys[0], slots)); CKR(alloc(ctx, &B.db.keys[1], slots));
@@ -489,7 +508,9 @@ int batched_setup(nbv_ctx* ctx, int v0, int nv) {
   CKR(alloc(ctx, &B.tcount, slots));
   CKR(alloc(ctx, &B.doffsets, slots + 1));
   CKR(alloc(ctx, &B.ranges, (size_t)nt));
-  CKR(alloc(ctx, &B.counter, 1));
+  CKR(alloc(ctx, &B.fwd, (size_t)nt * kTilePix));
+  CKR(alloc(ctx, &B.tile_first, (size_t)nt));
+  CKR(alloc(ctx, &B.counter, 2));
   CKR(alloc(ctx, &B.blocks, (size_t)nv * ctx->n_act * ctx->nBp));
   B.parts_cap = ctx->nsm * 64;      // >= the multi-view gains launch's warps (a few blocks of <= 8 per SM)
   CKR(alloc(ctx, &B.partial, (size_t)nv * B.parts_cap * 3));
@@ -551,7 +572,8 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
     CKR(check_launch(ctx, launch_scan_u32(B.tcount, B.doffsets, B.m, B.scan_tmp, st)));
     uint32_t* k32[2] = {reinterpret_cast<uint32_t*>(B.sb.keys[0]), reinterpret_cast<uint32_t*>(B.sb.keys[1])};
     CKR(check_launch(ctx, launch_duplicate_sorted(B.pr.rect, B.pr.r0, B.pr.r1, order, n, B.m, B.cams, B.tile_base,
-                                                  ctx->n_act < n ? B.mark : nullptr, B.doffsets, k32[0],
+                                                  ctx->n_act < n ? B.mark : nullptr,
+                                                  ctx->n_act < n ? B.bbox : nullptr, B.doffsets, k32[0],
                                                   B.sb.vals[0], st)));
     int which = 0;
     CKR(check_launch(ctx, launch_radix_sort32(k32, B.sb.vals, B.sb.hist, B.total, bits_for(B.ntiles), &which, st)));
@@ -565,7 +587,7 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
   }
   {
     Phase ph(ctx, NBV_PHASE_COMPOSITE);
-    CK(cudaMemsetAsync(B.counter, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(B.counter, 0, 2 * sizeof(int), st));
     if (ctx->prof) {
       ctx->composite_launches[0]++;
       ctx->binned_entries[0] += B.total;
@@ -588,7 +610,12 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
     a.n = n;
     a.slot = ctx->slot;
     a.n_act = ctx->n_act;
-    CKR(check_launch(ctx, launch_composite(a, ctx->c, st, ctx->stage)));   // records of view v start at slot v n
+    a.err = ctx->d_flags + 3;
+    a.fwd = B.fwd;
+    a.tile_first = B.tile_first;
+    CKR(check_launch(ctx, launch_forward(a, ctx->c, st)));   // records of view v start at slot v n
+    a.counter = B.counter + 1;
+    CKR(check_launch(ctx, launch_composite(a, ctx->c, st, ctx->stage)));
   }
   {
     Phase ph(ctx, NBV_PHASE_GAINS);
@@ -797,6 +824,7 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
     return NBV_ERR_CUDA;
   }
   ctx->nsm = device_sm_count();
+  cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int), ctx->st);
   launch_tri_table_init(ctx->st);
   if (cudaGetLastError() != cudaSuccess) {
     nbv_destroy(ctx);
@@ -823,9 +851,9 @@ void nbv_destroy(nbv_ctx* ctx) {
   {
     auto& B = ctx->bt;
     void* bp[] = {B.cams, B.tile_base, B.tile_view, B.pr.r0, B.pr.r1, B.pr.r2, B.pr.rect, B.pr.zbits,
-                  B.pr.touched, B.mark, B.flags, B.offsets, B.scan_tmp, B.sb.keys[0], B.sb.keys[1], B.sb.vals[0],
+                  B.pr.touched, B.mark, B.bbox, B.flags, B.offsets, B.scan_tmp, B.sb.keys[0], B.sb.keys[1], B.sb.vals[0],
                   B.sb.vals[1], B.sb.hist, B.qb.keys[0], B.qb.keys[1], B.qb.vals[0], B.qb.vals[1], B.qb.hist,
-                  B.ranges, B.counter, B.blocks, B.partial, B.db.keys[0], B.db.keys[1], B.db.vals[0],
+                  B.ranges, B.fwd, B.tile_first, B.counter, B.blocks, B.partial, B.db.keys[0], B.db.keys[1], B.db.vals[0],
                   B.db.vals[1], B.db.hist, B.tcount, B.doffsets};
     for (void* q : bp)
       if (q) cudaFree(q);
@@ -836,7 +864,7 @@ void nbv_destroy(nbv_ctx* ctx) {
   if (ctx->h_total64) cudaFreeHost(ctx->h_total64);
   if (ctx->d_total64) cudaFree(ctx->d_total64);
   for (void* p : {(void*)ctx->d_desc_cams, (void*)ctx->desc_raw, (void*)ctx->desc, (void*)ctx->d_pred,
-                  (void*)ctx->gacc})
+                  (void*)ctx->gacc, (void*)ctx->fwd, (void*)ctx->tile_first})
     if (p) cudaFree(p);
   if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   delete ctx;
@@ -921,6 +949,7 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
   const int nt = (int)ctx->train.size();
   ctx->prepared = false;
   ctx->scored = false;
+  CK(cudaMemsetAsync(ctx->d_flags + 3, 0, sizeof(int), st));
   {
     Phase ph(ctx, NBV_PHASE_PREP);
     CKR(check_launch(ctx, launch_scene_prep(dev_scene(ctx), ctx->c, target_obj, st)));
@@ -975,9 +1004,11 @@ int nbv_prepare(nbv_ctx* ctx, int target_obj) {
                        ctx->ig_train + 3 * t));
     }
   }
-  int herr = 0;
+  int herr = 0, hto = 0;
   CK(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hto, ctx->d_flags + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (hto) return fail(ctx, NBV_ERR_TIMEOUT, "a bounded wait for staged splat records gave up");
   if (herr) return fail(ctx, NBV_ERR_CUDA, "non-finite training Hessian");
   ctx->prepared = true;
   ctx->prepared_target = target_obj;
@@ -1014,15 +1045,16 @@ int nbv_score(nbv_ctx* ctx, float* ig_out, int out_on_device) {
                                               ctx->d_flags + 1, st)));
   }
   ctx->scored = true;
-  int empty = 0;
+  int fl[3] = {0, 0, 0};
   if (ig_out) {
     if (out_on_device) {
       CK(cudaMemcpyAsync(ig_out, ctx->out4, sizeof(float) * 4 * nc, cudaMemcpyDeviceToDevice, st));
     } else {
       CK(cudaMemcpyAsync(ig_out, ctx->out4, sizeof(float) * 4 * nc, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(&empty, ctx->d_flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(fl, ctx->d_flags + 1, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      if (empty) return fail(ctx, NBV_ERR_EMPTY, "a training normaliser is zero");
+      if (fl[2]) return fail(ctx, NBV_ERR_TIMEOUT, "a bounded wait for staged splat records gave up");
+      if (fl[0]) return fail(ctx, NBV_ERR_EMPTY, "a training normaliser is zero");
     }
   }
   return NBV_OK;
@@ -1031,13 +1063,14 @@ int nbv_score(nbv_ctx* ctx, float* ig_out, int out_on_device) {
 int nbv_argmax(nbv_ctx* ctx, int* best_view, float* best_score) {
   if (!ctx) return NBV_ERR_ARG;
   if (!ctx->scored) return fail(ctx, NBV_ERR_STATE, "nbv_argmax before nbv_score");
-  int flags[2] = {0, 0};
+  int flags[4] = {0, 0, 0, 0};
   float bs = 0.0f;
-  CK(cudaMemcpyAsync(flags, ctx->d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(flags, ctx->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaMemcpyAsync(&bs, ctx->d_best_score, sizeof(float), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   if (best_view) *best_view = flags[0];
   if (best_score) *best_score = bs;
+  if (flags[3]) return fail(ctx, NBV_ERR_TIMEOUT, "a bounded wait for staged splat records gave up");
   if (flags[1]) return fail(ctx, NBV_ERR_EMPTY, "a training normaliser is zero");
   return NBV_OK;
 }

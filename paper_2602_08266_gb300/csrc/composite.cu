@@ -103,12 +103,85 @@ __host__ __device__ __forceinline__ int u_rows(int K) { return 3 + 16 * u_tiles(
 constexpr int kCS = 36;
 constexpr int kVRows = 32;
 
+// Asynchronous staging of the forward pass's records (scoring launches):
+// every round's {r0, r1} pairs (2 x 16 bytes per splat, gathered by
+// Gaussian index) are fetched by bulk copies of the tensor memory accelerator
+// (cp.async.bulk, global -> shared) into one of two buffers, each completed
+// by its own mbarrier (expected bytes set by one arrival), while the block
+// composites the other buffer. Waits are bounded: on a time-out the kernel
+// sets *err, marks its pixels done and drains (again bounded) before leaving.
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+struct StageRing {
+  float4* buf;           // [2][2][kBatch]: buffer b, record r0 / r1, splat
+  uint32_t bar;          // shared address of two consecutive mbarriers
+  uint32_t use0, use1;   // phases waited for per buffer (the parity of the next wait)
+  int* err;
+
+  __device__ float4* rec(int b, int r, int kBatch) { return buf + (2 * b + r) * kBatch; }
+  // warp 0: round k of the list [lo, hi) into buffer k & 1
+  __device__ void issue(const CompositeArgs& a, uint32_t lo, uint32_t hi, uint32_t k, size_t rec_off, int lane,
+                        int kBatch) {
+    const uint32_t start = lo + k * (uint32_t)kBatch;
+    const int nj = (int)min((uint32_t)kBatch, hi - start);
+    const int b = (int)(k & 1u);
+    const uint32_t bb = bar + 8u * (uint32_t)b;
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"((uint32_t)(32 * nj))
+                   : "memory");
+    __syncwarp();
+    if (lane < nj) {
+      const uint32_t g = a.vals[start + lane];
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_g2s(rec(b, 0, kBatch) + lane, a.r0 + rec_off + g, 16u, bb);
+      bulk_g2s(rec(b, 1, kBatch) + lane, a.r1 + rec_off + g, 16u, bb);
+    }
+  }
+  // every thread: wait for buffer b's current phase (bounded)
+  __device__ bool wait(int b) {
+    const uint32_t bb = bar + 8u * (uint32_t)b, parity = (b ? use1 : use0) & 1u;
+    if (b) ++use1; else ++use0;
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+      uint32_t ok;
+      asm volatile(
+          "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+          : "=r"(ok)
+          : "r"(bb), "r"(parity)
+          : "memory");
+      if (ok) return true;
+    }
+    if (err) atomicExch(err, 1);
+    return false;
+  }
+};
+
+// Byte offset of the staging ring in the dynamic shared memory: after the
+// round's records, ids, probabilities, block accumulators, flags and the
+// per-warp contraction buffers, rounded up to 16 bytes.
+__host__ __device__ inline size_t ring_offset(int K, int KC, int nB, int kBatch) {
+  const int nBp = (nB + 3) & ~3;
+  const size_t end = sizeof(float4) * 3 * kBatch + sizeof(int) * kBatch + sizeof(float) * (size_t)kBatch * ((KC + 1) & ~1) +
+                     sizeof(float) * (size_t)kBatch * nBp + sizeof(int) * kBatch +
+                     sizeof(float) * (kTilePix / 32) * kCS * (size_t)(u_rows(K) + kVRows);
+  return (end + 15) & ~(size_t)15;
+}
+
 // One 16x16 tile of one view: both passes. blocks_v is the view's block
 // array (NULL: render only).
 template <int KCM, int kBatch, bool kSplit>
 __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const Consts& c, const DevCam& cam,
-                                               int tile, uint2 rg, float* blocks_v, size_t rec_off,
-                                               unsigned char* smem) {
+                                               int tile, uint32_t gt, uint2 rg, float* blocks_v, size_t rec_off,
+                                               unsigned char* smem, StageRing& ring) {
   const int KC = c.KC;
   const int nB = args.nB, nBp = (nB + 3) & ~3;
   float4* s0 = reinterpret_cast<float4*>(smem);
@@ -137,7 +210,11 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   // writes no image).
   __shared__ int s_first;
   uint32_t first_info = rg.x;
-  if (blocks_v != nullptr && args.n_act < args.n) {
+  const bool info_only = args.fwd != nullptr;        // the forward pass ran in launch_forward
+  if (info_only) {
+    first_info = args.tile_first[gt];
+    if (first_info >= rg.y) return;
+  } else if (blocks_v != nullptr && args.n_act < args.n) {
     if (tid == 0) s_first = (int)rg.y;
     __syncthreads();
     for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kTilePix) {
@@ -163,6 +240,42 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   // information pass needs only the final transmittance and list ends)
   const bool want_cd = args.rgb != nullptr || args.depth != nullptr;
   const bool want_o = args.obj != nullptr;
+  if (info_only) {
+    const uint2 f = args.fwd[(size_t)gt * kTilePix + tid];
+    T = __uint_as_float(f.x);
+    last = f.y;
+  } else if (!want_cd && !want_o) {
+    // records staged by bulk copies, the next round in flight meanwhile
+    const uint32_t nst = (rg.y - rg.x + kBatch - 1) / kBatch;
+    if (nst > 0 && wq == 0) ring.issue(args, rg.x, rg.y, 0, rec_off, lane, kBatch);
+    uint32_t k = 0;
+    for (; k < nst; ++k) {
+      if (__syncthreads_count(done) == kTilePix) break;
+      if (k + 1 < nst && wq == 0) ring.issue(args, rg.x, rg.y, k + 1, rec_off, lane, kBatch);
+      const int b = (int)(k & 1u);
+      if (!ring.wait(b)) done = true;
+      const float4* q0 = ring.rec(b, 0, kBatch);
+      const float4* q1 = ring.rec(b, 1, kBatch);
+      const uint32_t start = rg.x + k * kBatch;
+      const uint32_t nj = min((uint32_t)kBatch, rg.y - start);
+      if (!done) {
+        for (uint32_t j = 0; j < nj; ++j) {
+          const float4 a0 = q0[j], a1 = q1[j];
+          const float pw = splat_power(a0.x, a0.y, a1.x, a1.y, a1.z, pxc, pyc);
+          ++n_eval;
+          if (pw > 0.0f || pw < a0.z) continue;
+          const float alpha = (pw >= a0.w) ? c.alpha_max : a1.w * __expf(pw);
+          const float tt = T * (1.0f - alpha);
+          if (tt < c.t_min) { done = true; break; }
+          T = tt;
+          last = start + j + 1;
+          ++n_blend;
+        }
+      }
+    }
+    // a round fetched ahead but not composited (every pixel had stopped)
+    if (k < nst) ring.wait((int)(k & 1u));
+  } else {
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
     if (__syncthreads_count(done) == kTilePix) break;
     const uint32_t nj = min((uint32_t)kBatch, rg.y - start);
@@ -206,6 +319,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         ++n_blend;
       }
     }
+  }
   }
   if (args.stats) {
     __shared__ unsigned long long s_cnt[2];
@@ -306,7 +420,6 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       const int j = i / KCP, k = i - j * KCP;
       sp[i] = k < KC ? args.p[(size_t)args.vals[start + j] * KC + k] : 0.0f;
     }
-    for (int i = tid; i < nj * nBp; i += kTilePix) acc[i] = 0.0f;
     __syncthreads();
     for (int j = nj - 1; j >= 0; --j) {
       const uint32_t idx = start + j;
@@ -458,7 +571,9 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
     for (int i = tid; i < nj * n4; i += kTilePix) {
       const int j = i / n4, q = i - j * n4;
       if (!touched[j]) continue;
-      const float4 v = reinterpret_cast<const float4*>(acc + j * nBp)[q];
+      float4* src = reinterpret_cast<float4*>(acc + j * nBp) + q;
+      const float4 v = *src;
+      *src = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // the accumulators stay zero between rounds
       float4* dst = reinterpret_cast<float4*>(blocks_v + (size_t)sid[j] * nBp) + q;
       atomicAdd(dst, v);
     }
@@ -479,8 +594,28 @@ template <int KCM, int kBatch, bool kSplit>
 __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
     k_composite(CompositeArgs args, Consts c) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // per-splat block accumulators start at zero and are zeroed as they are
+  // flushed; the staging ring and its two mbarriers live past the per-warp
+  // buffers (offsets as launch_k sizes them)
+  const int KCP = (c.KC + 1) & ~1;
+  const int nBp = (args.nB + 3) & ~3;
+  float* acc = reinterpret_cast<float*>(smem + sizeof(float4) * 3 * kBatch + sizeof(int) * kBatch) + kBatch * KCP;
+  for (int i = threadIdx.x; i < kBatch * nBp; i += kTilePix) acc[i] = 0.0f;
+  const size_t ring_off = ring_offset(c.K, c.KC, args.nB, kBatch);
+  StageRing ring;
+  ring.buf = reinterpret_cast<float4*>(smem + ring_off);
+  ring.bar = smem_u32(smem + ring_off + sizeof(float4) * 4 * kBatch);
+  ring.use0 = ring.use1 = 0u;
+  ring.err = args.err;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ring.bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ring.bar + 8u) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   if (args.queue == nullptr) {                 // one tile of one view per block
-    composite_tile<KCM, kBatch, kSplit>(args, c, args.cam, blockIdx.x, args.ranges[blockIdx.x], args.blocks, 0, smem);
+    composite_tile<KCM, kBatch, kSplit>(args, c, args.cam, blockIdx.x, blockIdx.x, args.ranges[blockIdx.x],
+                                        args.blocks, 0, smem, ring);
     return;
   }
   // persistent: (view, tile) items in queue order (longest lists first)
@@ -494,18 +629,119 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
     const uint32_t gt = args.queue[it];
     const int v = args.tile_view[gt];
     const DevCam cam = args.cams[v];
-    composite_tile<KCM, kBatch, kSplit>(args, c, cam, (int)(gt - args.tile_base[v]), args.ranges[gt],
-                        args.blocks + (size_t)v * args.n_act * ((args.nB + 3) & ~3), (size_t)v * args.n, smem);
+    composite_tile<KCM, kBatch, kSplit>(args, c, cam, (int)(gt - args.tile_base[v]), gt, args.ranges[gt],
+                                        args.blocks + (size_t)v * args.n_act * ((args.nB + 3) & ~3),
+                                        (size_t)v * args.n, smem, ring);
+  }
+}
+
+// The forward pass of a scoring launch, on its own: a tile's list walked
+// front to back in rounds of kFwd splats staged by bulk copies (the next
+// round in flight meanwhile), per pixel only what the information pass needs
+// (transmittance, list ends). With an active subset, a tile without an
+// active splat is skipped (its first active entry recorded as its list end).
+constexpr int kFwd = 32;
+
+__device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Consts& c, const DevCam& cam, int tile,
+                                             uint32_t gt, uint2 rg, size_t rec_off, StageRing& ring) {
+  const int tx = tile % cam.GX, ty = tile / cam.GX;
+  const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
+  const int wx = cam.TW >> 3;
+  const int px = tx * cam.TW + 8 * (wq % wx) + (lane & 7), py = ty * cam.TH + 4 * (wq / wx) + (lane >> 3);
+  const bool inside = px < cam.W && py < cam.H;
+  const float pxc = fa((float)px, 0.5f), pyc = fa((float)py, 0.5f);
+  __shared__ int s_first;
+  uint32_t first_info = rg.x;
+  if (args.n_act < args.n) {
+    if (tid == 0) s_first = (int)rg.y;
+    __syncthreads();
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kTilePix) {
+      const uint32_t i = b0 + tid;
+      if (i < rg.y && args.slot[args.vals[i]] >= 0) atomicMin(&s_first, (int)i);
+      if (__syncthreads_or(s_first < (int)rg.y)) break;
+    }
+    first_info = (uint32_t)s_first;
+  }
+  if (tid == 0) args.tile_first[gt] = first_info;
+  float T = 1.0f;
+  uint32_t last = rg.x;
+  uint32_t n_eval = 0, n_blend = 0;
+  if (first_info < rg.y) {
+    bool done = !inside;
+    const uint32_t nst = (rg.y - rg.x + kFwd - 1) / kFwd;
+    if (nst > 0 && wq == 0) ring.issue(args, rg.x, rg.y, 0, rec_off, lane, kFwd);
+    uint32_t k = 0;
+    for (; k < nst; ++k) {
+      if (__syncthreads_count(done) == kTilePix) break;
+      if (k + 1 < nst && wq == 0) ring.issue(args, rg.x, rg.y, k + 1, rec_off, lane, kFwd);
+      const int b = (int)(k & 1u);
+      if (!ring.wait(b)) done = true;
+      const float4* q0 = ring.rec(b, 0, kFwd);
+      const float4* q1 = ring.rec(b, 1, kFwd);
+      const uint32_t start = rg.x + k * kFwd;
+      const uint32_t nj = min((uint32_t)kFwd, rg.y - start);
+      if (!done) {
+        for (uint32_t j = 0; j < nj; ++j) {
+          const float4 a0 = q0[j], a1 = q1[j];
+          const float pw = splat_power(a0.x, a0.y, a1.x, a1.y, a1.z, pxc, pyc);
+          ++n_eval;
+          if (pw > 0.0f || pw < a0.z) continue;
+          const float alpha = (pw >= a0.w) ? c.alpha_max : a1.w * __expf(pw);
+          const float tt = T * (1.0f - alpha);
+          if (tt < c.t_min) { done = true; break; }
+          T = tt;
+          last = start + j + 1;
+          ++n_blend;
+        }
+      }
+    }
+    if (k < nst) ring.wait((int)(k & 1u));   // a round fetched ahead but not composited
+  }
+  args.fwd[(size_t)gt * kTilePix + tid] = make_uint2(__float_as_uint(T), inside ? last : rg.x);
+  if (args.stats) {
+    const unsigned e = __reduce_add_sync(0xffffffffu, n_eval), bl = __reduce_add_sync(0xffffffffu, n_blend);
+    if (lane == 0 && e) {
+      atomicAdd(&args.stats[0], (unsigned long long)e);
+      atomicAdd(&args.stats[1], (unsigned long long)bl);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTilePix, 4) k_forward(CompositeArgs args, Consts c) {
+  __shared__ __align__(16) float4 ring_buf[4 * kFwd];
+  __shared__ __align__(8) uint64_t ring_bar[2];
+  StageRing ring;
+  ring.buf = ring_buf;
+  ring.bar = smem_u32(ring_bar);
+  ring.use0 = ring.use1 = 0u;
+  ring.err = args.err;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ring.bar) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ring.bar + 8u) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (args.queue == nullptr) {
+    forward_tile(args, c, args.cam, blockIdx.x, blockIdx.x, args.ranges[blockIdx.x], 0, ring);
+    return;
+  }
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(args.counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= args.n_items) break;
+    const uint32_t gt = args.queue[it];
+    const int v = args.tile_view[gt];
+    const DevCam cam = args.cams[v];
+    forward_tile(args, c, cam, (int)(gt - args.tile_base[v]), gt, args.ranges[gt], (size_t)v * args.n, ring);
   }
 }
 
 template <int KCM, int kBatch, bool kSplit>
 int launch_k(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
-  const int nBp = (a.nB + 3) & ~3;
-  const size_t sm = sizeof(float4) * 3 * kBatch + sizeof(int) * kBatch +
-                    sizeof(float) * (size_t)kBatch * ((c.KC + 1) & ~1) + sizeof(float) * (size_t)kBatch * nBp +
-                    sizeof(int) * kBatch +
-                    sizeof(float) * (kTilePix / 32) * kCS * (size_t)(u_rows(c.K) + kVRows);
+  const size_t sm = ring_offset(c.K, c.KC, a.nB, kBatch) + sizeof(float4) * 4 * kBatch + 16;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_composite<KCM, kBatch, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -548,6 +784,23 @@ int launch_stage(const CompositeArgs& a, const Consts& c, cudaStream_t st, int s
 
 int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage) {
   return c.tf32 ? launch_stage<false>(a, c, st, stage) : launch_stage<true>(a, c, st, stage);
+}
+
+int launch_forward(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
+  if (a.queue) {
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward, kTilePix, 0);
+    if (per_sm < 1) per_sm = 1;
+    int grid = device_sm_count() * per_sm;
+    if (grid > a.n_items) grid = a.n_items;
+    if (grid <= 0) return 0;
+    k_forward<<<grid, kTilePix, 0, st>>>(a, c);
+    return 1;
+  }
+  const int ntiles = a.cam.GX * a.cam.GY;
+  if (ntiles <= 0) return 0;
+  k_forward<<<ntiles, kTilePix, 0, st>>>(a, c);
+  return 1;
 }
 
 }  // namespace nbv

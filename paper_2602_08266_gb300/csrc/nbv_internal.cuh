@@ -123,7 +123,7 @@ struct SortBuffers {
 int launch_sum_u64(const uint32_t* in, int64_t n, unsigned long long* out, cudaStream_t st);
 // Exclusive scan of touched into offsets; total written to *d_total (device).
 int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st);
-int launch_duplicate(const DevProj& pr, int64_t n, int GX, int TW, int TH, const uint32_t* offsets, uint64_t* keys,
+int launch_duplicate(const DevProj& pr, int64_t n, const DevCam& cam, const uint32_t* offsets, uint64_t* keys,
                      uint32_t* vals, cudaStream_t st);
 // Stable LSD radix sort of (keys, vals) on the low `bits` key bits; the
 // result is in buffer index *which (0 or 1).
@@ -142,17 +142,21 @@ int launch_gather_touched(const uint32_t* touched, const uint32_t* order, int64_
 // tile keys and Gaussian indices; with a tile mark, only marked tiles.
 int launch_duplicate_sorted(const int4* rect, const float4* r0, const float4* r1, const uint32_t* order, int64_t n,
                             int64_t m, const DevCam* cams, const uint32_t* tile_base, const uint8_t* mark,
-                            const uint32_t* offsets, uint32_t* keys, uint32_t* vals, cudaStream_t st);
+                            const int4* bb, const uint32_t* offsets, uint32_t* keys, uint32_t* vals,
+                            cudaStream_t st);
 // mark [ntiles] (global tile ids; zeroed first) = 1 where a splat of the
 // active set passes tile_hit: the only tiles whose lists matter for the
-// information gain when only part of the scene carries a confidence.
+// information gain when only part of the scene carries a confidence; bb
+// [nv] = each view's bounding box of marked tiles {min x, min y, max x,
+// max y} (empty: max < 0).
 int launch_mark_tiles(const int4* rect, const float4* r0, const float4* r1, const int* act, int64_t n_act, int64_t n,
                       int nv, const DevCam* cams, const uint32_t* tile_base, uint8_t* mark, int64_t ntiles,
-                      cudaStream_t st);
+                      int4* bb, cudaStream_t st);
 // touched [nv n] = entries of every slot (rectangle tiles passing tile_hit,
-// marked ones only when mark != NULL).
+// marked ones inside the view's box bb only when mark != NULL).
 int launch_count_tiles(const int4* rect, const float4* r0, const float4* r1, int64_t n, int nv, const DevCam* cams,
-                       const uint32_t* tile_base, const uint8_t* mark, uint32_t* touched, cudaStream_t st);
+                       const uint32_t* tile_base, const uint8_t* mark, const int4* bb, uint32_t* touched,
+                       cudaStream_t st);
 // Depth keys (view << 31 | z bits) and slot values of the slots with
 // touched > 0, in slot order (flags / pos / scan_tmp: scratch of m words).
 int launch_compact_depth_keys(const uint32_t* touched, int64_t m, uint32_t* flags, uint32_t* pos, uint32_t* scan_tmp,
@@ -169,17 +173,20 @@ size_t radix_hist_elems(int64_t count);
 // Whether a splat can pass its alpha cut-off at some pixel centre of tile
 // (tx, ty): the minimum over the rectangle of the tile's pixel centres of
 // q(d) = A dx^2 + 2 B dx dy + C dy^2 (d = pixel centre - mean2D; zero when
-// the mean lies inside, else on an edge at the clamped stationary point)
-// against -2 thr (thr = log(alpha_min / sigma), the exponent of the skip
-// test), widened by 2^-8 relative, 2^-8 absolute and 2^-18 of
-// M = A max(dx^2) + C max(dy^2) over the tile. The rounding of q here and of
-// the per-pixel exponent is at most about 24 units of 2^-24 times M (the
-// cross term is at most M/2 for a positive-definite conic), so the widening
-// never drops a tile with a pixel that passes the skip test, however
-// elongated the splat. Correctly rounded single-precision operations in a
-// fixed order; the oracle repeats them, so tile lists agree bit for bit.
-__device__ __forceinline__ bool tile_hit(float A, float B, float C, float mx, float my, float thr, int tx, int ty,
-                                         int TW, int TH) {
+// the mean lies inside, else on an edge at the clamped stationary point, at
+// dy = bc dx on a vertical edge and dx = ba dy on a horizontal one, with the
+// ratios bc = -B / C and ba = -B / A rounded once per splat) against -2 thr
+// (thr = log(alpha_min / sigma), the exponent of the skip test), widened by
+// 2^-8 relative, 2^-8 absolute and 2^-18 of M = A max(dx^2) + C max(dy^2)
+// over the tile. q along an edge is a parabola about its minimum, so the
+// rounded ratio (off by a relative 2^-23) moves the evaluated point by a
+// second-order amount, C (2^-23 dy)^2 <= 2^-46 M; with the rounding of q here
+// and of the per-pixel exponent (at most about 24 units of 2^-24 times M: the
+// cross term is at most M/2 for a positive-definite conic) the widening
+// covers it, so no tile with a pixel that passes the skip test is dropped,
+// however elongated the splat.
+__device__ __forceinline__ bool tile_hit(float A, float B, float C, float mx, float my, float thr, float bc, float ba,
+                                         int tx, int ty, int TW, int TH) {
   const float xl = __fsub_rn(__fadd_rn((float)(tx * TW), 0.5f), mx);
   const float xh = __fsub_rn(__fsub_rn((float)((tx + 1) * TW), 0.5f), mx);
   const float yl = __fsub_rn(__fadd_rn((float)(ty * TH), 0.5f), my);
@@ -196,10 +203,10 @@ __device__ __forceinline__ bool tile_hit(float A, float B, float C, float mx, fl
     float dx, dy;
     if (e < 2) {
       dx = e == 0 ? xl : xh;
-      dy = fminf(fmaxf(-__fdiv_rn(__fmul_rn(B, dx), C), yl), yh);
+      dy = fminf(fmaxf(__fmul_rn(bc, dx), yl), yh);
     } else {
       dy = e == 2 ? yl : yh;
-      dx = fminf(fmaxf(-__fdiv_rn(__fmul_rn(B, dy), A), xl), xh);
+      dx = fminf(fmaxf(__fmul_rn(ba, dy), xl), xh);
     }
     const float q = __fadd_rn(__fadd_rn(__fmul_rn(A, __fmul_rn(dx, dx)), __fmul_rn(B2, __fmul_rn(dx, dy))),
                               __fmul_rn(C, __fmul_rn(dy, dy)));
@@ -243,9 +250,23 @@ struct CompositeArgs {
   int64_t n;                   // Gaussians (stride of the per-view record arrays)
   const int* slot;             // Gaussian -> block slot or -1 (no information block)
   int64_t n_act;               // active Gaussians (stride of the per-view block arrays)
+  int* err;                    // set to 1 when a bounded wait for staged records gave up (may be NULL)
+  // Scoring launches run as two kernels: the forward pass (launch_forward)
+  // writes every pixel's final transmittance and one past its last blended
+  // list index, fwd[tile * 256 + pixel] = {float bits of T, last}, and each
+  // tile's first list entry with an information block (its list end when it
+  // has none); the information pass (launch_composite with fwd != NULL)
+  // reads them instead of compositing again. Tiles are global tile ids in
+  // the persistent form, the view's tile index otherwise.
+  uint2* fwd;
+  uint32_t* tile_first;
 };
 // stage = Gaussians staged in shared memory per round (16 or 32).
 int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage = 32);
+// The forward pass of a scoring launch (no images): per pixel T and the last
+// blended index into a.fwd, per tile the first active entry into a.tile_first;
+// a.counter (persistent form) must be zeroed first.
+int launch_forward(const CompositeArgs& a, const Consts& c, cudaStream_t st);
 
 // Backward pass of the rasterizer for one view (backward.cu): per-pixel
 // output gradients in, per-Gaussian gradients of the projected quantities

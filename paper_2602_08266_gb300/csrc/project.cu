@@ -116,7 +116,7 @@ __device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, floa
 // kCount (one view at a time) also the radius and the number of rectangle
 // tiles that pass tile_hit; the multi-view path counts them in a separate
 // warp-cooperative pass (k_count_tiles).
-template <bool kCount>
+template <bool kCount, int DEG>
 __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, const DevCam& cam, int64_t g,
                                             const DevProj& pr, size_t o) {
   const float4 ms = s.mu_sig[g];
@@ -202,15 +202,18 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   // ---- view-dependent colour (values; ordinary single precision)
   float dv[3] = {ms.x - cam.campos[0], ms.y - cam.campos[1], ms.z - cam.campos[2]};
   const float il = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+  // the degree is a template argument, so the basis stays in registers
+  constexpr int NB = (DEG + 1) * (DEG + 1);
   float Y[16];
-  sh_eval(c.deg, dv[0] * il, dv[1] * il, dv[2] * il, Y);
+  sh_eval(DEG, dv[0] * il, dv[1] * il, dv[2] * il, Y);
   // SH coefficients as 16-byte vector loads: 3 nb floats per Gaussian start
   // 16-byte aligned when 3 nb is a multiple of 4 (SH degree 1 and 3)
-  const float* shg = s.sh + (size_t)g * c.nb * 3;
+  const float* shg = s.sh + (size_t)g * NB * 3;
   float rgb[3] = {0.5f, 0.5f, 0.5f};
-  if ((c.nb * 3) % 4 == 0) {
+  if constexpr ((NB * 3) % 4 == 0) {
     const float4* sh4 = reinterpret_cast<const float4*>(shg);
-    for (int q = 0; q < (c.nb * 3) / 4; ++q) {
+#pragma unroll
+    for (int q = 0; q < (NB * 3) / 4; ++q) {
       const float4 v4 = __ldg(sh4 + q);
       const float e[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
@@ -220,7 +223,8 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
       }
     }
   } else {
-    for (int k = 0; k < c.nb; ++k)
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
 #pragma unroll
       for (int ch = 0; ch < 3; ++ch) rgb[ch] += Y[k] * shg[3 * k + ch];
   }
@@ -234,22 +238,25 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   if (kCount) {
     pr.radius[o] = r;
     uint32_t hits = 0;
+    const float bc = -__fdiv_rn(B, C), ba = -__fdiv_rn(B, A);
     for (int tyi = y0; tyi < y1; ++tyi)
       for (int txi = x0; txi < x1; ++txi)
-        hits += tile_hit(A, B, C, mx, my, ss.w, txi, tyi, cam.TW, cam.TH) ? 1u : 0u;
+        hits += tile_hit(A, B, C, mx, my, ss.w, bc, ba, txi, tyi, cam.TW, cam.TH) ? 1u : 0u;
     pr.touched[o] = hits;
   }
 }
 
+template <int DEG>
 __global__ void k_project(DevScene s, Consts c, DevCam cam, DevProj pr) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= s.n) return;
-  project_one<true>(s, c, cam, g, pr, (size_t)g);
+  project_one<true, DEG>(s, c, cam, g, pr, (size_t)g);
 }
 
 // All views at once, one thread per (view, Gaussian): view blockIdx.y, slot
 // v n + g; consecutive threads take consecutive Gaussians of one view, so
 // every record load and store is coalesced and the camera is the block's.
+template <int DEG>
 __global__ void __launch_bounds__(256) k_project_views(DevScene s, Consts c, const DevCam* __restrict__ cams,
                                                        DevProj pr) {
   __shared__ DevCam cam;
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(256) k_project_views(DevScene s, Consts c, con
   __syncthreads();
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= s.n) return;
-  project_one<false>(s, c, cam, g, pr, (size_t)v * s.n + g);
+  project_one<false, DEG>(s, c, cam, g, pr, (size_t)v * s.n + g);
 }
 
 }  // namespace
@@ -267,7 +274,13 @@ int launch_project_views(const DevScene& s, const Consts& c, const DevCam* cams,
                          cudaStream_t st) {
   if (s.n <= 0 || nv <= 0) return 0;
   const int bs = 256;
-  k_project_views<<<dim3((unsigned)((s.n + bs - 1) / bs), (unsigned)nv), bs, 0, st>>>(s, c, cams, pr);
+  const dim3 grid((unsigned)((s.n + bs - 1) / bs), (unsigned)nv);
+  switch (c.deg) {
+    case 0: k_project_views<0><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
+    case 1: k_project_views<1><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
+    case 2: k_project_views<2><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
+    default: k_project_views<3><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
+  }
   return 1;
 }
 
@@ -346,7 +359,13 @@ int launch_project(const DevScene& s, const Consts& c, const DevCam& cam, const 
                    cudaStream_t st) {
   if (s.n <= 0) return 0;
   const int bs = 256;
-  k_project<<<(unsigned)((s.n + bs - 1) / bs), bs, 0, st>>>(s, c, cam, pr);
+  const unsigned grid = (unsigned)((s.n + bs - 1) / bs);
+  switch (c.deg) {
+    case 0: k_project<0><<<grid, bs, 0, st>>>(s, c, cam, pr); break;
+    case 1: k_project<1><<<grid, bs, 0, st>>>(s, c, cam, pr); break;
+    case 2: k_project<2><<<grid, bs, 0, st>>>(s, c, cam, pr); break;
+    default: k_project<3><<<grid, bs, 0, st>>>(s, c, cam, pr); break;
+  }
   return 1;
 }
 

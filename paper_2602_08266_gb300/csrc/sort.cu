@@ -86,57 +86,117 @@ int scan_rec(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaSt
   return launches + 1;
 }
 
+// One slot's tile walk: its tile rectangle {x0, x1, y0, y1} (x0 < 0: none),
+// the splat's mean, conic and skip exponent, the stationary-point ratios of
+// tile_hit, and the view's tile grid. The warp kernels below load one slot
+// per lane and then walk the non-empty rectangles one after the other with
+// all 32 lanes, each lane's fields broadcast by shuffles.
+struct SlotTiles {
+  int4 r;
+  float mx, my, thr, A, B, C, bc, ba;
+  uint32_t base;
+  int gx, tw, th;
+};
+
+__device__ __forceinline__ SlotTiles slot_tiles(int4 r, float4 a0, float4 a1, uint32_t base, const DevCam& cam) {
+  SlotTiles t;
+  t.r = r;
+  t.mx = a0.x; t.my = a0.y; t.thr = a0.z;
+  t.A = a1.x; t.B = a1.y; t.C = a1.z;
+  t.bc = -__fdiv_rn(a1.y, a1.z);
+  t.ba = -__fdiv_rn(a1.y, a1.x);
+  t.base = base;
+  t.gx = cam.GX; t.tw = cam.TW; t.th = cam.TH;
+  return t;
+}
+
+__device__ __forceinline__ SlotTiles no_tiles() {
+  SlotTiles t{};
+  t.r = make_int4(-1, -1, -1, -1);
+  t.tw = t.th = 1;
+  return t;
+}
+
+__device__ __forceinline__ SlotTiles shfl_tiles(const SlotTiles& t, int s) {
+  SlotTiles o;
+  o.r = make_int4(__shfl_sync(0xffffffffu, t.r.x, s), __shfl_sync(0xffffffffu, t.r.y, s),
+                  __shfl_sync(0xffffffffu, t.r.z, s), __shfl_sync(0xffffffffu, t.r.w, s));
+  o.mx = __shfl_sync(0xffffffffu, t.mx, s); o.my = __shfl_sync(0xffffffffu, t.my, s);
+  o.thr = __shfl_sync(0xffffffffu, t.thr, s);
+  o.A = __shfl_sync(0xffffffffu, t.A, s); o.B = __shfl_sync(0xffffffffu, t.B, s);
+  o.C = __shfl_sync(0xffffffffu, t.C, s);
+  o.bc = __shfl_sync(0xffffffffu, t.bc, s); o.ba = __shfl_sync(0xffffffffu, t.ba, s);
+  o.base = __shfl_sync(0xffffffffu, t.base, s);
+  o.gx = __shfl_sync(0xffffffffu, t.gx, s);
+  o.tw = __shfl_sync(0xffffffffu, t.tw, s); o.th = __shfl_sync(0xffffffffu, t.th, s);
+  return o;
+}
+
+// Walks rectangle q with the warp, 32 tiles at a time in row order; fn(tx,
+// ty, hit) is called by every lane each round (hit false past the end), so
+// that fn may use warp collectives. keep(tx, ty): a tile filter checked
+// before tile_hit (e.g. a mark).
+template <class Keep, class Fn>
+__device__ __forceinline__ void walk_tiles(const SlotTiles& q, int lane, Keep keep, Fn fn) {
+  const int w = q.r.y - q.r.x, cnt = w * (q.r.w - q.r.z);
+  // entry t = (ty - y0) w + (tx - x0); lane starts at t = lane, steps by 32
+  int qy = lane / w, qx = lane - qy * w;
+  const int dq = 32 / w, dr = 32 - dq * w;
+  for (int t0 = 0; t0 < cnt; t0 += 32) {
+    const int tx = q.r.x + qx, ty = q.r.z + qy;
+    const bool hit = t0 + lane < cnt && keep(tx, ty) &&
+                     tile_hit(q.A, q.B, q.C, q.mx, q.my, q.thr, q.bc, q.ba, tx, ty, q.tw, q.th);
+    fn(tx, ty, hit);
+    qy += dq;
+    qx += dr;
+    if (qx >= w) {
+      qx -= w;
+      ++qy;
+    }
+  }
+}
+
+// A slot's tile rectangle {x0, x1, y0, y1} (exclusive ends) cut to the view's
+// bounding box of marked tiles {min x, min y, max x, max y} (inclusive);
+// x0 = -1 when nothing is left. No tile outside the box is marked.
+__device__ __forceinline__ int4 clip_rect(int4 r, int4 b) {
+  const int4 c = make_int4(max(r.x, b.x), min(r.y, b.z + 1), max(r.z, b.y), min(r.w, b.w + 1));
+  return (c.x < c.y && c.z < c.w) ? c : make_int4(-1, -1, -1, -1);
+}
+
 // Every Gaussian's entries for the tiles of its rectangle that pass
 // tile_hit, in row order: a lane per Gaussian, then each Gaussian's
 // rectangle walked by the whole warp (32 tiles at a time, the passing ones
 // compacted by a ballot), so that the stores of a run are contiguous.
-__global__ void k_duplicate(DevProj pr, int64_t n, int GX, int TW, int TH, const uint32_t* __restrict__ offsets,
+__global__ void k_duplicate(DevProj pr, int64_t n, DevCam cam, const uint32_t* __restrict__ offsets,
                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  int4 r = make_int4(-1, -1, -1, -1);
+  SlotTiles st = no_tiles();
   uint32_t o = 0, zb = 0;
-  float4 a0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), a1 = a0;
   if (g < n) {
-    r = pr.rect[g];
+    const int4 r = pr.rect[g];
     if (r.x >= 0) {
+      st = slot_tiles(r, pr.r0[g], pr.r1[g], 0u, cam);
       o = offsets[g];
       zb = pr.zbits[g];
-      a0 = pr.r0[g];
-      a1 = pr.r1[g];
     }
   }
   const int64_t g0 = g - lane;
-  for (int s = 0; s < 32; ++s) {
-    const int rx = __shfl_sync(0xffffffffu, r.x, s), ry = __shfl_sync(0xffffffffu, r.y, s);
-    const int rz = __shfl_sync(0xffffffffu, r.z, s), rw = __shfl_sync(0xffffffffu, r.w, s);
-    const uint32_t os = __shfl_sync(0xffffffffu, o, s), zs = __shfl_sync(0xffffffffu, zb, s);
-    const float mx = __shfl_sync(0xffffffffu, a0.x, s), my = __shfl_sync(0xffffffffu, a0.y, s);
-    const float thr = __shfl_sync(0xffffffffu, a0.z, s);
-    const float A = __shfl_sync(0xffffffffu, a1.x, s), B = __shfl_sync(0xffffffffu, a1.y, s);
-    const float C = __shfl_sync(0xffffffffu, a1.z, s);
-    if (rx < 0) continue;                       // the same for the whole warp
-    const int w = ry - rx, cnt = w * (rw - rz);
-    int qy = lane / w, qx = lane - qy * w;
-    const int dq = 32 / w, dr = 32 - dq * w;
-    uint32_t wo = os;
-    for (int t0 = 0; t0 < cnt; t0 += 32) {
-      const int tx = rx + qx, ty = rz + qy;
-      const bool hit = t0 + lane < cnt && tile_hit(A, B, C, mx, my, thr, tx, ty, TW, TH);
+  for (unsigned todo = __ballot_sync(0xffffffffu, st.r.x >= 0); todo; todo &= todo - 1) {
+    const int s = __ffs(todo) - 1;
+    const SlotTiles q = shfl_tiles(st, s);
+    const uint32_t zs = __shfl_sync(0xffffffffu, zb, s);
+    uint32_t wo = __shfl_sync(0xffffffffu, o, s);
+    walk_tiles(q, lane, [](int, int) { return true; }, [&](int tx, int ty, bool hit) {
       const unsigned m = __ballot_sync(0xffffffffu, hit);
       if (hit) {
         const uint32_t at = wo + (uint32_t)__popc(m & ((1u << lane) - 1u));
-        keys[at] = ((uint64_t)(ty * GX + tx) << 32) | (uint64_t)zs;
+        keys[at] = ((uint64_t)(ty * q.gx + tx) << 32) | (uint64_t)zs;
         vals[at] = (uint32_t)(g0 + s);
       }
       wo += (uint32_t)__popc(m);
-      qy += dq;
-      qx += dr;
-      if (qx >= w) {
-        qx -= w;
-        ++qy;
-      }
-    }
+    });
   }
 }
 
@@ -270,175 +330,123 @@ __global__ void k_gather_touched(const uint32_t* __restrict__ touched, const uin
 // index) order. A warp takes 32 consecutive slots (one per lane) and then
 // walks their rectangles one slot after the other, 32 tiles at a time, the
 // passing ones compacted by a ballot, so that the stores are contiguous.
+// With a mark, only marked tiles (inside the view's box bb) are emitted.
 __global__ void k_duplicate_sorted(const int4* __restrict__ rect, const float4* __restrict__ r0,
                                    const float4* __restrict__ r1, const uint32_t* __restrict__ order, int64_t n,
                                    int64_t m, const DevCam* __restrict__ cams,
                                    const uint32_t* __restrict__ tile_base, const uint8_t* __restrict__ mark,
-                                   const uint32_t* __restrict__ offsets, uint32_t* __restrict__ keys,
-                                   uint32_t* __restrict__ vals) {
+                                   const int4* __restrict__ bb, const uint32_t* __restrict__ offsets,
+                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  int4 r = make_int4(-1, -1, -1, -1);
-  uint32_t g = 0, base = 0, o = 0;
-  int GX = 0, TW = 1, TH = 1;
-  float4 a0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), a1 = a0;
+  SlotTiles st = no_tiles();
+  uint32_t g = 0, o = 0;
   if (i < m) {
     const uint32_t slot = order[i];
-    r = rect[slot];
+    const int v = (int)(slot / (uint64_t)n);
+    int4 r = rect[slot];
+    if (r.x >= 0 && bb != nullptr) r = clip_rect(r, bb[v]);
     if (r.x >= 0) {
-      const int v = (int)(slot / (uint64_t)n);
       g = (uint32_t)(slot - (uint64_t)v * n);
-      GX = cams[v].GX;
-      TW = cams[v].TW;
-      TH = cams[v].TH;
-      base = tile_base[v];
+      st = slot_tiles(r, r0[slot], r1[slot], tile_base[v], cams[v]);
       o = offsets[i];
-      a0 = r0[slot];
-      a1 = r1[slot];
     }
   }
-  for (int s = 0; s < 32; ++s) {
-    const int rx = __shfl_sync(0xffffffffu, r.x, s), ry = __shfl_sync(0xffffffffu, r.y, s);
-    const int rz = __shfl_sync(0xffffffffu, r.z, s), rw = __shfl_sync(0xffffffffu, r.w, s);
-    const uint32_t gs = __shfl_sync(0xffffffffu, g, s), bs = __shfl_sync(0xffffffffu, base, s);
-    const uint32_t os = __shfl_sync(0xffffffffu, o, s);
-    const int gx = __shfl_sync(0xffffffffu, GX, s);
-    const int tw = __shfl_sync(0xffffffffu, TW, s), th = __shfl_sync(0xffffffffu, TH, s);
-    const float mx = __shfl_sync(0xffffffffu, a0.x, s), my = __shfl_sync(0xffffffffu, a0.y, s);
-    const float thr = __shfl_sync(0xffffffffu, a0.z, s);
-    const float A = __shfl_sync(0xffffffffu, a1.x, s), B = __shfl_sync(0xffffffffu, a1.y, s);
-    const float C = __shfl_sync(0xffffffffu, a1.z, s);
-    if (rx < 0) continue;                       // the same for the whole warp
-    const int w = ry - rx, cnt = w * (rw - rz);
-    // entry t = (ty - rz) w + (tx - rx); lane starts at t = lane, steps by 32
-    int qy = lane / w, qx = lane - qy * w;
-    const int dq = 32 / w, dr = 32 - dq * w;
-    uint32_t wo = os;
-    for (int t0 = 0; t0 < cnt; t0 += 32) {
-      const int tx = rx + qx, ty = rz + qy;
-      const bool hit = t0 + lane < cnt && (mark == nullptr || mark[bs + (uint32_t)(ty * gx + tx)] != 0) &&
-                       tile_hit(A, B, C, mx, my, thr, tx, ty, tw, th);
-      const unsigned mk = __ballot_sync(0xffffffffu, hit);
-      if (hit) {
-        const uint32_t at = wo + (uint32_t)__popc(mk & ((1u << lane) - 1u));
-        keys[at] = bs + (uint32_t)(ty * gx + tx);
-        vals[at] = gs;
-      }
-      wo += (uint32_t)__popc(mk);
-      qy += dq;
-      qx += dr;
-      if (qx >= w) {
-        qx -= w;
-        ++qy;
-      }
-    }
+  for (unsigned todo = __ballot_sync(0xffffffffu, st.r.x >= 0); todo; todo &= todo - 1) {
+    const int s = __ffs(todo) - 1;
+    const SlotTiles q = shfl_tiles(st, s);
+    const uint32_t gs = __shfl_sync(0xffffffffu, g, s);
+    uint32_t wo = __shfl_sync(0xffffffffu, o, s);
+    walk_tiles(
+        q, lane, [&](int tx, int ty) { return mark == nullptr || mark[q.base + (uint32_t)(ty * q.gx + tx)] != 0; },
+        [&](int tx, int ty, bool hit) {
+          const unsigned mk = __ballot_sync(0xffffffffu, hit);
+          if (hit) {
+            const uint32_t at = wo + (uint32_t)__popc(mk & ((1u << lane) - 1u));
+            keys[at] = q.base + (uint32_t)(ty * q.gx + tx);
+            vals[at] = gs;
+          }
+          wo += (uint32_t)__popc(mk);
+        });
   }
 }
 
 // The tiles (global ids) where a splat of the active set can pass its skip
 // test: its rectangle's tiles that pass tile_hit, one lane per active
-// (view, slot) pair, each rectangle walked by the whole warp.
+// (view, slot) pair, each rectangle walked by the whole warp; and each view's
+// bounding box of those tiles.
+__global__ void k_bbox_init(int4* __restrict__ bb, int nv) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nv) bb[v] = make_int4(0x7fffffff, 0x7fffffff, -1, -1);
+}
+
 __global__ void k_mark_tiles(const int4* __restrict__ rect, const float4* __restrict__ r0,
                              const float4* __restrict__ r1, const int* __restrict__ act, int64_t n_act, int64_t n,
                              int nv, const DevCam* __restrict__ cams, const uint32_t* __restrict__ tile_base,
-                             uint8_t* __restrict__ mark) {
+                             uint8_t* __restrict__ mark, int4* __restrict__ bb) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int4 r = make_int4(-1, -1, -1, -1);
-  uint32_t base = 0;
-  int GX = 0, TW = 1, TH = 1;
-  float4 a0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), a1 = a0;
+  const int lane = threadIdx.x & 31;
+  SlotTiles st = no_tiles();
+  int vv = 0;
   if (i < n_act * nv) {
     const int v = (int)(i / n_act);
     const size_t slot = (size_t)v * n + act[i - (int64_t)v * n_act];
-    r = rect[slot];
-    if (r.x >= 0) {
-      GX = cams[v].GX; TW = cams[v].TW; TH = cams[v].TH;
-      base = tile_base[v];
-      a0 = r0[slot];
-      a1 = r1[slot];
-    }
+    const int4 r = rect[slot];
+    vv = v;
+    if (r.x >= 0) st = slot_tiles(r, r0[slot], r1[slot], tile_base[v], cams[v]);
   }
-  const int lane = threadIdx.x & 31;
-  for (int s = 0; s < 32; ++s) {
-    const int rx = __shfl_sync(0xffffffffu, r.x, s), ry = __shfl_sync(0xffffffffu, r.y, s);
-    const int rz = __shfl_sync(0xffffffffu, r.z, s), rw = __shfl_sync(0xffffffffu, r.w, s);
-    const uint32_t bs = __shfl_sync(0xffffffffu, base, s);
-    const int gx = __shfl_sync(0xffffffffu, GX, s);
-    const int tw = __shfl_sync(0xffffffffu, TW, s), th = __shfl_sync(0xffffffffu, TH, s);
-    const float mx = __shfl_sync(0xffffffffu, a0.x, s), my = __shfl_sync(0xffffffffu, a0.y, s);
-    const float thr = __shfl_sync(0xffffffffu, a0.z, s);
-    const float A = __shfl_sync(0xffffffffu, a1.x, s), B = __shfl_sync(0xffffffffu, a1.y, s);
-    const float C = __shfl_sync(0xffffffffu, a1.z, s);
-    if (rx < 0) continue;                       // the same for the whole warp
-    const int w = ry - rx, cnt = w * (rw - rz);
-    // entry t = (ty - rz) w + (tx - rx); lane starts at t = lane, steps by 32
-    int qy = lane / w, qx = lane - qy * w;
-    const int dq = 32 / w, dr = 32 - dq * w;
-    for (int t = lane; t < cnt; t += 32) {
-      const int ty = rz + qy, tx = rx + qx;
-      if (tile_hit(A, B, C, mx, my, thr, tx, ty, tw, th)) mark[bs + (uint32_t)(ty * gx + tx)] = 1;
-      qy += dq;
-      qx += dr;
-      if (qx >= w) {
-        qx -= w;
-        ++qy;
+  for (unsigned todo = __ballot_sync(0xffffffffu, st.r.x >= 0); todo; todo &= todo - 1) {
+    const int s = __ffs(todo) - 1;
+    const SlotTiles q = shfl_tiles(st, s);
+    const int vs = __shfl_sync(0xffffffffu, vv, s);
+    int lo_x = 0x7fffffff, lo_y = 0x7fffffff, hi_x = -1, hi_y = -1;
+    walk_tiles(q, lane, [](int, int) { return true; }, [&](int tx, int ty, bool hit) {
+      if (hit) {
+        mark[q.base + (uint32_t)(ty * q.gx + tx)] = 1;
+        lo_x = min(lo_x, tx); hi_x = max(hi_x, tx);
+        lo_y = min(lo_y, ty); hi_y = max(hi_y, ty);
       }
+    });
+    // the view's bounding box of marked tiles (one set of atomics per rectangle)
+    lo_x = __reduce_min_sync(0xffffffffu, lo_x);
+    lo_y = __reduce_min_sync(0xffffffffu, lo_y);
+    hi_x = __reduce_max_sync(0xffffffffu, hi_x);
+    hi_y = __reduce_max_sync(0xffffffffu, hi_y);
+    if (lane == 0 && hi_x >= 0) {
+      int* b = reinterpret_cast<int*>(bb + vs);
+      atomicMin(b, lo_x);
+      atomicMin(b + 1, lo_y);
+      atomicMax(b + 2, hi_x);
+      atomicMax(b + 3, hi_y);
     }
   }
 }
 
 // Entries every (view, Gaussian) slot will emit: its rectangle's tiles that
-// pass tile_hit (and, with a mark, that a splat of the active set reaches).
-// A lane per slot, then each rectangle walked by the whole warp, 32 tiles at
-// a time, the passing ones counted by a ballot.
+// pass tile_hit (and, with a mark, that a splat of the active set reaches,
+// all inside the view's box bb). A lane per slot, then each non-empty
+// rectangle walked by the whole warp, the passing tiles counted by a ballot.
 __global__ void k_count_tiles(const int4* __restrict__ rect, const float4* __restrict__ r0,
                               const float4* __restrict__ r1, int64_t n, int nv, const DevCam* __restrict__ cams,
                               const uint32_t* __restrict__ tile_base, const uint8_t* __restrict__ mark,
-                              uint32_t* __restrict__ touched) {
+                              const int4* __restrict__ bb, uint32_t* __restrict__ touched) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  int4 r = make_int4(-1, -1, -1, -1);
-  uint32_t base = 0;
-  int GX = 0, TW = 1, TH = 1;
-  float4 a0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), a1 = a0;
+  SlotTiles st = no_tiles();
   if (i < n * nv) {
-    r = rect[i];
-    if (r.x >= 0) {
-      const int v = (int)(i / n);
-      GX = cams[v].GX; TW = cams[v].TW; TH = cams[v].TH;
-      base = tile_base[v];
-      a0 = r0[i];
-      a1 = r1[i];
-    }
+    const int v = (int)(i / n);
+    int4 r = rect[i];
+    if (r.x >= 0 && bb != nullptr) r = clip_rect(r, bb[v]);
+    if (r.x >= 0) st = slot_tiles(r, r0[i], r1[i], tile_base[v], cams[v]);
   }
   uint32_t mine = 0;
-  for (int s = 0; s < 32; ++s) {
-    const int rx = __shfl_sync(0xffffffffu, r.x, s), ry = __shfl_sync(0xffffffffu, r.y, s);
-    const int rz = __shfl_sync(0xffffffffu, r.z, s), rw = __shfl_sync(0xffffffffu, r.w, s);
-    const uint32_t bs = __shfl_sync(0xffffffffu, base, s);
-    const int gx = __shfl_sync(0xffffffffu, GX, s);
-    const int tw = __shfl_sync(0xffffffffu, TW, s), th = __shfl_sync(0xffffffffu, TH, s);
-    const float mx = __shfl_sync(0xffffffffu, a0.x, s), my = __shfl_sync(0xffffffffu, a0.y, s);
-    const float thr = __shfl_sync(0xffffffffu, a0.z, s);
-    const float A = __shfl_sync(0xffffffffu, a1.x, s), B = __shfl_sync(0xffffffffu, a1.y, s);
-    const float C = __shfl_sync(0xffffffffu, a1.z, s);
-    if (rx < 0) continue;                       // the same for the whole warp
-    const int w = ry - rx, cnt = w * (rw - rz);
-    int qy = lane / w, qx = lane - qy * w;
-    const int dq = 32 / w, dr = 32 - dq * w;
+  for (unsigned todo = __ballot_sync(0xffffffffu, st.r.x >= 0); todo; todo &= todo - 1) {
+    const int s = __ffs(todo) - 1;
+    const SlotTiles q = shfl_tiles(st, s);
     uint32_t tot = 0;
-    for (int t0 = 0; t0 < cnt; t0 += 32) {
-      const int ty = rz + qy, tx = rx + qx;
-      const bool hit = t0 + lane < cnt && (mark == nullptr || mark[bs + (uint32_t)(ty * gx + tx)] != 0) &&
-                       tile_hit(A, B, C, mx, my, thr, tx, ty, tw, th);
-      tot += (uint32_t)__popc(__ballot_sync(0xffffffffu, hit));
-      qy += dq;
-      qx += dr;
-      if (qx >= w) {
-        qx -= w;
-        ++qy;
-      }
-    }
+    walk_tiles(
+        q, lane, [&](int tx, int ty) { return mark == nullptr || mark[q.base + (uint32_t)(ty * q.gx + tx)] != 0; },
+        [&](int, int, bool hit) { tot += (uint32_t)__popc(__ballot_sync(0xffffffffu, hit)); });
     if (lane == s) mine = tot;
   }
   if (i < n * nv) touched[i] = mine;
@@ -529,10 +537,10 @@ int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
   return l + 1;
 }
 
-int launch_duplicate(const DevProj& pr, int64_t n, int GX, int TW, int TH, const uint32_t* offsets, uint64_t* keys,
+int launch_duplicate(const DevProj& pr, int64_t n, const DevCam& cam, const uint32_t* offsets, uint64_t* keys,
                      uint32_t* vals, cudaStream_t st) {
   if (n <= 0) return 0;
-  k_duplicate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pr, n, GX, TW, TH, offsets, keys, vals);
+  k_duplicate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pr, n, cam, offsets, keys, vals);
   return 1;
 }
 
@@ -561,28 +569,32 @@ int launch_gather_touched(const uint32_t* touched, const uint32_t* order, int64_
 
 int launch_duplicate_sorted(const int4* rect, const float4* r0, const float4* r1, const uint32_t* order, int64_t n,
                             int64_t m, const DevCam* cams, const uint32_t* tile_base, const uint8_t* mark,
-                            const uint32_t* offsets, uint32_t* keys, uint32_t* vals, cudaStream_t st) {
+                            const int4* bb, const uint32_t* offsets, uint32_t* keys, uint32_t* vals,
+                            cudaStream_t st) {
   if (m <= 0) return 0;
   k_duplicate_sorted<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, order, n, m, cams, tile_base, mark,
-                                                                  offsets, keys, vals);
+                                                                  bb, offsets, keys, vals);
   return 1;
 }
 
 int launch_mark_tiles(const int4* rect, const float4* r0, const float4* r1, const int* act, int64_t n_act, int64_t n,
                       int nv, const DevCam* cams, const uint32_t* tile_base, uint8_t* mark, int64_t ntiles,
-                      cudaStream_t st) {
+                      int4* bb, cudaStream_t st) {
   cudaMemsetAsync(mark, 0, (size_t)ntiles, st);
+  k_bbox_init<<<(nv + 255) / 256, 256, 0, st>>>(bb, nv);
   const int64_t m = n_act * nv;
-  if (m <= 0) return 0;
-  k_mark_tiles<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, act, n_act, n, nv, cams, tile_base, mark);
-  return 1;
+  if (m <= 0) return 1;
+  k_mark_tiles<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, act, n_act, n, nv, cams, tile_base, mark,
+                                                            bb);
+  return 2;
 }
 
 int launch_count_tiles(const int4* rect, const float4* r0, const float4* r1, int64_t n, int nv, const DevCam* cams,
-                       const uint32_t* tile_base, const uint8_t* mark, uint32_t* touched, cudaStream_t st) {
+                       const uint32_t* tile_base, const uint8_t* mark, const int4* bb, uint32_t* touched,
+                       cudaStream_t st) {
   const int64_t m = n * nv;
   if (m <= 0) return 0;
-  k_count_tiles<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, n, nv, cams, tile_base, mark, touched);
+  k_count_tiles<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, n, nv, cams, tile_base, mark, bb, touched);
   return 1;
 }
 

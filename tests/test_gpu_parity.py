@@ -626,3 +626,25 @@ def test_tile_culling_elongated_splats_valid(P, aniso):
         if aniso < 1.0:
             _compare_render(sc, o, cam, 0, 1)
         sc.close()
+
+
+def test_batch_workload_reduced_target_parity(P):
+    """The batching workload's structure (32 blobs + table, K = 32, SH 3,
+    candidates alternating 320x240 and 640x480, object-centric on object 1,
+    Eq. 12) with a fiftieth of the Gaussians, 2 candidates and the training
+    views at 320x240 (so that the oracle finishes in about a minute): the
+    multi-view graph path (tiles an active splat reaches are the only ones
+    binned) and the per-view path against the oracle at 1e-4."""
+    wl = S.make_workload("batch", n_views=2, scale=0.02)
+    wl.train = S.training_cameras(320, 240, 262.5)
+    assert wl.target == 1 and set(wl.cand.width.tolist()) == {320, 640}
+    ref = O.OracleScene(wl.scene, target=wl.target).score(wl.train, wl.cand)
+    for batched in (1, 0):
+        sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=batched)
+        sc.load_scene(wl.scene)
+        sc.set_train_views(wl.train)
+        sc.set_candidates(wl.cand)
+        sc.prepare(wl.target)
+        for _ in range(2 if batched else 1):
+            _check_scores(sc.score_host().astype(np.float64), ref, sc.train_gains().astype(np.float64))
+        sc.close()
