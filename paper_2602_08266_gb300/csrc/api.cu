@@ -443,20 +443,18 @@ int binning_counts(nbv_ctx* ctx, cudaStream_t st) {
   const int64_t slots = (int64_t)B.nv * n;
   const DevScene s = dev_scene(ctx);
   int l = 0;
+  const bool target = ctx->n_act < n;
   {
     Phase ph(ctx, NBV_PHASE_PROJECT);
-    l += launch_project_views(s, ctx->c, B.cams, B.nv, B.pr, st);
+    if (target)   // marks, boxes and per-slot counts in the projection itself
+      l += launch_project_target(s, ctx->c, B.cams, B.nv, B.pr, B.mark, B.ntiles, B.bbox, B.tile_base, st);
+    else
+      l += launch_project_views(s, ctx->c, B.cams, B.nv, B.pr, st);
   }
   Phase ph(ctx, NBV_PHASE_SORT);
-  const uint8_t* mark = nullptr;
-  const int4* bbox = nullptr;
-  if (ctx->n_act < n) {
-    l += launch_mark_tiles(B.pr.rect, B.pr.r0, B.pr.r1, ctx->act, ctx->n_act, n, B.nv, B.cams, B.tile_base, B.mark,
-                           B.ntiles, B.bbox, st);
-    mark = B.mark;
-    bbox = B.bbox;
-  }
-  l += launch_count_tiles(B.pr.rect, B.pr.r0, B.pr.r1, n, B.nv, B.cams, B.tile_base, mark, bbox, B.pr.touched, st);
+  if (!target)
+    l += launch_count_tiles(B.pr.rect, B.pr.r0, B.pr.r1, n, B.nv, B.cams, B.tile_base, nullptr, nullptr,
+                            B.pr.touched, st);
   l += launch_compact_depth_keys(B.pr.touched, slots, B.flags, B.offsets, B.scan_tmp, B.pr.zbits, n, B.db.keys[0],
                                  B.db.vals[0], st);
   return l;

@@ -1547,6 +1547,109 @@ __device__ __forceinline__ float obj_logdet_rows(int u, int K, float cg, float w
   return logf(mant) + (float)ex * 0.693147180559945309f;
 }
 
+// The same for 32 < u <= UO <= 64 rows: lane l holds rows l and l + 32. Row r
+// of G = I + c W B is formed from row r of W (shared memory) and the
+// structured B: G[r][c < 6] = [r = c] + c sum_k W[r][k] B[k][c] (B's first six
+// columns are Q above X), and for j < K
+//   G[r][6 + j] = [r = 6 + j] + c (sum_{k<6} W[r][k] X[j][k] + w2 (W[r][6 + j] + sum_{k>=6} W[r][k]))
+// (B's probability block is w2 (I + 1 1^T)). Gaussian elimination with
+// partial pivoting (the largest |G[.][k]| among the rows left, by one warp
+// max over 6-bit row keys; near-ties within 2^-17 relative go to the lower
+// row), the rows shifted left by one column per step.
+template <int UO>
+__device__ __forceinline__ float obj_logdet_rows2(int u, int K, float cg, float w2, const float* W, const float* Qs,
+                                                  const float* Xs, int lane, int crit) {
+  const int ra = lane, rb = lane + 32;
+  const bool rowa = ra < u, rowb = rb < u;
+  if (crit != 0) {   // trace criteria: c tr(W B) = c sum_r sum_k W[r][k] B[k][r]
+    float br = 0.0f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = h ? rb : ra;
+      if (!(h ? rowb : rowa)) continue;
+      const float* Wr = W + r * u;
+      if (r < 6) {
+        for (int k = 0; k < u; ++k) br += Wr[k] * (k < 6 ? Qs[k * 6 + r] : Xs[(k - 6) * 6 + r]);
+      } else {
+        const int j = r - 6;
+        float sw = 0.0f;
+        for (int k = 6; k < u; ++k) sw += Wr[k];
+        for (int k = 0; k < 6; ++k) br += Wr[k] * Xs[j * 6 + k];
+        br += w2 * (Wr[r] + sw);
+      }
+    }
+    for (int o = 16; o >= 1; o >>= 1) br += __shfl_xor_sync(0xffffffffu, br, o);
+    return cg * br;
+  }
+  float ga[UO], gb[UO];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int r = h ? rb : ra;
+    const bool row = h ? rowb : rowa;
+    float* g = h ? gb : ga;
+    const float* Wr = W + (row ? r : 0) * u;
+    float a[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float sw = 0.0f, w6[6];
+    for (int k = 0; k < u; ++k) {
+      const float wk = row ? Wr[k] : 0.0f;
+      if (k >= 6) sw += wk;
+      const float* bk = k < 6 ? Qs + k * 6 : Xs + (k - 6) * 6;
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) a[cc] += wk * bk[cc];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w6[k] = row ? Wr[k] : 0.0f;
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) g[cc] = (r == cc ? 1.0f : 0.0f) + cg * a[cc];
+#pragma unroll
+    for (int j = 0; j < UO - 6; ++j) {
+      float t = 0.0f;
+      if (j < K) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) t += w6[k] * Xs[j * 6 + k];
+        t += w2 * ((row ? Wr[6 + j] : 0.0f) + sw);
+      }
+      g[6 + j] = (r == 6 + j ? 1.0f : 0.0f) + (j < K ? cg * t : 0.0f);
+    }
+  }
+  bool done_a = !rowa, done_b = !rowb;
+  float mant = 1.0f;
+  int ex = 0;
+  for (int k = 0; k < u; ++k) {
+    const unsigned ka = done_a ? 0u : ((__float_as_uint(fabsf(ga[0])) & ~63u) | (unsigned)(63 - ra));
+    const unsigned kb = done_b ? 0u : ((__float_as_uint(fabsf(gb[0])) & ~63u) | (unsigned)(63 - rb));
+    const int prow = 63 - (int)(__reduce_max_sync(0xffffffffu, max(ka, kb)) & 63u);
+    const int bl = prow & 31;
+    const bool hb = prow >= 32;                 // the same for the whole warp
+    const float piv = hb ? __shfl_sync(0xffffffffu, gb[0], bl) : __shfl_sync(0xffffffffu, ga[0], bl);
+    {
+      const uint32_t b = __float_as_uint(mant * fabsf(piv));
+      ex += (int)((b >> 23) & 0xFFu) - 127;
+      mant = __uint_as_float((b & 0x007FFFFFu) | 0x3F800000u);
+    }
+    const float fa_ = (!done_a && ra != prow) ? __fdividef(ga[0], piv) : 0.0f;
+    const float fb_ = (!done_b && rb != prow) ? __fdividef(gb[0], piv) : 0.0f;
+    const int live = u - k - 1;
+#pragma unroll
+    for (int j0 = 0; j0 < UO - 1; j0 += 4) {
+      if (j0 < live) {
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          if (j0 + jj < UO - 1) {
+            const float pj = hb ? __shfl_sync(0xffffffffu, gb[j0 + jj + 1], bl)
+                                : __shfl_sync(0xffffffffu, ga[j0 + jj + 1], bl);
+            ga[j0 + jj] = ga[j0 + jj + 1] - fa_ * pj;
+            gb[j0 + jj] = gb[j0 + jj + 1] - fb_ * pj;
+          }
+        }
+      }
+    }
+    if (ra == prow) done_a = true;
+    if (rb == prow) done_b = true;
+  }
+  return logf(mant) + (float)ex * 0.693147180559945309f;
+}
+
 struct GmLayout {     // per-warp shared memory (floats)
   int nt0, nt1, nt2;  // packed sizes of L~ per output
   int l2, u2;         // object output sizes
@@ -1693,14 +1796,15 @@ __global__ void __launch_bounds__(256, 1) k_gains_gm(DevScene s, Consts c, const
         Wo[cc * u2 + r] = w;
       }
       float d2;
-      if (u2 <= 32) {
+      if (u2 <= 40) {
         // Q (full 6 x 6) and X of this view's block into shared memory
         for (int i = lane; i < 36 + 6 * K; i += 32)
           Bo[i] = i < 36 ? q6(bsrc + kOffQo, i / 6, i % 6) : bsrc[kOffXo + i - 36];
         __syncwarp();
         const float w2 = bsrc[kOffW2];
-        d2 = u2 <= 24 ? obj_logdet_rows<24>(u2, K, cg, w2, Wo, Bo, Bo + 36, lane, c.crit)
-                      : obj_logdet_rows<32>(u2, K, cg, w2, Wo, Bo, Bo + 36, lane, c.crit);
+        d2 = u2 <= 24   ? obj_logdet_rows<24>(u2, K, cg, w2, Wo, Bo, Bo + 36, lane, c.crit)
+             : u2 <= 32 ? obj_logdet_rows<32>(u2, K, cg, w2, Wo, Bo, Bo + 36, lane, c.crit)
+                        : obj_logdet_rows2<40>(u2, K, cg, w2, Wo, Bo, Bo + 36, lane, c.crit);
         __syncwarp();
       } else {
         build_B(2, bsrc, c, Bo, lane);                 // ends with __syncwarp

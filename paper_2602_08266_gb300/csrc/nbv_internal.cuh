@@ -108,6 +108,13 @@ int launch_project(const DevScene& s, const Consts& c, const DevCam& cam, const 
 // Projection of every Gaussian into nv views (device camera array); slot v n + g.
 int launch_project_views(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const DevProj& pr,
                          cudaStream_t st);
+// The same with an active subset (s.n_act < s.n): the active slots are
+// projected first and their tiles marked (mark [ntiles], zeroed here; bb [nv]
+// each view's box of marked tiles), then every slot gets pr.touched = its
+// marked tiles inside the box that pass tile_hit, and records only if that is
+// not zero (no other slot's records are read).
+int launch_project_target(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const DevProj& pr,
+                          uint8_t* mark, int64_t ntiles, int4* bb, const uint32_t* tile_base, cudaStream_t st);
 
 struct SortBuffers {
   uint64_t* keys[2];
@@ -144,14 +151,6 @@ int launch_duplicate_sorted(const int4* rect, const float4* r0, const float4* r1
                             int64_t m, const DevCam* cams, const uint32_t* tile_base, const uint8_t* mark,
                             const int4* bb, const uint32_t* offsets, uint32_t* keys, uint32_t* vals,
                             cudaStream_t st);
-// mark [ntiles] (global tile ids; zeroed first) = 1 where a splat of the
-// active set passes tile_hit: the only tiles whose lists matter for the
-// information gain when only part of the scene carries a confidence; bb
-// [nv] = each view's bounding box of marked tiles {min x, min y, max x,
-// max y} (empty: max < 0).
-int launch_mark_tiles(const int4* rect, const float4* r0, const float4* r1, const int* act, int64_t n_act, int64_t n,
-                      int nv, const DevCam* cams, const uint32_t* tile_base, uint8_t* mark, int64_t ntiles,
-                      int4* bb, cudaStream_t st);
 // touched [nv n] = entries of every slot (rectangle tiles passing tile_hit,
 // marked ones inside the view's box bb only when mark != NULL).
 int launch_count_tiles(const int4* rect, const float4* r0, const float4* r1, int64_t n, int nv, const DevCam* cams,

@@ -112,24 +112,43 @@ __device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, floa
   (void)kPi;
 }
 
-// Project Gaussian g into camera cam; the records go to slot o of pr. With
-// kCount (one view at a time) also the radius and the number of rectangle
-// tiles that pass tile_hit; the multi-view path counts them in a separate
-// warp-cooperative pass (k_count_tiles).
-template <bool kCount, int DEG>
+// What project_one does besides computing a slot's records.
+enum ProjMode {
+  kProjAll = 0,      // multi-view: records of every slot (tiles counted by k_count_tiles)
+  kProjCount = 1,    // one view: records, radius and the number of rectangle tiles that pass tile_hit
+  kProjMark = 2,     // multi-view, active slots: records, and their tiles marked in the view's tile mark
+  kProjTarget = 3    // multi-view with a mark: the number of marked tiles inside the view's box that
+                     // pass tile_hit; records only for a slot with at least one
+};
+
+// Tile marks of the multi-view pass with an active subset.
+struct TileMark {
+  uint8_t* mark;            // [global tiles]
+  int4* bb;                 // [views] bounding box of marked tiles {min x, min y, max x, max y}
+  uint32_t base;            // the view's first global tile
+  int lo_x, lo_y, hi_x, hi_y;   // kProjMark: the box of the tiles this slot marked (hi_x < 0: none)
+};
+
+// Project Gaussian g into camera cam; the records go to slot o of pr (see
+// ProjMode for what else).
+template <int kMode, int DEG>
 __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, const DevCam& cam, int64_t g,
-                                            const DevProj& pr, size_t o) {
+                                            const DevProj& pr, size_t o, TileMark* tm = nullptr) {
   const float4 ms = s.mu_sig[g];
   const float4 ss = s.scale_skip[g];
   const float4 qq = s.qn[g];
   const float4 ax = s.aux[g];
   const float* R = cam.R;
-  if (kCount) {
+  if (kMode == kProjCount) {
     pr.touched[o] = 0u;
     pr.radius[o] = 0.0f;
   }
-  pr.rect[o] = make_int4(-1, -1, -1, -1);
-  pr.zbits[o] = 0u;
+  if (kMode == kProjTarget) {
+    pr.touched[o] = 0u;           // records are read only for slots with entries
+  } else {
+    pr.rect[o] = make_int4(-1, -1, -1, -1);
+    pr.zbits[o] = 0u;
+  }
   // ---- key path: correctly rounded single precision, fixed order
   const float tx = fa(fa(fa(fm(R[0], ms.x), fm(R[1], ms.y)), fm(R[2], ms.z)), cam.t[0]);
   const float ty = fa(fa(fa(fm(R[3], ms.x), fm(R[4], ms.y)), fm(R[5], ms.z)), cam.t[1]);
@@ -199,6 +218,23 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   const int y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)cam.GY);
   const int y1 = (int)fminf(fmaxf(fy1, 0.0f), (float)cam.GY);
   if (x0 >= x1 || y0 >= y1) return;
+  if (kMode == kProjTarget) {
+    // marked tiles of the rectangle inside the view's box that pass tile_hit
+    const int4 b = tm->bb[0];
+    const int cx0 = max(x0, b.x), cx1 = min(x1, b.z + 1), cy0 = max(y0, b.y), cy1 = min(y1, b.w + 1);
+    uint32_t hits = 0;
+    if (cx0 < cx1 && cy0 < cy1) {
+      const float bc = -__fdiv_rn(B, C), ba = -__fdiv_rn(B, A);
+      for (int tyi = cy0; tyi < cy1; ++tyi)
+        for (int txi = cx0; txi < cx1; ++txi)
+          hits += (tm->mark[tm->base + (uint32_t)(tyi * cam.GX + txi)] != 0 &&
+                   tile_hit(A, B, C, mx, my, ss.w, bc, ba, txi, tyi, cam.TW, cam.TH))
+                      ? 1u
+                      : 0u;
+    }
+    pr.touched[o] = hits;
+    if (hits == 0) return;
+  }
   // ---- view-dependent colour (values; ordinary single precision)
   float dv[3] = {ms.x - cam.campos[0], ms.y - cam.campos[1], ms.z - cam.campos[2]};
   const float il = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
@@ -235,7 +271,21 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   pr.r2[o] = make_float4(rgb[0], rgb[1], rgb[2], tz);
   pr.rect[o] = make_int4(x0, x1, y0, y1);
   pr.zbits[o] = __float_as_uint(tz);
-  if (kCount) {
+  if (kMode == kProjMark) {
+    // mark this active splat's tiles and grow the view's box around them
+    const float bc = -__fdiv_rn(B, C), ba = -__fdiv_rn(B, A);
+    int lo_x = 0x7fffffff, lo_y = 0x7fffffff, hi_x = -1, hi_y = -1;
+    for (int tyi = y0; tyi < y1; ++tyi)
+      for (int txi = x0; txi < x1; ++txi)
+        if (tile_hit(A, B, C, mx, my, ss.w, bc, ba, txi, tyi, cam.TW, cam.TH)) {
+          uint8_t* mk = tm->mark + tm->base + (uint32_t)(tyi * cam.GX + txi);
+          if (*mk == 0) *mk = 1;     // most tiles are marked by many splats: read before writing
+          lo_x = min(lo_x, txi); hi_x = max(hi_x, txi);
+          lo_y = min(lo_y, tyi); hi_y = max(hi_y, tyi);
+        }
+    tm->lo_x = lo_x; tm->lo_y = lo_y; tm->hi_x = hi_x; tm->hi_y = hi_y;   // the caller merges them into the box
+  }
+  if (kMode == kProjCount) {
     pr.radius[o] = r;
     uint32_t hits = 0;
     const float bc = -__fdiv_rn(B, C), ba = -__fdiv_rn(B, A);
@@ -250,22 +300,50 @@ template <int DEG>
 __global__ void k_project(DevScene s, Consts c, DevCam cam, DevProj pr) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= s.n) return;
-  project_one<true, DEG>(s, c, cam, g, pr, (size_t)g);
+  project_one<kProjCount, DEG>(s, c, cam, g, pr, (size_t)g);
 }
 
 // All views at once, one thread per (view, Gaussian): view blockIdx.y, slot
 // v n + g; consecutive threads take consecutive Gaussians of one view, so
 // every record load and store is coalesced and the camera is the block's.
-template <int DEG>
+template <int DEG, int kMode>
 __global__ void __launch_bounds__(256) k_project_views(DevScene s, Consts c, const DevCam* __restrict__ cams,
-                                                       DevProj pr) {
+                                                       DevProj pr, uint8_t* mark, int4* bb,
+                                                       const uint32_t* __restrict__ tile_base) {
   __shared__ DevCam cam;
   const int v = blockIdx.y;
   if (threadIdx.x == 0) cam = cams[v];
   __syncthreads();
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= s.n) return;
-  project_one<false, DEG>(s, c, cam, g, pr, (size_t)v * s.n + g);
+  TileMark tm{};
+  if (kMode == kProjTarget) tm = TileMark{mark, bb + v, tile_base[v], 0, 0, -1, -1};
+  project_one<kMode, DEG>(s, c, cam, g, pr, (size_t)v * s.n + g, &tm);
+}
+
+// Active slots of the multi-view pass (thread per (view, active slot)):
+// records, and their tiles marked with the view's box of marked tiles.
+template <int DEG>
+__global__ void __launch_bounds__(256) k_project_active(DevScene s, Consts c, const DevCam* __restrict__ cams,
+                                                        int nv, DevProj pr, uint8_t* mark, int4* bb,
+                                                        const uint32_t* __restrict__ tile_base) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= s.n_act * nv) return;
+  const int v = (int)(i / s.n_act);
+  const int64_t g = s.act[i - (int64_t)v * s.n_act];
+  TileMark tm{mark, bb + v, tile_base[v], 0x7fffffff, 0x7fffffff, -1, -1};
+  project_one<kProjMark, DEG>(s, c, cams[v], g, pr, (size_t)v * s.n + g, &tm);
+  // merge into the view's box: one set of atomics per view present in the warp
+  const unsigned peers = __match_any_sync(__activemask(), v);
+  const int lo_x = __reduce_min_sync(peers, tm.lo_x), lo_y = __reduce_min_sync(peers, tm.lo_y);
+  const int hi_x = __reduce_max_sync(peers, tm.hi_x), hi_y = __reduce_max_sync(peers, tm.hi_y);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1 && hi_x >= 0) {
+    int* b = reinterpret_cast<int*>(bb + v);
+    atomicMin(b, lo_x);
+    atomicMin(b + 1, lo_y);
+    atomicMax(b + 2, hi_x);
+    atomicMax(b + 3, hi_y);
+  }
 }
 
 }  // namespace
@@ -276,12 +354,47 @@ int launch_project_views(const DevScene& s, const Consts& c, const DevCam* cams,
   const int bs = 256;
   const dim3 grid((unsigned)((s.n + bs - 1) / bs), (unsigned)nv);
   switch (c.deg) {
-    case 0: k_project_views<0><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
-    case 1: k_project_views<1><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
-    case 2: k_project_views<2><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
-    default: k_project_views<3><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
+    case 0: k_project_views<0, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr, nullptr, nullptr, nullptr); break;
+    case 1: k_project_views<1, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr, nullptr, nullptr, nullptr); break;
+    case 2: k_project_views<2, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr, nullptr, nullptr, nullptr); break;
+    default: k_project_views<3, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr, nullptr, nullptr, nullptr); break;
   }
   return 1;
+}
+
+namespace {
+__global__ void k_bbox_reset(int4* __restrict__ bb, int nv) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nv) bb[v] = make_int4(0x7fffffff, 0x7fffffff, -1, -1);
+}
+}  // namespace
+
+int launch_project_target(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const DevProj& pr,
+                          uint8_t* mark, int64_t ntiles, int4* bb, const uint32_t* tile_base, cudaStream_t st) {
+  if (s.n <= 0 || nv <= 0) return 0;
+  cudaMemsetAsync(mark, 0, (size_t)ntiles, st);
+  k_bbox_reset<<<(nv + 255) / 256, 256, 0, st>>>(bb, nv);
+  int l = 1;
+  const int bs = 256;
+  const int64_t na = s.n_act * nv;
+  if (na > 0) {
+    const unsigned ga = (unsigned)((na + bs - 1) / bs);
+    switch (c.deg) {
+      case 0: k_project_active<0><<<ga, bs, 0, st>>>(s, c, cams, nv, pr, mark, bb, tile_base); break;
+      case 1: k_project_active<1><<<ga, bs, 0, st>>>(s, c, cams, nv, pr, mark, bb, tile_base); break;
+      case 2: k_project_active<2><<<ga, bs, 0, st>>>(s, c, cams, nv, pr, mark, bb, tile_base); break;
+      default: k_project_active<3><<<ga, bs, 0, st>>>(s, c, cams, nv, pr, mark, bb, tile_base); break;
+    }
+    ++l;
+  }
+  const dim3 grid((unsigned)((s.n + bs - 1) / bs), (unsigned)nv);
+  switch (c.deg) {
+    case 0: k_project_views<0, kProjTarget><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
+    case 1: k_project_views<1, kProjTarget><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
+    case 2: k_project_views<2, kProjTarget><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
+    default: k_project_views<3, kProjTarget><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
+  }
+  return l + 1;
 }
 
 namespace {

@@ -371,57 +371,6 @@ __global__ void k_duplicate_sorted(const int4* __restrict__ rect, const float4* 
   }
 }
 
-// The tiles (global ids) where a splat of the active set can pass its skip
-// test: its rectangle's tiles that pass tile_hit, one lane per active
-// (view, slot) pair, each rectangle walked by the whole warp; and each view's
-// bounding box of those tiles.
-__global__ void k_bbox_init(int4* __restrict__ bb, int nv) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < nv) bb[v] = make_int4(0x7fffffff, 0x7fffffff, -1, -1);
-}
-
-__global__ void k_mark_tiles(const int4* __restrict__ rect, const float4* __restrict__ r0,
-                             const float4* __restrict__ r1, const int* __restrict__ act, int64_t n_act, int64_t n,
-                             int nv, const DevCam* __restrict__ cams, const uint32_t* __restrict__ tile_base,
-                             uint8_t* __restrict__ mark, int4* __restrict__ bb) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  SlotTiles st = no_tiles();
-  int vv = 0;
-  if (i < n_act * nv) {
-    const int v = (int)(i / n_act);
-    const size_t slot = (size_t)v * n + act[i - (int64_t)v * n_act];
-    const int4 r = rect[slot];
-    vv = v;
-    if (r.x >= 0) st = slot_tiles(r, r0[slot], r1[slot], tile_base[v], cams[v]);
-  }
-  for (unsigned todo = __ballot_sync(0xffffffffu, st.r.x >= 0); todo; todo &= todo - 1) {
-    const int s = __ffs(todo) - 1;
-    const SlotTiles q = shfl_tiles(st, s);
-    const int vs = __shfl_sync(0xffffffffu, vv, s);
-    int lo_x = 0x7fffffff, lo_y = 0x7fffffff, hi_x = -1, hi_y = -1;
-    walk_tiles(q, lane, [](int, int) { return true; }, [&](int tx, int ty, bool hit) {
-      if (hit) {
-        mark[q.base + (uint32_t)(ty * q.gx + tx)] = 1;
-        lo_x = min(lo_x, tx); hi_x = max(hi_x, tx);
-        lo_y = min(lo_y, ty); hi_y = max(hi_y, ty);
-      }
-    });
-    // the view's bounding box of marked tiles (one set of atomics per rectangle)
-    lo_x = __reduce_min_sync(0xffffffffu, lo_x);
-    lo_y = __reduce_min_sync(0xffffffffu, lo_y);
-    hi_x = __reduce_max_sync(0xffffffffu, hi_x);
-    hi_y = __reduce_max_sync(0xffffffffu, hi_y);
-    if (lane == 0 && hi_x >= 0) {
-      int* b = reinterpret_cast<int*>(bb + vs);
-      atomicMin(b, lo_x);
-      atomicMin(b + 1, lo_y);
-      atomicMax(b + 2, hi_x);
-      atomicMax(b + 3, hi_y);
-    }
-  }
-}
-
 // Entries every (view, Gaussian) slot will emit: its rectangle's tiles that
 // pass tile_hit (and, with a mark, that a splat of the active set reaches,
 // all inside the view's box bb). A lane per slot, then each non-empty
@@ -575,18 +524,6 @@ int launch_duplicate_sorted(const int4* rect, const float4* r0, const float4* r1
   k_duplicate_sorted<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, order, n, m, cams, tile_base, mark,
                                                                   bb, offsets, keys, vals);
   return 1;
-}
-
-int launch_mark_tiles(const int4* rect, const float4* r0, const float4* r1, const int* act, int64_t n_act, int64_t n,
-                      int nv, const DevCam* cams, const uint32_t* tile_base, uint8_t* mark, int64_t ntiles,
-                      int4* bb, cudaStream_t st) {
-  cudaMemsetAsync(mark, 0, (size_t)ntiles, st);
-  k_bbox_init<<<(nv + 255) / 256, 256, 0, st>>>(bb, nv);
-  const int64_t m = n_act * nv;
-  if (m <= 0) return 1;
-  k_mark_tiles<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(rect, r0, r1, act, n_act, n, nv, cams, tile_base, mark,
-                                                            bb);
-  return 2;
 }
 
 int launch_count_tiles(const int4* rect, const float4* r0, const float4* r1, int64_t n, int nv, const DevCam* cams,

@@ -648,3 +648,25 @@ def test_batch_workload_reduced_target_parity(P):
         for _ in range(2 if batched else 1):
             _check_scores(sc.score_host().astype(np.float64), ref, sc.train_gains().astype(np.float64))
         sc.close()
+
+
+@pytest.mark.parametrize("crit,batched", [(0, 1), (1, 1), (0, 0)])
+def test_k32_object_gains_parity(P, crit, batched):
+    """K = 32 objects (the object block of a Gaussian is 38 x 38, eliminated
+    two rows per lane) on the tiny scene with its logits padded to 33
+    channels: log-det and first-order trace gains against the oracle."""
+    wl = S.make_workload("tiny")
+    sc0 = wl.scene
+    K = 32
+    rng = np.random.default_rng(11)
+    obj = rng.normal(-1.0, 0.5, (sc0.n, K + 1)).astype(np.float32)
+    obj[:, : sc0.K + 1] = sc0.obj_logits
+    wl.scene = S.Scene(sc0.means, sc0.log_scales, sc0.quats, sc0.opacity, sc0.sh, obj, sc0.sh_degree, K)
+    sc = P.NBVScorer(K, wl.scene.sh_degree, batched=batched, criterion=crit)
+    sc.load_scene(wl.scene)
+    sc.set_train_views(wl.train)
+    sc.set_candidates(wl.cand)
+    sc.prepare(-1)
+    ref = O.OracleScene(wl.scene, hyper=O.Hyper(crit=crit)).score(wl.train, wl.cand)
+    _check_scores(sc.score_host().astype(np.float64), ref, sc.train_gains().astype(np.float64))
+    sc.close()
