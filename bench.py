@@ -147,16 +147,25 @@ class Clocks:
 
 
 # ------------------------------------------------------- roofline numbers
+def forward_fp32_flops(stats, K):
+    """Algorithmic FP32 work of the forward pass by the scope table's
+    measurement constant: 16 + (K+1) flops per (pixel, splat) pair it
+    evaluates (exponent, alpha, transmittance, weight, colour, depth and the
+    K+1 object sums; a scoring launch needs only the first four)."""
+    return stats["pairs_evaluated"] * (16 + K + 1)
+
+
+def information_fp32_flops(stats, K):
+    """Algorithmic FP32 work of the information pass: 110 + 8 (K+1) flops per
+    (pixel, splat) pair (d out / d alpha of every output and the per-pixel
+    block contributions), pairs = the blended pixels of splats that carry a
+    block (c_g > 0)."""
+    return stats["pairs_information"] * (110 + 8 * (K + 1))
+
+
 def composite_fp32_flops(stats, K):
-    """Algorithmic FP32 work of the compositing kernel by the per-pair
-    constants of the scope table's measurement row: 16 + (K+1) flops per
-    (pixel, splat) pair evaluated by the forward pass (exponent, alpha,
-    transmittance, weight, colour, depth and K+1 object sums) and
-    110 + 8 (K+1) per pair of the information pass (d out / d alpha of every
-    output and the per-pixel block contributions). Pairs of the information
-    pass are the blended pixels of splats that carry a block (c_g > 0)."""
-    kc = K + 1
-    return stats["pairs_evaluated"] * (16 + kc) + stats["pairs_information"] * (110 + 8 * kc)
+    """Both passes' algorithmic FP32 work (forward + information)."""
+    return forward_fp32_flops(stats, K) + information_fp32_flops(stats, K)
 
 
 def composite_tensor_flops(stats, K):
@@ -165,6 +174,17 @@ def composite_tensor_flops(stats, K):
     splat's structured block (2 flops each), which the kernel contracts on
     the TF32 tensor cores."""
     return stats["pairs_information"] * 2 * (88 + 6 * K)
+
+
+# DRAM bytes (read + write) per candidate view of the batching workload's
+# information pass (k_composite) and forward pass (k_forward), from ncu
+# captures of one launch each on the same workload with 8 candidates
+# (profiles/k_composite_batch8_ncu_full.md, profiles/k_forward_batch8_ncu_full.md);
+# a full launch's traffic is taken as this times its candidates (the tiles,
+# lists and blocks grow with the views). None when no capture of the
+# current kernels exists.
+BATCH_INFO_DRAM_BYTES_PER_VIEW = 20_207_872 / 8
+BATCH_FORWARD_DRAM_BYTES_PER_VIEW = (27_336_448 + 29_952) / 8
 
 
 def project_bytes(n, nv, sh_degree):
@@ -353,27 +373,36 @@ def run_ours(args):
 
     K = wl.scene.K
     cst = score_p["stats"]
-    comp_ms = score_p["phases"]["composite"][0] / psteps
     launches = max(cst["composite_launches"] // psteps, 1)
     per_launch = {k: v / psteps / launches for k, v in cst.items() if k != "composite_launches"}
-    comp_launch_s = comp_ms / 1e3 / launches
-    fl32 = composite_fp32_flops(per_launch, K)
+    info_s = score_p["phases"]["composite"][0] / psteps / launches / 1e3
+    fwd_s = score_p["phases"]["forward"][0] / psteps / launches / 1e3
+    fl_info = information_fp32_flops(per_launch, K)
+    fl_fwd = forward_fp32_flops(per_launch, K)
     fltc = composite_tensor_flops(per_launch, K)
-    achieved = fl32 / comp_launch_s / 1e12
-    traffic = None   # DRAM bytes per launch from an ncu capture of the current kernel (none yet)
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": traffic,
-                "kernel": "k_composite (forward + information pass, all 256 candidates in one persistent launch)",
-                "peak_basis": (f"measured FP32 FMA throughput on this GPU (fma.rn.f32: {fma_scalar:.1f}, "
-                               f"fma.rn.f32x2: {fma_packed:.1f} TFLOP/s), the larger"),
-                "flops_per_launch": round(fl32), "launch_ms": round(comp_launch_s * 1e3, 3),
-                "flop_constants": f"{16 + K + 1} per forward pair, {110 + 8 * (K + 1)} per information pair",
-                "tensor": {"tf32_flops_per_launch": round(fltc),
-                           "achieved_tflops": round(fltc / comp_launch_s / 1e12, 3),
-                           "peak_tflops": round(peaks["bf16_tflops"] / 2, 1),
-                           "peak_basis": f"{peaks['basis']} bf16 dense x 1/2 (nominal tf32 : bf16)"}}
+    nv = wl.cand.n
+    peak_note = (f"measured FP32 FMA throughput on this GPU (fma.rn.f32: {fma_scalar:.1f}, "
+                 f"fma.rn.f32x2: {fma_packed:.1f} TFLOP/s), the larger")
+
+    def alu_roof(flops, sec, kernel, consts, traffic_per_view):
+        ach = flops / sec / 1e12 if sec > 0 else 0.0
+        traffic = None
+        if traffic_per_view is not None and args.workload == "batch" and args.views is None:
+            traffic = int(traffic_per_view * nv)
+        return {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(ach / fp32_peak, 4), "traffic": traffic, "kernel": kernel, "peak_basis": peak_note,
+                "flops_per_launch": round(flops), "launch_ms": round(sec * 1e3, 3), "flop_constants": consts}
+
+    roofline = alu_roof(fl_info, info_s, "k_composite: information pass, all candidates in one persistent launch",
+                        f"{110 + 8 * (K + 1)} per information pair", BATCH_INFO_DRAM_BYTES_PER_VIEW)
+    roofline["tensor"] = {"tf32_flops_per_launch": round(fltc),
+                          "achieved_tflops": round(fltc / info_s / 1e12, 3) if info_s > 0 else 0.0,
+                          "peak_tflops": round(peaks["bf16_tflops"] / 2, 1),
+                          "peak_basis": f"{peaks['basis']} bf16 dense x 1/2 (nominal tf32 : bf16)"}
+    roof_fwd = alu_roof(fl_fwd, fwd_s, "k_forward: forward pass, all candidates in one persistent launch",
+                        f"{16 + K + 1} per forward pair", BATCH_FORWARD_DRAM_BYTES_PER_VIEW)
     # projection and sort of the candidates' pass (HBM)
-    n, nv = wl.scene.n, wl.cand.n
+    n = wl.scene.n
     proj_ms = score_p["phases"]["project"][0] / psteps
     pb = project_bytes(n, nv, wl.scene.sh_degree)
     sort_ms = score_p["phases"]["sort"][0] / psteps
@@ -404,7 +433,9 @@ def run_ours(args):
                    "tile": f"{tiling[0]}x{tiling[1]}", "stage": tiling[2], "autotuned": not args.no_autotune},
         "gpu_launches": int(head["launches"]),
         "roofline": roofline,
-        "roofline_project": hbm_roof(pb, proj_ms, "k_project_views (all candidates)",
+        "roofline_forward": roof_fwd,
+        "roofline_project": hbm_roof(pb, proj_ms, "projection phase of the candidates' pass (active slots, "
+                                     "then every slot with its marked-tile count)",
                                      "48 + 12 (d+1)^2 B read per Gaussian, 44 B written per (view, Gaussian)"),
         "roofline_sort": hbm_roof(sort_bytes(entries, nv, ntiles), sort_ms,
                                   "binning of the candidates' pass (all kernels of the sort phase)",

@@ -222,8 +222,9 @@ enum {
   NBV_PHASE_GAINS = 5,     /* per-Gaussian log-det gains and their sums (Eqs. 5-6) */
   NBV_PHASE_SCORE = 6,     /* normalisation, weighting, argmax (Eqs. 10-11) */
   NBV_PHASE_TRAIN_COMPOSITE = 7, /* compositing + information blocks of the training views (prepare);
-                                    NBV_PHASE_COMPOSITE holds the candidates' launches */
-  NBV_NUM_PHASES = 8
+                                    NBV_PHASE_COMPOSITE holds the candidates' information pass */
+  NBV_PHASE_FORWARD = 8,   /* the candidates' forward pass (transmittance and list ends per pixel) */
+  NBV_NUM_PHASES = 9
 };
 
 /* Switch per-phase timing on (1) or off (0); either call clears the

@@ -393,7 +393,7 @@ class NBVScorer:
                                                   _dptr(ids), total, ctypes.byref(cnt)))
         return off, ids[:total]
 
-    PHASES = ("prep", "project", "sort", "composite", "factors", "gains", "score", "train_composite")
+    PHASES = ("prep", "project", "sort", "composite", "factors", "gains", "score", "train_composite", "forward")
 
     def set_profiling(self, on: bool):
         self._check(self.lib.nbv_set_profiling(self._h, 1 if on else 0))

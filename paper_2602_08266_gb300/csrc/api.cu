@@ -376,10 +376,13 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
     a.tile_first = ctx->tile_first;
   }
   if (blocks || rgb || depth || alpha || obj) {
-    Phase ph(ctx, training ? NBV_PHASE_TRAIN_COMPOSITE : NBV_PHASE_COMPOSITE);
     Consts cc = ctx->c;
     if (compensated) cc.tf32 = 0;
-    if (scoring) CKR(check_launch(ctx, launch_forward(a, cc, st)));
+    if (scoring) {
+      Phase ph(ctx, training ? NBV_PHASE_TRAIN_COMPOSITE : NBV_PHASE_FORWARD);
+      CKR(check_launch(ctx, launch_forward(a, cc, st)));
+    }
+    Phase ph(ctx, training ? NBV_PHASE_TRAIN_COMPOSITE : NBV_PHASE_COMPOSITE);
     CKR(check_launch(ctx, launch_composite(a, cc, st, ctx->stage)));
     if (ctx->prof) ctx->composite_launches[training ? 1 : 0]++;
   }
@@ -584,7 +587,6 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
     qv = B.qb.vals[qw];
   }
   {
-    Phase ph(ctx, NBV_PHASE_COMPOSITE);
     CK(cudaMemsetAsync(B.counter, 0, 2 * sizeof(int), st));
     if (ctx->prof) {
       ctx->composite_launches[0]++;
@@ -611,7 +613,11 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
     a.err = ctx->d_flags + 3;
     a.fwd = B.fwd;
     a.tile_first = B.tile_first;
-    CKR(check_launch(ctx, launch_forward(a, ctx->c, st)));   // records of view v start at slot v n
+    {
+      Phase ph(ctx, NBV_PHASE_FORWARD);
+      CKR(check_launch(ctx, launch_forward(a, ctx->c, st)));   // records of view v start at slot v n
+    }
+    Phase ph(ctx, NBV_PHASE_COMPOSITE);
     a.counter = B.counter + 1;
     CKR(check_launch(ctx, launch_composite(a, ctx->c, st, ctx->stage)));
   }
