@@ -530,34 +530,26 @@ def diff_eval(args, P, S, torch, np, dev):
             "loss": "L1 colour + L1 depth + 0.1 object cross-entropy against a perturbed copy"}
 
 
+SURROGATE_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2602_08266_gb300",
+                                 "surrogate_k64.npz")
+
+
 def surrogate_eval(args, P, S, torch, np, dev):
-    """The learned pre-scoring on scene-scale workloads: labels from the exact
-    path on 48 seeded training scenes (256 candidates each), 400 Adam steps on
-    exp(2 z) / 4 of the per-scene standardised scores, then on 4 unseen scenes
-    with 512 candidates each: the exact best among all 512 (multi-view path)
-    against the best of the 64 the network keeps (nbv_score_pruned), and the
-    pruned step's throughput (prepare + descriptors + MLP + exact scoring of
-    the 64 kept) against the unpruned multi-view step on the same scenes;
-    CUDA events, L2 flushed between steps."""
-    from paper_2602_08266_gb300 import surrogate as SG
-    t0 = time.perf_counter()
-    xs, zs = [], []
-    for s in range(48):
-        wl = S.make_workload("scene", seed=5000 + s, n_views=256)
-        x, z, _ = SG.scene_labels(P, wl)
-        xs.append(x)
-        zs.append(z)
-    X, Y = torch.cat(xs), SG.rank_target(torch.cat(zs))
-    t_labels = time.perf_counter() - t0
-    mlp = P.MLP(448, 256, seed=7)
-    t1 = time.perf_counter()
-    losses = SG.train(mlp, X, Y, steps=400, batch=512, lr=1e-3)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t1
-    keep, ncand, trials = 64, 512, 4
-    agree = 0
-    ratios = []
-    times, full_times = [], []
+    """The learned pre-scoring on the 1M-Gaussian workload (K = 64, SH degree 3,
+    1,024 candidates at 640x480): the network trained on 100 seeded scenes by
+    paper_2602_08266_gb300.train_surrogate (its weights in the package),
+    on one scene it never saw in training (seed 20000, the first of that run's
+    evaluation scenes). Exact best among all 1,024 (the unpruned multi-view
+    step, timed once) against the best of the 32 the network keeps
+    (nbv_score_pruned: prepare + descriptors + MLP + exact scoring of the
+    kept, timed over the bench's steps); CUDA events, L2 flushed before
+    every step."""
+    if not os.path.exists(SURROGATE_WEIGHTS):
+        return {"unavailable": "no trained network in the package (run paper_2602_08266_gb300.train_surrogate)"}
+    w = np.load(SURROGATE_WEIGHTS)
+    mlp = P.MLP(int(w["d_in"]), int(w["width"]), seed=0)
+    mlp.set_params(torch.from_numpy(w["params"]).to(dev))
+    keep = 32
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -571,42 +563,35 @@ def surrogate_eval(args, P, S, torch, np, dev):
         e1.synchronize()
         return r, e0.elapsed_time(e1)
 
-    for s in range(trials):
-        wl = S.make_workload("scene", seed=9000 + s, n_views=ncand)
-        sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=1)
-        sc.load_scene(wl.scene)
-        sc.set_train_views(wl.train)
-        sc.set_candidates(wl.cand)
-        sc.prepare(-1)
-        full = sc.score_host().astype(np.float64)
-        best_exact = int(np.argmax(full[:, 3]))
-        out = torch.empty((ncand, 4), device=dev)
-        for i in range(args.warmup + args.steps):
-            _, ms = timed(lambda: (sc.prepare(-1), sc.score(out), sc.argmax()))
-            if i >= args.warmup:
-                full_times.append(ms)
-        for i in range(args.warmup + args.steps):
-            r, ms = timed(lambda: (sc.prepare(-1), sc.score_pruned(mlp, keep))[1])
-            if i >= args.warmup:
-                times.append(ms)
-        agree += int(r["best"] == best_exact)
-        ratios.append(float(full[r["best"], 3] / full[best_exact, 3]))
-        sc.close()
+    wl = S.make_workload("surrogate", seed=20000)
+    ncand = wl.cand.n
+    sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=1)
+    sc.load_scene(wl.scene)
+    sc.set_train_views(wl.train)
+    sc.set_candidates(wl.cand)
+    out = torch.empty((ncand, 4), device=dev)
+    sc.prepare(wl.target)
+    _, ms_full = timed(lambda: (sc.prepare(wl.target), sc.score(out), sc.argmax()))
+    full = out.cpu().numpy().astype(np.float64)
+    best_exact = int(np.argmax(full[:, 3]))
+    times = []
+    for i in range(args.warmup + args.steps):
+        r, ms = timed(lambda: (sc.prepare(wl.target), sc.score_pruned(mlp, keep))[1])
+        if i >= args.warmup:
+            times.append(ms)
+    sc.close()
     mlp.close()
     ms = float(np.mean(times))
-    ms_full = float(np.mean(full_times))
-    value = ncand / (ms / 1e3)
-    return {"value": round(value, 3), "unit": UNIT, "ms_per_step": round(ms, 3),
-            "candidates_per_step": ncand, "kept": keep,
-            "top1_agreement": f"{agree}/{trials}",
-            "chosen_over_best_exact_score": [round(x, 4) for x in ratios],
-            "unpruned_multi_view": {"value": round(ncand / (ms_full / 1e3), 3), "ms_per_step": round(ms_full, 3)},
+    return {"value": round(ncand / (ms / 1e3), 3), "unit": UNIT, "ms_per_step": round(ms, 3),
+            "workload": workload_desc(wl), "candidates_per_step": ncand, "kept": keep,
+            "chosen_is_exact_best": bool(r["best"] == best_exact),
+            "chosen_over_best_exact_score": round(float(full[r["best"], 3] / full[best_exact, 3]), 6),
+            "unpruned_multi_view": {"value": round(ncand / (ms_full / 1e3), 3), "ms_per_step": round(ms_full, 3),
+                                    "steps": 1},
             "speedup_vs_unpruned_multi_view": round(ms_full / ms, 2),
-            "train": {"scenes": 48, "labels": int(X.shape[0]), "steps": 400, "first_loss": round(losses[0], 4),
-                      "last_loss": round(losses[-1], 4), "label_s": round(t_labels, 1),
-                      "train_s": round(t_train, 1)},
-            "path": "per-view descriptors + BF16 tcgen05 MLP over all candidates, exact multi-view scoring "
-                    "of the 64 kept; step includes prepare"}
+            "network": "448 -> 256 -> 256 -> 1, BF16 on tcgen05; trained on 100 scenes x 250 labelled candidates",
+            "path": "per-view descriptors + MLP over all candidates, exact multi-view scoring of the 32 kept; "
+                    "step includes prepare"}
 
 
 def e2e_host(args, P, wl, torch, np, tiling):

@@ -38,10 +38,14 @@ def _cams_subset(S, cams, idx):
 
 
 def run(P, S, truth, init, train, cand, held_out, iterations=3, refine_steps=10, lr=2e-3, target=-1,
-        mlp=None, keep=64):
+        mlp=None, keep=64, on_choice=None):
     """truth / init: nbv_synth.Scene (ground truth, starting map); train:
     the initially observed cameras; cand: candidate cameras; held_out:
-    cameras the map is evaluated on. Returns a LoopResult."""
+    cameras the map is evaluated on. on_choice(map_scene, observed, remaining,
+    chosen, scores), if given, is called at every choice with the map that
+    was scored (an nbv_synth.Scene copy), the observed cameras, the remaining
+    candidates' indices, the chosen index and the exact scores [n, 4] of the
+    remaining candidates (None when an MLP pruned them). Returns a LoopResult."""
     import torch
 
     from . import diff
@@ -89,6 +93,7 @@ def run(P, S, truth, init, train, cand, held_out, iterations=3, refine_steps=10,
         sub = _cams_subset(S, cand, remaining)
         sc.set_candidates(sub)
         sc.prepare(target)
+        scores = None
         if mlp is not None:
             r = sc.score_pruned(mlp, keep)
             best_local, best_score = r["best"], r["best_score"]
@@ -96,6 +101,9 @@ def run(P, S, truth, init, train, cand, held_out, iterations=3, refine_steps=10,
             scores = sc.score_host()
             best_local = int(np.argmax(scores[:, 3]))
             best_score = float(scores[best_local, 3])
+        if on_choice is not None:
+            snap = [p.detach().cpu().numpy().copy() for p in params]
+            on_choice(S.Scene(*snap, deg, K), observed, list(remaining), remaining[best_local], scores)
         chosen = remaining.pop(best_local)
         new = _cams_subset(S, cand, [chosen])
         observed = S.Cameras(*[np.concatenate([getattr(observed, f), getattr(new, f)])

@@ -123,3 +123,73 @@ def test_autograd_function_and_refinement(P):
         l1 = float(total_loss())
     assert l1 < 0.8 * l0, (l0, l1)
     s.close()
+
+
+def test_backward_on_a_1000_gaussian_crop_of_the_500k_scene(P):
+    """The backward on the 500,000-Gaussian table-top scene's densest
+    region: the 1,000 Gaussians nearest the first observed view's central
+    ray, rendered at 640x480 with K=32 objects and SH degree 3. Per
+    parameter type, 16 sampled (Gaussian, component) pairs among the
+    Gaussians with the larger gradients, and 4 random directions over all
+    1,000 Gaussians, against FP64 central differences of the oracle's frozen
+    renders. The perturbation actually applied is the float32 difference,
+    so rounding of the perturbed parameters does not enter the comparison."""
+    wl = S.make_workload("diff", seed=0)
+    full, cams = wl.scene, wl.train
+    pc = full.means @ cams.R[0].T + cams.t[0]
+    ray = np.where(pc[:, 2] > 0.1, np.hypot(pc[:, 0] / pc[:, 2], pc[:, 1] / pc[:, 2]), np.inf)
+    c = int(np.argmin(ray))
+    sc = full.subset(np.sort(np.argsort(np.linalg.norm(full.means - full.means[c], axis=1))[:1000]))
+    H, W = int(cams.height[0]), int(cams.width[0])
+    rng = np.random.default_rng(42)
+    wts = dict(rgb=rng.normal(0, 1, (H, W, 3)), depth=rng.normal(0, 1, (H, W)), alpha=rng.normal(0, 1, (H, W)),
+               obj=rng.normal(0, 1, (H, W, sc.K + 1)))
+    s = P.NBVScorer(sc.K, sc.sh_degree)
+    s.load_scene(sc)
+    t = {k: torch.from_numpy(v.astype(np.float32)).cuda() for k, v in wts.items()}
+    g = s.render_backward(cams, 0, t["rgb"], t["depth"], t["alpha"], t["obj"])
+    g = {k: v.cpu().numpy().astype(np.float64).reshape(sc.n, -1) for k, v in g.items()}
+    s.close()
+    fz = O.OracleScene(sc).freeze(cams, 0)
+
+    def loss(scene):
+        r = O.OracleScene(scene).render_frozen(fz, cams, 0)
+        return sum(float((r[k] * wts[k]).sum()) for k in wts)
+
+    def shifted(which, delta):
+        """The scene with `delta` added to one parameter array in float32,
+        and the perturbation that float32 actually applied."""
+        sc2 = S.Scene(sc.means.copy(), sc.log_scales.copy(), sc.quats.copy(), sc.opacity.copy(),
+                      sc.sh.copy(), sc.obj_logits.copy(), sc.sh_degree, sc.K)
+        arr = getattr(sc2, which)
+        base = arr.reshape(sc.n, -1).astype(np.float64)
+        new = (base + delta).astype(np.float32)
+        arr.reshape(sc.n, -1)[...] = new
+        return sc2, new.astype(np.float64) - base
+
+    h = 2.0 ** -14
+    for which in ("means", "log_scales", "quats", "opacity", "sh", "obj_logits"):
+        gw = g[which]
+        cols = gw.shape[1]
+        row = np.abs(gw).max(1)
+        strong = np.nonzero(row >= np.quantile(row, 0.75))[0]
+        assert row.max() > 0, which
+        scale = np.abs(gw).max()
+        for _ in range(16):
+            gi, j = int(rng.choice(strong)), int(rng.integers(cols))
+            e = np.zeros((sc.n, cols))
+            e[gi, j] = h
+            sp, dp = shifted(which, e)
+            sm, dm = shifted(which, -e)
+            fd = (loss(sp) - loss(sm)) / (dp[gi, j] - dm[gi, j])
+            assert abs(gw[gi, j] - fd) <= 2e-3 * scale, (which, gi, j, gw[gi, j], fd, scale)
+        for _ in range(4):
+            v = rng.normal(0, 1, (sc.n, cols))
+            sp, dp = shifted(which, h * v)
+            sm, dm = shifted(which, -h * v)
+            fd = loss(sp) - loss(sm)
+            lin = float((gw * (dp - dm)).sum())
+            # errors in single entries add up like a random walk over the
+            # terms, so the bar follows the terms' 2-norm
+            mag = float(np.linalg.norm(gw * (dp - dm)))
+            assert abs(lin - fd) <= 1e-3 * abs(fd) + 1e-2 * mag, (which, lin, fd, mag)

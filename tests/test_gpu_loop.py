@@ -28,3 +28,39 @@ def test_closed_loop_refines_the_map():
     for s in res.steps:
         assert np.isfinite(s.score) and s.loss_after < s.loss_before
     assert res.steps[-1].held_out_error < res.initial_held_out_error
+
+
+def test_loop_choices_equal_the_oracle_argmax_on_the_refined_map():
+    """Every view the closed loop chooses (Eq. 5 on the map refined so far,
+    scored against the views observed so far) is the oracle's argmax on that
+    same map, observed set and remaining candidates, unless the oracle's top
+    two are within the score tolerance; the loop's scores match the
+    oracle's at 1e-4."""
+    import paper_2602_08266_gb300 as P
+    from oracle import oracle as O
+    from paper_2602_08266_gb300 import loop
+    P.build()
+    P.load_library()
+    wl = S.make_workload("tiny", n_views=16)
+    truth = wl.scene
+    rng = np.random.default_rng(5)
+    init = S.Scene(truth.means + rng.normal(0, 0.004, truth.means.shape).astype(np.float32),
+                   truth.log_scales.copy(), truth.quats.copy(),
+                   (truth.opacity + rng.normal(0, 0.2, truth.opacity.shape)).astype(np.float32),
+                   truth.sh.copy(), truth.obj_logits.copy(), truth.sh_degree, truth.K)
+    held = S.sphere_cameras(np.random.default_rng(78), 2, 0.6, 64, 48, 60.0)
+    checked = []
+
+    def on_choice(map_scene, observed, remaining, chosen, scores):
+        cand = wl.cand.subset(remaining)
+        ref = O.OracleScene(map_scene).score(observed, cand)
+        tot = ref["score"]
+        np.testing.assert_allclose(scores[:, 3].astype(np.float64), tot, rtol=1e-4)
+        order = np.argsort(-tot)
+        if len(tot) < 2 or tot[order[0]] - tot[order[1]] > 2e-4 * abs(tot[order[0]]):
+            assert chosen == remaining[int(order[0])], (chosen, remaining[int(order[0])])
+        checked.append(chosen)
+
+    res = loop.run(P, S, truth, init, wl.train, wl.cand, held, iterations=3, refine_steps=10,
+                   on_choice=on_choice)
+    assert len(checked) == 3 and checked == [s.chosen for s in res.steps]

@@ -43,6 +43,34 @@ def test_gemm_bf16_tcgen05(P, M, N, K, ta, tb):
     assert np.all(np.abs(D - want) <= 1e-4 * scale + 1e-6)
 
 
+def test_gemm_bounded_wait_runs_out_and_device_stays_usable(P):
+    """The first wait for the tensor cores' commit given no polls gives up
+    at once: the launch records the time-out (NBV_ERR_TIMEOUT), drains what
+    it has in flight with the full bound and frees its tensor memory; with
+    the default restored the same product is exact again, and an MLP forward
+    pass still works."""
+    rng = np.random.default_rng(3)
+    a = SO.bf16(rng.normal(0, 1, (200, 96)).astype(np.float32))
+    b = SO.bf16(rng.normal(0, 1, (48, 96)).astype(np.float32))
+    A, B = _bf(a), _bf(b)
+    try:
+        P.set_gemm_wait_polls(0)
+        for _ in range(2):
+            with pytest.raises(P.NBVError) as e:
+                P.gemm_bf16(A, (96, 1), B, (96, 1), 200, 48, 96)
+            assert e.value.code == -5
+    finally:
+        P.set_gemm_wait_polls(-1)
+    D = P.gemm_bf16(A, (96, 1), B, (96, 1), 200, 48, 96).cpu().numpy().astype(np.float64)
+    want = a.astype(np.float64) @ b.astype(np.float64).T
+    scale = np.abs(a).astype(np.float64) @ np.abs(b).astype(np.float64).T
+    assert np.all(np.abs(D - want) <= 1e-4 * scale + 1e-6)
+    mlp = P.MLP(96, 64, seed=1)
+    y = mlp.forward(torch.from_numpy(a).cuda())
+    assert torch.isfinite(y).all()
+    mlp.close()
+
+
 @pytest.mark.parametrize("name,target,scale", [("tiny", -1, None), ("tiny", 2, None), ("scene", -1, 0.05)])
 def test_descriptors_match_oracle(P, name, target, scale):
     wl = S.make_workload(name, n_views=12, scale=scale)
