@@ -81,8 +81,9 @@ typedef struct {
   int stage;             /* Gaussians the compositing kernel stages in shared memory per round:
                             32 (default) or 16; only speed depends on it */
   int max_batch_views;   /* batched path: candidates per multi-view pass (0 = as many as keep the
-                            per-(view, Gaussian) state under 32 GB); larger sets run in chunks,
-                            eagerly, and only a single-chunk set is replayed as a CUDA graph */
+                            per-(view, Gaussian) state under 45% of the free device memory);
+                            larger sets run in chunks, eagerly, and only a single-chunk set is
+                            replayed as a CUDA graph */
   int criterion;         /* per-Gaussian information criterion of Eq. 6's block-diagonal form:
                             0 (default) log det(H_T + c A_v) - log det H_T, the paper's;
                             1 tr(H_T^-1 c A_v), its first-order term (an expected-information
@@ -413,6 +414,15 @@ int nbv_mlp_train_step(nbv_mlp* mlp, const float* x, const float* t, int rows, f
  * if a bounded wait for the tensor cores gave up. Asynchronous. */
 int nbv_gemm_bf16(const uint16_t* A, int64_t a_sm, int64_t a_sk, const uint16_t* B, int64_t b_sn, int64_t b_sk,
                   float* D, int64_t ldd, int M, int N, int K, int* d_err, void* cuda_stream);
+
+/* Polls the first wait of every nbv_gemm_bf16 launch for the tensor cores'
+ * commit makes before it gives up (polls = 0: at once; polls < 0 restores
+ * the default 2^20). After giving up a launch records *d_err = 1 (NBV_ERR_TIMEOUT
+ * for the MLP calls), waits once more with the full bound for the work it
+ * has in flight, frees its tensor memory and returns, so the device stays
+ * usable. For tests of that path; process-wide, not thread-safe.
+ * Errors: NBV_ERR_ARG (polls above 2^32 - 1). */
+int nbv_set_gemm_wait_polls(int64_t polls);
 
 /* Pre-score every candidate with the MLP over its descriptor, keep the
  * `keep` highest predictions (ties to the lower index) and score only those

@@ -101,6 +101,7 @@ _SIGS = [
     ("nbv_score_pruned", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_float)]),
     ("nbv_set_entry_limit", ctypes.c_int, [_P, ctypes.c_int64]),
+    ("nbv_set_gemm_wait_polls", ctypes.c_int, [ctypes.c_int64]),
     ("nbv_last_error", ctypes.c_char_p, [_P]),
     ("nbv_launch_count", ctypes.c_int64, [_P]),
 ]
@@ -522,6 +523,14 @@ class MLP:
                                          ctypes.byref(loss) if want_loss else None)
         self._check(rc, "train_step")
         return float(loss.value) if want_loss else None
+
+
+def set_gemm_wait_polls(polls: int):
+    """Polls of the first tensor-core wait of every GEMM launch before it
+    gives up (0: at once; negative: the default); for time-out tests."""
+    rc = load_library().nbv_set_gemm_wait_polls(int(polls))
+    if rc != NBV_OK:
+        raise NBVError(rc, "nbv_set_gemm_wait_polls")
 
 
 def gemm_bf16(A, a_strides, B, b_strides, M, N, K):

@@ -89,7 +89,7 @@ struct nbv_ctx {
   DevProj pr{};
   // sort
   SortBuffers sb{};
-  uint2* fwd = nullptr;           // per-view scoring: forward results per (tile, pixel)
+  uint4* fwd = nullptr;           // per-view scoring: forward results per (tile, pixel)
   uint32_t* tile_first = nullptr; // and each tile's first active entry
   size_t fwd_cap = 0, tile_first_cap = 0;
   uint32_t* h_total = nullptr;   // pinned
@@ -162,7 +162,7 @@ struct nbv_ctx {
     SortBuffers sb{};               // entries (32-bit tile keys, stored in the 64-bit arrays)
     SortBuffers qb{};               // work queue
     uint2* ranges = nullptr;        // [ntiles]
-    uint2* fwd = nullptr;           // [ntiles][256] forward results
+    uint4* fwd = nullptr;           // [ntiles][256] forward results
     uint32_t* tile_first = nullptr; // [ntiles]
     int* counter = nullptr;         // [2] work-queue heads of the forward and information passes
     float* blocks = nullptr;        // [nv][n][nBp]
@@ -640,12 +640,20 @@ int batched_sequence(nbv_ctx* ctx, bool final_scores) {
 }
 
 // Candidates per multi-view pass: all of them unless their per-(view,
-// Gaussian) state (blocks, records, binning slots) would pass 32 GB, or the
+// Gaussian) state (blocks, records, binning slots) would take more than 45%
+// of the device memory free now (at least 4 GB; the rest is left for the
+// entries of the binning, which scale with the views too), or the
 // configuration caps it.
 int batched_chunk(const nbv_ctx* ctx) {
   const int nc = (int)ctx->cand.size();
   const double per_view = (double)ctx->n * 128.0 + (double)ctx->n_act * (double)ctx->nBp * 4.0;
-  int chunk = (int)std::max(1.0, std::floor(32.0e9 / std::max(per_view, 1.0)));
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = 0;
+  }
+  const double budget = std::max(4.0e9, 0.45 * (double)free_b);
+  int chunk = (int)std::max(1.0, std::floor(budget / std::max(per_view, 1.0)));
   // slot ids (view n + Gaussian) and the depth keys' view field are 31-bit
   chunk = (int)std::min<int64_t>(chunk, std::max<int64_t>(1, ((int64_t(1) << 31) - 1) / std::max<int64_t>(ctx->n, 1)));
   if (ctx->cfg.max_batch_views > 0) chunk = std::min(chunk, ctx->cfg.max_batch_views);

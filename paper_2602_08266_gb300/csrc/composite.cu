@@ -234,6 +234,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
 #pragma unroll
   for (int q = 0; q < KCM / 2; ++q) O2[q] = make_float2(0.0f, 0.0f);
   uint32_t last = rg.x;     // one past the list index of the last blended splat
+  uint32_t first_pix = kNoEntry;   // the first blended splat with an information block
   bool done = !inside;
   uint32_t n_eval = 0, n_blend = 0;
   // colour, depth and object sums only when an image is asked for (the
@@ -241,9 +242,10 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   const bool want_cd = args.rgb != nullptr || args.depth != nullptr;
   const bool want_o = args.obj != nullptr;
   if (info_only) {
-    const uint2 f = args.fwd[(size_t)gt * kTilePix + tid];
+    const uint4 f = args.fwd[(size_t)gt * kTilePix + tid];
     T = __uint_as_float(f.x);
     last = f.y;
+    first_pix = f.z;
   } else if (!want_cd && !want_o) {
     // records staged by bulk copies, the next round in flight meanwhile
     const uint32_t nst = (rg.y - rg.x + kBatch - 1) / kBatch;
@@ -350,13 +352,24 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
   if (blocks_v == nullptr) return;
 
   // ------------------------------------------------------------- pass 2
-  if (tid == 0) s_last_max = (int)rg.x;
+  // The walk runs back to front from the tile's last blended splat. With the
+  // forward pass's per-pixel first information splat it ends, per warp, at
+  // the earliest one among the warp's pixels (nothing in front of it reaches
+  // a block: it would only extend suffix sums that are no longer read), and
+  // per tile at the earliest among all pixels.
+  __shared__ uint32_t s_first_min;
+  if (tid == 0) { s_last_max = (int)rg.x; s_first_min = kNoEntry; }
   __syncthreads();
-  if (inside) atomicMax(&s_last_max, (int)last);
+  if (inside) {
+    atomicMax(&s_last_max, (int)last);
+    if (info_only) atomicMin(&s_first_min, first_pix);
+  }
   __syncthreads();
   const uint32_t last_max = (uint32_t)s_last_max;
+  if (info_only) first_info = max(first_info, s_first_min);
   // splats at or past every pixel of this warp's last blended one are skipped warp-wide
   const uint32_t wlast = __reduce_max_sync(0xffffffffu, inside ? last : rg.x);
+  const uint32_t wfirst = info_only ? __reduce_min_sync(0xffffffffu, inside ? first_pix : kNoEntry) : 0u;
   const float Tf = T;
   float Rr0 = 0.0f, Rr1 = 0.0f, Rr2 = 0.0f, Rd = 0.0f;
   float2 Ro2[KCM / 2];                      // object suffix sums in pairs
@@ -424,6 +437,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
     for (int j = nj - 1; j >= 0; --j) {
       const uint32_t idx = start + j;
       if (idx >= wlast) continue;
+      if (idx < wfirst) break;            // warp-uniform: nothing of this warp's is left in front
       bool act = false;
       const float4 a0 = s0[j], a1 = s1[j], a2 = s2[j];
       float pw = 0.0f;
@@ -638,9 +652,10 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
 // The forward pass of a scoring launch, on its own: a tile's list walked
 // front to back in rounds of kFwd splats staged by bulk copies (the next
 // round in flight meanwhile), per pixel only what the information pass needs
-// (transmittance, list ends). With an active subset, a tile without an
-// active splat is skipped (its first active entry recorded as its list end).
-constexpr int kFwd = 32;
+// (transmittance, list ends, the first blended splat with an information
+// block). With an active subset, a tile without an active splat is skipped
+// (its first active entry recorded as its list end).
+constexpr int kFwd = 32;   // one bit per staged splat in a 32-bit mask
 
 __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Consts& c, const DevCam& cam, int tile,
                                              uint32_t gt, uint2 rg, size_t rec_off, StageRing& ring) {
@@ -664,22 +679,43 @@ __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Co
   }
   if (tid == 0) args.tile_first[gt] = first_info;
   float T = 1.0f;
-  uint32_t last = rg.x;
+  uint32_t last = rg.x, first_pix = kNoEntry;
   uint32_t n_eval = 0, n_blend = 0;
+  // Per round, a mask of the staged splats that have an information block:
+  // warp 0 loads it with the round's copies and stores it before the
+  // barrier that opens the round (the slot loads' latency hides behind the
+  // round before).
+  __shared__ uint32_t s_info[2];
+  const bool subset = args.n_act < args.n;
+  auto info_mask = [&](uint32_t kk) -> uint32_t {      // warp 0, all lanes
+    const uint32_t s = rg.x + kk * kFwd;
+    const uint32_t m = min((uint32_t)kFwd, rg.y - s);
+    const bool on = (uint32_t)lane < m && (!subset || args.slot[args.vals[s + lane]] >= 0);
+    return __ballot_sync(0xffffffffu, on);
+  };
   if (first_info < rg.y) {
     bool done = !inside;
     const uint32_t nst = (rg.y - rg.x + kFwd - 1) / kFwd;
-    if (nst > 0 && wq == 0) ring.issue(args, rg.x, rg.y, 0, rec_off, lane, kFwd);
+    if (nst > 0 && wq == 0) {
+      ring.issue(args, rg.x, rg.y, 0, rec_off, lane, kFwd);
+      const uint32_t m0 = info_mask(0);
+      if (lane == 0) s_info[0] = m0;
+    }
     uint32_t k = 0;
     for (; k < nst; ++k) {
       if (__syncthreads_count(done) == kTilePix) break;
-      if (k + 1 < nst && wq == 0) ring.issue(args, rg.x, rg.y, k + 1, rec_off, lane, kFwd);
+      uint32_t pend = 0;
+      if (k + 1 < nst && wq == 0) {
+        ring.issue(args, rg.x, rg.y, k + 1, rec_off, lane, kFwd);
+        pend = info_mask(k + 1);
+      }
       const int b = (int)(k & 1u);
       if (!ring.wait(b)) done = true;
       const float4* q0 = ring.rec(b, 0, kFwd);
       const float4* q1 = ring.rec(b, 1, kFwd);
       const uint32_t start = rg.x + k * kFwd;
       const uint32_t nj = min((uint32_t)kFwd, rg.y - start);
+      const uint32_t imask = s_info[b];
       if (!done) {
         for (uint32_t j = 0; j < nj; ++j) {
           const float4 a0 = q0[j], a1 = q1[j];
@@ -691,13 +727,18 @@ __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Co
           if (tt < c.t_min) { done = true; break; }
           T = tt;
           last = start + j + 1;
+          if (first_pix == kNoEntry && ((imask >> j) & 1u)) first_pix = start + j;
           ++n_blend;
         }
       }
+      // every warp has read s_info[(k + 1) & 1] of round k - 1 (it passed this
+      // round's opening barrier); the next round's barrier publishes the store
+      if (k + 1 < nst && wq == 0 && lane == 0) s_info[(k + 1) & 1u] = pend;
     }
     if (k < nst) ring.wait((int)(k & 1u));   // a round fetched ahead but not composited
   }
-  args.fwd[(size_t)gt * kTilePix + tid] = make_uint2(__float_as_uint(T), inside ? last : rg.x);
+  args.fwd[(size_t)gt * kTilePix + tid] =
+      make_uint4(__float_as_uint(T), inside ? last : rg.x, inside ? first_pix : kNoEntry, 0u);
   if (args.stats) {
     const unsigned e = __reduce_add_sync(0xffffffffu, n_eval), bl = __reduce_add_sync(0xffffffffu, n_blend);
     if (lane == 0 && e) {
@@ -739,13 +780,32 @@ __global__ void __launch_bounds__(kTilePix, 4) k_forward(CompositeArgs args, Con
   }
 }
 
+// Dynamic shared memory of k_composite for K objects and rounds of kBatch splats.
+inline size_t composite_smem(const Consts& c, int nB, int kBatch) {
+  return ring_offset(c.K, c.KC, nB, kBatch) + sizeof(float4) * 4 * kBatch + 16;
+}
+
+// The largest dynamic shared memory a block of this device may opt into.
+inline size_t smem_optin() {
+  static int v = -1;
+  if (v < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 48 * 1024;
+    }
+  }
+  return (size_t)v;
+}
+
 template <int KCM, int kBatch, bool kSplit>
 int launch_k(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
-  const size_t sm = ring_offset(c.K, c.KC, a.nB, kBatch) + sizeof(float4) * 4 * kBatch + 16;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_composite<KCM, kBatch, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
+  const size_t sm = composite_smem(c, a.nB, kBatch);
+  static size_t attr_set = 0;
+  if (attr_set < sm) {
+    cudaFuncSetAttribute(k_composite<KCM, kBatch, kSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr_set = sm;
   }
   if (a.queue) {
     int per_sm = 1;
@@ -766,6 +826,9 @@ int launch_k(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
 
 template <bool kSplit>
 int launch_stage(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage) {
+  // rounds of 32 splats need the most shared memory (many object channels):
+  // 16 where 32 does not fit (the stage depth changes only speed)
+  if (stage != 16 && composite_smem(c, a.nB, 32) > smem_optin()) stage = 16;
   if (stage == 16) {
     if (c.KC <= 8) return launch_k<8, 16, kSplit>(a, c, st);
     if (c.KC <= 24) return launch_k<24, 16, kSplit>(a, c, st);

@@ -5,16 +5,22 @@
 // serves all five products).
 //
 // One CTA of 4 warps computes a 128 x NT tile of D with NT <= 256. For every
-// block of 64 k the threads stage A (128 x 64) and B (NT x 64) into shared
-// memory in the canonical K-major layout without swizzle: 8-row x 16-byte
-// core matrices of 128 contiguous bytes, core matrices adjacent in k 128
-// bytes apart (leading byte offset), 8-row groups 1024 bytes apart (stride
-// byte offset). One elected thread then issues four tcgen05.mma (K = 16
-// each, M = 128, N = NT, FP32 accumulators in tensor memory) and commits
-// them to an mbarrier that every thread waits on (a bounded wait: on a
-// time-out the kernel records an error, waits once more with a bound, frees
-// its tensor memory and returns). After the last block each warp reads its
-// 32 accumulator lanes (rows) with tcgen05.ld and writes D.
+// block of 64 k, A (128 x 64) and B (NT x 64) are staged into shared memory
+// in the canonical K-major layout without swizzle: 8-row x 16-byte core
+// matrices of 128 contiguous bytes, core matrices adjacent in k 128 bytes
+// apart (leading byte offset), 8-row groups 1024 bytes apart (stride byte
+// offset). Every 16-byte row segment (8 consecutive k of one row) that is
+// contiguous and aligned in global memory and lies inside the matrix is
+// fetched by a bulk copy of the tensor memory accelerator (cp.async.bulk,
+// completed on a staging mbarrier on which every thread arrives with its
+// byte count); the other segments (matrix edges, strided operands) are
+// loaded by the threads. One elected thread then issues four tcgen05.mma
+// (K = 16 each, M = 128, N = NT, FP32 accumulators in tensor memory) and
+// commits them to an mbarrier that every thread waits on. Waits are
+// bounded: on a time-out the kernel records an error, waits once more with
+// a bound for what it has in flight, frees its tensor memory and returns.
+// After the last block each warp reads its 32 accumulator lanes (rows) with
+// tcgen05.ld and writes D.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -52,8 +58,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
@@ -65,16 +71,48 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
+// Stages row r of one operand's k-block [k0, k0 + 64) (global row gr of a
+// rows-x-K matrix with element (row, k) at X[row sx_r + k sx_k]) into the
+// canonical layout at dst: 16-byte segments by bulk copy where possible.
+// Returns the bytes the bulk copies will deliver to the staging barrier.
+__device__ __forceinline__ uint32_t stage_row(const __nv_bfloat16* __restrict__ X, int64_t sx_r, int64_t sx_k,
+                                              int rows, int K, int gr, int k0, int r, unsigned char* dst,
+                                              uint32_t tbar) {
+  uint32_t bytes = 0;
+#pragma unroll
+  for (int ch = 0; ch < kKB / 8; ++ch) {
+    const int gk = k0 + 8 * ch;
+    unsigned char* d = dst + canon_off(r, 8 * ch);
+    const __nv_bfloat16* src = X + (int64_t)gr * sx_r + (int64_t)gk * sx_k;
+    const bool bulk = gr < rows && gk + 8 <= K && sx_k == 1 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
+    if (bulk) {
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 16, [%2];"
+                   ::"r"(smem_u32(d)), "l"(src), "r"(tbar)
+                   : "memory");
+      bytes += 16;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        __nv_bfloat16 v = __float2bfloat16(0.0f);
+        if (gr < rows && gk + q < K) v = X[(int64_t)gr * sx_r + (int64_t)(gk + q) * sx_k];
+        reinterpret_cast<__nv_bfloat16*>(d)[q] = v;
+      }
+    }
+  }
+  return bytes;
+}
+
 __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(const __nv_bfloat16* __restrict__ A, int64_t a_sm,
                                                             int64_t a_sk, const __nv_bfloat16* __restrict__ B,
                                                             int64_t b_sn, int64_t b_sk, float* __restrict__ D,
                                                             int64_t ldd, int M, int N, int K, int NT,
-                                                            int* __restrict__ err) {
+                                                            int* __restrict__ err, uint32_t first_polls) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sa = smem;                             // 128 x 64 bf16 = 16 KB
   unsigned char* sb = smem + kTM * kKB * 2;             // NT x 64 bf16
   uint64_t* bar = reinterpret_cast<uint64_t*>(sb + 256 * kKB * 2);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint64_t* tbar = bar + 1;                             // staging barrier: kGemmThreads arrivals
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * NT;
   const uint32_t ncols = NT <= 32 ? 32u : (NT <= 64 ? 64u : (NT <= 128 ? 128u : 256u));
@@ -86,6 +124,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(const __nv_bfloat16*
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(tbar)), "r"(kGemmThreads) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -97,23 +136,23 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(const __nv_bfloat16*
   bool ok = true;
   for (int kb = 0; kb < nkb && ok; ++kb) {
     const int k0 = kb * kKB;
-    // stage the A and B blocks (zero outside the matrices)
-    for (int e = tid; e < kTM * kKB; e += kGemmThreads) {
-      const int r = e / kKB, k = e - r * kKB;
-      const int gm = m0 + r, gk = k0 + k;
-      __nv_bfloat16 v = __float2bfloat16(0.0f);
-      if (gm < M && gk < K) v = A[(int64_t)gm * a_sm + (int64_t)gk * a_sk];
-      *reinterpret_cast<__nv_bfloat16*>(sa + canon_off(r, k)) = v;
-    }
-    for (int e = tid; e < NT * kKB; e += kGemmThreads) {
-      const int r = e / kKB, k = e - r * kKB;
-      const int gn = n0 + r, gk = k0 + k;
-      __nv_bfloat16 v = __float2bfloat16(0.0f);
-      if (gn < N && gk < K) v = B[(int64_t)gn * b_sn + (int64_t)gk * b_sk];
-      *reinterpret_cast<__nv_bfloat16*>(sb + canon_off(r, k)) = v;
+    // stage the A and B blocks (zero outside the matrices): one row of A and
+    // up to two rows of B per thread, then one arrival per thread with the
+    // bytes its bulk copies will deliver
+    uint32_t bytes = stage_row(A, a_sm, a_sk, M, K, m0 + tid, k0, tid, sa, smem_u32(tbar));
+    for (int r = tid; r < NT; r += kGemmThreads) bytes += stage_row(B, b_sn, b_sk, N, K, n0 + r, k0, r, sb, smem_u32(tbar));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(tbar)), "r"(bytes)
+                 : "memory");
+    bool staged = mbar_wait(smem_u32(tbar), (uint32_t)(kb & 1));
+    if (!staged) {
+      if (err && lane == 0) atomicExch(err, 1);
+      mbar_wait(smem_u32(tbar), (uint32_t)(kb & 1));   // the copies in flight land before the kernel leaves
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    if (!__syncthreads_and(staged ? 1 : 0)) {
+      ok = false;
+      break;
+    }
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -131,14 +170,17 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(const __nv_bfloat16*
                        smem_u32(bar))
                    : "memory");
     }
-    ok = mbar_wait(smem_u32(bar), (uint32_t)(kb & 1));
+    ok = mbar_wait(smem_u32(bar), (uint32_t)(kb & 1), kb == 0 ? first_polls : kWaitLimit);
     if (!ok && err && lane == 0) atomicExch(err, 1);
+    if (!ok) {
+      // the commit did not arrive in time: one more bounded wait before the
+      // tensor memory is released
+      mbar_wait(smem_u32(bar), (uint32_t)(kb & 1));
+    }
     ok = __syncthreads_and(ok ? 1 : 0) != 0;
   }
   if (!ok) {
-    // the last commit did not arrive in time: give it one more bounded wait
-    // before the tensor memory is released
-    mbar_wait(smem_u32(bar), (uint32_t)((nkb - 1) & 1));
+    // nothing more in flight (every wait above was followed by a bounded drain)
   } else if (nkb > 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int row = m0 + warp * 32 + lane;
@@ -176,7 +218,15 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(const __nv_bfloat16*
 
 }  // namespace
 
-size_t gemm_bf16_smem() { return (size_t)kTM * kKB * 2 + (size_t)256 * kKB * 2 + 16; }
+size_t gemm_bf16_smem() { return (size_t)kTM * kKB * 2 + (size_t)256 * kKB * 2 + 32; }
+
+namespace {
+// Polls of the first wait for the tensor cores' commit in a GEMM launch
+// (tests of the time-out path set 0: that wait gives up at once; the drain
+// wait after it keeps the full bound, so nothing is in flight when the
+// tensor memory is released).
+uint32_t g_first_polls = kWaitLimit;
+}  // namespace
 
 int launch_gemm_bf16(const void* A, int64_t a_sm, int64_t a_sk, const void* B, int64_t b_sn, int64_t b_sk,
                      float* D, int64_t ldd, int M, int N, int K, int* err, cudaStream_t st) {
@@ -194,8 +244,14 @@ int launch_gemm_bf16(const void* A, int64_t a_sm, int64_t a_sk, const void* B, i
   dim3 grid((unsigned)((M + kTM - 1) / kTM), (unsigned)((N + NT - 1) / NT));
   k_gemm_bf16<<<grid, kGemmThreads, sm, st>>>(static_cast<const __nv_bfloat16*>(A), a_sm, a_sk,
                                                static_cast<const __nv_bfloat16*>(B), b_sn, b_sk, D, ldd, M, N,
-                                               K, NT, err);
+                                               K, NT, err, g_first_polls);
   return 1;
 }
 
 }  // namespace nbv
+
+extern "C" int nbv_set_gemm_wait_polls(int64_t polls) {
+  if (polls > (int64_t)0xFFFFFFFF) return NBV_ERR_ARG;
+  nbv::g_first_polls = polls < 0 ? nbv::kWaitLimit : (uint32_t)polls;
+  return NBV_OK;
+}

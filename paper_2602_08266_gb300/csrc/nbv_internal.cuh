@@ -251,19 +251,23 @@ struct CompositeArgs {
   int64_t n_act;               // active Gaussians (stride of the per-view block arrays)
   int* err;                    // set to 1 when a bounded wait for staged records gave up (may be NULL)
   // Scoring launches run as two kernels: the forward pass (launch_forward)
-  // writes every pixel's final transmittance and one past its last blended
-  // list index, fwd[tile * 256 + pixel] = {float bits of T, last}, and each
-  // tile's first list entry with an information block (its list end when it
-  // has none); the information pass (launch_composite with fwd != NULL)
-  // reads them instead of compositing again. Tiles are global tile ids in
-  // the persistent form, the view's tile index otherwise.
-  uint2* fwd;
+  // writes every pixel's final transmittance, one past its last blended
+  // list index and the list index of the first splat with an information
+  // block that it blended (kNoEntry if none), fwd[tile * 256 + pixel] =
+  // {float bits of T, last, first, 0}, and each tile's first list entry with
+  // an information block (its list end when it has none); the information
+  // pass (launch_composite with fwd != NULL) reads them instead of
+  // compositing again, and a warp's walk back to front ends at its pixels'
+  // earliest such splat. Tiles are global tile ids in the persistent form,
+  // the view's tile index otherwise.
+  uint4* fwd;
   uint32_t* tile_first;
 };
+constexpr uint32_t kNoEntry = 0xffffffffu;
 // stage = Gaussians staged in shared memory per round (16 or 32).
 int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, int stage = 32);
-// The forward pass of a scoring launch (no images): per pixel T and the last
-// blended index into a.fwd, per tile the first active entry into a.tile_first;
+// The forward pass of a scoring launch (no images): per pixel T, the last
+// blended index and the first blended index with an information block into a.fwd, per tile the first active entry into a.tile_first;
 // a.counter (persistent form) must be zeroed first.
 int launch_forward(const CompositeArgs& a, const Consts& c, cudaStream_t st);
 

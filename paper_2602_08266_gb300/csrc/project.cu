@@ -161,6 +161,28 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   const float limy = fm(c.guard, fd(fm(0.5f, (float)cam.H), cam.fy));
   const float xz = fminf(limx, fmaxf(-limx, xr));
   const float yz = fminf(limy, fmaxf(-limy, yr));
+  if (kMode == kProjTarget) {
+    // Early rejection of a slot whose rectangle cannot reach the view's box
+    // of marked tiles, before the rest of the key path. lambda_max of the 2D
+    // covariance is at most its trace + sqrt(0.1) (the square root's floor),
+    // and the trace at most ||J||_F^2 s_max^2 + 2 dilation, with
+    // ||J||_F^2 = (fx^2 (1 + xz^2) + fy^2 (1 + yz^2)) / tz^2 for the clamped
+    // xz, yz above and s_max the largest scale (the rotation is orthonormal).
+    // The bound on the radius (3 sqrt(lambda) rounded up) carries a 1%
+    // margin and 2 pixels for the rounding of this ordinary float estimate,
+    // so only slots with no tile in the box are dropped.
+    const int4 bx = tm->bb[0];
+    if (bx.z < bx.x || bx.w < bx.y) return;              // no marked tile in this view
+    const float smax = fmaxf(ss.x, fmaxf(ss.y, ss.z));
+    const float iz = 1.0f / tz;
+    const float jx = cam.fx * iz, jy = cam.fy * iz;
+    const float tr = (jx * jx * (1.0f + xz * xz) + jy * jy * (1.0f + yz * yz)) * (smax * smax) + 2.0f * c.dilation;
+    const float rb = 3.0f * sqrtf(tr + 0.5f) * 1.01f + 2.0f;
+    const float twb = (float)cam.TW, thb = (float)cam.TH;
+    if (mx + rb < (float)bx.x * twb || mx - rb >= (float)(bx.z + 1) * twb || my + rb < (float)bx.y * thb ||
+        my - rb >= (float)(bx.w + 1) * thb)
+      return;
+  }
   const float txp = fm(xz, tz), typ = fm(yz, tz);
   const float tz2 = fm(tz, tz);
   const float j00 = fd(cam.fx, tz), j02 = -fd(fm(cam.fx, txp), tz2);

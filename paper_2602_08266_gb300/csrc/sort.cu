@@ -89,8 +89,7 @@ int scan_rec(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaSt
 // One slot's tile walk: its tile rectangle {x0, x1, y0, y1} (x0 < 0: none),
 // the splat's mean, conic and skip exponent, the stationary-point ratios of
 // tile_hit, and the view's tile grid. The warp kernels below load one slot
-// per lane and then walk the non-empty rectangles one after the other with
-// all 32 lanes, each lane's fields broadcast by shuffles.
+// per lane and walk the tiles of all 32 rectangles together (packed_walk).
 struct SlotTiles {
   int4 r;
   float mx, my, thr, A, B, C, bc, ba;
@@ -117,42 +116,52 @@ __device__ __forceinline__ SlotTiles no_tiles() {
   return t;
 }
 
-__device__ __forceinline__ SlotTiles shfl_tiles(const SlotTiles& t, int s) {
-  SlotTiles o;
-  o.r = make_int4(__shfl_sync(0xffffffffu, t.r.x, s), __shfl_sync(0xffffffffu, t.r.y, s),
-                  __shfl_sync(0xffffffffu, t.r.z, s), __shfl_sync(0xffffffffu, t.r.w, s));
-  o.mx = __shfl_sync(0xffffffffu, t.mx, s); o.my = __shfl_sync(0xffffffffu, t.my, s);
-  o.thr = __shfl_sync(0xffffffffu, t.thr, s);
-  o.A = __shfl_sync(0xffffffffu, t.A, s); o.B = __shfl_sync(0xffffffffu, t.B, s);
-  o.C = __shfl_sync(0xffffffffu, t.C, s);
-  o.bc = __shfl_sync(0xffffffffu, t.bc, s); o.ba = __shfl_sync(0xffffffffu, t.ba, s);
-  o.base = __shfl_sync(0xffffffffu, t.base, s);
-  o.gx = __shfl_sync(0xffffffffu, t.gx, s);
-  o.tw = __shfl_sync(0xffffffffu, t.tw, s); o.th = __shfl_sync(0xffffffffu, t.th, s);
-  return o;
-}
+constexpr int kDupThreads = 256;   // blocks of the tile-walking kernels
 
-// Walks rectangle q with the warp, 32 tiles at a time in row order; fn(tx,
-// ty, hit) is called by every lane each round (hit false past the end), so
-// that fn may use warp collectives. keep(tx, ty): a tile filter checked
-// before tile_hit (e.g. a mark).
+// The tiles of a warp's 32 slots (lane l holds slot l; an empty rectangle
+// has x0 < 0) walked as one sequence: slot order, then row order within a
+// rectangle, numbered by an inclusive scan of the areas, 32 tiles per round,
+// each lane finding its slot by a binary search of the scan. Small
+// rectangles share rounds, and the sequence order is the order of walking
+// the rectangles one after the other. fn(s, q, tx, ty, hit) is called by every
+// lane each round (s = the lane's slot, hit false past the end), so fn may
+// use warp collectives; keep(q, tx, ty) filters tiles before tile_hit.
+// s_st / s_incl: 32 entries of this warp's shared memory.
 template <class Keep, class Fn>
-__device__ __forceinline__ void walk_tiles(const SlotTiles& q, int lane, Keep keep, Fn fn) {
-  const int w = q.r.y - q.r.x, cnt = w * (q.r.w - q.r.z);
-  // entry t = (ty - y0) w + (tx - x0); lane starts at t = lane, steps by 32
-  int qy = lane / w, qx = lane - qy * w;
-  const int dq = 32 / w, dr = 32 - dq * w;
-  for (int t0 = 0; t0 < cnt; t0 += 32) {
-    const int tx = q.r.x + qx, ty = q.r.z + qy;
-    const bool hit = t0 + lane < cnt && keep(tx, ty) &&
-                     tile_hit(q.A, q.B, q.C, q.mx, q.my, q.thr, q.bc, q.ba, tx, ty, q.tw, q.th);
-    fn(tx, ty, hit);
-    qy += dq;
-    qx += dr;
-    if (qx >= w) {
-      qx -= w;
-      ++qy;
+__device__ __forceinline__ void packed_walk(const SlotTiles& st, SlotTiles* s_st, int* s_incl, int lane, Keep keep,
+                                            Fn fn) {
+  const int area = st.r.x >= 0 ? (st.r.y - st.r.x) * (st.r.w - st.r.z) : 0;
+  int incl = area;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();
+  s_st[lane] = st;
+  s_incl[lane] = incl;
+  __syncwarp();
+  for (int t0 = 0; t0 < total; t0 += 32) {
+    const int t = t0 + lane;
+    int lo = 0, tx = 0, ty = 0;
+    bool hit = false;
+    if (t < total) {
+      int hi = 32;                               // the first slot whose inclusive end passes t
+#pragma unroll
+      for (int it = 0; it < 5; ++it) {
+        const int mid = (lo + hi) >> 1;
+        if (s_incl[mid] > t) hi = mid; else lo = mid + 1;
+      }
+      const SlotTiles& q = s_st[lo];
+      const int idx = t - (lo > 0 ? s_incl[lo - 1] : 0);
+      const int w = q.r.y - q.r.x;
+      const int qy = idx / w, qx = idx - qy * w;
+      tx = q.r.x + qx;
+      ty = q.r.z + qy;
+      hit = keep(q, tx, ty) && tile_hit(q.A, q.B, q.C, q.mx, q.my, q.thr, q.bc, q.ba, tx, ty, q.tw, q.th);
     }
+    fn(lo, s_st[lo], tx, ty, hit);
   }
 }
 
@@ -165,39 +174,43 @@ __device__ __forceinline__ int4 clip_rect(int4 r, int4 b) {
 }
 
 // Every Gaussian's entries for the tiles of its rectangle that pass
-// tile_hit, in row order: a lane per Gaussian, then each Gaussian's
-// rectangle walked by the whole warp (32 tiles at a time, the passing ones
-// compacted by a ballot), so that the stores of a run are contiguous.
-__global__ void k_duplicate(DevProj pr, int64_t n, DevCam cam, const uint32_t* __restrict__ offsets,
-                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// tile_hit, in row order: a lane per Gaussian, the warp's 32 rectangles
+// walked together (packed_walk), the passing tiles of a round compacted by a
+// ballot, so that the warp's entries leave as one contiguous run.
+__global__ void __launch_bounds__(kDupThreads) k_duplicate(DevProj pr, int64_t n, DevCam cam,
+                                                          const uint32_t* __restrict__ offsets,
+                                                          uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  __shared__ SlotTiles s_st[kDupThreads / 32][32];
+  __shared__ int s_incl[kDupThreads / 32][32];
+  __shared__ uint32_t s_z[kDupThreads / 32][32];
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t g0 = g - lane;
+  if (g0 >= n) return;                           // warp-uniform; no block-wide barrier below
   SlotTiles st = no_tiles();
-  uint32_t o = 0, zb = 0;
+  uint32_t zb = 0;
   if (g < n) {
     const int4 r = pr.rect[g];
     if (r.x >= 0) {
       st = slot_tiles(r, pr.r0[g], pr.r1[g], 0u, cam);
-      o = offsets[g];
       zb = pr.zbits[g];
     }
   }
-  const int64_t g0 = g - lane;
-  for (unsigned todo = __ballot_sync(0xffffffffu, st.r.x >= 0); todo; todo &= todo - 1) {
-    const int s = __ffs(todo) - 1;
-    const SlotTiles q = shfl_tiles(st, s);
-    const uint32_t zs = __shfl_sync(0xffffffffu, zb, s);
-    uint32_t wo = __shfl_sync(0xffffffffu, o, s);
-    walk_tiles(q, lane, [](int, int) { return true; }, [&](int tx, int ty, bool hit) {
-      const unsigned m = __ballot_sync(0xffffffffu, hit);
-      if (hit) {
-        const uint32_t at = wo + (uint32_t)__popc(m & ((1u << lane) - 1u));
-        keys[at] = ((uint64_t)(ty * q.gx + tx) << 32) | (uint64_t)zs;
-        vals[at] = (uint32_t)(g0 + s);
-      }
-      wo += (uint32_t)__popc(m);
-    });
-  }
+  s_z[wid][lane] = zb;                           // published by packed_walk's __syncwarp
+  // the warp's slots are consecutive in the scan of their entry counts
+  uint32_t wo = offsets[g0];
+  const unsigned lt = (1u << lane) - 1u;
+  packed_walk(
+      st, s_st[wid], s_incl[wid], lane, [](const SlotTiles&, int, int) { return true; },
+      [&](int sl, const SlotTiles& q, int tx, int ty, bool hit) {
+        const unsigned mk = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const uint32_t at = wo + (uint32_t)__popc(mk & lt);
+          keys[at] = ((uint64_t)(ty * q.gx + tx) << 32) | (uint64_t)s_z[wid][sl];
+          vals[at] = (uint32_t)(g0 + sl);
+        }
+        wo += (uint32_t)__popc(mk);
+      });
 }
 
 // Work-queue keys: longest tile list first, ties by tile id.
@@ -214,21 +227,30 @@ constexpr int kRadixThreads = 256;
 constexpr int kRadixRounds = 11;   // tile of 2816 keys: the staging fits the 48 KB of static shared memory
 constexpr int kRadixTile = kRadixThreads * kRadixRounds;
 
-template <typename K>
+// Digits of RB bits (8, or 9 for 32-bit keys where that saves a pass);
+// each of the 256 threads owns DPT = 2^RB / 256 consecutive digits.
+template <typename K, int RB>
 __global__ void k_radix_hist(const K* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ ghist,
                              int nblocks) {
-  __shared__ uint32_t h[256];
+  constexpr int D = 1 << RB, DPT = D / kRadixThreads;
+  constexpr unsigned kMask = (unsigned)D - 1u;
+  __shared__ uint32_t h[D];
   const int tid = threadIdx.x;
-  h[tid] = 0;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) h[tid + q * kRadixThreads] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kRadixTile;
 #pragma unroll
   for (int r = 0; r < kRadixRounds; ++r) {
     const int64_t i = base + r * kRadixThreads + tid;
-    if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 255u], 1u);
+    if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & kMask], 1u);
   }
   __syncthreads();
-  ghist[(int64_t)tid * nblocks + blockIdx.x] = h[tid];
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    const int d = tid + q * kRadixThreads;
+    ghist[(int64_t)d * nblocks + blockIdx.x] = h[d];
+  }
 }
 
 // One stable counting pass over a tile of kRadixTile keys: every element's
@@ -236,21 +258,29 @@ __global__ void k_radix_hist(const K* __restrict__ keys, int64_t n, int shift, u
 // round by round (warp match + per-warp counts), the tile is rearranged by
 // digit in shared memory, and written out in that order, so that each
 // digit's elements leave as one contiguous run.
-template <typename K>
+template <typename K, int RB>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const K* __restrict__ kin,
                                                                  const uint32_t* __restrict__ vin,
                                                                  K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                                  int64_t n, int shift,
                                                                  const uint32_t* __restrict__ ghist,
                                                                  const uint32_t* __restrict__ gscan, int nblocks) {
-  __shared__ uint32_t cnt[kRadixThreads / 32][256];
-  __shared__ uint32_t run[256], lstart[256], gbase[256], wsum[kRadixThreads / 32];
+  constexpr int D = 1 << RB, DPT = D / kRadixThreads;
+  constexpr unsigned kMask = (unsigned)D - 1u;
+  __shared__ uint32_t cnt[kRadixThreads / 32][D];
+  __shared__ uint32_t run[D], lstart[D], gbase[D], wsum[kRadixThreads / 32];
   __shared__ K sk[kRadixTile];
   __shared__ uint32_t sv[kRadixTile];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // tile-local start of each digit: exclusive scan of this tile's counts
-  const uint32_t myc = ghist[(int64_t)tid * nblocks + blockIdx.x];
-  uint32_t x = myc;
+  // (thread t holds digits DPT t .. DPT t + DPT - 1)
+  uint32_t myc[DPT], mysum = 0;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    myc[q] = ghist[(int64_t)(DPT * tid + q) * nblocks + blockIdx.x];
+    mysum += myc[q];
+  }
+  uint32_t x = mysum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -260,25 +290,33 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const K* __rest
   __syncthreads();
   uint32_t pre = 0;
   for (int w = 0; w < wid; ++w) pre += wsum[w];
-  lstart[tid] = pre + x - myc;
-  gbase[tid] = gscan[(int64_t)tid * nblocks + blockIdx.x];
-  run[tid] = 0;
+  uint32_t s = pre + x - mysum;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    const int d = DPT * tid + q;
+    lstart[d] = s;
+    s += myc[q];
+    gbase[d] = gscan[(int64_t)d * nblocks + blockIdx.x];
+    run[d] = 0;
+  }
   const unsigned lt = (1u << lane) - 1u;
   const int64_t base = (int64_t)blockIdx.x * kRadixTile;
   const int tile_n = (int)((n - base) < kRadixTile ? (n - base) : kRadixTile);
   for (int r = 0; r < kRadixRounds; ++r) {
 #pragma unroll
-    for (int w = 0; w < kRadixThreads / 32; ++w) cnt[w][tid] = 0;
+    for (int w = 0; w < kRadixThreads / 32; ++w)
+#pragma unroll
+      for (int q = 0; q < DPT; ++q) cnt[w][tid + q * kRadixThreads] = 0;
     __syncthreads();
     const int li = r * kRadixThreads + tid;
     const bool valid = li < tile_n;
     K key = 0;
     uint32_t val = 0;
-    int digit = 256;
+    int digit = D;
     if (valid) {
       key = kin[base + li];
       val = vin[base + li];
-      digit = (int)((key >> shift) & 255u);
+      digit = (int)((key >> shift) & kMask);
     }
     const unsigned peers = __match_any_sync(0xffffffffu, digit);
     const int lrank = __popc(peers & lt);
@@ -291,15 +329,19 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const K* __rest
       sv[pos] = val;
     }
     __syncthreads();
-    uint32_t add = 0;
 #pragma unroll
-    for (int w = 0; w < kRadixThreads / 32; ++w) add += cnt[w][tid];
-    run[tid] += add;
+    for (int q = 0; q < DPT; ++q) {
+      const int d = tid + q * kRadixThreads;
+      uint32_t add = 0;
+#pragma unroll
+      for (int w = 0; w < kRadixThreads / 32; ++w) add += cnt[w][d];
+      run[d] += add;
+    }
   }
   __syncthreads();
   for (int i = tid; i < tile_n; i += kRadixThreads) {
     const K key = sk[i];
-    const int d = (int)((key >> shift) & 255u);
+    const int d = (int)((key >> shift) & kMask);
     const uint32_t o = gbase[d] + (uint32_t)i - lstart[d];
     kout[o] = key;
     vout[o] = sv[i];
@@ -327,20 +369,29 @@ __global__ void k_gather_touched(const uint32_t* __restrict__ touched, const uin
 // Slots in depth order (per view): each emits its tiles that pass tile_hit
 // (global tile id, 32-bit key) and its Gaussian index, so that a stable sort
 // on the tile id alone leaves every tile's entries in (depth bits, Gaussian
-// index) order. A warp takes 32 consecutive slots (one per lane) and then
-// walks their rectangles one slot after the other, 32 tiles at a time, the
-// passing ones compacted by a ballot, so that the stores are contiguous.
-// With a mark, only marked tiles (inside the view's box bb) are emitted.
-__global__ void k_duplicate_sorted(const int4* __restrict__ rect, const float4* __restrict__ r0,
-                                   const float4* __restrict__ r1, const uint32_t* __restrict__ order, int64_t n,
-                                   int64_t m, const DevCam* __restrict__ cams,
-                                   const uint32_t* __restrict__ tile_base, const uint8_t* __restrict__ mark,
-                                   const int4* __restrict__ bb, const uint32_t* __restrict__ offsets,
-                                   uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// index) order. A warp takes 32 consecutive slots (one per lane), numbers
+// the tiles of their rectangles one after the other (slot order, then row
+// order within a rectangle: an exclusive scan of the areas) and walks that
+// sequence 32 tiles per round, each lane finding its slot by a binary search
+// of the scan, so that small rectangles share rounds; the passing tiles of a
+// round are compacted by a ballot. The warp's slots are consecutive in the
+// scan of their entry counts, so its entries form one contiguous run from
+// the first slot's offset. With a mark, only marked tiles (inside the view's
+// box bb) are emitted.
+__global__ void __launch_bounds__(kDupThreads) k_duplicate_sorted(
+    const int4* __restrict__ rect, const float4* __restrict__ r0, const float4* __restrict__ r1,
+    const uint32_t* __restrict__ order, int64_t n, int64_t m, const DevCam* __restrict__ cams,
+    const uint32_t* __restrict__ tile_base, const uint8_t* __restrict__ mark, const int4* __restrict__ bb,
+    const uint32_t* __restrict__ offsets, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  __shared__ SlotTiles s_st[kDupThreads / 32][32];
+  __shared__ int s_incl[kDupThreads / 32][32];
+  __shared__ uint32_t s_g[kDupThreads / 32][32];
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t i0 = i - lane;                   // the warp's first slot
+  if (i0 >= m) return;                           // warp-uniform; no block-wide barrier below
   SlotTiles st = no_tiles();
-  uint32_t g = 0, o = 0;
+  uint32_t g = 0;
   if (i < m) {
     const uint32_t slot = order[i];
     const int v = (int)(slot / (uint64_t)n);
@@ -349,38 +400,41 @@ __global__ void k_duplicate_sorted(const int4* __restrict__ rect, const float4* 
     if (r.x >= 0) {
       g = (uint32_t)(slot - (uint64_t)v * n);
       st = slot_tiles(r, r0[slot], r1[slot], tile_base[v], cams[v]);
-      o = offsets[i];
     }
   }
-  for (unsigned todo = __ballot_sync(0xffffffffu, st.r.x >= 0); todo; todo &= todo - 1) {
-    const int s = __ffs(todo) - 1;
-    const SlotTiles q = shfl_tiles(st, s);
-    const uint32_t gs = __shfl_sync(0xffffffffu, g, s);
-    uint32_t wo = __shfl_sync(0xffffffffu, o, s);
-    walk_tiles(
-        q, lane, [&](int tx, int ty) { return mark == nullptr || mark[q.base + (uint32_t)(ty * q.gx + tx)] != 0; },
-        [&](int tx, int ty, bool hit) {
-          const unsigned mk = __ballot_sync(0xffffffffu, hit);
-          if (hit) {
-            const uint32_t at = wo + (uint32_t)__popc(mk & ((1u << lane) - 1u));
-            keys[at] = q.base + (uint32_t)(ty * q.gx + tx);
-            vals[at] = gs;
-          }
-          wo += (uint32_t)__popc(mk);
-        });
-  }
+  s_g[wid][lane] = g;                            // published by packed_walk's __syncwarp
+  uint32_t wo = offsets[i0];
+  const unsigned lt = (1u << lane) - 1u;
+  packed_walk(
+      st, s_st[wid], s_incl[wid], lane,
+      [&](const SlotTiles& q, int tx, int ty) {
+        return mark == nullptr || mark[q.base + (uint32_t)(ty * q.gx + tx)] != 0;
+      },
+      [&](int sl, const SlotTiles& q, int tx, int ty, bool hit) {
+        const unsigned mk = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const uint32_t at = wo + (uint32_t)__popc(mk & lt);
+          keys[at] = q.base + (uint32_t)(ty * q.gx + tx);
+          vals[at] = s_g[wid][sl];
+        }
+        wo += (uint32_t)__popc(mk);
+      });
 }
 
 // Entries every (view, Gaussian) slot will emit: its rectangle's tiles that
 // pass tile_hit (and, with a mark, that a splat of the active set reaches,
-// all inside the view's box bb). A lane per slot, then each non-empty
-// rectangle walked by the whole warp, the passing tiles counted by a ballot.
-__global__ void k_count_tiles(const int4* __restrict__ rect, const float4* __restrict__ r0,
-                              const float4* __restrict__ r1, int64_t n, int nv, const DevCam* __restrict__ cams,
-                              const uint32_t* __restrict__ tile_base, const uint8_t* __restrict__ mark,
-                              const int4* __restrict__ bb, uint32_t* __restrict__ touched) {
+// all inside the view's box bb). A lane per slot, the warp's rectangles
+// walked together (packed_walk), each passing tile counted for its slot.
+__global__ void __launch_bounds__(kDupThreads) k_count_tiles(
+    const int4* __restrict__ rect, const float4* __restrict__ r0, const float4* __restrict__ r1, int64_t n, int nv,
+    const DevCam* __restrict__ cams, const uint32_t* __restrict__ tile_base, const uint8_t* __restrict__ mark,
+    const int4* __restrict__ bb, uint32_t* __restrict__ touched) {
+  __shared__ SlotTiles s_st[kDupThreads / 32][32];
+  __shared__ int s_incl[kDupThreads / 32][32];
+  __shared__ uint32_t s_cnt[kDupThreads / 32][32];
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (i - lane >= n * nv) return;                // warp-uniform; no block-wide barrier below
   SlotTiles st = no_tiles();
   if (i < n * nv) {
     const int v = (int)(i / n);
@@ -388,17 +442,17 @@ __global__ void k_count_tiles(const int4* __restrict__ rect, const float4* __res
     if (r.x >= 0 && bb != nullptr) r = clip_rect(r, bb[v]);
     if (r.x >= 0) st = slot_tiles(r, r0[i], r1[i], tile_base[v], cams[v]);
   }
-  uint32_t mine = 0;
-  for (unsigned todo = __ballot_sync(0xffffffffu, st.r.x >= 0); todo; todo &= todo - 1) {
-    const int s = __ffs(todo) - 1;
-    const SlotTiles q = shfl_tiles(st, s);
-    uint32_t tot = 0;
-    walk_tiles(
-        q, lane, [&](int tx, int ty) { return mark == nullptr || mark[q.base + (uint32_t)(ty * q.gx + tx)] != 0; },
-        [&](int, int, bool hit) { tot += (uint32_t)__popc(__ballot_sync(0xffffffffu, hit)); });
-    if (lane == s) mine = tot;
-  }
-  if (i < n * nv) touched[i] = mine;
+  s_cnt[wid][lane] = 0u;
+  packed_walk(
+      st, s_st[wid], s_incl[wid], lane,
+      [&](const SlotTiles& q, int tx, int ty) {
+        return mark == nullptr || mark[q.base + (uint32_t)(ty * q.gx + tx)] != 0;
+      },
+      [&](int sl, const SlotTiles&, int, int, bool hit) {
+        if (hit) atomicAdd(&s_cnt[wid][sl], 1u);
+      });
+  __syncwarp();
+  if (i < n * nv) touched[i] = s_cnt[wid][lane];
 }
 
 // Multi-view depth order of the slots that emit entries: for every slot
@@ -428,20 +482,20 @@ __global__ void k_ranges32(const uint32_t* __restrict__ keys, int64_t n, uint2* 
   if (i == n - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
 }
 
-template <typename K>
+template <typename K, int RB>
 int radix_passes(K* keys[2], uint32_t* vals[2], uint32_t* hist, int64_t count, int bits, int* which,
                  cudaStream_t st) {
   *which = 0;
   if (count <= 1) return 0;
   const int nblocks = (int)((count + kRadixTile - 1) / kRadixTile);
   int l = 0;
-  for (int shift = 0; shift < bits; shift += 8) {
+  for (int shift = 0; shift < bits; shift += RB) {
     const int src = *which, dst = 1 - src;
-    k_radix_hist<K><<<nblocks, kRadixThreads, 0, st>>>(keys[src], count, shift, hist, nblocks);
-    const int64_t hn = 256LL * nblocks;
+    k_radix_hist<K, RB><<<nblocks, kRadixThreads, 0, st>>>(keys[src], count, shift, hist, nblocks);
+    const int64_t hn = (int64_t)(1 << RB) * nblocks;
     l += 1 + scan_rec(hist, hist + hn, hn, hist + 2 * hn, st);
-    k_radix_scatter<K><<<nblocks, kRadixThreads, 0, st>>>(keys[src], vals[src], keys[dst], vals[dst], count, shift,
-                                                          hist, hist + hn, nblocks);
+    k_radix_scatter<K, RB><<<nblocks, kRadixThreads, 0, st>>>(keys[src], vals[src], keys[dst], vals[dst], count,
+                                                              shift, hist, hist + hn, nblocks);
     ++l;
     *which = dst;
   }
@@ -494,12 +548,14 @@ int launch_duplicate(const DevProj& pr, int64_t n, const DevCam& cam, const uint
 }
 
 int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaStream_t st) {
-  return radix_passes<uint64_t>(b.keys, b.vals, b.hist, count, bits, which, st);
+  return radix_passes<uint64_t, 8>(b.keys, b.vals, b.hist, count, bits, which, st);
 }
 
 int launch_radix_sort32(uint32_t* keys[2], uint32_t* vals[2], uint32_t* hist, int64_t count, int bits, int* which,
                         cudaStream_t st) {
-  return radix_passes<uint32_t>(keys, vals, hist, count, bits, which, st);
+  // 9-bit digits where they take fewer passes (e.g. 18 bits: 2 instead of 3)
+  if ((bits + 8) / 9 < (bits + 7) / 8) return radix_passes<uint32_t, 9>(keys, vals, hist, count, bits, which, st);
+  return radix_passes<uint32_t, 8>(keys, vals, hist, count, bits, which, st);
 }
 
 int launch_depth_keys(const uint32_t* zbits, int64_t n, int nv, uint64_t* keys, uint32_t* vals, cudaStream_t st) {
@@ -558,10 +614,10 @@ int launch_radix_pass(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, 
   if (count <= 0) return 0;
   const int nblocks = (int)((count + kRadixTile - 1) / kRadixTile);
   const int64_t hn = 256LL * nblocks;
-  k_radix_hist<uint64_t><<<nblocks, kRadixThreads, 0, st>>>(kin, count, shift, hist, nblocks);
+  k_radix_hist<uint64_t, 8><<<nblocks, kRadixThreads, 0, st>>>(kin, count, shift, hist, nblocks);
   int l = 1 + scan_rec(hist, hist + hn, hn, hist + 2 * hn, st);
-  k_radix_scatter<uint64_t><<<nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, count, shift, hist, hist + hn,
-                                                               nblocks);
+  k_radix_scatter<uint64_t, 8><<<nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, count, shift, hist,
+                                                                  hist + hn, nblocks);
   return l + 1;
 }
 
@@ -591,7 +647,7 @@ size_t scan_scratch_elems(int64_t n) {
 
 size_t radix_hist_elems(int64_t count) {
   const int64_t nblocks = (count + kRadixTile - 1) / kRadixTile;
-  const int64_t hn = 256 * nblocks;
+  const int64_t hn = 512 * nblocks;      // digits of up to 9 bits
   return (size_t)(2 * hn) + scan_scratch_elems(hn);
 }
 

@@ -496,6 +496,48 @@ def test_contraction_modes_log_det_parity(P, batched):
 
 
 @pytest.mark.slow
+def test_batched_target_tile_lists_valid(P):
+    """With a target object (Eq. 12) the multi-view pass bins only the tiles
+    where a splat of the target can pass its alpha cut-off (marked by the
+    active slots' projection), drops slots whose rectangle cannot reach the
+    view's box of such tiles before their key path, and duplicates the
+    survivors' tiles in packed warp rounds. Its lists must still be ordered
+    sub-lists of the oracle's rectangle lists, and every tile where the
+    oracle finds a target splat passing the skip test at an in-image pixel
+    must hold every splat (target or not) needed there."""
+    wl = S.make_workload("batch", n_views=6, scale=0.05)
+    sc = P.NBVScorer(wl.scene.K, wl.scene.sh_degree, batched=1)
+    sc.load_scene(wl.scene)
+    sc.set_train_views(wl.train)
+    sc.set_candidates(wl.cand)
+    sc.prepare(wl.target)
+    sc.score_host()
+    o = O.OracleScene(wl.scene, target=wl.target)
+    act = o.confidence() > 0
+    assert 0 < act.sum() < wl.scene.n
+    for v in range(wl.cand.n):
+        off, ids = sc.debug_tile_lists(2, v)
+        goff, gids = off.cpu().numpy().astype(np.int64), ids.cpu().numpy().astype(np.int64)
+        roff, rids = o.tile_lists(wl.cand, v)
+        noff, nids = o.tile_needed(wl.cand, v)
+        nt = len(roff) - 1
+        assert len(goff) == nt + 1 and goff[-1] == len(gids)
+        N = wl.scene.n
+        rkey = np.repeat(np.arange(nt), np.diff(roff)) * N + rids
+        gkey = np.repeat(np.arange(nt), np.diff(goff)) * N + gids
+        ntile = np.repeat(np.arange(nt), np.diff(noff))
+        order = np.argsort(rkey, kind="stable")
+        sk = rkey[order]
+        at = np.searchsorted(sk, gkey)
+        assert ((at < len(sk)) & (sk[np.minimum(at, len(sk) - 1)] == gkey)).all(), v
+        assert (np.diff(order[at]) > 0).all(), v
+        target_tiles = np.unique(ntile[act[nids]])
+        need = np.isin(ntile, target_tiles)
+        assert need.any(), v
+        assert np.isin(ntile[need] * N + nids[need], gkey).all(), v
+    sc.close()
+
+
 def test_batch_workload_full_size():
     """The batching workload at full size (300k Gaussians, K = 32, 256
     candidates alternating 320x240 / 640x480, IG restricted to object 1),
