@@ -147,7 +147,9 @@ __device__ __forceinline__ void packed_walk(const SlotTiles& st, SlotTiles* s_st
     int lo = 0, tx = 0, ty = 0;
     bool hit = false;
     if (t < total) {
-      int hi = 32;                               // the first slot whose inclusive end passes t
+      // the first slot whose inclusive end passes t: it lies in [0, 31]
+      // (t < total = incl[31]), so five halvings of [lo, hi] end on it
+      int hi = 31;
 #pragma unroll
       for (int it = 0; it < 5; ++it) {
         const int mid = (lo + hi) >> 1;
