@@ -630,29 +630,6 @@ def e2e_host(args, P, wl, torch, np, tiling):
 
 
 # --------------------------------------------------------- CPU oracle legs
-def oracle_sample(o, wl, stride, cand_ids):
-    """Oracle time of the training state (all training views) and of the
-    given candidate views, every `stride`-th pixel row only."""
-    t0 = time.perf_counter()
-    o.prepare(wl.train, row_stride=stride)
-    t_prep = time.perf_counter() - t0
-    t_cand = []
-    for v in cand_ids:
-        t0 = time.perf_counter()
-        o.score_views(wl.cand.subset([v]), row_stride=stride)
-        t_cand.append(time.perf_counter() - t0)
-    return t_prep, t_cand
-
-
-def fit_full(t1, t2, s1, s2):
-    """t(s) = a + b / s through two row strides, evaluated at s = 1: a is the
-    per-call cost that does not shrink with the rows (per-Gaussian
-    log-determinants, allocation), b the row-proportional part."""
-    b = max((t2 - t1) / (1.0 / s2 - 1.0 / s1), 0.0)
-    a = max(t1 - b / s1, 0.0)
-    return a + b
-
-
 def cand_groups(wl):
     """One candidate of each resolution and how many candidates share it."""
     seen = {}
@@ -664,32 +641,47 @@ def cand_groups(wl):
     return [tuple(x) for x in seen.values()]
 
 
-def cpu_baseline(wl, strides=(64, 32)):
-    """The oracle's step time on this host's cores: the training state of
-    the 4 training views and one candidate of each resolution, each timed at
-    two pixel-row strides; every part is extrapolated to all rows by
-    t(s) = a + b / s, and the step = training state + each resolution's
-    candidate time x its candidate count."""
+def timed_prepare(o, wl):
+    """Oracle time of the training state (every training view, every pixel)."""
+    t0 = time.perf_counter()
+    o.prepare(wl.train)
+    return time.perf_counter() - t0
+
+
+def timed_view(o, wl, v):
+    """Oracle time of one whole candidate view's gains against the kept training state."""
+    t0 = time.perf_counter()
+    o.score_views(wl.cand.subset([v]))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl):
+    """The oracle's step time on this host's cores, from whole views: the
+    training state of the training views and one candidate of each
+    resolution, each timed in full; the step = training state + each
+    resolution's candidate time x its candidate count."""
     from oracle import oracle as O
     O.build()
     groups = cand_groups(wl)
     o = O.OracleScene(wl.scene, target=wl.target)
     t_all0 = time.perf_counter()
-    runs = [oracle_sample(o, wl, s, [g[0] for g in groups]) for s in strides]
+    prep = timed_prepare(o, wl)
+    cand = [timed_view(o, wl, g[0]) for g in groups]
     wall = time.perf_counter() - t_all0
-    prep = fit_full(runs[0][0], runs[1][0], *strides)
-    cand = [fit_full(runs[0][1][i], runs[1][1][i], *strides) for i in range(len(groups))]
     t_step = prep + sum(c * g[1] for c, g in zip(cand, groups))
     return {"value": round(wl.cand.n / t_step, 6), "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": (f"training state ({wl.train.n} views) and one candidate of each resolution "
-                       f"({', '.join(str(g[0]) for g in groups)}) at pixel-row strides {strides[0]} and "
-                       f"{strides[1]} ({wall:.1f} s of CPU time in all), each part extrapolated to all rows "
-                       f"by t = a + b / stride; step = training state {prep:.1f} s + "
+            "sample": (f"training state ({wl.train.n} views) and one whole candidate of each resolution "
+                       f"({', '.join(str(g[0]) for g in groups)}), every pixel ({wall:.1f} s of CPU time); "
+                       f"step = training state {prep:.1f} s + "
                        + " + ".join(f"{g[1]} x {c:.1f} s" for c, g in zip(cand, groups))
                        + f" = {t_step:.1f} s for {wl.cand.n} candidates")}
 
 
 def run_reference(args):
+    """The oracle as the reference arm: the training state once (in the first
+    warm-up step), then one whole candidate view per step, the resolutions in
+    turn; the value is the candidates of a step over the training state plus
+    each resolution's mean view time x its candidate count."""
     world, rank, _ = dist_info()
     if rank != 0:
         return
@@ -699,25 +691,24 @@ def run_reference(args):
     wl = S.make_workload(args.workload, seed=0)
     groups = cand_groups(wl)
     o = O.OracleScene(wl.scene, target=wl.target)
-    s_fast, s_slow = 64, 32
     t_all0 = time.perf_counter()
-    # warm-up steps at the second stride fix the row-independent part of the model
-    warm = [oracle_sample(o, wl, s_slow, [g[0] for g in groups]) for _ in range(max(1, args.warmup))]
-    per_step, est = [], []
+    t_prep = timed_prepare(o, wl)
+    for i in range(max(0, args.warmup - 1)):
+        timed_view(o, wl, groups[i % len(groups)][0])
+    per_group = [[] for _ in groups]
+    per_step = []
     for i in range(args.steps):
-        t0 = time.perf_counter()
-        tp, tc = oracle_sample(o, wl, s_fast, [g[0] for g in groups])
-        per_step.append(time.perf_counter() - t0)
-        prep = fit_full(tp, warm[-1][0], s_fast, s_slow)
-        cand = [fit_full(tc[j], warm[-1][1][j], s_fast, s_slow) for j in range(len(groups))]
-        est.append(prep + sum(c * g[1] for c, g in zip(cand, groups)))
-    value = wl.cand.n / statistics.mean(est)
+        j = i % len(groups)
+        t = timed_view(o, wl, groups[j][0])
+        per_group[j].append(t)
+        per_step.append(t)
+    means = [statistics.mean(t) if t else statistics.mean(per_step) for t in per_group]
+    t_job = t_prep + sum(m * g[1] for m, g in zip(means, groups))
+    value = wl.cand.n / t_job
     ms_step = statistics.mean(per_step) * 1e3
-    sample = (f"per step: the training state ({wl.train.n} views) and one candidate of each resolution at "
-              f"pixel-row stride {s_fast} (timed: {ms_step / 1e3:.1f} s); each part extrapolated to all rows by "
-              f"t = a + b / stride with a from the warm-up steps at stride {s_slow}; value = {wl.cand.n} "
-              f"candidates / (training state + each resolution's candidate time x its count) = "
-              f"{statistics.mean(est):.1f} s")
+    sample = (f"training state ({wl.train.n} views, every pixel) {t_prep:.1f} s once, then per step one whole "
+              f"candidate view, the resolutions in turn (mean {ms_step / 1e3:.1f} s); value = {wl.cand.n} "
+              f"candidates / (training state + each resolution's mean view time x its count) = {t_job:.1f} s")
     result = {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 1),
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
