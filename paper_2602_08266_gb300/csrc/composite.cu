@@ -24,6 +24,8 @@
 // term), over the tile's warps in shared memory, and added to the
 // per-Gaussian block in global memory with one vector atomic per 4 floats
 // per (tile, Gaussian).
+#include <type_traits>
+
 #include "nbv_internal.cuh"
 
 namespace nbv {
@@ -122,6 +124,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
+// Per-thread asynchronous gathers (cp.async) into shared memory: 16-byte
+// records and 4-byte words; each thread waits for its own copies, and a
+// barrier afterwards publishes them to the block.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 struct StageRing {
   float4* buf;           // [2][2][kBatch]: buffer b, record r0 / r1, splat
   uint32_t bar;          // shared address of two consecutive mbarriers
@@ -174,6 +188,16 @@ __host__ __device__ inline size_t ring_offset(int K, int KC, int nB, int kBatch)
                      sizeof(float) * (size_t)kBatch * nBp + sizeof(int) * kBatch +
                      sizeof(float) * (kTilePix / 32) * kCS * (size_t)(u_rows(K) + kVRows);
   return (end + 15) & ~(size_t)15;
+}
+
+// Byte offset of the information pass's second staging set (the records,
+// block slots, flags and probabilities of the round after the current one),
+// past the staging ring and its barriers; and its size.
+__host__ __device__ inline size_t stage2_offset(int K, int KC, int nB, int kBatch) {
+  return (ring_offset(K, KC, nB, kBatch) + sizeof(float4) * 4 * kBatch + 16 + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t stage2_bytes(int KC, int kBatch) {
+  return sizeof(float4) * 3 * kBatch + sizeof(int) * 2 * kBatch + sizeof(float) * (size_t)kBatch * ((KC + 1) & ~1);
 }
 
 // One 16x16 tile of one view: both passes. blocks_v is the view's block
@@ -417,29 +441,87 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       }
       ex[mt][i] = e;
     }
-  for (uint32_t end = last_max; end > first_info;) {
-    const uint32_t start = (end - first_info > (uint32_t)kBatch) ? end - kBatch : first_info;
+  // The records of this pass are staged one round ahead: while the block
+  // works on round r from one set of buffers, every warp gathers its share
+  // of round r + 1 (the 16-byte records, the block slot and the K + 1
+  // probabilities of kSPW splats) into the other set with cp.async, using
+  // Gaussian ids it loaded during round r - 1; each thread waits for its own
+  // copies after the round's flush, and the next round's opening barrier
+  // publishes them.
+  constexpr int kSPW = kBatch / (kTilePix / 32);          // splats a warp stages per round
+  unsigned char* st2 = smem + stage2_offset(K, KC, nB, kBatch);
+  float4* x0 = reinterpret_cast<float4*>(st2);
+  float4* x1 = x0 + kBatch;
+  float4* x2 = x1 + kBatch;
+  int* xid = reinterpret_cast<int*>(x2 + kBatch);
+  int* xtouched = xid + kBatch;
+  float* xsp = reinterpret_cast<float*>(xtouched + kBatch);
+  auto rstart = [&](uint32_t e) -> uint32_t {
+    return (e - first_info > (uint32_t)kBatch) ? e - kBatch : first_info;
+  };
+  // lanes < kSPW: the Gaussian ids of this warp's splats of round [st_, en_)
+  auto load_ids = [&](uint32_t st_, uint32_t en_) -> uint32_t {
+    const int j = wq * kSPW + lane;
+    return (lane < kSPW && j < (int)(en_ - st_)) ? args.vals[st_ + j] : 0u;
+  };
+  auto issue = [&](uint32_t st_, uint32_t en_, int set, uint32_t gq) {
+    float4* d0 = set ? x0 : s0;
+    float4* d1 = set ? x1 : s1;
+    float4* d2 = set ? x2 : s2;
+    int* did = set ? xid : sid;
+    float* dp = set ? xsp : sp;
+    const int njr = (int)(en_ - st_);
+#pragma unroll
+    for (int q = 0; q < kSPW; ++q) {
+      const int j = wq * kSPW + q;
+      const uint32_t g = __shfl_sync(0xffffffffu, gq, q);
+      if (j < njr) {                                        // warp-uniform
+        if (lane == 0) cp_async16(d0 + j, args.r0 + rec_off + g);
+        else if (lane == 1) cp_async16(d1 + j, args.r1 + rec_off + g);
+        else if (lane == 2) cp_async16(d2 + j, args.r2 + rec_off + g);
+        else if (lane == 3) cp_async4(did + j, args.slot + g);   // block slot, or -1: only extends the suffix sums
+        for (int k = lane; k < KCP; k += 32) {
+          float* d = dp + j * KCP + k;
+          if (k < KC) cp_async4(d, args.p + (size_t)g * KC + k);
+          else *d = 0.0f;
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  uint32_t gnext = 0u;
+  if (tid < kBatch) touched[tid] = 0;
+  if (last_max > first_info) {
+    const uint32_t st0 = rstart(last_max);
+    issue(st0, last_max, 0, load_ids(st0, last_max));
+    if (st0 > first_info) gnext = load_ids(rstart(st0), st0);
+    cp_async_wait_all();
+  }
+  int set = 0;
+  for (uint32_t end = last_max; end > first_info; set ^= 1) {
+    const uint32_t start = rstart(end);
     const int nj = (int)(end - start);
-    __syncthreads();
-    if (tid < nj) {
-      const uint32_t g = args.vals[start + tid];
-      s0[tid] = args.r0[rec_off + g];
-      s1[tid] = args.r1[rec_off + g];
-      s2[tid] = args.r2[rec_off + g];
-      sid[tid] = args.slot[g];          // block slot, or -1: only extends the suffix sums
-      touched[tid] = 0;
+    __syncthreads();     // this round's set is complete and published; the last round's flush is done
+    const float4* c0 = set ? x0 : s0;
+    const float4* c1 = set ? x1 : s1;
+    const float4* c2 = set ? x2 : s2;
+    const int* cid = set ? xid : sid;
+    const float* csp = set ? xsp : sp;
+    int* ctouched = set ? xtouched : touched;
+    // the other set's flags were last read by the flush before this barrier
+    // and are next written in the following round
+    if (tid < kBatch) (set ? touched : xtouched)[tid] = 0;
+    if (start > first_info) {
+      const uint32_t s1n = rstart(start);
+      issue(s1n, start, set ^ 1, gnext);
+      gnext = (s1n > first_info) ? load_ids(rstart(s1n), s1n) : 0u;
     }
-    for (int i = tid; i < nj * KCP; i += kTilePix) {
-      const int j = i / KCP, k = i - j * KCP;
-      sp[i] = k < KC ? args.p[(size_t)args.vals[start + j] * KC + k] : 0.0f;
-    }
-    __syncthreads();
     for (int j = nj - 1; j >= 0; --j) {
       const uint32_t idx = start + j;
       if (idx >= wlast) continue;
       if (idx < wfirst) break;            // warp-uniform: nothing of this warp's is left in front
       bool act = false;
-      const float4 a0 = s0[j], a1 = s1[j], a2 = s2[j];
+      const float4 a0 = c0[j], a1 = c1[j], a2 = c2[j];
       float pw = 0.0f;
       if (inside && idx < last) {
         pw = splat_power(a0.x, a0.y, a1.x, a1.y, a1.z, pxc, pyc);
@@ -447,7 +529,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       }
       const unsigned any = __ballot_sync(0xffffffffu, act);
       if (any == 0u) continue;
-      const bool info = sid[j] >= 0;     // the same for the whole tile
+      const bool info = cid[j] >= 0;     // the same for the whole tile
       // active pixels are compacted into the first rows of the warp's buffers
       const int nact = __popc(any);
       const int nks = (nact + 7) >> 3;
@@ -460,7 +542,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
         const float inv_om = __fdividef(1.0f, 1.0f - alpha);
         const float Ti = Tb * inv_om;
         const float w = alpha * Ti;
-        const float2* pj2 = reinterpret_cast<const float2*>(sp + j * KCP);
+        const float2* pj2 = reinterpret_cast<const float2*>(csp + j * KCP);
         if (info) {
         const float ae = clamped ? 0.0f : alpha;
         const float wa = w * ae;
@@ -520,7 +602,7 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
       }
       if (!info) continue;
       n_ig += act ? 1u : 0u;
-      if (lane == 0) touched[j] = 1;
+      if (lane == 0) ctouched[j] = 1;
       __syncwarp();
       float dq[3][4], dxo[MTBM][4];
 #pragma unroll
@@ -581,16 +663,17 @@ __device__ __forceinline__ void composite_tile(const CompositeArgs& args, const 
     __syncthreads();
     // flush the tile's share of each touched Gaussian's block
     const int n4 = nBp / 4;
-    if (args.stats && tid < nj && touched[tid]) atomicAdd(&args.stats[2], 1ull);
+    if (args.stats && tid < nj && ctouched[tid]) atomicAdd(&args.stats[2], 1ull);
     for (int i = tid; i < nj * n4; i += kTilePix) {
       const int j = i / n4, q = i - j * n4;
-      if (!touched[j]) continue;
+      if (!ctouched[j]) continue;
       float4* src = reinterpret_cast<float4*>(acc + j * nBp) + q;
       const float4 v = *src;
       *src = make_float4(0.0f, 0.0f, 0.0f, 0.0f);   // the accumulators stay zero between rounds
-      float4* dst = reinterpret_cast<float4*>(blocks_v + (size_t)sid[j] * nBp) + q;
+      float4* dst = reinterpret_cast<float4*>(blocks_v + (size_t)cid[j] * nBp) + q;
       atomicAdd(dst, v);
     }
+    cp_async_wait_all();   // this thread's copies of the next round have landed
     end = start;
   }
   if (args.stats) {
@@ -716,7 +799,11 @@ __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Co
       const uint32_t start = rg.x + k * kFwd;
       const uint32_t nj = min((uint32_t)kFwd, rg.y - start);
       const uint32_t imask = s_info[b];
-      if (!done) {
+      // the first-splat check only in rounds with an information splat that
+      // a pixel of the warp may still need (warp-uniform, so the common
+      // rounds run the plain loop)
+      const bool watch = __any_sync(0xffffffffu, first_pix == kNoEntry && !done) && imask != 0u;
+      auto walk = [&](auto kWatch) {
         for (uint32_t j = 0; j < nj; ++j) {
           const float4 a0 = q0[j], a1 = q1[j];
           const float pw = splat_power(a0.x, a0.y, a1.x, a1.y, a1.z, pxc, pyc);
@@ -727,9 +814,15 @@ __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Co
           if (tt < c.t_min) { done = true; break; }
           T = tt;
           last = start + j + 1;
-          if (first_pix == kNoEntry && ((imask >> j) & 1u)) first_pix = start + j;
+          if constexpr (decltype(kWatch)::value) {
+            if (first_pix == kNoEntry && ((imask >> j) & 1u)) first_pix = start + j;
+          }
           ++n_blend;
         }
+      };
+      if (!done) {
+        if (watch) walk(std::true_type{});
+        else walk(std::false_type{});
       }
       // every warp has read s_info[(k + 1) & 1] of round k - 1 (it passed this
       // round's opening barrier); the next round's barrier publishes the store
@@ -782,7 +875,7 @@ __global__ void __launch_bounds__(kTilePix, 4) k_forward(CompositeArgs args, Con
 
 // Dynamic shared memory of k_composite for K objects and rounds of kBatch splats.
 inline size_t composite_smem(const Consts& c, int nB, int kBatch) {
-  return ring_offset(c.K, c.KC, nB, kBatch) + sizeof(float4) * 4 * kBatch + 16;
+  return stage2_offset(c.K, c.KC, nB, kBatch) + stage2_bytes(c.KC, kBatch);
 }
 
 // The largest dynamic shared memory a block of this device may opt into.

@@ -116,10 +116,9 @@ __device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, floa
 enum ProjMode {
   kProjAll = 0,      // multi-view: records of every slot (tiles counted by k_count_tiles)
   kProjCount = 1,    // one view: records, radius and the number of rectangle tiles that pass tile_hit
-  kProjMark = 2,     // multi-view, active slots: records, and their tiles marked in the view's tile mark
-  kProjTarget = 3    // multi-view with a mark: the number of marked tiles inside the view's box that
-                     // pass tile_hit; records only for a slot with at least one
+  kProjMark = 2      // multi-view, active slots: records, and their tiles marked in the view's tile mark
 };
+// (Every slot of the multi-view pass with a mark: k_project_target.)
 
 // Tile marks of the multi-view pass with an active subset.
 struct TileMark {
@@ -129,31 +128,24 @@ struct TileMark {
   int lo_x, lo_y, hi_x, hi_y;   // kProjMark: the box of the tiles this slot marked (hi_x < 0: none)
 };
 
-// Project Gaussian g into camera cam; the records go to slot o of pr (see
-// ProjMode for what else).
-template <int kMode, int DEG>
-__device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, const DevCam& cam, int64_t g,
-                                            const DevProj& pr, size_t o, TileMark* tm = nullptr) {
-  const float4 ms = s.mu_sig[g];
-  const float4 ss = s.scale_skip[g];
-  const float4 qq = s.qn[g];
-  const float4 ax = s.aux[g];
+// The key path of Gaussian g in camera cam: culling, the conic, radius and
+// tile rectangle in correctly rounded single precision and a fixed order.
+// With a box (the view's box of marked tiles) a slot whose conservative
+// radius bound cannot reach it is dropped after the projected centre.
+// False: no rectangle (culled, degenerate, off the grid or dropped).
+struct KeyPath {
+  float mx, my, A, B, C, tz, r;
+  int4 rect;                // {x0, x1, y0, y1}
+};
+
+__device__ __forceinline__ bool key_path(const Consts& c, const DevCam& cam, const float4& ms, const float4& ss,
+                                         const float4& qq, const int4* box, KeyPath& kp) {
   const float* R = cam.R;
-  if (kMode == kProjCount) {
-    pr.touched[o] = 0u;
-    pr.radius[o] = 0.0f;
-  }
-  if (kMode == kProjTarget) {
-    pr.touched[o] = 0u;           // records are read only for slots with entries
-  } else {
-    pr.rect[o] = make_int4(-1, -1, -1, -1);
-    pr.zbits[o] = 0u;
-  }
   // ---- key path: correctly rounded single precision, fixed order
   const float tx = fa(fa(fa(fm(R[0], ms.x), fm(R[1], ms.y)), fm(R[2], ms.z)), cam.t[0]);
   const float ty = fa(fa(fa(fm(R[3], ms.x), fm(R[4], ms.y)), fm(R[5], ms.z)), cam.t[1]);
   const float tz = fa(fa(fa(fm(R[6], ms.x), fm(R[7], ms.y)), fm(R[8], ms.z)), cam.t[2]);
-  if (!(tz > c.near_z)) return;
+  if (!(tz > c.near_z)) return false;
   const float xr = fd(tx, tz), yr = fd(ty, tz);
   const float mx = fa(fm(cam.fx, xr), cam.cx);
   const float my = fa(fm(cam.fy, yr), cam.cy);
@@ -161,7 +153,7 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   const float limy = fm(c.guard, fd(fm(0.5f, (float)cam.H), cam.fy));
   const float xz = fminf(limx, fmaxf(-limx, xr));
   const float yz = fminf(limy, fmaxf(-limy, yr));
-  if (kMode == kProjTarget) {
+  if (box != nullptr) {
     // Early rejection of a slot whose rectangle cannot reach the view's box
     // of marked tiles, before the rest of the key path. lambda_max of the 2D
     // covariance is at most its trace + sqrt(0.1) (the square root's floor),
@@ -171,8 +163,8 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
     // The bound on the radius (3 sqrt(lambda) rounded up) carries a 1%
     // margin and 2 pixels for the rounding of this ordinary float estimate,
     // so only slots with no tile in the box are dropped.
-    const int4 bx = tm->bb[0];
-    if (bx.z < bx.x || bx.w < bx.y) return;              // no marked tile in this view
+    const int4 bx = *box;
+    if (bx.z < bx.x || bx.w < bx.y) return false;        // no marked tile in this view
     const float smax = fmaxf(ss.x, fmaxf(ss.y, ss.z));
     const float iz = 1.0f / tz;
     const float jx = cam.fx * iz, jy = cam.fy * iz;
@@ -181,7 +173,7 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
     const float twb = (float)cam.TW, thb = (float)cam.TH;
     if (mx + rb < (float)bx.x * twb || mx - rb >= (float)(bx.z + 1) * twb || my + rb < (float)bx.y * thb ||
         my - rb >= (float)(bx.w + 1) * thb)
-      return;
+      return false;
   }
   const float txp = fm(xz, tz), typ = fm(yz, tz);
   const float tz2 = fm(tz, tz);
@@ -227,7 +219,7 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   const float b = fa(fa(fm(U0[0], T1[0]), fm(U0[1], T1[1])), fm(U0[2], T1[2]));
   const float cc = fa(fa(fa(fm(U1[0], T1[0]), fm(U1[1], T1[1])), fm(U1[2], T1[2])), c.dilation);
   const float det = fs(fm(a, cc), fm(b, b));
-  if (!(det > 0.0f)) return;
+  if (!(det > 0.0f)) return false;
   const float A = fd(cc, det), B = fd(-b, det), C = fd(a, det);
   const float mid = fm(0.5f, fa(a, cc));
   const float lam = fa(mid, __fsqrt_rn(fmaxf(0.1f, fs(fm(mid, mid), det))));
@@ -239,24 +231,21 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   const int x1 = (int)fminf(fmaxf(fx1, 0.0f), (float)cam.GX);
   const int y0 = (int)fminf(fmaxf(fy0, 0.0f), (float)cam.GY);
   const int y1 = (int)fminf(fmaxf(fy1, 0.0f), (float)cam.GY);
-  if (x0 >= x1 || y0 >= y1) return;
-  if (kMode == kProjTarget) {
-    // marked tiles of the rectangle inside the view's box that pass tile_hit
-    const int4 b = tm->bb[0];
-    const int cx0 = max(x0, b.x), cx1 = min(x1, b.z + 1), cy0 = max(y0, b.y), cy1 = min(y1, b.w + 1);
-    uint32_t hits = 0;
-    if (cx0 < cx1 && cy0 < cy1) {
-      const float bc = -__fdiv_rn(B, C), ba = -__fdiv_rn(B, A);
-      for (int tyi = cy0; tyi < cy1; ++tyi)
-        for (int txi = cx0; txi < cx1; ++txi)
-          hits += (tm->mark[tm->base + (uint32_t)(tyi * cam.GX + txi)] != 0 &&
-                   tile_hit(A, B, C, mx, my, ss.w, bc, ba, txi, tyi, cam.TW, cam.TH))
-                      ? 1u
-                      : 0u;
-    }
-    pr.touched[o] = hits;
-    if (hits == 0) return;
-  }
+  if (x0 >= x1 || y0 >= y1) return false;
+  kp.mx = mx; kp.my = my; kp.A = A; kp.B = B; kp.C = C; kp.tz = tz; kp.r = r;
+  kp.rect = make_int4(x0, x1, y0, y1);
+  return true;
+}
+
+// The records of a slot with entries: {mx, my, skip and clamp thresholds},
+// {A, B, C, sigma}, the view-dependent colour (real SH, ordinary single
+// precision) with camera z, the rectangle and the depth bits.
+template <int DEG>
+__device__ __forceinline__ void write_records(const DevScene& s, const DevCam& cam, int64_t g, const float4& ms,
+                                              const float4& ss, const float4& ax, const KeyPath& kp,
+                                              const DevProj& pr, size_t o) {
+  const float mx = kp.mx, my = kp.my, A = kp.A, B = kp.B, C = kp.C, tz = kp.tz;
+  const int x0 = kp.rect.x, x1 = kp.rect.y, y0 = kp.rect.z, y1 = kp.rect.w;
   // ---- view-dependent colour (values; ordinary single precision)
   float dv[3] = {ms.x - cam.campos[0], ms.y - cam.campos[1], ms.z - cam.campos[2]};
   const float il = rsqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
@@ -293,6 +282,28 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
   pr.r2[o] = make_float4(rgb[0], rgb[1], rgb[2], tz);
   pr.rect[o] = make_int4(x0, x1, y0, y1);
   pr.zbits[o] = __float_as_uint(tz);
+}
+
+// Project Gaussian g into camera cam; the records go to slot o of pr (see
+// ProjMode for what else).
+template <int kMode, int DEG>
+__device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, const DevCam& cam, int64_t g,
+                                            const DevProj& pr, size_t o, TileMark* tm = nullptr) {
+  const float4 ms = s.mu_sig[g];
+  const float4 ss = s.scale_skip[g];
+  const float4 qq = s.qn[g];
+  const float4 ax = s.aux[g];
+  if (kMode == kProjCount) {
+    pr.touched[o] = 0u;
+    pr.radius[o] = 0.0f;
+  }
+  pr.rect[o] = make_int4(-1, -1, -1, -1);
+  pr.zbits[o] = 0u;
+  KeyPath kp;
+  if (!key_path(c, cam, ms, ss, qq, nullptr, kp)) return;
+  const float mx = kp.mx, my = kp.my, A = kp.A, B = kp.B, C = kp.C;
+  const int x0 = kp.rect.x, x1 = kp.rect.y, y0 = kp.rect.z, y1 = kp.rect.w;
+  write_records<DEG>(s, cam, g, ms, ss, ax, kp, pr, o);
   if (kMode == kProjMark) {
     // mark this active splat's tiles and grow the view's box around them
     const float bc = -__fdiv_rn(B, C), ba = -__fdiv_rn(B, A);
@@ -308,7 +319,7 @@ __device__ __forceinline__ void project_one(const DevScene& s, const Consts& c, 
     tm->lo_x = lo_x; tm->lo_y = lo_y; tm->hi_x = hi_x; tm->hi_y = hi_y;   // the caller merges them into the box
   }
   if (kMode == kProjCount) {
-    pr.radius[o] = r;
+    pr.radius[o] = kp.r;
     uint32_t hits = 0;
     const float bc = -__fdiv_rn(B, C), ba = -__fdiv_rn(B, A);
     for (int tyi = y0; tyi < y1; ++tyi)
@@ -330,17 +341,54 @@ __global__ void k_project(DevScene s, Consts c, DevCam cam, DevProj pr) {
 // every record load and store is coalesced and the camera is the block's.
 template <int DEG, int kMode>
 __global__ void __launch_bounds__(256) k_project_views(DevScene s, Consts c, const DevCam* __restrict__ cams,
-                                                       DevProj pr, uint8_t* mark, int4* bb,
-                                                       const uint32_t* __restrict__ tile_base) {
+                                                       DevProj pr) {
   __shared__ DevCam cam;
   const int v = blockIdx.y;
   if (threadIdx.x == 0) cam = cams[v];
   __syncthreads();
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= s.n) return;
-  TileMark tm{};
-  if (kMode == kProjTarget) tm = TileMark{mark, bb + v, tile_base[v], 0, 0, -1, -1};
-  project_one<kMode, DEG>(s, c, cam, g, pr, (size_t)v * s.n + g, &tm);
+  project_one<kMode, DEG>(s, c, cam, g, pr, (size_t)v * s.n + g);
+}
+
+// Every (view, Gaussian) slot of the multi-view pass with a target: the key
+// path (dropping slots that cannot reach the view's box of marked tiles),
+// the number of marked tiles inside the box that pass tile_hit (each thread
+// walks its own rectangle: with the rectangles cut to the box, packing the
+// warp's tiles into shared rounds measured slower), and the records of the
+// slots with at least one.
+template <int DEG>
+__global__ void __launch_bounds__(256) k_project_target(DevScene s, Consts c, const DevCam* __restrict__ cams,
+                                                        DevProj pr, const uint8_t* __restrict__ mark,
+                                                        const int4* __restrict__ bb,
+                                                        const uint32_t* __restrict__ tile_base) {
+  __shared__ DevCam cam;
+  const int v = blockIdx.y;
+  if (threadIdx.x == 0) cam = cams[v];
+  __syncthreads();
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= s.n) return;
+  const size_t o = (size_t)v * s.n + g;
+  pr.touched[o] = 0u;                            // records are read only for slots with entries
+  const float4 ms = s.mu_sig[g];
+  const float4 ss = s.scale_skip[g];
+  const int4 box = bb[v];
+  KeyPath kp;
+  if (!key_path(c, cam, ms, ss, s.qn[g], &box, kp)) return;
+  const int4 r = clip_rect(kp.rect, box);
+  if (r.x < 0) return;
+  const float bc = -__fdiv_rn(kp.B, kp.C), ba = -__fdiv_rn(kp.B, kp.A);
+  const uint32_t base = tile_base[v];
+  uint32_t hits = 0;
+  for (int tyi = r.z; tyi < r.w; ++tyi)
+    for (int txi = r.x; txi < r.y; ++txi)
+      hits += (mark[base + (uint32_t)(tyi * cam.GX + txi)] != 0 &&
+               tile_hit(kp.A, kp.B, kp.C, kp.mx, kp.my, ss.w, bc, ba, txi, tyi, cam.TW, cam.TH))
+                  ? 1u
+                  : 0u;
+  if (hits == 0) return;
+  pr.touched[o] = hits;
+  write_records<DEG>(s, cam, g, ms, ss, s.aux[g], kp, pr, o);
 }
 
 // Active slots of the multi-view pass (thread per (view, active slot)):
@@ -376,10 +424,10 @@ int launch_project_views(const DevScene& s, const Consts& c, const DevCam* cams,
   const int bs = 256;
   const dim3 grid((unsigned)((s.n + bs - 1) / bs), (unsigned)nv);
   switch (c.deg) {
-    case 0: k_project_views<0, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr, nullptr, nullptr, nullptr); break;
-    case 1: k_project_views<1, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr, nullptr, nullptr, nullptr); break;
-    case 2: k_project_views<2, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr, nullptr, nullptr, nullptr); break;
-    default: k_project_views<3, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr, nullptr, nullptr, nullptr); break;
+    case 0: k_project_views<0, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
+    case 1: k_project_views<1, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
+    case 2: k_project_views<2, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
+    default: k_project_views<3, kProjAll><<<grid, bs, 0, st>>>(s, c, cams, pr); break;
   }
   return 1;
 }
@@ -411,10 +459,10 @@ int launch_project_target(const DevScene& s, const Consts& c, const DevCam* cams
   }
   const dim3 grid((unsigned)((s.n + bs - 1) / bs), (unsigned)nv);
   switch (c.deg) {
-    case 0: k_project_views<0, kProjTarget><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
-    case 1: k_project_views<1, kProjTarget><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
-    case 2: k_project_views<2, kProjTarget><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
-    default: k_project_views<3, kProjTarget><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
+    case 0: k_project_target<0><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
+    case 1: k_project_target<1><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
+    case 2: k_project_target<2><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
+    default: k_project_target<3><<<grid, bs, 0, st>>>(s, c, cams, pr, mark, bb, tile_base); break;
   }
   return l + 1;
 }

@@ -86,95 +86,6 @@ int scan_rec(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaSt
   return launches + 1;
 }
 
-// One slot's tile walk: its tile rectangle {x0, x1, y0, y1} (x0 < 0: none),
-// the splat's mean, conic and skip exponent, the stationary-point ratios of
-// tile_hit, and the view's tile grid. The warp kernels below load one slot
-// per lane and walk the tiles of all 32 rectangles together (packed_walk).
-struct SlotTiles {
-  int4 r;
-  float mx, my, thr, A, B, C, bc, ba;
-  uint32_t base;
-  int gx, tw, th;
-};
-
-__device__ __forceinline__ SlotTiles slot_tiles(int4 r, float4 a0, float4 a1, uint32_t base, const DevCam& cam) {
-  SlotTiles t;
-  t.r = r;
-  t.mx = a0.x; t.my = a0.y; t.thr = a0.z;
-  t.A = a1.x; t.B = a1.y; t.C = a1.z;
-  t.bc = -__fdiv_rn(a1.y, a1.z);
-  t.ba = -__fdiv_rn(a1.y, a1.x);
-  t.base = base;
-  t.gx = cam.GX; t.tw = cam.TW; t.th = cam.TH;
-  return t;
-}
-
-__device__ __forceinline__ SlotTiles no_tiles() {
-  SlotTiles t{};
-  t.r = make_int4(-1, -1, -1, -1);
-  t.tw = t.th = 1;
-  return t;
-}
-
-constexpr int kDupThreads = 256;   // blocks of the tile-walking kernels
-
-// The tiles of a warp's 32 slots (lane l holds slot l; an empty rectangle
-// has x0 < 0) walked as one sequence: slot order, then row order within a
-// rectangle, numbered by an inclusive scan of the areas, 32 tiles per round,
-// each lane finding its slot by a binary search of the scan. Small
-// rectangles share rounds, and the sequence order is the order of walking
-// the rectangles one after the other. fn(s, q, tx, ty, hit) is called by every
-// lane each round (s = the lane's slot, hit false past the end), so fn may
-// use warp collectives; keep(q, tx, ty) filters tiles before tile_hit.
-// s_st / s_incl: 32 entries of this warp's shared memory.
-template <class Keep, class Fn>
-__device__ __forceinline__ void packed_walk(const SlotTiles& st, SlotTiles* s_st, int* s_incl, int lane, Keep keep,
-                                            Fn fn) {
-  const int area = st.r.x >= 0 ? (st.r.y - st.r.x) * (st.r.w - st.r.z) : 0;
-  int incl = area;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
-  __syncwarp();
-  s_st[lane] = st;
-  s_incl[lane] = incl;
-  __syncwarp();
-  for (int t0 = 0; t0 < total; t0 += 32) {
-    const int t = t0 + lane;
-    int lo = 0, tx = 0, ty = 0;
-    bool hit = false;
-    if (t < total) {
-      // the first slot whose inclusive end passes t: it lies in [0, 31]
-      // (t < total = incl[31]), so five halvings of [lo, hi] end on it
-      int hi = 31;
-#pragma unroll
-      for (int it = 0; it < 5; ++it) {
-        const int mid = (lo + hi) >> 1;
-        if (s_incl[mid] > t) hi = mid; else lo = mid + 1;
-      }
-      const SlotTiles& q = s_st[lo];
-      const int idx = t - (lo > 0 ? s_incl[lo - 1] : 0);
-      const int w = q.r.y - q.r.x;
-      const int qy = idx / w, qx = idx - qy * w;
-      tx = q.r.x + qx;
-      ty = q.r.z + qy;
-      hit = keep(q, tx, ty) && tile_hit(q.A, q.B, q.C, q.mx, q.my, q.thr, q.bc, q.ba, tx, ty, q.tw, q.th);
-    }
-    fn(lo, s_st[lo], tx, ty, hit);
-  }
-}
-
-// A slot's tile rectangle {x0, x1, y0, y1} (exclusive ends) cut to the view's
-// bounding box of marked tiles {min x, min y, max x, max y} (inclusive);
-// x0 = -1 when nothing is left. No tile outside the box is marked.
-__device__ __forceinline__ int4 clip_rect(int4 r, int4 b) {
-  const int4 c = make_int4(max(r.x, b.x), min(r.y, b.z + 1), max(r.z, b.y), min(r.w, b.w + 1));
-  return (c.x < c.y && c.z < c.w) ? c : make_int4(-1, -1, -1, -1);
-}
-
 // Every Gaussian's entries for the tiles of its rectangle that pass
 // tile_hit, in row order: a lane per Gaussian, the warp's 32 rectangles
 // walked together (packed_walk), the passing tiles of a round compacted by a
