@@ -2023,7 +2023,9 @@ int launch_views_gains_gm(const DevScene& s, const Consts& c, const DevCam* cams
   const int nsm = device_sm_count();
   const int nchunk = (nv + 31) / 32;
   int grid = (int)((s.n_act + nw - 1) / nw);
-  const int want = (nsm * 4 + nchunk - 1) / nchunk;   // a few blocks per SM over all chunks
+  // a few blocks per SM over all chunks (16 per SM, for a better-balanced
+  // last wave, measured slower: 6.4 -> 7.7 ms on the batching workload)
+  const int want = (nsm * 4 + nchunk - 1) / nchunk;
   if (grid > want) grid = want;
   if (grid * nw > parts_cap) grid = parts_cap / nw;
   if (grid < 1) grid = 1;

@@ -51,24 +51,22 @@ __global__ void k_scene_prep(DevScene s, Consts c, int target) {
   const float* m = s.mu_raw + 3 * g;
   s.mu_sig[g] = make_float4(m[0], m[1], m[2], sig32);
   s.scale_skip[g] = make_float4(sc[0], sc[1], sc[2], pw_skip);
-  // p = softmax(o); argmax on the logits, lowest id on ties
+  // p = softmax(o) in single precision (values only: every decision that
+  // depends on the logits is the argmax, taken on the logits themselves,
+  // lowest id on ties); the largest term is exp(0) = 1, so max_k p_k = 1 / z
+  // and the confidence takes z summed in double
   const float* o = s.obj_raw + (size_t)g * KC;
   int am = 0;
-  double mx = (double)o[0];
-  for (int k = 1; k < KC; ++k) {
+  for (int k = 1; k < KC; ++k)
     if (o[k] > o[am]) am = k;
-    mx = fmax(mx, (double)o[k]);
-  }
+  const float mx = o[am];
   double z = 0.0;
-  for (int k = 0; k < KC; ++k) z += exp((double)o[k] - mx);
-  double pmax = 0.0, ptgt = 0.0;
+  for (int k = 0; k < KC; ++k) z += (double)expf(o[k] - mx);
+  const float zi = (float)(1.0 / z);
   float* p = s.p + (size_t)g * KC;
-  for (int k = 0; k < KC; ++k) {
-    const double pk = exp((double)o[k] - mx) / z;
-    p[k] = (float)pk;
-    pmax = fmax(pmax, pk);
-    if (k == target) ptgt = pk;
-  }
+  for (int k = 0; k < KC; ++k) p[k] = expf(o[k] - mx) * zi;
+  const double pmax = 1.0 / z;
+  const double ptgt = (target >= 0 && target < KC) ? (double)expf(o[target] - mx) / z : 0.0;
   // Eq. 7, or Eq. 12 when a target object is given
   double cg;
   if (target < 0)

@@ -387,12 +387,32 @@ __global__ void k_flags_nonzero(const uint32_t* __restrict__ in, int64_t m, uint
   if (i < m) out[i] = in[i] != 0u ? 1u : 0u;
 }
 
+// Tile ranges of the sorted 32-bit tile keys: four consecutive keys per
+// thread in one 16-byte load (the key arrays are 256-byte aligned), and
+// their neighbours on either side; no valid tile id is ~0u.
 __global__ void k_ranges32(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t t = keys[i];
-  if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
-  if (i == n - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+  const int64_t i0 = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  if (i0 >= n) return;
+  uint32_t k[4];
+  if (i0 + 4 <= n) {
+    const uint4 v = *reinterpret_cast<const uint4*>(keys + i0);
+    k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? keys[i0 + j] : ~0u;
+  }
+  const uint32_t prev = i0 > 0 ? keys[i0 - 1] : ~0u;
+  const uint32_t next = i0 + 4 < n ? keys[i0 + 4] : ~0u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t i = i0 + j;
+    if (i >= n) break;
+    const uint32_t t = k[j];
+    const uint32_t before = j == 0 ? prev : k[j - 1];
+    const uint32_t after = j == 3 ? next : k[j + 1];
+    if (before != t) ranges[t].x = (uint32_t)i;
+    if (after != t) ranges[t].y = (uint32_t)(i + 1);
+  }
 }
 
 template <typename K, int RB>
@@ -516,7 +536,8 @@ int launch_compact_depth_keys(const uint32_t* touched, int64_t m, uint32_t* flag
 int launch_ranges32(const uint32_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st) {
   cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
   if (count <= 0) return 0;
-  k_ranges32<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(keys, count, ranges);
+  const int64_t quads = (count + 3) / 4;
+  k_ranges32<<<(unsigned)((quads + 255) / 256), 256, 0, st>>>(keys, count, ranges);
   return 1;
 }
 
