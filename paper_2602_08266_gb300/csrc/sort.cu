@@ -137,8 +137,10 @@ __global__ void k_queue_keys(const uint2* __restrict__ ranges, int ntiles, uint6
 }
 
 constexpr int kRadixThreads = 256;
-constexpr int kRadixRounds = 11;   // tile of 2816 keys: the staging fits the 48 KB of static shared memory
-constexpr int kRadixTile = kRadixThreads * kRadixRounds;
+constexpr int kRadixItems = 4;     // keys a thread ranks per round
+constexpr int kRadixRounds = 4;
+constexpr int kRadixTile = kRadixThreads * kRadixItems * kRadixRounds;   // 4096 keys per block
+constexpr int kRadixWarps = kRadixThreads / 32;
 
 // Digits of RB bits (8, or 9 for 32-bit keys where that saves a pass);
 // each of the 256 threads owns DPT = 2^RB / 256 consecutive digits.
@@ -153,8 +155,8 @@ __global__ void k_radix_hist(const K* __restrict__ keys, int64_t n, int shift, u
   for (int q = 0; q < DPT; ++q) h[tid + q * kRadixThreads] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-#pragma unroll
-  for (int r = 0; r < kRadixRounds; ++r) {
+#pragma unroll 4
+  for (int r = 0; r < kRadixTile / kRadixThreads; ++r) {
     const int64_t i = base + r * kRadixThreads + tid;
     if (i < n) atomicAdd(&h[(unsigned)(keys[i] >> shift) & kMask], 1u);
   }
@@ -166,11 +168,25 @@ __global__ void k_radix_hist(const K* __restrict__ keys, int64_t n, int shift, u
   }
 }
 
-// One stable counting pass over a tile of kRadixTile keys: every element's
-// place among the tile's elements of its digit (in input order) is ranked
-// round by round (warp match + per-warp counts), the tile is rearranged by
-// digit in shared memory, and written out in that order, so that each
-// digit's elements leave as one contiguous run.
+// Dynamic shared memory of k_radix_scatter<K, RB>: two sets of per-warp
+// digit counts, the per-digit round base, run, tile start and global base,
+// the warp sums, and the tile's keys and values.
+template <typename K, int RB>
+constexpr size_t radix_scatter_smem() {
+  return sizeof(uint32_t) * (2 * kRadixWarps * (1 << RB) + 4 * (1 << RB) + kRadixWarps) +
+         (sizeof(K) + sizeof(uint32_t)) * kRadixTile;
+}
+
+// One stable counting pass over a tile of kRadixTile keys, in rounds of
+// 1024: warp w ranks the round's keys [128 w, 128 w + 128) four at a time
+// (warp match on the digit; the lowest lane of each digit group reads and
+// advances the warp's running count of that digit), so that a key's rank
+// in its warp follows its input order; the digits' owners then turn the
+// warps' counts into exclusive prefixes in place and advance each digit's
+// run, and every key goes to lstart + run + (earlier warps) + (its rank)
+// in shared memory. The two count sets alternate between rounds (the owners
+// clear the next one), so two barriers a round suffice. The tile leaves
+// rearranged by digit, each digit's keys as one contiguous run.
 template <typename K, int RB>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const K* __restrict__ kin,
                                                                  const uint32_t* __restrict__ vin,
@@ -180,10 +196,15 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const K* __rest
                                                                  const uint32_t* __restrict__ gscan, int nblocks) {
   constexpr int D = 1 << RB, DPT = D / kRadixThreads;
   constexpr unsigned kMask = (unsigned)D - 1u;
-  __shared__ uint32_t cnt[kRadixThreads / 32][D];
-  __shared__ uint32_t run[D], lstart[D], gbase[D], wsum[kRadixThreads / 32];
-  __shared__ K sk[kRadixTile];
-  __shared__ uint32_t sv[kRadixTile];
+  extern __shared__ __align__(16) unsigned char rsm[];
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(rsm);            // [2][kRadixWarps][D]
+  uint32_t* rbase = cnt + 2 * kRadixWarps * D;                  // [D]
+  uint32_t* run = rbase + D;                                    // [D]
+  uint32_t* lstart = run + D;                                   // [D]
+  uint32_t* gbase = lstart + D;                                 // [D]
+  uint32_t* wsum = gbase + D;                                   // [kRadixWarps]
+  K* sk = reinterpret_cast<K*>(rsm + sizeof(uint32_t) * (2 * kRadixWarps * D + 4 * D + kRadixWarps));
+  uint32_t* sv = reinterpret_cast<uint32_t*>(sk + kRadixTile);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   // tile-local start of each digit: exclusive scan of this tile's counts
   // (thread t holds digits DPT t .. DPT t + DPT - 1)
@@ -200,6 +221,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const K* __rest
     if (lane >= o) x += y;
   }
   if (lane == 31) wsum[wid] = x;
+  for (int i = tid; i < 2 * kRadixWarps * D; i += kRadixThreads) cnt[i] = 0;
   __syncthreads();
   uint32_t pre = 0;
   for (int w = 0; w < wid; ++w) pre += wsum[w];
@@ -213,42 +235,57 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const K* __rest
     run[d] = 0;
   }
   const unsigned lt = (1u << lane) - 1u;
-  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-  const int tile_n = (int)((n - base) < kRadixTile ? (n - base) : kRadixTile);
+  const int64_t tbase = (int64_t)blockIdx.x * kRadixTile;
+  const int tile_n = (int)((n - tbase) < kRadixTile ? (n - tbase) : kRadixTile);
+  __syncthreads();
   for (int r = 0; r < kRadixRounds; ++r) {
+    uint32_t* c = cnt + (r & 1) * kRadixWarps * D;
+    uint32_t* cw = c + wid * D;
+    K key[kRadixItems];
+    uint32_t val[kRadixItems], rk[kRadixItems];
+    int dig[kRadixItems];
 #pragma unroll
-    for (int w = 0; w < kRadixThreads / 32; ++w)
-#pragma unroll
-      for (int q = 0; q < DPT; ++q) cnt[w][tid + q * kRadixThreads] = 0;
-    __syncthreads();
-    const int li = r * kRadixThreads + tid;
-    const bool valid = li < tile_n;
-    K key = 0;
-    uint32_t val = 0;
-    int digit = D;
-    if (valid) {
-      key = kin[base + li];
-      val = vin[base + li];
-      digit = (int)((key >> shift) & kMask);
+    for (int it = 0; it < kRadixItems; ++it) {
+      const int li = r * (kRadixThreads * kRadixItems) + wid * (32 * kRadixItems) + it * 32 + lane;
+      const bool valid = li < tile_n;
+      key[it] = valid ? kin[tbase + li] : K(0);
+      val[it] = valid ? vin[tbase + li] : 0u;
+      const int d = valid ? (int)((key[it] >> shift) & kMask) : D;   // D: no digit, never counted
+      dig[it] = d;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int leader = __ffs(peers) - 1;
+      uint32_t before = 0;
+      if (valid && lane == leader) before = cw[d];
+      before = __shfl_sync(0xffffffffu, before, leader);
+      rk[it] = before + (uint32_t)__popc(peers & lt);
+      if (valid && lane == leader) cw[d] = before + (uint32_t)__popc(peers);
+      __syncwarp();
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, digit);
-    const int lrank = __popc(peers & lt);
-    if (valid && lrank == 0) cnt[wid][digit] = (uint32_t)__popc(peers);
-    __syncthreads();
-    if (valid) {
-      uint32_t pos = lstart[digit] + run[digit] + (uint32_t)lrank;
-      for (int w = 0; w < wid; ++w) pos += cnt[w][digit];
-      sk[pos] = key;
-      sv[pos] = val;
-    }
-    __syncthreads();
+    __syncthreads();            // every warp's counts of this round
+    uint32_t* cn = cnt + ((r + 1) & 1) * kRadixWarps * D;
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
       const int d = tid + q * kRadixThreads;
-      uint32_t add = 0;
+      uint32_t acc = 0;
 #pragma unroll
-      for (int w = 0; w < kRadixThreads / 32; ++w) add += cnt[w][d];
-      run[d] += add;
+      for (int w = 0; w < kRadixWarps; ++w) {
+        const uint32_t v = c[w * D + d];
+        c[w * D + d] = acc;     // keys of digit d in the round's earlier warps
+        acc += v;
+        cn[w * D + d] = 0u;     // the next round's counts start at zero
+      }
+      rbase[d] = lstart[d] + run[d];
+      run[d] += acc;
+    }
+    __syncthreads();            // prefixes, bases and the cleared set are published
+#pragma unroll
+    for (int it = 0; it < kRadixItems; ++it) {
+      const int d = dig[it];
+      if (d < D) {
+        const uint32_t pos = rbase[d] + c[wid * D + d] + rk[it];
+        sk[pos] = key[it];
+        sv[pos] = val[it];
+      }
     }
   }
   __syncthreads();
@@ -259,6 +296,14 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const K* __rest
     kout[o] = key;
     vout[o] = sv[i];
   }
+}
+
+// Opts k_radix_scatter<K, RB> into its dynamic shared memory on the current
+// device (a host-side attribute, set before every launch).
+template <typename K, int RB>
+void radix_scatter_attr() {
+  cudaFuncSetAttribute(k_radix_scatter<K, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)radix_scatter_smem<K, RB>());
 }
 
 // Depth keys of every (view, Gaussian) slot: (view << 31) | the low 31 bits
@@ -427,7 +472,9 @@ int radix_passes(K* keys[2], uint32_t* vals[2], uint32_t* hist, int64_t count, i
     k_radix_hist<K, RB><<<nblocks, kRadixThreads, 0, st>>>(keys[src], count, shift, hist, nblocks);
     const int64_t hn = (int64_t)(1 << RB) * nblocks;
     l += 1 + scan_rec(hist, hist + hn, hn, hist + 2 * hn, st);
-    k_radix_scatter<K, RB><<<nblocks, kRadixThreads, 0, st>>>(keys[src], vals[src], keys[dst], vals[dst], count,
+    radix_scatter_attr<K, RB>();
+    k_radix_scatter<K, RB><<<nblocks, kRadixThreads, radix_scatter_smem<K, RB>(), st>>>(keys[src], vals[src],
+                                                                                          keys[dst], vals[dst], count,
                                                               shift, hist, hist + hn, nblocks);
     ++l;
     *which = dst;
@@ -550,7 +597,9 @@ int launch_radix_pass(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, 
   const int64_t hn = 256LL * nblocks;
   k_radix_hist<uint64_t, 8><<<nblocks, kRadixThreads, 0, st>>>(kin, count, shift, hist, nblocks);
   int l = 1 + scan_rec(hist, hist + hn, hn, hist + 2 * hn, st);
-  k_radix_scatter<uint64_t, 8><<<nblocks, kRadixThreads, 0, st>>>(kin, vin, kout, vout, count, shift, hist,
+  radix_scatter_attr<uint64_t, 8>();
+  k_radix_scatter<uint64_t, 8><<<nblocks, kRadixThreads, radix_scatter_smem<uint64_t, 8>(), st>>>(
+      kin, vin, kout, vout, count, shift, hist,
                                                                   hist + hn, nblocks);
   return l + 1;
 }
