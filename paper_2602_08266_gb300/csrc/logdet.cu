@@ -1673,9 +1673,13 @@ __host__ __device__ inline GmLayout gm_layout(const Consts& c) {
   y.off_Zp = y.off_s + r4(y.l2);
   y.off_Zg = y.off_Zp + r4(y.l2 * c.K);
   y.off_W = y.off_Zg + r4(y.l2 * 6);
+  // u <= 40 takes the row eliminations, which read only W, Q (6 x 6) and
+  // X (K x 6): B holds those and there is no G workspace; larger u takes
+  // logdet_IcWB with a full u x u B and G
+  const bool rows = y.u2 <= 40;
   y.off_B = y.off_W + r4(y.u2 * y.u2);
-  y.off_G = y.off_B + r4(y.u2 * y.u2);
-  y.per_warp = y.off_G + r4(y.u2 * y.u2);
+  y.off_G = y.off_B + (rows ? r4(36 + 6 * c.K) : r4(y.u2 * y.u2));
+  y.per_warp = y.off_G + (rows ? 0 : r4(y.u2 * y.u2));
   return y;
 }
 
