@@ -89,10 +89,23 @@ struct nbv_ctx {
   DevProj pr{};
   // sort
   SortBuffers sb{};
+  // per-view binning in depth order: the slots with entries compacted with
+  // their depth keys and sorted, their entry counts gathered and scanned in
+  // that order, the view's camera and tile base on the device
+  struct ViewBin {
+    uint32_t* flags = nullptr;
+    uint32_t* pos = nullptr;        // [n + 1]
+    uint32_t* scan_tmp = nullptr;
+    SortBuffers db{};               // depth keys of the slots with entries
+    uint32_t* tcount = nullptr;     // [n]
+    uint32_t* doffsets = nullptr;   // [n + 1]
+    DevCam* d_cam = nullptr;        // [1]
+    uint32_t* d_tbase = nullptr;    // [1] = 0
+  } vb;
   uint4* fwd = nullptr;           // per-view scoring: forward results per (tile, pixel)
   uint32_t* tile_first = nullptr; // and each tile's first active entry
   size_t fwd_cap = 0, tile_first_cap = 0;
-  uint32_t* h_total = nullptr;   // pinned
+  uint32_t* h_total = nullptr;   // pinned [2]: entries of the last per-view pass, its slots with entries
   unsigned long long* h_total64 = nullptr;   // pinned: 64-bit entry count of the last pass
   unsigned long long* d_total64 = nullptr;
   int64_t entry_limit = kMaxPassEntries;     // entries one binning pass may hold
@@ -299,6 +312,8 @@ struct Phase {
   }
 };
 
+int bits_for(int64_t n);
+
 // Project, bin and sort one view; composite it (images and/or IG blocks).
 int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, float* depth,
                 float* alpha, float* obj, bool compensated = false, bool training = false) {
@@ -310,12 +325,18 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
     Phase ph(ctx, NBV_PHASE_PROJECT);
     CKR(check_launch(ctx, launch_project(s, ctx->c, dc, ctx->pr, st)));
   }
+  auto& V = ctx->vb;
   {
     Phase ph(ctx, NBV_PHASE_SORT);
     CKR(check_launch(ctx, launch_scan_u32(ctx->pr.touched, ctx->sb.offsets, ctx->n, ctx->sb.scan_tmp, st)));
     CKR(check_launch(ctx, launch_sum_u64(ctx->pr.touched, ctx->n, ctx->d_total64, st)));
+    // the slots with entries and their depth keys (0 << 31 | z bits), in Gaussian order
+    CKR(check_launch(ctx, launch_compact_depth_keys(ctx->pr.touched, ctx->n, V.flags, V.pos, V.scan_tmp,
+                                                    ctx->pr.zbits, ctx->n, V.db.keys[0], V.db.vals[0], st)));
     CK(cudaMemcpyAsync(ctx->h_total, ctx->sb.offsets + ctx->n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->h_total + 1, V.pos + ctx->n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(ctx->h_total64, ctx->d_total64, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(V.d_cam, &dc, sizeof(DevCam), cudaMemcpyHostToDevice, st));
   }
   CK(cudaStreamSynchronize(st));
   // the 64-bit count decides: the 32-bit scan (and every offset after the
@@ -324,7 +345,8 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
     return fail(ctx, NBV_ERR_ARG, "a view has " + std::to_string(*ctx->h_total64) +
                                       " (tile, Gaussian) entries, more than one binning pass holds (" +
                                       std::to_string(ctx->entry_limit) + ")");
-  const int64_t total = (int64_t)*ctx->h_total;
+  const int64_t total = (int64_t)ctx->h_total[0];
+  const int64_t m = (int64_t)ctx->h_total[1];
   if (ctx->prof) ctx->binned_entries[training ? 1 : 0] += total;
   if ((size_t)total > ctx->sb.cap) {
     size_t cap = ctx->sb.cap;
@@ -339,19 +361,29 @@ int render_view(nbv_ctx* ctx, const nbv_camera& cam, float* blocks, float* rgb, 
   }
   CKR(grow(ctx, &ctx->sb.ranges, &ctx->ranges_cap, (size_t)ntiles));
   {
+    // the slots in depth order (a stable sort of the compacted slots: ties in
+    // Gaussian order), their entries emitted in that order with 32-bit tile
+    // ids, and a stable sort on the tile id alone: every tile's list in
+    // (depth bits, Gaussian index) order
     Phase ph(ctx, NBV_PHASE_SORT);
-    CKR(check_launch(ctx, launch_duplicate(ctx->pr, ctx->n, dc, ctx->sb.offsets, ctx->sb.keys[0],
-                                           ctx->sb.vals[0], st)));
-    int tile_bits = 1;
-    while ((1 << tile_bits) < ntiles) ++tile_bits;
+    int dw = 0;
+    CKR(check_launch(ctx, launch_radix_sort(V.db, m, 31, &dw, st)));
+    const uint32_t* order = V.db.vals[dw];
+    CKR(check_launch(ctx, launch_gather_touched(ctx->pr.touched, order, m, V.tcount, st)));
+    CKR(check_launch(ctx, launch_scan_u32(V.tcount, V.doffsets, m, V.scan_tmp, st)));
+    uint32_t* k32[2] = {reinterpret_cast<uint32_t*>(ctx->sb.keys[0]), reinterpret_cast<uint32_t*>(ctx->sb.keys[1])};
+    CKR(check_launch(ctx, launch_duplicate_sorted(ctx->pr.rect, ctx->pr.r0, ctx->pr.r1, order, ctx->n, m, V.d_cam,
+                                                  V.d_tbase, nullptr, nullptr, V.doffsets, k32[0],
+                                                  ctx->sb.vals[0], st)));
     int which = 0;
-    CKR(check_launch(ctx, launch_radix_sort(ctx->sb, total, 32 + tile_bits, &which, st)));
+    CKR(check_launch(ctx, launch_radix_sort32(k32, ctx->sb.vals, ctx->sb.hist, total, bits_for(ntiles), &which, st)));
     if (which != 0) {
       // keep the sorted result in buffer 0
       std::swap(ctx->sb.keys[0], ctx->sb.keys[1]);
       std::swap(ctx->sb.vals[0], ctx->sb.vals[1]);
     }
-    CKR(check_launch(ctx, launch_ranges(ctx->sb.keys[0], total, ctx->sb.ranges, ntiles, st)));
+    CKR(check_launch(ctx, launch_ranges32(reinterpret_cast<uint32_t*>(ctx->sb.keys[0]), total, ctx->sb.ranges,
+                                          ntiles, st)));
   }
   CompositeArgs a{};
   a.cam = dc;
@@ -747,6 +779,18 @@ int ensure_scene_buffers(nbv_ctx* ctx, int64_t n) {
   CKR(alloc(ctx, &ctx->pr.touched, n)); CKR(alloc(ctx, &ctx->pr.radius, n));
   CKR(alloc(ctx, &ctx->sb.offsets, n + 1));
   CKR(alloc(ctx, &ctx->sb.scan_tmp, scan_scratch_elems(n + 1)));
+  {
+    auto& V = ctx->vb;
+    CKR(alloc(ctx, &V.flags, n)); CKR(alloc(ctx, &V.pos, n + 1));
+    CKR(alloc(ctx, &V.scan_tmp, scan_scratch_elems(n + 1)));
+    CKR(alloc(ctx, &V.db.keys[0], n)); CKR(alloc(ctx, &V.db.keys[1], n));
+    CKR(alloc(ctx, &V.db.vals[0], n)); CKR(alloc(ctx, &V.db.vals[1], n));
+    CKR(alloc(ctx, &V.db.hist, radix_hist_elems(n)));
+    V.db.cap = (size_t)n;
+    CKR(alloc(ctx, &V.tcount, n)); CKR(alloc(ctx, &V.doffsets, n + 1));
+    CKR(alloc(ctx, &V.d_cam, 1)); CKR(alloc(ctx, &V.d_tbase, 1));
+    CK(cudaMemsetAsync(V.d_tbase, 0, sizeof(uint32_t), ctx->st));
+  }
   CKR(alloc(ctx, &ctx->blocks, (size_t)n * ctx->nBp));
   for (int f = 0; f < 3; ++f) {
     const int l = f == 0 ? kNG + 3 * nb : (f == 1 ? kNG : kNG + KC);
@@ -825,7 +869,7 @@ int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out) {
   ctx->st = static_cast<cudaStream_t>(cuda_stream);
   if (cudaGetDevice(&ctx->device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMallocHost(reinterpret_cast<void**>(&ctx->h_total), sizeof(uint32_t)) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&ctx->h_total), 2 * sizeof(uint32_t)) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&ctx->h_total64), sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_total64), sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_flags), 4 * sizeof(int)) != cudaSuccess ||
@@ -855,7 +899,10 @@ void nbv_destroy(nbv_ctx* ctx) {
                   ctx->sb.keys[1], ctx->sb.vals[0], ctx->sb.vals[1], ctx->sb.offsets, ctx->sb.scan_tmp,
                   ctx->sb.hist, ctx->sb.ranges, ctx->blocks, ctx->train_blocks, ctx->partial,
                   ctx->ig_train, ctx->ig_cand, ctx->out4, ctx->d_flags, ctx->d_best_score, ctx->d_err,
-                  ctx->F.L[0], ctx->F.L[1], ctx->F.L[2], ctx->slot, ctx->act};
+                  ctx->F.L[0], ctx->F.L[1], ctx->F.L[2], ctx->slot, ctx->act, ctx->vb.flags, ctx->vb.pos,
+                  ctx->vb.scan_tmp, ctx->vb.db.keys[0], ctx->vb.db.keys[1], ctx->vb.db.vals[0],
+                  ctx->vb.db.vals[1], ctx->vb.db.hist, ctx->vb.tcount, ctx->vb.doffsets, ctx->vb.d_cam,
+                  ctx->vb.d_tbase};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (ctx->d_stats) cudaFree(ctx->d_stats);

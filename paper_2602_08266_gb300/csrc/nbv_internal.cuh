@@ -130,20 +130,15 @@ struct SortBuffers {
 int launch_sum_u64(const uint32_t* in, int64_t n, unsigned long long* out, cudaStream_t st);
 // Exclusive scan of touched into offsets; total written to *d_total (device).
 int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t st);
-int launch_duplicate(const DevProj& pr, int64_t n, const DevCam& cam, const uint32_t* offsets, uint64_t* keys,
-                     uint32_t* vals, cudaStream_t st);
-// Stable LSD radix sort of (keys, vals) on the low `bits` key bits; the
-// result is in buffer index *which (0 or 1).
 // Candidate descriptors [nv][448] (raw: scratch of the same size); tcams: the
 // training cameras; tblocks: their blocks [n_train][n][nBp] (W2 entries read).
 int launch_descriptors(const DevScene& s, const Consts& c, const DevCam* cams, int nv, const DevCam* tcams,
                        int n_train, const float* tblocks, int nBp, float* raw, float* out, cudaStream_t st);
-// Stable LSD radix sort of 32-bit keys (8 bits a pass) over `bits` bits,
+// Stable LSD radix sort of 32-bit keys (8-bit digits, 9-bit where that takes fewer passes) over `bits` bits,
 // ping-ponging between keys[0/1], vals[0/1]; *which = the buffer holding the result.
 int launch_radix_sort32(uint32_t* keys[2], uint32_t* vals[2], uint32_t* hist, int64_t count, int bits, int* which,
                         cudaStream_t st);
-// Multi-view depth order: keys (view << 31 | 31 low z bits), vals = slot v n + g.
-int launch_depth_keys(const uint32_t* zbits, int64_t n, int nv, uint64_t* keys, uint32_t* vals, cudaStream_t st);
+// Entry counts of the m slots in `order` (touched[order[i]]), for their scan in that order.
 int launch_gather_touched(const uint32_t* touched, const uint32_t* order, int64_t m, uint32_t* out, cudaStream_t st);
 // Entries of the m slots in `order` (n Gaussians per view): 32-bit global
 // tile keys and Gaussian indices; with a tile mark, only marked tiles.
@@ -161,8 +156,9 @@ int launch_count_tiles(const int4* rect, const float4* r0, const float4* r1, int
 int launch_compact_depth_keys(const uint32_t* touched, int64_t m, uint32_t* flags, uint32_t* pos, uint32_t* scan_tmp,
                               const uint32_t* zbits, int64_t n, uint64_t* keys, uint32_t* vals, cudaStream_t st);
 int launch_ranges32(const uint32_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st);
+// Stable LSD radix sort of 64-bit keys with 32-bit values on their low `bits`
+// bits (8 a pass); *which = the buffer holding the result.
 int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaStream_t st);
-int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st);
 
 // Work-queue keys: longest tile lists first.
 int launch_queue_keys(const uint2* ranges, int ntiles, uint64_t* keys, uint32_t* vals, cudaStream_t st);

@@ -86,46 +86,6 @@ int scan_rec(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaSt
   return launches + 1;
 }
 
-// Every Gaussian's entries for the tiles of its rectangle that pass
-// tile_hit, in row order: a lane per Gaussian, the warp's 32 rectangles
-// walked together (packed_walk), the passing tiles of a round compacted by a
-// ballot, so that the warp's entries leave as one contiguous run.
-__global__ void __launch_bounds__(kDupThreads) k_duplicate(DevProj pr, int64_t n, DevCam cam,
-                                                          const uint32_t* __restrict__ offsets,
-                                                          uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  __shared__ SlotTiles s_st[kDupThreads / 32][32];
-  __shared__ int s_incl[kDupThreads / 32][32];
-  __shared__ uint32_t s_z[kDupThreads / 32][32];
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t g0 = g - lane;
-  if (g0 >= n) return;                           // warp-uniform; no block-wide barrier below
-  SlotTiles st = no_tiles();
-  uint32_t zb = 0;
-  if (g < n) {
-    const int4 r = pr.rect[g];
-    if (r.x >= 0) {
-      st = slot_tiles(r, pr.r0[g], pr.r1[g], 0u, cam);
-      zb = pr.zbits[g];
-    }
-  }
-  s_z[wid][lane] = zb;                           // published by packed_walk's __syncwarp
-  // the warp's slots are consecutive in the scan of their entry counts
-  uint32_t wo = offsets[g0];
-  const unsigned lt = (1u << lane) - 1u;
-  packed_walk(
-      st, s_st[wid], s_incl[wid], lane, [](const SlotTiles&, int, int) { return true; },
-      [&](int sl, const SlotTiles& q, int tx, int ty, bool hit) {
-        const unsigned mk = __ballot_sync(0xffffffffu, hit);
-        if (hit) {
-          const uint32_t at = wo + (uint32_t)__popc(mk & lt);
-          keys[at] = ((uint64_t)(ty * q.gx + tx) << 32) | (uint64_t)s_z[wid][sl];
-          vals[at] = (uint32_t)(g0 + sl);
-        }
-        wo += (uint32_t)__popc(mk);
-      });
-}
-
 // Work-queue keys: longest tile list first, ties by tile id.
 __global__ void k_queue_keys(const uint2* __restrict__ ranges, int ntiles, uint64_t* __restrict__ keys,
                              uint32_t* __restrict__ vals) {
@@ -306,18 +266,6 @@ void radix_scatter_attr() {
                        (int)radix_scatter_smem<K, RB>());
 }
 
-// Depth keys of every (view, Gaussian) slot: (view << 31) | the low 31 bits
-// of the float bits of camera z (z > near > 0, so the sign bit is clear for
-// every slot that has entries); value = the slot.
-__global__ void k_depth_keys(const uint32_t* __restrict__ zbits, int64_t n, int nv, uint64_t* __restrict__ keys,
-                             uint32_t* __restrict__ vals) {
-  const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (slot >= n * nv) return;
-  const uint64_t v = (uint64_t)(slot / n);
-  keys[slot] = (v << 31) | (uint64_t)(zbits[slot] & 0x7FFFFFFFu);
-  vals[slot] = (uint32_t)slot;
-}
-
 __global__ void k_gather_touched(const uint32_t* __restrict__ touched, const uint32_t* __restrict__ order,
                                  int64_t m, uint32_t* __restrict__ out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -482,13 +430,6 @@ int radix_passes(K* keys[2], uint32_t* vals[2], uint32_t* hist, int64_t count, i
   return l;
 }
 
-__global__ void k_ranges(const uint64_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t t = (uint32_t)(keys[i] >> 32);
-  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
-  if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
-}
 
 // 64-bit sum of n 32-bit counts into *out (zeroed by the caller): the entry
 // count of a binning pass without the wrap of the 32-bit scan.
@@ -520,12 +461,6 @@ int launch_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
   return l + 1;
 }
 
-int launch_duplicate(const DevProj& pr, int64_t n, const DevCam& cam, const uint32_t* offsets, uint64_t* keys,
-                     uint32_t* vals, cudaStream_t st) {
-  if (n <= 0) return 0;
-  k_duplicate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pr, n, cam, offsets, keys, vals);
-  return 1;
-}
 
 int launch_radix_sort(SortBuffers& b, int64_t count, int bits, int* which, cudaStream_t st) {
   return radix_passes<uint64_t, 8>(b.keys, b.vals, b.hist, count, bits, which, st);
@@ -538,12 +473,6 @@ int launch_radix_sort32(uint32_t* keys[2], uint32_t* vals[2], uint32_t* hist, in
   return radix_passes<uint32_t, 8>(keys, vals, hist, count, bits, which, st);
 }
 
-int launch_depth_keys(const uint32_t* zbits, int64_t n, int nv, uint64_t* keys, uint32_t* vals, cudaStream_t st) {
-  const int64_t m = n * nv;
-  if (m <= 0) return 0;
-  k_depth_keys<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(zbits, n, nv, keys, vals);
-  return 1;
-}
 
 int launch_gather_touched(const uint32_t* touched, const uint32_t* order, int64_t m, uint32_t* out,
                           cudaStream_t st) {
@@ -604,12 +533,6 @@ int launch_radix_pass(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, 
   return l + 1;
 }
 
-int launch_ranges(const uint64_t* keys, int64_t count, uint2* ranges, int ntiles, cudaStream_t st) {
-  cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)ntiles, st);
-  if (count <= 0) return 0;
-  k_ranges<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(keys, count, ranges);
-  return 1;
-}
 
 int launch_queue_keys(const uint2* ranges, int ntiles, uint64_t* keys, uint32_t* vals, cudaStream_t st) {
   if (ntiles <= 0) return 0;
