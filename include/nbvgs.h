@@ -114,8 +114,9 @@ void nbv_config_default(nbv_config* cfg, int K, int sh_degree);
 /* Create a context bound to the CUDA device current on the calling thread
  * and to `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
  * On success *out owns every device buffer the context allocates later.
- * Errors: NBV_ERR_ARG (bad config: K < 1 or > 106 (the information pass of
- * K + 1 channels must fit one block's shared memory), sh_degree outside 0..3,
+ * Errors: NBV_ERR_ARG (bad config: K < 1 or > 98 (the per-Gaussian object
+ * gain's u x u workspace, u = 6 + K, must fit one block's shared memory),
+ * sh_degree outside 0..3,
  * tile not 16x16, 32x8 or 0x0, non-finite or out-of-range constants),
  * NBV_ERR_CUDA. */
 int nbv_create(const nbv_config* cfg, void* cuda_stream, nbv_ctx** out);

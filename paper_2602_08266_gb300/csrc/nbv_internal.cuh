@@ -12,7 +12,7 @@ namespace nbv {
 
 constexpr int kTile = 16;           // 16x16 screen tiles, one thread per pixel
 constexpr int kTilePix = kTile * kTile;
-constexpr int kMaxK = 106;          // the information pass of K + 1 channels fits one block's shared memory at 16 splats a round
+constexpr int kMaxK = 98;           // the view-major gains kernel's object workspace (2 l u + 3 u^2 floats, u = 6 + K) fits one block's shared memory
 constexpr int kNG = 11;             // geometric parameters: mu(3) log-scale(3) quat(4) opacity logit(1)
 
 // Structured per-(view, Gaussian) 2D block layout (floats). With

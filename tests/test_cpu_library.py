@@ -44,8 +44,8 @@ def test_config_defaults_are_the_papers():
 def test_create_rejects_bad_config_without_gpu():
     P.build()
     lib = P.load_library()
-    # K = 107: the information pass of 108 channels does not fit a block's shared memory
-    for kw in (dict(K=0), dict(K=107), dict(sh_degree=4), dict(tile_w=8), dict(tile_w=32), dict(stage=24),
+    # K = 99: the object gain's workspace does not fit a block's shared memory
+    for kw in (dict(K=0), dict(K=99), dict(sh_degree=4), dict(tile_w=8), dict(tile_w=32), dict(stage=24),
                dict(lambda_damp=0.0), dict(alpha_max=1.0)):
         cfg = P.config_default(4, 0)
         for k, v in kw.items():
