@@ -24,6 +24,15 @@
 // term), over the tile's warps in shared memory, and added to the
 // per-Gaussian block in global memory with one vector atomic per 4 floats
 // per (tile, Gaussian).
+//
+// A scoring launch (blocks, no images) runs the two passes as two kernels:
+// k_forward (pass 1 only: transmittance, list ends and the first splat with
+// an information block per pixel; records staged by bulk copies into a
+// double-buffered mbarrier ring) and k_composite reading those results
+// (pass 2 only, each warp walking back to front down to its pixels' first
+// information splat, the next round's records gathered by cp.async while
+// the current one runs). Images (and the rare launch that wants both) run
+// both passes in k_composite.
 #include <type_traits>
 
 #include "nbv_internal.cuh"
