@@ -749,20 +749,35 @@ __global__ void __launch_bounds__(kTilePix, (KCM <= 24 ? 2 : 1))
 // (its first active entry recorded as its list end).
 constexpr int kFwd = 32;   // one bit per staged splat in a 32-bit mask
 
+// Two pixels per thread: thread t takes the information pass's pixels t and
+// t + kFwdThreads (the same column, 8 rows apart in a 16x16 tile, 4 in a
+// 32x8 one), so every staged record is read once for both and each thread
+// has two independent blend chains.
+constexpr int kFwdThreads = kTilePix / 2;
+
 __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Consts& c, const DevCam& cam, int tile,
                                              uint32_t gt, uint2 rg, size_t rec_off, StageRing& ring) {
   const int tx = tile % cam.GX, ty = tile / cam.GX;
   const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
   const int wx = cam.TW >> 3;
-  const int px = tx * cam.TW + 8 * (wq % wx) + (lane & 7), py = ty * cam.TH + 4 * (wq / wx) + (lane >> 3);
-  const bool inside = px < cam.W && py < cam.H;
-  const float pxc = fa((float)px, 0.5f), pyc = fa((float)py, 0.5f);
+  // pixel of the information pass's thread t (its 8 x 4 warp blocks)
+  auto pixel = [&](int t, int& px, int& py) {
+    const int q = t >> 5, l = t & 31;
+    px = tx * cam.TW + 8 * (q % wx) + (l & 7);
+    py = ty * cam.TH + 4 * (q / wx) + (l >> 3);
+  };
+  int px0, py0, px1, py1;
+  pixel(tid, px0, py0);
+  pixel(tid + kFwdThreads, px1, py1);
+  const bool in0 = px0 < cam.W && py0 < cam.H, in1 = px1 < cam.W && py1 < cam.H;
+  const float pxc0 = fa((float)px0, 0.5f), pyc0 = fa((float)py0, 0.5f);
+  const float pxc1 = fa((float)px1, 0.5f), pyc1 = fa((float)py1, 0.5f);
   __shared__ int s_first;
   uint32_t first_info = rg.x;
   if (args.n_act < args.n) {
     if (tid == 0) s_first = (int)rg.y;
     __syncthreads();
-    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kTilePix) {
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += kFwdThreads) {
       const uint32_t i = b0 + tid;
       if (i < rg.y && args.slot[args.vals[i]] >= 0) atomicMin(&s_first, (int)i);
       if (__syncthreads_or(s_first < (int)rg.y)) break;
@@ -770,8 +785,8 @@ __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Co
     first_info = (uint32_t)s_first;
   }
   if (tid == 0) args.tile_first[gt] = first_info;
-  float T = 1.0f;
-  uint32_t last = rg.x, first_pix = kNoEntry;
+  float T0 = 1.0f, T1 = 1.0f;
+  uint32_t last0 = rg.x, last1 = rg.x, first0 = kNoEntry, first1 = kNoEntry;
   uint32_t n_eval = 0, n_blend = 0;
   // Per round, a mask of the staged splats that have an information block:
   // warp 0 loads it with the round's copies and stores it before the
@@ -786,7 +801,7 @@ __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Co
     return __ballot_sync(0xffffffffu, on);
   };
   if (first_info < rg.y) {
-    bool done = !inside;
+    bool done0 = !in0, done1 = !in1;
     const uint32_t nst = (rg.y - rg.x + kFwd - 1) / kFwd;
     if (nst > 0 && wq == 0) {
       ring.issue(args, rg.x, rg.y, 0, rec_off, lane, kFwd);
@@ -795,14 +810,14 @@ __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Co
     }
     uint32_t k = 0;
     for (; k < nst; ++k) {
-      if (__syncthreads_count(done) == kTilePix) break;
+      if (__syncthreads_count(done0 && done1) == kFwdThreads) break;
       uint32_t pend = 0;
       if (k + 1 < nst && wq == 0) {
         ring.issue(args, rg.x, rg.y, k + 1, rec_off, lane, kFwd);
         pend = info_mask(k + 1);
       }
       const int b = (int)(k & 1u);
-      if (!ring.wait(b)) done = true;
+      if (!ring.wait(b)) done0 = done1 = true;
       const float4* q0 = ring.rec(b, 0, kFwd);
       const float4* q1 = ring.rec(b, 1, kFwd);
       const uint32_t start = rg.x + k * kFwd;
@@ -811,25 +826,33 @@ __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Co
       // the first-splat check only in rounds with an information splat that
       // a pixel of the warp may still need (warp-uniform, so the common
       // rounds run the plain loop)
-      const bool watch = __any_sync(0xffffffffu, first_pix == kNoEntry && !done) && imask != 0u;
+      const bool watch =
+          __any_sync(0xffffffffu, (first0 == kNoEntry && !done0) || (first1 == kNoEntry && !done1)) && imask != 0u;
       auto walk = [&](auto kWatch) {
-        for (uint32_t j = 0; j < nj; ++j) {
-          const float4 a0 = q0[j], a1 = q1[j];
+        // one pixel's blend step with splat j (the decisions as in pass 1)
+        auto step = [&](float pxc, float pyc, const float4& a0, const float4& a1, uint32_t j, float& T,
+                        uint32_t& last, uint32_t& first, bool& done) {
           const float pw = splat_power(a0.x, a0.y, a1.x, a1.y, a1.z, pxc, pyc);
           ++n_eval;
-          if (pw > 0.0f || pw < a0.z) continue;
+          if (pw > 0.0f || pw < a0.z) return;
           const float alpha = (pw >= a0.w) ? c.alpha_max : a1.w * __expf(pw);
           const float tt = T * (1.0f - alpha);
-          if (tt < c.t_min) { done = true; break; }
+          if (tt < c.t_min) { done = true; return; }
           T = tt;
           last = start + j + 1;
           if constexpr (decltype(kWatch)::value) {
-            if (first_pix == kNoEntry && ((imask >> j) & 1u)) first_pix = start + j;
+            if (first == kNoEntry && ((imask >> j) & 1u)) first = start + j;
           }
           ++n_blend;
+        };
+        for (uint32_t j = 0; j < nj; ++j) {
+          const float4 a0 = q0[j], a1 = q1[j];
+          if (!done0) step(pxc0, pyc0, a0, a1, j, T0, last0, first0, done0);
+          if (!done1) step(pxc1, pyc1, a0, a1, j, T1, last1, first1, done1);
+          if (done0 && done1) break;
         }
       };
-      if (!done) {
+      if (!(done0 && done1)) {
         if (watch) walk(std::true_type{});
         else walk(std::false_type{});
       }
@@ -839,8 +862,9 @@ __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Co
     }
     if (k < nst) ring.wait((int)(k & 1u));   // a round fetched ahead but not composited
   }
-  args.fwd[(size_t)gt * kTilePix + tid] =
-      make_uint4(__float_as_uint(T), inside ? last : rg.x, inside ? first_pix : kNoEntry, 0u);
+  uint4* f = args.fwd + (size_t)gt * kTilePix;
+  f[tid] = make_uint4(__float_as_uint(T0), in0 ? last0 : rg.x, in0 ? first0 : kNoEntry, 0u);
+  f[tid + kFwdThreads] = make_uint4(__float_as_uint(T1), in1 ? last1 : rg.x, in1 ? first1 : kNoEntry, 0u);
   if (args.stats) {
     const unsigned e = __reduce_add_sync(0xffffffffu, n_eval), bl = __reduce_add_sync(0xffffffffu, n_blend);
     if (lane == 0 && e) {
@@ -850,7 +874,7 @@ __device__ __forceinline__ void forward_tile(const CompositeArgs& args, const Co
   }
 }
 
-__global__ void __launch_bounds__(kTilePix, 4) k_forward(CompositeArgs args, Consts c) {
+__global__ void __launch_bounds__(kFwdThreads, 8) k_forward(CompositeArgs args, Consts c) {
   __shared__ __align__(16) float4 ring_buf[4 * kFwd];
   __shared__ __align__(8) uint64_t ring_bar[2];
   StageRing ring;
@@ -954,17 +978,17 @@ int launch_composite(const CompositeArgs& a, const Consts& c, cudaStream_t st, i
 int launch_forward(const CompositeArgs& a, const Consts& c, cudaStream_t st) {
   if (a.queue) {
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward, kTilePix, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forward, kFwdThreads, 0);
     if (per_sm < 1) per_sm = 1;
     int grid = device_sm_count() * per_sm;
     if (grid > a.n_items) grid = a.n_items;
     if (grid <= 0) return 0;
-    k_forward<<<grid, kTilePix, 0, st>>>(a, c);
+    k_forward<<<grid, kFwdThreads, 0, st>>>(a, c);
     return 1;
   }
   const int ntiles = a.cam.GX * a.cam.GY;
   if (ntiles <= 0) return 0;
-  k_forward<<<ntiles, kTilePix, 0, st>>>(a, c);
+  k_forward<<<ntiles, kFwdThreads, 0, st>>>(a, c);
   return 1;
 }
 
