@@ -184,7 +184,7 @@ def composite_tensor_flops(stats, K):
 # lists and blocks grow with the views). None when no capture of the
 # current kernels exists.
 BATCH_INFO_DRAM_BYTES_PER_VIEW = 22_817_536 / 8
-BATCH_FORWARD_DRAM_BYTES_PER_VIEW = (27_340_032 + 144_384) / 8
+BATCH_FORWARD_DRAM_BYTES_PER_VIEW = (27_037_696 + 132_864) / 8
 
 
 def project_bytes(n, nv, sh_degree):
